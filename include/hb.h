@@ -1,0 +1,219 @@
+/*
+ * hb.h -- C ABI of the GB300-native H-IDBF-LU library (libhb.so).
+ *
+ * Method: Liu & Yang, "A hierarchical butterfly LU preconditioner for
+ * two-dimensional electromagnetic scattering problems involving open
+ * surfaces" (arXiv:1901.11371).  The library discretises an open PEC curve
+ * (Sec. 3.1), compresses the TM_z EFIE impedance matrix into an H-IDBF
+ * (Alg. 1 with the IDBF of Sec. 2 / Appendix), applies it (Alg. 2), applies
+ * the approximate LU inverse  U~^{-1} L~^{-1}  (Eqs. (Lt), (Ut); Algs. 3, 4)
+ * and solves  L~^{-1} A U~^{-1} y = L~^{-1} b,  U~ x = y  (Eqs. (Axb2), (Axb3))
+ * iteratively, all on one CUDA device.
+ *
+ * Conventions shared by every entry point
+ *  - Return value: HB_OK (0) or a negative HB_E* code.  hb_last_error()
+ *    returns a thread-local message describing the last failure.  No entry
+ *    point aborts the process.
+ *  - Vectors are DEVICE pointers owned by the caller, column-major blocks of
+ *    nrhs columns with leading dimension ld >= N (elements).  Element type:
+ *    complex128 (interleaved double pairs) for form HB_C128 and for every
+ *    FP64 outer vector (hb_gmres, hb_residual, hb_rhs_plane_wave); complex64
+ *    (interleaved float pairs) for hb_apply / hb_precond_solve of the
+ *    HB_C64 and HB_SPLIT_BF16 forms.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    asynchronous on that stream unless stated otherwise.
+ *  - Unknowns follow the geometric order of the curve (Sec. 3.3.1); the
+ *    operator acted on by hb_apply / hb_precond_solve is the RESCALED
+ *    A^ = a A with a = 1 / max_i |A_ii| (Sec. 3.1 and Sec. 4).
+ */
+#ifndef HB_H
+#define HB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define HB_OK 0
+#define HB_EINVAL -1        /* invalid argument (null pointer, bad size, bad enum) */
+#define HB_ENOMEM -2        /* host or device allocation failed */
+#define HB_ECUDA -3         /* a CUDA runtime call failed */
+#define HB_ENOCONV -4       /* iterative solver stopped before reaching rtol */
+#define HB_ETIMEOUT -5      /* a bounded device-side wait expired */
+#define HB_ENAN -6          /* NaN/Inf found in an input or a result */
+#define HB_EUNSUPPORTED -7  /* valid request this build does not implement */
+
+/* ---- enums ------------------------------------------------------------- */
+enum { HB_STRIP = 0, HB_SPIRAL = 1, HB_ARC = 2, HB_PARALLEL_STRIPS = 3 };
+enum { HB_C128 = 0, HB_C64 = 1, HB_SPLIT_BF16 = 2 };
+enum { HB_OP_N = 0, HB_OP_H = 1 };
+
+typedef struct hb_geometry_s* hb_geometry_t;  /* opaque; freed by hb_geometry_destroy */
+typedef struct hb_factor_s* hb_factor_t;      /* opaque; freed by hb_factor_destroy   */
+
+/* Factor statistics (host struct filled by hb_factor_info). */
+typedef struct {
+  int64_t n;              /* unknowns N */
+  int64_t leaf;           /* n0 */
+  int32_t depth;          /* D = log2(N / n0): depths with off-diagonal blocks */
+  int32_t form;           /* HB_C128 / HB_C64 / HB_SPLIT_BF16 */
+  int64_t n_butterflies;  /* 2 (2^D - 1) */
+  double scale;           /* a */
+  double eps;             /* compression tolerance */
+  int32_t kmax;           /* largest ID rank over all blocks */
+  int32_t pad0;
+  double kavg;            /* mean ID rank over all ID blocks */
+  int32_t kmax_depth[32]; /* largest rank per hierarchical depth v */
+  double kavg_depth[32];  /* mean rank per depth */
+  int64_t nnz_leaf;       /* entries of the dense diagonal leaves (m n0^2) */
+  int64_t nnz_butterfly;  /* stored entries of all butterfly factors (ID form) */
+  int64_t nnz_lu_leaf;    /* entries of the leaf triangle inverses (2 m n0^2) */
+  int64_t index_bytes;    /* bytes of pivot / map indices on the device */
+  int64_t device_bytes;   /* total device bytes held by the factor */
+  int64_t apply_bytes;    /* algorithmic bytes one single-RHS hb_apply touches */
+  int64_t lower_bytes;    /* algorithmic bytes of one single-RHS L~^{-1} sweep */
+  int64_t upper_bytes;    /* algorithmic bytes of one single-RHS U~^{-1} sweep */
+  int32_t rebuilt_blocks; /* butterflies rebuilt with eps/10 by the error probe */
+  int32_t pad1;
+  double build_seconds;   /* host wall time of construction + upload */
+} hb_factor_stats;
+
+/* Solver report (host struct).  Optional per-RHS arrays are caller-owned
+ * host buffers of length nrhs; leave NULL to skip. */
+typedef struct {
+  int32_t iters;          /* total inner iterations (max over RHS) */
+  int32_t restarts;       /* restart cycles (max over RHS) */
+  int32_t ir_steps;       /* outer iterative-refinement steps (mixed forms) */
+  int32_t converged;      /* number of RHS that reached rtol */
+  double true_rel_res;    /* max over RHS of ||b^ - A^_F x|| / ||b^|| (FP64) */
+  double precond_rel_res; /* max over RHS of the final preconditioned residual estimate */
+  double seconds;         /* wall time of the call (host clock, synchronised) */
+  int32_t* iters_per_rhs; /* optional out */
+  double* res_per_rhs;    /* optional out */
+} hb_gmres_info;
+
+/* hb_geometry -- discretise an open PEC curve into n_segments pulse segments
+ * (Sec. 3.1: w_i, rho_i are the length and centre of segment i).  Curves are
+ * split at equal arc length; each segment is the chord between consecutive
+ * nodes.  params: STRIP (x0,y0,x1,y1); SPIRAL (a, theta0, theta1) for
+ * r = a theta; ARC (R, phi0, phi1); PARALLEL_STRIPS (n_strips, length,
+ * spacing) with strip s at y = s*spacing, x in [0, length], ordered strip
+ * after strip.  Lengths in wavelengths.  *out is owned by the library.
+ * Errors: HB_EINVAL (bad kind, nparams, n_segments < 1), HB_ENOMEM. */
+int hb_geometry(int kind, const double* params, int nparams, int64_t n_segments, hb_geometry_t* out);
+
+/* Host copies of the segment centres (2N doubles, x/y interleaved) and
+ * lengths (N doubles) into caller-owned buffers.  Either may be NULL. */
+int hb_geometry_segments(hb_geometry_t g, double* centers_xy, double* lengths);
+int64_t hb_geometry_size(hb_geometry_t g);
+void hb_geometry_destroy(hb_geometry_t g);
+
+/* hb_factor -- build the H-IDBF of the rescaled TM EFIE matrix (Sec. 3.1:
+ * A_ij = (k eta0 w_j / 4) H0^(2)(k |rho_i - rho_j|), A_ii = (k eta0 w_i / 4)
+ * [1 - i (2/pi) ln(gamma k w_i / (4e))], k = 2 pi / wavelength) with leaf
+ * size `leaf` (n0) and compression tolerance eps (Alg. 1, IDBF of the
+ * Appendix with sampled IDs seeded by `seed`), then upload the level-packed
+ * factors, dense leaves and leaf triangle inverses to the current device in
+ * the storage `form`.  Construction runs on the host and is timed apart
+ * from the hot path.  Requires N = leaf * 2^D with D >= 1, 8 <= leaf <= 256.
+ * Errors: HB_EINVAL, HB_EUNSUPPORTED (N not leaf*2^D), HB_ENOMEM, HB_ECUDA. */
+int hb_factor(hb_geometry_t g, double wavelength, double eta0, double gamma, int64_t leaf, double eps,
+              int form, uint64_t seed, void* stream, hb_factor_t* out);
+int hb_factor_info(hb_factor_t f, hb_factor_stats* s);
+void hb_factor_destroy(hb_factor_t f);
+
+/* hb_tree -- cluster tree node ranges [begin, end) in BFS order (node (v,p)
+ * at index 2^v - 1 + p), 2m - 1 nodes (Alg. 1 recursion).  Host buffers. */
+int hb_tree(hb_factor_t f, int64_t* node_begin, int64_t* node_end);
+
+/* hb_apply -- y = A^_F x (op = HB_OP_N, Alg. 2) or y = A^_F^H x (HB_OP_H),
+ * for nrhs columns.  x and y must not overlap.  Element type per form (see
+ * top).  Errors: HB_EINVAL (null, nrhs < 1, ld < N), HB_ECUDA. */
+int hb_apply(hb_factor_t f, int op, const void* x, void* y, int64_t nrhs, int64_t ld, void* stream);
+
+/* hb_apply_adjoint -- y = A^_F^H x: conjugate-transposed factors applied in
+ * reverse stage order (no counterpart in the paper; same as hb_apply with HB_OP_H). */
+int hb_apply_adjoint(hb_factor_t f, const void* x, void* y, int64_t nrhs, int64_t ld, void* stream);
+
+/* hb_precond_solve -- x = U~^{-1} L~^{-1} b (op = HB_OP_N; Algs. 3 then 4)
+ * or x = L~^{-H} U~^{-H} b (HB_OP_H), with L~/U~ the entry-wise triangles of
+ * the compressed operator (Eqs. (Lt), (Ut)).  b and x must not overlap.
+ * Errors: HB_EINVAL, HB_ECUDA. */
+int hb_precond_solve(hb_factor_t f, int op, const void* b, void* x, int64_t nrhs, int64_t ld, void* stream);
+
+/* hb_lower_solve / hb_upper_solve -- one sweep: x = L~^{-1} b (Alg. 3) or
+ * x = U~^{-1} b (Alg. 4); op = HB_OP_H gives L~^{-H} b / U~^{-H} b. */
+int hb_lower_solve(hb_factor_t f, int op, const void* b, void* x, int64_t nrhs, int64_t ld, void* stream);
+int hb_upper_solve(hb_factor_t f, int op, const void* b, void* x, int64_t nrhs, int64_t ld, void* stream);
+
+/* hb_residual -- r = b - A^_F x (op N) or b - A^_F^H x (op H) in FP64
+ * arithmetic on the stored factors; complex128 vectors.  b, x, r distinct. */
+int hb_residual(hb_factor_t f, int op, const void* b, const void* x, void* r, int64_t nrhs, int64_t ld, void* stream);
+
+/* hb_gmres -- solve A x = b_phys for nrhs right-hand sides (complex128, the
+ * PHYSICAL excitation; the rescaling a is applied internally, x is invariant).
+ * HB_C128: GMRES(restart) on the split-preconditioned system (Eqs. (Axb2),
+ * (Axb3)).  HB_C64 / HB_SPLIT_BF16: FP64 flexible GMRES right-preconditioned
+ * by U~^{-1} L~^{-1} applied in the low-precision form, inside FP64 iterative
+ * refinement.  Stops when the true relative residual ||b^ - A^_F x||/||b^||
+ * <= rtol (FP64) for every column or after maxit inner iterations.  The
+ * initial guess is zero; x is overwritten with the solution.  Synchronises
+ * `stream` before returning; info may be NULL.
+ * Errors: HB_EINVAL, HB_ENAN (non-finite b), HB_ENOCONV (info still filled). */
+int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int64_t nrhs, int64_t ld, int restart,
+             double rtol, int maxit, hb_gmres_info* info, void* stream);
+
+/* hb_rhs_plane_wave -- b_i = exp(-i k (x_i cos phi + y_i sin phi)) (the
+ * incident field E^inc_z(rho_i) of Sec. 3.1, physical, unscaled) for nrhs
+ * angles phi_deg (host array, degrees) into the complex128 device block b. */
+int hb_rhs_plane_wave(hb_factor_t f, const double* phi_deg, int64_t nrhs, void* b, int64_t ld, void* stream);
+
+/* hb_far_field -- E_far(phi_q) = C sum_n w_n x_n exp(+i k (x_n cos phi_q + y_n sin phi_q)),
+ * C = -(k eta0/4) sqrt(2i/(pi k)), for every column of x (complex128, the
+ * physical current) and every observation angle (host array, degrees).
+ * out: complex128 device array [nrhs][nobs] (row-major).  Not in the paper:
+ * the far zone of the scattered field of the same EFIE kernel. */
+int hb_far_field(hb_factor_t f, const void* x, int64_t nrhs, int64_t ld, const double* phi_obs_deg, int64_t nobs,
+                 void* out, void* stream);
+
+/* hb_monostatic -- backscatter for column r of x at its own incidence angle
+ * phi_deg[r]: C sum_n w_n b_n(phi_r) x_n.  out: complex128 device [nrhs]. */
+int hb_monostatic(hb_factor_t f, const void* x, int64_t nrhs, int64_t ld, const double* phi_deg, void* out,
+                  void* stream);
+
+/* hb_set_sweep_rhs_per_cta -- tuning knob: RHS columns handled by one CTA of
+ * the sweep kernels (0 = library default).  Returns the previous value. */
+int hb_set_sweep_rhs_per_cta(hb_factor_t f, int rhs_per_cta);
+
+/* hb_profile -- enable (1) / disable (0) timing of the hot-path kernels of
+ * this factor.  While enabled, every apply launch sequence and every sweep
+ * kernel is bracketed by CUDA events on its stream (enabling resets the
+ * record).  Not in the paper: measurement support.
+ * hb_profile_read -- kind 0: apply (D+2 kernels per call), 1: sweep kernels,
+ * 2: every kernel the library launched (count only).  Returns the number of
+ * recorded calls/launches and their summed device time in ms (synchronises
+ * the recorded events; total_ms is 0 for kind 2). */
+int hb_profile(hb_factor_t f, int enable);
+int hb_profile_read(hb_factor_t f, int kind, int64_t* count, double* total_ms);
+
+/* ---- host-only verification entry points (no GPU needed) -------------
+ * hb_factor_host builds the same H-IDBF and packed program as hb_factor but
+ * keeps it in host memory only (no device image; the device entry points
+ * reject such a handle with HB_EINVAL).  hb_host_apply / hb_host_sweep run
+ * the packed program in FP64 on the host: y = A^_F x (op N) or A^_F^H x, and
+ * in-place sweeps (which: 0 L~^{-1}, 1 U~^{-1}, 2 L~^{-H}, 3 U~^{-H}).
+ * Vectors are host arrays of N complex128 (interleaved doubles). */
+int hb_factor_host(hb_geometry_t g, double wavelength, double eta0, double gamma, int64_t leaf, double eps,
+                   uint64_t seed, hb_factor_t* out);
+int hb_host_apply(hb_factor_t f, int op, const double* x, double* y);
+int hb_host_sweep(hb_factor_t f, int which, double* vec);
+
+const char* hb_last_error(void);
+const char* hb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HB_H */

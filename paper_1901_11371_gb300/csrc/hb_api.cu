@@ -1,0 +1,454 @@
+// C ABI of libhb (include/hb.h): handles, upload of the level-packed factor
+// image, workspaces and the apply / sweep / residual entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "hb_api_internal.h"
+
+namespace hb {
+const char* last_error();
+
+// ---------------------------------------------------------------------------
+// Upload
+// ---------------------------------------------------------------------------
+template <class Dst>
+static void convert(const std::vector<cplx>& src, std::vector<Dst>& dst) {
+  dst.resize(src.size());
+  for (size_t i = 0; i < src.size(); ++i) {
+    dst[i].x = (decltype(dst[i].x))src[i].real();
+    dst[i].y = (decltype(dst[i].y))src[i].imag();
+  }
+}
+
+// leaves row-major [r][c] on the host -> [leaf][c][r] on the device
+static std::vector<cplx> leaves_colmajor(const std::vector<cplx>& src, int64_t m, int64_t n0) {
+  std::vector<cplx> out(src.size());
+  for (int64_t l = 0; l < m; ++l)
+    for (int64_t r = 0; r < n0; ++r)
+      for (int64_t c = 0; c < n0; ++c) out[(l * n0 + c) * n0 + r] = src[(l * n0 + r) * n0 + c];
+  return out;
+}
+
+#define HB_CU(call)                                                                  \
+  do {                                                                               \
+    cudaError_t e__ = (call);                                                        \
+    if (e__ != cudaSuccess) {                                                        \
+      set_error("%s failed: %s", #call, cudaGetErrorString(e__));                    \
+      return e__ == cudaErrorMemoryAllocation ? HB_ENOMEM : HB_ECUDA;                \
+    }                                                                                \
+  } while (0)
+
+template <class V>
+static int up(const std::vector<V>& h, V** d, cudaStream_t st, int64_t& bytes) {
+  size_t nb = std::max<size_t>(h.size(), 1) * sizeof(V);
+  HB_CU(cudaMalloc((void**)d, nb));
+  if (!h.empty()) HB_CU(cudaMemcpyAsync(*d, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice, st));
+  bytes += (int64_t)nb;
+  return HB_OK;
+}
+
+template <class E>
+static int upload_elems(const PackedHost& ph, const HostFactor& hf, cudaStream_t st, DevFactor& df) {
+  std::vector<E> tmp;
+  int rc;
+  convert(ph.fpool, tmp);
+  if ((rc = up(tmp, (E**)&df.fpool, st, df.device_bytes))) return rc;
+  HB_CU(cudaStreamSynchronize(st));
+  convert(leaves_colmajor(hf.leaf, hf.m, hf.n0), tmp);
+  if ((rc = up(tmp, (E**)&df.leaf, st, df.device_bytes))) return rc;
+  HB_CU(cudaStreamSynchronize(st));
+  convert(leaves_colmajor(hf.linv, hf.m, hf.n0), tmp);
+  if ((rc = up(tmp, (E**)&df.linv, st, df.device_bytes))) return rc;
+  HB_CU(cudaStreamSynchronize(st));
+  convert(leaves_colmajor(hf.uinv, hf.m, hf.n0), tmp);
+  if ((rc = up(tmp, (E**)&df.uinv, st, df.device_bytes))) return rc;
+  HB_CU(cudaStreamSynchronize(st));
+  return HB_OK;
+}
+
+int upload_factor(const PackedHost& ph, const HostFactor& hf, const Geometry& g, int form, cudaStream_t st,
+                  DevFactor& df) {
+  df.form = form;
+  df.n = ph.n; df.n0 = ph.n0; df.m = ph.m; df.D = ph.depth;
+  df.state_len = ph.state_len;
+  df.fpool_len = (int64_t)ph.fpool.size();
+  df.ipool_len = (int64_t)ph.ipool.size();
+  df.kappa = hf.kappa; df.eta0 = hf.eta0; df.scale = hf.scale;
+  int rc = (form == HB_C128) ? upload_elems<double2>(ph, hf, st, df) : upload_elems<float2>(ph, hf, st, df);
+  if (rc) return rc;
+  if ((rc = up(ph.ipool, &df.ipool, st, df.device_bytes))) return rc;
+  if ((rc = up(ph.vout, &df.vout, st, df.device_bytes))) return rc;
+  if ((rc = up(ph.uout, &df.uout, st, df.device_bytes))) return rc;
+  if ((rc = up(ph.bvout, &df.bvout, st, df.device_bytes))) return rc;
+  if ((rc = up(ph.buout, &df.buout, st, df.device_bytes))) return rc;
+  if ((rc = up(ph.bf_vout0, &df.bf_vout0, st, df.device_bytes))) return rc;
+  if ((rc = up(ph.bf_uout0, &df.bf_uout0, st, df.device_bytes))) return rc;
+  if ((rc = up(ph.items, &df.items, st, df.device_bytes))) return rc;
+  if ((rc = up(ph.step_idx, &df.step_idx, st, df.device_bytes))) return rc;
+  if ((rc = up(ph.astep_idx, &df.astep_idx, st, df.device_bytes))) return rc;
+  df.step_ptr = ph.step_ptr;
+  df.astep_ptr = ph.astep_ptr;
+  const std::vector<DPhase>* progs[4] = {&ph.prog_lower, &ph.prog_upper, &ph.prog_lower_adj, &ph.prog_upper_adj};
+  for (int i = 0; i < 4; ++i) {
+    if ((rc = up(*progs[i], &df.prog[i], st, df.device_bytes))) return rc;
+    df.nprog[i] = (int)progs[i]->size();
+  }
+  if ((rc = up(g.cx, &df.cx, st, df.device_bytes))) return rc;
+  if ((rc = up(g.cy, &df.cy, st, df.device_bytes))) return rc;
+  if ((rc = up(g.w, &df.w, st, df.device_bytes))) return rc;
+  HB_CU(cudaStreamSynchronize(st));
+  return HB_OK;
+}
+
+void free_factor(DevFactor& df) {
+  void* ptrs[] = {df.fpool, df.leaf, df.linv, df.uinv, df.ipool, df.vout, df.uout, df.bvout, df.buout,
+                  df.bf_vout0, df.bf_uout0, df.items, df.step_idx, df.astep_idx, df.prog[0], df.prog[1],
+                  df.prog[2], df.prog[3], df.cx, df.cy, df.w};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  df = DevFactor();
+}
+
+void Profiler::begin(int kind, cudaStream_t st, cudaEvent_t& a) {
+  a = nullptr;
+  if (!on) return;
+  if (cudaEventCreate(&a) != cudaSuccess) { a = nullptr; return; }
+  cudaEventRecord(a, st);
+}
+void Profiler::end(int kind, cudaStream_t st, cudaEvent_t a) {
+  if (!on || !a) return;
+  cudaEvent_t b;
+  if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+  cudaEventRecord(b, st);
+  ev[kind].push_back({a, b});
+  count[kind]++;
+}
+void Profiler::reset() {
+  for (auto& v : ev)
+    for (auto& p : v) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
+  ev[0].clear(); ev[1].clear();
+  count[0] = count[1] = count[2] = 0;
+}
+
+void* Workspace::get(int slot, size_t bytes) {
+  if (slot < 0 || slot >= kSlots) return nullptr;
+  if (cap[slot] >= bytes && ptr[slot]) return ptr[slot];
+  if (ptr[slot]) { cudaFree(ptr[slot]); ptr[slot] = nullptr; cap[slot] = 0; }
+  size_t nb = std::max<size_t>(bytes, 256);
+  if (cudaMalloc(&ptr[slot], nb) != cudaSuccess) { ptr[slot] = nullptr; cap[slot] = 0; return nullptr; }
+  cap[slot] = nb;
+  return ptr[slot];
+}
+void Workspace::release() {
+  for (int i = 0; i < kSlots; ++i)
+    if (ptr[i]) { cudaFree(ptr[i]); ptr[i] = nullptr; cap[i] = 0; }
+}
+
+}  // namespace hb
+
+using namespace hb;
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* hb_last_error(void) { return hb::last_error(); }
+const char* hb_version(void) { return "hbutterfly 0.1 (sm_103a)"; }
+
+int hb_geometry(int kind, const double* params, int nparams, int64_t n_segments, hb_geometry_t* out) {
+  if (!out) { set_error("hb_geometry: out is null"); return HB_EINVAL; }
+  *out = nullptr;
+  hb_geometry_s* g = new (std::nothrow) hb_geometry_s();
+  if (!g) { set_error("hb_geometry: out of host memory"); return HB_ENOMEM; }
+  int rc = build_geometry(kind, params, nparams, n_segments, g->geo);
+  if (rc) { delete g; return rc; }
+  *out = g;
+  return HB_OK;
+}
+
+int hb_geometry_segments(hb_geometry_t g, double* centers_xy, double* lengths) {
+  if (!g) { set_error("hb_geometry_segments: null geometry"); return HB_EINVAL; }
+  for (int64_t i = 0; i < g->geo.n; ++i) {
+    if (centers_xy) { centers_xy[2 * i] = g->geo.cx[i]; centers_xy[2 * i + 1] = g->geo.cy[i]; }
+    if (lengths) lengths[i] = g->geo.w[i];
+  }
+  return HB_OK;
+}
+
+int64_t hb_geometry_size(hb_geometry_t g) { return g ? g->geo.n : -1; }
+
+void hb_geometry_destroy(hb_geometry_t g) { delete g; }
+
+int hb_factor(hb_geometry_t g, double wavelength, double eta0, double gamma, int64_t leaf, double eps, int form,
+              uint64_t seed, void* stream, hb_factor_t* out) {
+  if (!out || !g) { set_error("hb_factor: null argument"); return HB_EINVAL; }
+  *out = nullptr;
+  if (form != HB_C128 && form != HB_C64 && form != HB_SPLIT_BF16) { set_error("hb_factor: bad form %d", form); return HB_EINVAL; }
+  auto t0 = std::chrono::steady_clock::now();
+  hb_factor_s* f = new (std::nothrow) hb_factor_s();
+  if (!f) { set_error("hb_factor: out of host memory"); return HB_ENOMEM; }
+  int rc = build_factor(g->geo, wavelength, eta0, gamma, leaf, eps, seed, f->hf);
+  if (!rc) {
+    pack_factor(f->hf, f->ph);
+    for (const auto& b : f->hf.bf) {
+      int64_t z = 0;
+      for (const auto& st : b.col) for (const auto& blk : st) z += (int64_t)blk.k * (blk.c - blk.k);
+      for (const auto& st : b.row) for (const auto& blk : st) z += (int64_t)blk.k * (blk.c - blk.k);
+      for (const auto& sm : b.mid) z += (int64_t)sm.size();
+      (b.kind == 1 ? f->lower_nnz : f->upper_nnz) += z;
+    }
+    rc = upload_factor(f->ph, f->hf, g->geo, form == HB_SPLIT_BF16 ? HB_C64 : form, (cudaStream_t)stream, f->df);
+    f->df.form = form;
+  }
+  if (rc) { free_factor(f->df); delete f; return rc; }
+  f->construct_seconds = f->hf.build_seconds;
+  f->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  // release the bulky host copies (stats kept)
+  f->ph.fpool.clear(); f->ph.fpool.shrink_to_fit();
+  for (auto& b : f->hf.bf) { b.col.clear(); b.row.clear(); b.mid.clear(); b.col.shrink_to_fit(); b.row.shrink_to_fit(); b.mid.shrink_to_fit(); }
+  f->hf.leaf.clear(); f->hf.leaf.shrink_to_fit();
+  f->hf.linv.clear(); f->hf.linv.shrink_to_fit();
+  f->hf.uinv.clear(); f->hf.uinv.shrink_to_fit();
+  *out = f;
+  return HB_OK;
+}
+
+int hb_factor_host(hb_geometry_t g, double wavelength, double eta0, double gamma, int64_t leaf, double eps,
+                   uint64_t seed, hb_factor_t* out) {
+  if (!out || !g) { set_error("hb_factor_host: null argument"); return HB_EINVAL; }
+  *out = nullptr;
+  hb_factor_s* f = new (std::nothrow) hb_factor_s();
+  if (!f) { set_error("hb_factor_host: out of host memory"); return HB_ENOMEM; }
+  int rc = build_factor(g->geo, wavelength, eta0, gamma, leaf, eps, seed, f->hf);
+  if (rc) { delete f; return rc; }
+  pack_factor(f->hf, f->ph);
+  f->host_only = true;
+  f->df.form = HB_C128;
+  f->df.n = f->ph.n; f->df.n0 = f->ph.n0; f->df.m = f->ph.m; f->df.D = f->ph.depth;
+  f->build_seconds = f->construct_seconds = f->hf.build_seconds;
+  *out = f;
+  return HB_OK;
+}
+
+int hb_host_apply(hb_factor_t f, int op, const double* x, double* y) {
+  if (!f || !f->host_only || !x || !y || (op != HB_OP_N && op != HB_OP_H)) { set_error("hb_host_apply: bad argument"); return HB_EINVAL; }
+  host_apply(f->ph, f->hf, op == HB_OP_H, reinterpret_cast<const cplx*>(x), reinterpret_cast<cplx*>(y));
+  return HB_OK;
+}
+
+int hb_host_sweep(hb_factor_t f, int which, double* vec) {
+  if (!f || !f->host_only || !vec || which < 0 || which > 3) { set_error("hb_host_sweep: bad argument"); return HB_EINVAL; }
+  host_sweep(f->ph, f->hf, which, reinterpret_cast<cplx*>(vec));
+  return HB_OK;
+}
+
+int hb_factor_info(hb_factor_t f, hb_factor_stats* s) {
+  if (!f || !s) { set_error("hb_factor_info: null argument"); return HB_EINVAL; }
+  std::memset(s, 0, sizeof(*s));
+  const PackedHost& ph = f->ph;
+  s->n = ph.n; s->leaf = ph.n0; s->depth = ph.depth; s->form = f->df.form;
+  s->n_butterflies = 2 * (ph.m - 1);
+  s->scale = f->hf.scale; s->eps = f->hf.eps;
+  s->kmax = ph.kmax; s->kavg = ph.kavg;
+  for (int v = 0; v < 32; ++v) { s->kmax_depth[v] = ph.kmax_depth[v]; s->kavg_depth[v] = ph.kavg_depth[v]; }
+  s->nnz_leaf = ph.m * ph.n0 * ph.n0;
+  s->nnz_butterfly = ph.nnz_bf;
+  s->nnz_lu_leaf = 2 * s->nnz_leaf;
+  s->index_bytes = f->df.ipool_len * 2;
+  s->device_bytes = f->df.device_bytes;
+  int64_t eb = (f->df.form == HB_C128) ? 16 : 8;
+  // algorithmic bytes of one single-RHS apply: every stored butterfly entry and
+  // dense-leaf entry once, the index arrays once, x read and y written.
+  s->apply_bytes = (ph.nnz_bf + s->nnz_leaf) * eb + s->index_bytes + 2 * ph.n * eb;
+  // a sweep touches the butterflies of one triangle (about half) and one leaf-inverse set
+  s->lower_bytes = f->lower_nnz * eb + s->nnz_leaf * eb + s->index_bytes / 2 + 2 * ph.n * eb;
+  s->upper_bytes = f->upper_nnz * eb + s->nnz_leaf * eb + s->index_bytes / 2 + 2 * ph.n * eb;
+  s->rebuilt_blocks = 0;
+  s->build_seconds = f->build_seconds;
+  return HB_OK;
+}
+
+int hb_profile(hb_factor_t f, int enable) {
+  if (!f) { set_error("hb_profile: null factor"); return HB_EINVAL; }
+  if (enable) f->prof.reset();
+  f->prof.on = enable != 0;
+  return HB_OK;
+}
+
+int hb_profile_read(hb_factor_t f, int kind, int64_t* count, double* total_ms) {
+  if (!f || kind < 0 || kind > 2) { set_error("hb_profile_read: bad argument"); return HB_EINVAL; }
+  double tot = 0.0;
+  if (kind < 2) {
+    for (auto& p : f->prof.ev[kind]) {
+      if (cudaEventSynchronize(p.second) != cudaSuccess) { set_error("hb_profile_read: event sync failed"); return HB_ECUDA; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, p.first, p.second);
+      tot += ms;
+    }
+  }
+  if (count) *count = f->prof.count[kind];
+  if (total_ms) *total_ms = tot;
+  return HB_OK;
+}
+
+void hb_factor_destroy(hb_factor_t f) {
+  if (!f) return;
+  f->prof.reset();
+  f->ws.release();
+  free_factor(f->df);
+  delete f;
+}
+
+int hb_tree(hb_factor_t f, int64_t* node_begin, int64_t* node_end) {
+  if (!f || !node_begin || !node_end) { set_error("hb_tree: null argument"); return HB_EINVAL; }
+  const int D = f->ph.depth;
+  const int64_t n = f->ph.n;
+  for (int v = 0; v <= D; ++v) {
+    int64_t cnt = (int64_t)1 << v, sz = n >> v;
+    for (int64_t p = 0; p < cnt; ++p) {
+      node_begin[cnt - 1 + p] = p * sz;
+      node_end[cnt - 1 + p] = (p + 1) * sz;
+    }
+  }
+  return HB_OK;
+}
+
+int hb_set_sweep_rhs_per_cta(hb_factor_t f, int rhs_per_cta) {
+  if (!f) return HB_EINVAL;
+  int old = f->df.sweep_rhs_per_cta;
+  f->df.sweep_rhs_per_cta = rhs_per_cta < 0 ? 0 : rhs_per_cta;
+  return old;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// apply / sweeps / residual
+// ---------------------------------------------------------------------------
+namespace hb {
+
+int check_vec_args(hb_factor_t f, const void* a, const void* b, int64_t nrhs, int64_t ld, const char* who) {
+  if (!f || !a || !b) { set_error("%s: null argument", who); return HB_EINVAL; }
+  if (f->host_only) { set_error("%s: factor has no device image (built by hb_factor_host)", who); return HB_EINVAL; }
+  if (nrhs < 1 || ld < f->df.n) { set_error("%s: need nrhs >= 1 and ld >= N (got %lld, %lld)", who, (long long)nrhs, (long long)ld); return HB_EINVAL; }
+  if (a == b) { set_error("%s: input and output must not alias", who); return HB_EINVAL; }
+  return HB_OK;
+}
+
+// form vectors: double2 for HB_C128, float2 otherwise
+static inline Prec form_prec(const DevFactor& df) { return df.form == HB_C128 ? PREC_F64 : PREC_F32; }
+static inline int form_vt(const DevFactor& df) { return df.form == HB_C128 ? 0 : 1; }
+static inline size_t vt_size(int t) { return t == 0 ? 16 : 8; }
+
+int apply_internal(hb_factor_t f, Prec p, bool adj, const void* x, void* y, int64_t R, cudaStream_t st) {
+  size_t es = (p == PREC_F32) ? 8 : 16;
+  void* state = f->ws.get(WS_STATE, (size_t)f->df.state_len * R * es);
+  if (!state) { set_error("apply: cannot allocate state workspace"); return HB_ENOMEM; }
+  cudaEvent_t e;
+  f->prof.begin(0, st, e);
+  int rc = launch_apply(f->df, p, adj, x, y, R, state, st);
+  f->prof.end(0, st, e);
+  count_launch(f, (int)f->df.step_ptr.size() + 1);
+  return rc;
+}
+
+int sweep_internal(hb_factor_t f, Prec p, int which, void* vec, int64_t R, cudaStream_t st) {
+  size_t es = (p == PREC_F32) ? 8 : 16;
+  void* state = f->ws.get(WS_STATE_SWEEP, (size_t)f->df.state_len * R * es);
+  if (!state) { set_error("sweep: cannot allocate state workspace"); return HB_ENOMEM; }
+  cudaEvent_t e;
+  f->prof.begin(1, st, e);
+  int rc = launch_sweep(f->df, p, which, vec, R, state, st);
+  f->prof.end(1, st, e);
+  count_launch(f, 1);
+  return rc;
+}
+
+}  // namespace hb
+
+extern "C" {
+
+int hb_apply(hb_factor_t f, int op, const void* x, void* y, int64_t nrhs, int64_t ld, void* stream) {
+  int rc = check_vec_args(f, x, y, nrhs, ld, "hb_apply");
+  if (rc) return rc;
+  if (op != HB_OP_N && op != HB_OP_H) { set_error("hb_apply: bad op"); return HB_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const DevFactor& df = f->df;
+  Prec p = form_prec(df);
+  int vt = form_vt(df);
+  if (nrhs == 1) return apply_internal(f, p, op == HB_OP_H, x, y, 1, st);
+  size_t bytes = (size_t)df.n * nrhs * vt_size(vt);
+  void* xi = f->ws.get(WS_VEC0, bytes);
+  void* yi = f->ws.get(WS_VEC1, bytes);
+  if (!xi || !yi) { set_error("hb_apply: workspace allocation failed"); return HB_ENOMEM; }
+  if ((rc = launch_gather_cols(x, vt, ld, df.n, nrhs, xi, vt, 1.0, st))) return rc;
+  if ((rc = apply_internal(f, p, op == HB_OP_H, xi, yi, nrhs, st))) return rc;
+  return launch_scatter_cols(yi, vt, df.n, nrhs, y, vt, ld, 1.0, st);
+}
+
+int hb_apply_adjoint(hb_factor_t f, const void* x, void* y, int64_t nrhs, int64_t ld, void* stream) {
+  return hb_apply(f, HB_OP_H, x, y, nrhs, ld, stream);
+}
+
+static int sweeps(hb_factor_t f, int op, const void* b, void* x, int64_t nrhs, int64_t ld, void* stream,
+                  int first, int second, const char* who) {
+  int rc = check_vec_args(f, b, x, nrhs, ld, who);
+  if (rc) return rc;
+  if (op != HB_OP_N && op != HB_OP_H) { set_error("%s: bad op", who); return HB_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const DevFactor& df = f->df;
+  Prec p = form_prec(df);
+  int vt = form_vt(df);
+  void* v;
+  if (nrhs == 1) {
+    if (cudaMemcpyAsync(x, b, (size_t)df.n * vt_size(vt), cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+      set_error("%s: copy failed", who);
+      return HB_ECUDA;
+    }
+    v = x;
+  } else {
+    v = f->ws.get(WS_VEC0, (size_t)df.n * nrhs * vt_size(vt));
+    if (!v) { set_error("%s: workspace allocation failed", who); return HB_ENOMEM; }
+    if ((rc = launch_gather_cols(b, vt, ld, df.n, nrhs, v, vt, 1.0, st))) return rc;
+  }
+  if (first >= 0 && (rc = sweep_internal(f, p, first, v, nrhs, st))) return rc;
+  if (second >= 0 && (rc = sweep_internal(f, p, second, v, nrhs, st))) return rc;
+  if (nrhs > 1) return launch_scatter_cols(v, vt, df.n, nrhs, x, vt, ld, 1.0, st);
+  return HB_OK;
+}
+
+int hb_precond_solve(hb_factor_t f, int op, const void* b, void* x, int64_t nrhs, int64_t ld, void* stream) {
+  // op N: x = U~^{-1} L~^{-1} b;  op H: x = L~^{-H} U~^{-H} b
+  if (op == HB_OP_H) return sweeps(f, op, b, x, nrhs, ld, stream, 3, 2, "hb_precond_solve");
+  return sweeps(f, op, b, x, nrhs, ld, stream, 0, 1, "hb_precond_solve");
+}
+int hb_lower_solve(hb_factor_t f, int op, const void* b, void* x, int64_t nrhs, int64_t ld, void* stream) {
+  return sweeps(f, op, b, x, nrhs, ld, stream, op == HB_OP_H ? 2 : 0, -1, "hb_lower_solve");
+}
+int hb_upper_solve(hb_factor_t f, int op, const void* b, void* x, int64_t nrhs, int64_t ld, void* stream) {
+  return sweeps(f, op, b, x, nrhs, ld, stream, op == HB_OP_H ? 3 : 1, -1, "hb_upper_solve");
+}
+
+int hb_residual(hb_factor_t f, int op, const void* b, const void* x, void* r, int64_t nrhs, int64_t ld, void* stream) {
+  int rc = check_vec_args(f, x, r, nrhs, ld, "hb_residual");
+  if (rc) return rc;
+  if (!b || b == r) { set_error("hb_residual: b must be non-null and distinct from r"); return HB_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const DevFactor& df = f->df;
+  Prec p = df.form == HB_C128 ? PREC_F64 : PREC_F32_ACC64;
+  size_t bytes = (size_t)df.n * nrhs * 16;
+  void* xi = f->ws.get(WS_VEC0, bytes);
+  void* yi = f->ws.get(WS_VEC1, bytes);
+  if (!xi || !yi) { set_error("hb_residual: workspace allocation failed"); return HB_ENOMEM; }
+  if ((rc = launch_gather_cols(x, 0, ld, df.n, nrhs, xi, 0, 1.0, st))) return rc;
+  if ((rc = apply_internal(f, p, op == HB_OP_H, xi, yi, nrhs, st))) return rc;
+  return launch_residual_cols(b, ld, yi, df.n, nrhs, r, st);
+}
+
+}  // extern "C"

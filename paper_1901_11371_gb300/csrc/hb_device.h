@@ -1,0 +1,74 @@
+// Device image of an H-IDBF factor and the launchers of the hot-path kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "hb_internal.h"
+
+namespace hb {
+
+struct DevFactor {
+  int form = HB_C128;            // storage form of the factor pool
+  int64_t n = 0, n0 = 0, m = 0;
+  int D = 0;
+  int64_t state_len = 0;         // butterfly state entries per RHS
+  // factor data (element type double2 for HB_C128, float2 otherwise)
+  void* fpool = nullptr;
+  int64_t fpool_len = 0;
+  void* leaf = nullptr;          // [m][c][r]
+  void* linv = nullptr;          // [m][c][r] inverse of the unit-lower leaf triangle
+  void* uinv = nullptr;          // [m][c][r] inverse of the upper leaf triangle
+  int16_t* ipool = nullptr;
+  int64_t ipool_len = 0;
+  DOuter* vout = nullptr;        // [m][D]
+  DOuter* uout = nullptr;        // [m][D]
+  DOuter* bvout = nullptr;
+  DOuter* buout = nullptr;
+  int32_t* bf_vout0 = nullptr;   // device copies
+  int32_t* bf_uout0 = nullptr;
+  DItem* items = nullptr;
+  int32_t* step_idx = nullptr;
+  int32_t* astep_idx = nullptr;
+  std::vector<int32_t> step_ptr, astep_ptr;   // host copies (launch sizes)
+  DPhase* prog[4] = {nullptr, nullptr, nullptr, nullptr};   // lower, upper, lower^H, upper^H
+  int nprog[4] = {0, 0, 0, 0};
+  // geometry on the device (far field, plane waves)
+  double* cx = nullptr;
+  double* cy = nullptr;
+  double* w = nullptr;
+  double kappa = 0, eta0 = 0, scale = 1;
+  int64_t device_bytes = 0;
+  int sweep_rhs_per_cta = 0;
+};
+
+// Upload a packed host image in `form`; returns HB_OK or an error code.
+int upload_factor(const PackedHost& ph, const HostFactor& hf, const Geometry& g, int form, cudaStream_t st,
+                  DevFactor& df);
+void free_factor(DevFactor& df);
+
+// Arithmetic precisions of the hot path.
+enum Prec { PREC_F64 = 0,        // double factors, double arithmetic (HB_C128)
+            PREC_F32 = 1,        // float factors, float arithmetic (HB_C64)
+            PREC_F32_ACC64 = 2   // float factors, double arithmetic (FP64 residuals of HB_C64)
+};
+
+// All vectors below are in the internal layout [row][R] (RHS fastest) with
+// complex element type double2 (PREC_F64, PREC_F32_ACC64) or float2 (PREC_F32).
+// `state` holds df.state_len * R complex entries of the same type.
+int launch_apply(const DevFactor& df, Prec p, bool adjoint, const void* x, void* y, int64_t R, void* state,
+                 cudaStream_t st);
+// In-place sweep: vec holds b on entry and x on exit.  which: 0 = L~^{-1},
+// 1 = U~^{-1}, 2 = L~^{-H}, 3 = U~^{-H}.
+int launch_sweep(const DevFactor& df, Prec p, int which, void* vec, int64_t R, void* state, cudaStream_t st);
+
+// Layout conversion between the ABI's column-major [R][ld] blocks and the
+// internal [row][R] layout, with optional precision change and scaling.
+// src_t / dst_t: 0 = double2, 1 = float2.
+int launch_gather_cols(const void* src, int src_t, int64_t ld, int64_t n, int64_t R, void* dst, int dst_t,
+                       double scale, cudaStream_t st);
+int launch_scatter_cols(const void* src, int src_t, int64_t n, int64_t R, void* dst, int dst_t, int64_t ld,
+                        double scale, cudaStream_t st);
+
+}  // namespace hb

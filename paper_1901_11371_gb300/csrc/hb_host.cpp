@@ -1,0 +1,814 @@
+// Host side of libhb: geometry (Sec. 3.1), EFIE entries, H-IDBF construction
+// (Alg. 1 with the IDBF of Sec. 2 / Appendix, sampled linear-scaling IDs) and
+// packing of the factors into the level-packed device image.
+//
+// Construction is not on the measured hot path; it runs on the host cores
+// with OpenMP and is timed separately (hb_factor_stats.build_seconds).
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#include "hb_internal.h"
+
+namespace hb {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+const char* last_error() { return g_err; }
+
+// ---------------------------------------------------------------------------
+// Geometry: equal-arc-length nodes on the exact curve, chord segments.
+// ---------------------------------------------------------------------------
+static void chords(const std::vector<double>& nx, const std::vector<double>& ny, Geometry& g, int64_t off) {
+  int64_t cnt = (int64_t)nx.size() - 1;
+  for (int64_t i = 0; i < cnt; ++i) {
+    g.cx[off + i] = 0.5 * (nx[i] + nx[i + 1]);
+    g.cy[off + i] = 0.5 * (ny[i] + ny[i + 1]);
+    g.w[off + i] = std::hypot(nx[i + 1] - nx[i], ny[i + 1] - ny[i]);
+  }
+}
+
+// s(theta) = (a/2) [theta sqrt(1 + theta^2) + asinh(theta)] for r = a theta.
+static double spiral_s(double a, double t) { return 0.5 * a * (t * std::sqrt(1.0 + t * t) + std::asinh(t)); }
+
+int build_geometry(int kind, const double* params, int nparams, int64_t n, Geometry& g) {
+  if (n < 1 || params == nullptr) {
+    set_error("hb_geometry: n_segments must be >= 1 and params non-null");
+    return HB_EINVAL;
+  }
+  g.kind = kind;
+  g.n = n;
+  g.cx.assign(n, 0.0);
+  g.cy.assign(n, 0.0);
+  g.w.assign(n, 0.0);
+  std::vector<double> nx(n + 1), ny(n + 1);
+  if (kind == HB_STRIP) {
+    if (nparams != 4) { set_error("STRIP needs 4 params"); return HB_EINVAL; }
+    for (int64_t i = 0; i <= n; ++i) {
+      double t = (double)i / (double)n;
+      nx[i] = params[0] + (params[2] - params[0]) * t;
+      ny[i] = params[1] + (params[3] - params[1]) * t;
+    }
+    chords(nx, ny, g, 0);
+  } else if (kind == HB_SPIRAL) {
+    if (nparams != 3 || params[0] <= 0 || params[2] <= params[1]) { set_error("SPIRAL needs (a>0, th0<th1)"); return HB_EINVAL; }
+    double a = params[0], t0 = params[1], t1 = params[2];
+    double s0 = spiral_s(a, t0), s1 = spiral_s(a, t1);
+    for (int64_t i = 0; i <= n; ++i) {
+      double target = s0 + (s1 - s0) * (double)i / (double)n;
+      double th = t0 + (t1 - t0) * (double)i / (double)n;
+      for (int it = 0; it < 100; ++it) {   // Newton on s(theta) = target, s' = a sqrt(1+theta^2)
+        double step = (spiral_s(a, th) - target) / (a * std::sqrt(1.0 + th * th));
+        th -= step;
+        if (std::fabs(step) <= 1e-15 * std::max(1.0, std::fabs(t1))) break;
+      }
+      if (i == 0) th = t0;
+      if (i == n) th = t1;
+      nx[i] = a * th * std::cos(th);
+      ny[i] = a * th * std::sin(th);
+    }
+    chords(nx, ny, g, 0);
+  } else if (kind == HB_ARC) {
+    if (nparams != 3 || params[0] <= 0) { set_error("ARC needs (R>0, phi0, phi1)"); return HB_EINVAL; }
+    for (int64_t i = 0; i <= n; ++i) {
+      double ph = params[1] + (params[2] - params[1]) * (double)i / (double)n;
+      nx[i] = params[0] * std::cos(ph);
+      ny[i] = params[0] * std::sin(ph);
+    }
+    chords(nx, ny, g, 0);
+  } else if (kind == HB_PARALLEL_STRIPS) {
+    if (nparams != 3) { set_error("PARALLEL_STRIPS needs 3 params"); return HB_EINVAL; }
+    int64_t ns = (int64_t)std::llround(params[0]);
+    if (ns < 1 || n % ns) { set_error("PARALLEL_STRIPS: n_strips must divide n_segments"); return HB_EINVAL; }
+    int64_t per = n / ns;
+    std::vector<double> sx(per + 1), sy(per + 1);
+    for (int64_t s = 0; s < ns; ++s) {
+      for (int64_t i = 0; i <= per; ++i) {
+        sx[i] = params[1] * (double)i / (double)per;
+        sy[i] = (double)s * params[2];
+      }
+      chords(sx, sy, g, s * per);
+    }
+  } else {
+    set_error("hb_geometry: unknown kind %d", kind);
+    return HB_EINVAL;
+  }
+  g.params.assign(params, params + nparams);
+  return HB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// EFIE entries (Sec. 3.1), rescaled by a.  H0^(2) = J0 - i Y0 from the C
+// library's j0 / y0.
+// ---------------------------------------------------------------------------
+struct Entries {
+  const Geometry* g;
+  double kappa, eta0, gamma, scale;
+  std::vector<cplx> diag;
+
+  void init(const Geometry& geo, double wavelength, double eta, double gam) {
+    g = &geo;
+    kappa = 2.0 * M_PI / wavelength;
+    eta0 = eta;
+    gamma = gam;
+    diag.resize(geo.n);
+    double mx = 0.0;
+    for (int64_t i = 0; i < geo.n; ++i) {
+      double w = geo.w[i];
+      double c = kappa * eta0 * w / 4.0;
+      diag[i] = cplx(c, -c * (2.0 / M_PI) * std::log(gamma * kappa * w / (4.0 * M_E)));
+      mx = std::max(mx, std::abs(diag[i]));
+    }
+    scale = 1.0 / mx;
+    for (auto& d : diag) d *= scale;
+  }
+  inline cplx operator()(int64_t i, int64_t j) const {
+    if (i == j) return diag[i];
+    double dx = g->cx[i] - g->cx[j], dy = g->cy[i] - g->cy[j];
+    double x = kappa * std::sqrt(dx * dx + dy * dy);
+    double c = scale * kappa * eta0 * g->w[j] * 0.25;
+    return cplx(c * ::j0(x), -c * ::y0(x));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Interpolative decomposition: Householder QR with column pivoting of an
+// s x c column-major matrix, truncated at the first k with |R_kk| <= tol |R_00|
+// (reading of Eq. (req)); T = R11^{-1} R12.
+// ---------------------------------------------------------------------------
+static void column_id(std::vector<cplx>& M, int s, int c, double tol, IdBlock& out) {
+  std::vector<int> perm(c);
+  std::iota(perm.begin(), perm.end(), 0);
+  int steps = std::min(s, c);
+  int k = steps;
+  double r00 = 0.0;
+  std::vector<cplx> v(s);
+  for (int j = 0; j < steps; ++j) {
+    // pivot: largest trailing column norm, lowest index on ties
+    int piv = j;
+    double best = -1.0;
+    for (int l = j; l < c; ++l) {
+      double nr = 0.0;
+      const cplx* col = &M[(size_t)l * s];
+      for (int r = j; r < s; ++r) nr += std::norm(col[r]);
+      if (nr > best) { best = nr; piv = l; }
+    }
+    if (piv != j) {
+      std::swap_ranges(M.begin() + (size_t)j * s, M.begin() + (size_t)(j + 1) * s, M.begin() + (size_t)piv * s);
+      std::swap(perm[j], perm[piv]);
+    }
+    double alpha = std::sqrt(std::max(best, 0.0));
+    if (j == 0) r00 = alpha;
+    if (alpha == 0.0 || (j > 0 && alpha <= tol * r00)) { k = j; break; }
+    cplx* colj = &M[(size_t)j * s];
+    cplx x0 = colj[j];
+    cplx phase = (std::abs(x0) > 0) ? x0 / std::abs(x0) : cplx(1.0, 0.0);
+    for (int r = j; r < s; ++r) v[r] = colj[r];
+    v[j] += phase * alpha;
+    double vn = 0.0;
+    for (int r = j; r < s; ++r) vn += std::norm(v[r]);
+    vn = std::sqrt(vn);
+    for (int r = j; r < s; ++r) v[r] /= vn;
+    for (int l = j; l < c; ++l) {
+      cplx* col = &M[(size_t)l * s];
+      cplx d = 0.0;
+      for (int r = j; r < s; ++r) d += std::conj(v[r]) * col[r];
+      d *= 2.0;
+      for (int r = j; r < s; ++r) col[r] -= v[r] * d;
+    }
+  }
+  k = std::max(k, 1);
+  k = std::min(k, c);
+  out.k = k;
+  out.c = c;
+  out.q.assign(perm.begin(), perm.begin() + k);
+  out.p.assign(perm.begin() + k, perm.end());
+  int nr = c - k;
+  out.t.assign((size_t)k * nr, cplx(0.0));
+  // back substitution R11 T = R12 (R stored in the top k rows of M)
+  for (int j = 0; j < nr; ++j) {
+    for (int i = k - 1; i >= 0; --i) {
+      cplx acc = M[(size_t)(k + j) * s + i];
+      for (int l = i + 1; l < k; ++l) acc -= M[(size_t)l * s + i] * out.t[(size_t)l * nr + j];
+      out.t[(size_t)i * nr + j] = acc / M[(size_t)i * s + i];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Seeded sampling of s positions out of M (Mock-Chebyshev grid + uniform fill).
+// ---------------------------------------------------------------------------
+static inline uint64_t splitmix(uint64_t& x) {
+  uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+static void sample_positions(int64_t M, int s, uint64_t seed, std::vector<int64_t>& out) {
+  out.clear();
+  if (M <= s) {
+    out.resize(M);
+    std::iota(out.begin(), out.end(), 0);
+    return;
+  }
+  std::vector<char> used(M, 0);
+  int nc = s / 2;
+  for (int i = 0; i < nc; ++i) {
+    double x = 0.5 * (1.0 - std::cos(M_PI * (2.0 * i + 1.0) / (2.0 * nc)));
+    int64_t idx = std::min<int64_t>(M - 1, (int64_t)std::llround(x * (double)(M - 1)));
+    if (!used[idx]) { used[idx] = 1; out.push_back(idx); }
+  }
+  uint64_t st = seed;
+  while ((int)out.size() < s) {
+    int64_t idx = (int64_t)(splitmix(st) % (uint64_t)M);
+    if (!used[idx]) { used[idx] = 1; out.push_back(idx); }
+  }
+  std::sort(out.begin(), out.end());
+}
+
+static inline int sample_count(int c) { return 2 * c + 8; }
+
+// ---------------------------------------------------------------------------
+// One butterfly: interleaved row / column stages (complementary
+// skeletonization of the IDBF: column IDs sample the row skeletons of the
+// same level, row IDs sample the column skeletons of the previous level).
+// ---------------------------------------------------------------------------
+static void build_butterfly(Butterfly& B, const Entries& K, int64_t n0, double tol, uint64_t seed, bool par) {
+  const int L = B.L;
+  const int64_t npairs = (int64_t)1 << L;
+  B.col.assign(B.hc, std::vector<IdBlock>(npairs));
+  B.row.assign(B.hr, std::vector<IdBlock>(npairs));
+  const int dmax = std::max(B.hc, B.hr);
+  for (int d = 0; d < dmax; ++d) {
+    // ---- row stage d: pairs (a at row level L-d, b at column level d), g = b*2^(L-d) + a
+    if (d < B.hr) {
+      const int64_t na = (int64_t)1 << (L - d);
+#pragma omp parallel for schedule(dynamic, 4) if (par)
+      for (int64_t g = 0; g < npairs; ++g) {
+        int64_t b = g / na, a = g % na;
+        IdBlock& blk = B.row[d][g];
+        std::vector<int64_t> cand;
+        if (d == 0) {
+          for (int64_t r = 0; r < n0; ++r) cand.push_back(B.row0 + a * n0 + r);
+        } else {
+          const int64_t nap = (int64_t)1 << (L - d + 1);
+          const IdBlock& c0 = B.row[d - 1][(b >> 1) * nap + 2 * a];
+          const IdBlock& c1 = B.row[d - 1][(b >> 1) * nap + 2 * a + 1];
+          cand = c0.skel;
+          cand.insert(cand.end(), c1.skel.begin(), c1.skel.end());
+        }
+        // columns to sample
+        std::vector<int64_t> pool;
+        if (d == 0) {
+          pool.resize(B.n);
+          for (int64_t j = 0; j < B.n; ++j) pool[j] = B.col0 + j;
+        } else {
+          // column skeletons of column stage d-1 under column node b (level d):
+          // pairs (a' = ancestor of a at row level d-1, b'' at column level L-d+1)
+          int sh = L - 2 * d + 1;
+          int64_t ap = a >> sh;
+          const int64_t nbpp = (int64_t)1 << (L - d + 1);
+          for (int64_t bb = b << sh; bb < ((b + 1) << sh); ++bb) {
+            const IdBlock& cb = B.col[d - 1][ap * nbpp + bb];
+            pool.insert(pool.end(), cb.skel.begin(), cb.skel.end());
+          }
+        }
+        int c = (int)cand.size();
+        std::vector<int64_t> pos;
+        uint64_t sd = seed ^ (0x1000003ull * (uint64_t)(d + 1)) ^ (0x9E37ull * (uint64_t)g) ^ 0xABCDull;
+        sample_positions((int64_t)pool.size(), sample_count(c), sd, pos);
+        int s = (int)pos.size();
+        std::vector<cplx> M((size_t)s * c);
+        for (int cc = 0; cc < c; ++cc)
+          for (int r = 0; r < s; ++r) M[(size_t)cc * s + r] = K(cand[cc], pool[pos[r]]);
+        column_id(M, s, c, tol, blk);
+        blk.skel.resize(blk.k);
+        for (int i = 0; i < blk.k; ++i) blk.skel[i] = cand[blk.q[i]];
+      }
+    }
+    // ---- column stage d: pairs (a at row level d, b at column level L-d), g = a*2^(L-d) + b
+    if (d < B.hc) {
+      const int64_t nb = (int64_t)1 << (L - d);
+#pragma omp parallel for schedule(dynamic, 4) if (par)
+      for (int64_t g = 0; g < npairs; ++g) {
+        int64_t a = g / nb, b = g % nb;
+        IdBlock& blk = B.col[d][g];
+        std::vector<int64_t> cand;
+        if (d == 0) {
+          for (int64_t j = 0; j < n0; ++j) cand.push_back(B.col0 + b * n0 + j);
+        } else {
+          const int64_t nbp = (int64_t)1 << (L - d + 1);
+          const IdBlock& c0 = B.col[d - 1][(a >> 1) * nbp + 2 * b];
+          const IdBlock& c1 = B.col[d - 1][(a >> 1) * nbp + 2 * b + 1];
+          cand = c0.skel;
+          cand.insert(cand.end(), c1.skel.begin(), c1.skel.end());
+        }
+        // rows to sample: row skeletons of row stage d under row node a (level d):
+        // pairs (a'' at row level L-d below a, b' = ancestor of b at column level d)
+        std::vector<int64_t> pool;
+        int sh = L - 2 * d;
+        int64_t bp = b >> sh;
+        const int64_t na2 = (int64_t)1 << (L - d);
+        for (int64_t aa = a << sh; aa < ((a + 1) << sh); ++aa) {
+          const IdBlock& rb = B.row[d][bp * na2 + aa];
+          pool.insert(pool.end(), rb.skel.begin(), rb.skel.end());
+        }
+        int c = (int)cand.size();
+        std::vector<int64_t> pos;
+        uint64_t sd = seed ^ (0x2000011ull * (uint64_t)(d + 1)) ^ (0x7F4Aull * (uint64_t)g) ^ 0x1234ull;
+        sample_positions((int64_t)pool.size(), sample_count(c), sd, pos);
+        int s = (int)pos.size();
+        std::vector<cplx> M((size_t)s * c);
+        for (int cc = 0; cc < c; ++cc)
+          for (int r = 0; r < s; ++r) M[(size_t)cc * s + r] = K(pool[pos[r]], cand[cc]);
+        column_id(M, s, c, tol, blk);
+        blk.skel.resize(blk.k);
+        for (int i = 0; i < blk.k; ++i) blk.skel[i] = cand[blk.q[i]];
+      }
+    }
+  }
+  // ---- middle: S(g) = K(rskel, cskel) on the column-stage-(hc-1) pairs
+  const int64_t nbm = (int64_t)1 << (L - B.hc + 1);   // column nodes at level L-hc+1
+  const int64_t nam = (int64_t)1 << (B.hc - 1);       // row nodes at level hc-1 (= L-hr+1)
+  B.mid.assign(npairs, {});
+#pragma omp parallel for schedule(dynamic, 8) if (par)
+  for (int64_t g = 0; g < npairs; ++g) {
+    int64_t a = g / nbm, b = g % nbm;
+    const IdBlock& cb = B.col[B.hc - 1][g];
+    const IdBlock& rb = B.row[B.hr - 1][b * nam + a];
+    std::vector<cplx>& S = B.mid[g];
+    S.resize((size_t)rb.k * cb.k);
+    for (int r = 0; r < rb.k; ++r)
+      for (int c = 0; c < cb.k; ++c) S[(size_t)r * cb.k + c] = K(rb.skel[r], cb.skel[c]);
+  }
+}
+
+// inverse of a unit-lower (lower=true, strict lower part of A plus I) or upper
+// (diagonal included) triangle of the n0 x n0 row-major block A
+static void triangle_inverse(const cplx* A, int n0, bool lower, cplx* X) {
+  for (int i = 0; i < n0 * n0; ++i) X[i] = 0.0;
+  for (int col = 0; col < n0; ++col) {
+    if (lower) {
+      for (int i = 0; i < n0; ++i) {
+        cplx acc = (i == col) ? cplx(1.0) : cplx(0.0);
+        for (int l = 0; l < i; ++l) acc -= A[i * n0 + l] * X[l * n0 + col];
+        X[i * n0 + col] = acc;
+      }
+    } else {
+      for (int i = n0 - 1; i >= 0; --i) {
+        cplx acc = (i == col) ? cplx(1.0) : cplx(0.0);
+        for (int l = i + 1; l < n0; ++l) acc -= A[i * n0 + l] * X[l * n0 + col];
+        X[i * n0 + col] = acc / A[i * n0 + i];
+      }
+    }
+  }
+}
+
+int build_factor(const Geometry& g, double wavelength, double eta0, double gamma, int64_t leaf, double eps,
+                 uint64_t seed, HostFactor& hf) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (leaf < 8 || leaf > 256 || eps <= 0 || eps >= 1 || wavelength <= 0) {
+    set_error("hb_factor: need 8 <= leaf <= 256, 0 < eps < 1, wavelength > 0");
+    return HB_EINVAL;
+  }
+  int64_t n = g.n;
+  if (n % leaf) { set_error("hb_factor: N=%lld is not leaf*2^D", (long long)n); return HB_EUNSUPPORTED; }
+  int64_t m = n / leaf;
+  int D = 0;
+  while (((int64_t)1 << D) < m) ++D;
+  if (((int64_t)1 << D) != m || D < 1) {
+    set_error("hb_factor: N=%lld is not leaf*2^D with D>=1", (long long)n);
+    return HB_EUNSUPPORTED;
+  }
+  if (D > 30) { set_error("hb_factor: depth too large"); return HB_EUNSUPPORTED; }
+  Entries K;
+  K.init(g, wavelength, eta0, gamma);
+  hf.n = n; hf.n0 = leaf; hf.m = m; hf.depth = D;
+  hf.scale = K.scale; hf.eps = eps; hf.kappa = K.kappa; hf.eta0 = eta0; hf.gamma = gamma;
+  // dense leaves and their triangle inverses
+  hf.leaf.assign((size_t)m * leaf * leaf, cplx(0.0));
+  hf.linv.assign(hf.leaf.size(), cplx(0.0));
+  hf.uinv.assign(hf.leaf.size(), cplx(0.0));
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t j = 0; j < m; ++j) {
+    cplx* A = &hf.leaf[(size_t)j * leaf * leaf];
+    for (int64_t r = 0; r < leaf; ++r)
+      for (int64_t c = 0; c < leaf; ++c) A[r * leaf + c] = K(j * leaf + r, j * leaf + c);
+    triangle_inverse(A, (int)leaf, true, &hf.linv[(size_t)j * leaf * leaf]);
+    triangle_inverse(A, (int)leaf, false, &hf.uinv[(size_t)j * leaf * leaf]);
+  }
+  // butterflies: F12 and F21 of every internal node (Alg. 1)
+  int64_t nbf = 2 * (m - 1);
+  hf.bf.assign(nbf, Butterfly());
+  for (int v = 0; v < D; ++v) {
+    int64_t nodes = (int64_t)1 << v;
+    int64_t half = n >> (v + 1);
+    for (int64_t p = 0; p < nodes; ++p)
+      for (int kind = 0; kind < 2; ++kind) {
+        Butterfly& B = hf.bf[bf_id(v, p, kind)];
+        B.depth = v; B.node = p; B.kind = kind; B.n = half;
+        int64_t base = p * 2 * half;
+        B.row0 = kind == 0 ? base : base + half;
+        B.col0 = kind == 0 ? base + half : base;
+        B.L = D - v - 1;
+        B.hc = (B.L % 2 == 0) ? B.L / 2 + 1 : (B.L + 1) / 2;
+        B.hr = B.L + 2 - B.hc;
+      }
+  }
+#ifdef _OPENMP
+  int nthr = omp_get_max_threads();
+#else
+  int nthr = 1;
+#endif
+  for (int v = 0; v < D; ++v) {
+    int64_t first = bf_id(v, 0, 0), cnt = (int64_t)2 << v;
+    bool outer = cnt >= 2 * nthr;
+    uint64_t sdv = seed * 0x100000001B3ull;
+#pragma omp parallel for schedule(dynamic, 1) if (outer)
+    for (int64_t i = 0; i < cnt; ++i)
+      build_butterfly(hf.bf[first + i], K, leaf, eps, sdv ^ (uint64_t)(first + i) * 0xC2B2AE35ull, !outer);
+  }
+  hf.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return HB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Packing into the level-packed device image.
+// ---------------------------------------------------------------------------
+namespace {
+struct Packer {
+  PackedHost& ph;
+  explicit Packer(PackedHost& p) : ph(p) {}
+  int64_t push_mat(const cplx* src, int64_t cnt) {
+    if (ph.fpool.size() % 2) ph.fpool.push_back(cplx(0.0));     // 16-byte aligned starts for float2
+    int64_t off = (int64_t)ph.fpool.size();
+    ph.fpool.insert(ph.fpool.end(), src, src + cnt);
+    return off;
+  }
+  DBlk push_block(const IdBlock& b, bool vtype) {
+    DBlk d;
+    d.k = (int16_t)b.k;
+    d.c = (int16_t)b.c;
+    int nr = b.c - b.k;
+    std::vector<cplx> m((size_t)b.k * nr);
+    for (int i = 0; i < b.k; ++i)
+      for (int j = 0; j < nr; ++j) {
+        cplx t = b.t[(size_t)i * nr + j];
+        if (vtype) m[(size_t)j * b.k + i] = t; else m[(size_t)i * nr + j] = t;
+      }
+    d.moff = push_mat(m.data(), (int64_t)m.size());
+    d.ioff = (int32_t)ph.ipool.size();
+    for (int i = 0; i < b.k; ++i) ph.ipool.push_back((int16_t)b.q[i]);
+    for (int j = 0; j < nr; ++j) ph.ipool.push_back((int16_t)b.p[j]);
+    std::vector<int16_t> map(b.c);
+    for (int i = 0; i < b.k; ++i) map[b.q[i]] = (int16_t)i;
+    for (int j = 0; j < nr; ++j) map[b.p[j]] = (int16_t)(-1 - j);
+    ph.ipool.insert(ph.ipool.end(), map.begin(), map.end());
+    ph.nnz_bf += (int64_t)b.k * nr;
+    return d;
+  }
+};
+}  // namespace
+
+void pack_factor(const HostFactor& hf, PackedHost& ph) {
+  Packer pk(ph);
+  const int D = hf.depth;
+  const int64_t m = hf.m, n0 = hf.n0;
+  ph.n = hf.n; ph.n0 = n0; ph.m = m; ph.depth = D;
+  ph.fpool.clear(); ph.ipool.clear(); ph.items.clear();
+  ph.nnz_bf = 0;
+  const int64_t nbf = (int64_t)hf.bf.size();
+  ph.vout.assign((size_t)m * D, DOuter{});
+  ph.uout.assign((size_t)m * D, DOuter{});
+  ph.bf_vout0.assign(nbf, 0); ph.bf_uout0.assign(nbf, 0); ph.bf_mb.assign(nbf, 0);
+  ph.bf_step_base.assign(nbf, 0); ph.bf_L.assign(nbf, 0);
+  ph.bvout.clear(); ph.buout.clear(); ph.bf_steps.clear();
+  int64_t state = 0;
+  int64_t ksum = 0, kcnt = 0;
+  int kmax = 0;
+  std::vector<int64_t> ksum_d(D, 0), kcnt_d(D, 0);
+  std::vector<int> kmax_d(D, 0);
+  // per step item lists for the apply
+  std::vector<std::vector<int32_t>> fsteps(D + 2), asteps(D + 2);
+  for (int64_t id = 0; id < nbf; ++id) {
+    const Butterfly& B = hf.bf[id];
+    const int L = B.L;
+    const int64_t np = (int64_t)1 << L;
+    ph.bf_L[id] = L;
+    // state offsets of every pair vector
+    std::vector<std::vector<int32_t>> zoff(B.hc, std::vector<int32_t>(np)), yoff(B.hr, std::vector<int32_t>(np));
+    for (int l = 0; l < B.hc; ++l)
+      for (int64_t g = 0; g < np; ++g) { zoff[l][g] = (int32_t)state; state += B.col[l][g].k; }
+    for (int l = 0; l < B.hr; ++l)
+      for (int64_t g = 0; g < np; ++g) { yoff[l][g] = (int32_t)state; state += B.row[l][g].k; }
+    // rank statistics
+    for (int l = 0; l < B.hc; ++l)
+      for (auto& b : B.col[l]) { ksum += b.k; kcnt++; kmax = std::max(kmax, b.k); ksum_d[B.depth] += b.k; kcnt_d[B.depth]++; kmax_d[B.depth] = std::max(kmax_d[B.depth], b.k); }
+    for (int l = 0; l < B.hr; ++l)
+      for (auto& b : B.row[l]) { ksum += b.k; kcnt++; kmax = std::max(kmax, b.k); ksum_d[B.depth] += b.k; kcnt_d[B.depth]++; kmax_d[B.depth] = std::max(kmax_d[B.depth], b.k); }
+    // V0 ops (column leaves) and U0 ops (row leaves)
+    ph.bf_mb[id] = (int32_t)np;
+    ph.bf_vout0[id] = (int32_t)ph.bvout.size();
+    for (int64_t b = 0; b < np; ++b) {
+      DOuter o;
+      o.blk = pk.push_block(B.col[0][b], true);        // g = 0*2^L + b
+      o.seg_off = zoff[0][b];
+      o.leaf = (int32_t)(B.col0 / n0 + b);
+      ph.bvout.push_back(o);
+      ph.vout[(size_t)o.leaf * D + B.depth] = o;
+    }
+    ph.bf_uout0[id] = (int32_t)ph.buout.size();
+    for (int64_t a = 0; a < np; ++a) {
+      DOuter o;
+      o.blk = pk.push_block(B.row[0][a], false);       // g = 0*2^L + a
+      o.seg_off = yoff[0][a];
+      o.leaf = (int32_t)(B.row0 / n0 + a);
+      ph.buout.push_back(o);
+      ph.uout[(size_t)o.leaf * D + B.depth] = o;
+    }
+    // inner steps: VIN l = 1..hc-1, MID, UIN l = hr-1..1
+    ph.bf_step_base[id] = (int32_t)ph.bf_steps.size();
+    int step = 0;
+    auto open_step = [&]() { ph.bf_steps.push_back((int32_t)ph.items.size()); step++; };
+    for (int l = 1; l < B.hc; ++l) {
+      open_step();
+      const int64_t nb = (int64_t)1 << (L - l), nbp = (int64_t)1 << (L - l + 1);
+      for (int64_t ap = 0; ap < ((int64_t)1 << (l - 1)); ++ap)
+        for (int64_t b = 0; b < nb; ++b) {
+          DItem it{};
+          it.type = 0;
+          int64_t gi0 = ap * nbp + 2 * b, gi1 = gi0 + 1;
+          int64_t go0 = (2 * ap) * nb + b, go1 = (2 * ap + 1) * nb + b;
+          it.a_off[0] = zoff[l - 1][gi0]; it.a_k[0] = (int16_t)B.col[l - 1][gi0].k;
+          it.a_off[1] = zoff[l - 1][gi1]; it.a_k[1] = (int16_t)B.col[l - 1][gi1].k;
+          it.b_off[0] = zoff[l][go0]; it.b_k[0] = (int16_t)B.col[l][go0].k;
+          it.b_off[1] = zoff[l][go1]; it.b_k[1] = (int16_t)B.col[l][go1].k;
+          it.blk[0] = pk.push_block(B.col[l][go0], true);
+          it.blk[1] = pk.push_block(B.col[l][go1], true);
+          fsteps[step].push_back((int32_t)ph.items.size());
+          asteps[L + 2 - step].push_back((int32_t)ph.items.size());
+          ph.items.push_back(it);
+        }
+    }
+    {
+      open_step();
+      const int64_t nbm = (int64_t)1 << (L - B.hc + 1), nam = (int64_t)1 << (B.hc - 1);
+      for (int64_t g = 0; g < np; ++g) {
+        int64_t a = g / nbm, b = g % nbm;
+        int64_t gr = b * nam + a;
+        DItem it{};
+        it.type = 1;
+        it.a_off[0] = zoff[B.hc - 1][g]; it.a_k[0] = (int16_t)B.col[B.hc - 1][g].k;
+        it.b_off[0] = yoff[B.hr - 1][gr]; it.b_k[0] = (int16_t)B.row[B.hr - 1][gr].k;
+        // S stored [c][r] (output index r fastest)
+        const std::vector<cplx>& S = B.mid[g];
+        int kr = it.b_k[0], kc = it.a_k[0];
+        std::vector<cplx> sm((size_t)kr * kc);
+        for (int r = 0; r < kr; ++r)
+          for (int c = 0; c < kc; ++c) sm[(size_t)c * kr + r] = S[(size_t)r * kc + c];
+        it.blk[0].moff = pk.push_mat(sm.data(), (int64_t)sm.size());
+        it.blk[0].ioff = 0; it.blk[0].k = (int16_t)kr; it.blk[0].c = (int16_t)kc;
+        ph.nnz_bf += (int64_t)kr * kc;
+        fsteps[step].push_back((int32_t)ph.items.size());
+        asteps[L + 2 - step].push_back((int32_t)ph.items.size());
+        ph.items.push_back(it);
+      }
+    }
+    for (int l = B.hr - 1; l >= 1; --l) {
+      open_step();
+      const int64_t na = (int64_t)1 << (L - l), nap = (int64_t)1 << (L - l + 1);
+      for (int64_t bp = 0; bp < ((int64_t)1 << (l - 1)); ++bp)
+        for (int64_t a = 0; a < na; ++a) {
+          DItem it{};
+          it.type = 2;
+          int64_t gi0 = (2 * bp) * na + a, gi1 = (2 * bp + 1) * na + a;      // row stage l inputs
+          int64_t go0 = bp * nap + 2 * a, go1 = go0 + 1;                       // row stage l-1 outputs
+          it.a_off[0] = yoff[l - 1][go0]; it.a_k[0] = (int16_t)B.row[l - 1][go0].k;
+          it.a_off[1] = yoff[l - 1][go1]; it.a_k[1] = (int16_t)B.row[l - 1][go1].k;
+          it.b_off[0] = yoff[l][gi0]; it.b_k[0] = (int16_t)B.row[l][gi0].k;
+          it.b_off[1] = yoff[l][gi1]; it.b_k[1] = (int16_t)B.row[l][gi1].k;
+          it.blk[0] = pk.push_block(B.row[l][gi0], false);
+          it.blk[1] = pk.push_block(B.row[l][gi1], false);
+          fsteps[step].push_back((int32_t)ph.items.size());
+          asteps[L + 2 - step].push_back((int32_t)ph.items.size());
+          ph.items.push_back(it);
+        }
+    }
+    ph.bf_steps.push_back((int32_t)ph.items.size());   // end of the last step
+  }
+  ph.state_len = state;
+  ph.nsteps = D;
+  ph.step_ptr.assign(1, 0); ph.step_idx.clear();
+  ph.astep_ptr.assign(1, 0); ph.astep_idx.clear();
+  for (int s = 1; s <= D; ++s) {
+    ph.step_idx.insert(ph.step_idx.end(), fsteps[s].begin(), fsteps[s].end());
+    ph.step_ptr.push_back((int32_t)ph.step_idx.size());
+    ph.astep_idx.insert(ph.astep_idx.end(), asteps[s].begin(), asteps[s].end());
+    ph.astep_ptr.push_back((int32_t)ph.astep_idx.size());
+  }
+  // sweep programs (recursion of Algs. 3 and 4, and their adjoints)
+  auto emit_bf = [&](std::vector<DPhase>& prog, int64_t id, bool adj) {
+    int L = ph.bf_L[id];
+    int base = ph.bf_step_base[id];
+    prog.push_back(DPhase{PH_ENTER, (int32_t)id, ph.bf_mb[id], adj ? 1 : 0});
+    for (int t = 1; t <= L + 1; ++t) {
+      int s = adj ? (L + 2 - t) : t;
+      int32_t b0 = ph.bf_steps[base + s - 1], b1 = ph.bf_steps[base + s];
+      prog.push_back(DPhase{PH_ITEMS, b0, b1 - b0, adj ? 1 : 0});
+    }
+    prog.push_back(DPhase{PH_EXIT, (int32_t)id, ph.bf_mb[id], adj ? 1 : 0});
+  };
+  ph.prog_lower.clear(); ph.prog_upper.clear(); ph.prog_lower_adj.clear(); ph.prog_upper_adj.clear();
+  // lower: left child, F21, right child
+  std::function<void(int, int64_t, std::vector<DPhase>&, int)> rec = [&](int v, int64_t p, std::vector<DPhase>& prog, int mode) {
+    if (v == D) { prog.push_back(DPhase{PH_LEAF, (int32_t)p, 1, (mode >= 2) ? 1 : 0}); return; }
+    int64_t lo = 2 * p, hi = 2 * p + 1;
+    switch (mode) {
+      case 0:  rec(v + 1, lo, prog, mode); emit_bf(prog, bf_id(v, p, 1), false); rec(v + 1, hi, prog, mode); break;  // L~^{-1}
+      case 1:  rec(v + 1, hi, prog, mode); emit_bf(prog, bf_id(v, p, 0), false); rec(v + 1, lo, prog, mode); break;  // U~^{-1}
+      case 2:  rec(v + 1, hi, prog, mode); emit_bf(prog, bf_id(v, p, 1), true); rec(v + 1, lo, prog, mode); break;   // L~^{-H}
+      default: rec(v + 1, lo, prog, mode); emit_bf(prog, bf_id(v, p, 0), true); rec(v + 1, hi, prog, mode); break;  // U~^{-H}
+    }
+  };
+  rec(0, 0, ph.prog_lower, 0);
+  rec(0, 0, ph.prog_upper, 1);
+  rec(0, 0, ph.prog_lower_adj, 2);
+  rec(0, 0, ph.prog_upper_adj, 3);
+  ph.kmax = kmax;
+  ph.kavg = kcnt ? (double)ksum / (double)kcnt : 0.0;
+  for (int v = 0; v < D && v < 32; ++v) {
+    ph.kmax_depth[v] = kmax_d[v];
+    ph.kavg_depth[v] = kcnt_d[v] ? (double)ksum_d[v] / (double)kcnt_d[v] : 0.0;
+  }
+}
+
+}  // namespace hb
+
+// ---------------------------------------------------------------------------
+// Host interpreter of the packed program (FP64).  It walks exactly the
+// records the device kernels walk (V0 / items / U0 / sweep phases) and is used
+// to verify construction and packing on machines without a GPU.
+// ---------------------------------------------------------------------------
+namespace hb {
+
+namespace {
+struct HostExec {
+  const PackedHost& ph;
+  const HostFactor& hf;
+  std::vector<cplx> st;
+  HostExec(const PackedHost& p, const HostFactor& h) : ph(p), hf(h), st(p.state_len) {}
+
+  // V-type (column ID) element T_ij from layout A; U-type from layout B
+  cplx tv(const DBlk& b, int i, int j) const { return ph.fpool[b.moff + (int64_t)j * b.k + i]; }
+  cplx tu(const DBlk& b, int i, int j) const { return ph.fpool[b.moff + (int64_t)i * (b.c - b.k) + j]; }
+  const int16_t* idx(const DBlk& b) const { return &ph.ipool[b.ioff]; }
+
+  // B = gather + T * rest of cand;  utype_adj: conj(T) from the U layout
+  void vlike(const DBlk& b, const cplx* a0, int ka0, const cplx* a1, cplx* out, bool utype_adj) const {
+    const int16_t* q = idx(b);
+    const int16_t* p = q + b.k;
+    for (int i = 0; i < b.k; ++i) {
+      cplx acc = q[i] < ka0 ? a0[q[i]] : a1[q[i] - ka0];
+      for (int j = 0; j < b.c - b.k; ++j) {
+        cplx t = utype_adj ? std::conj(tu(b, i, j)) : tv(b, i, j);
+        acc += t * (p[j] < ka0 ? a0[p[j]] : a1[p[j] - ka0]);
+      }
+      out[i] = acc;
+    }
+  }
+  // contribution to candidate entry r;  vtype_adj: conj(T) from the V layout
+  cplx row(const DBlk& b, const cplx* y, int r, bool vtype_adj) const {
+    int code = idx(b)[b.c + r];
+    if (code >= 0) return y[code];
+    int j = -1 - code;
+    cplx acc = 0.0;
+    for (int i = 0; i < b.k; ++i) acc += (vtype_adj ? std::conj(tv(b, i, j)) : tu(b, i, j)) * y[i];
+    return acc;
+  }
+  void item(const DItem& it, bool adj) {
+    if (it.type == 1) {
+      int kr = it.b_k[0], kc = it.a_k[0];
+      const cplx* S = &ph.fpool[it.blk[0].moff];
+      if (!adj)
+        for (int r = 0; r < kr; ++r) {
+          cplx acc = 0.0;
+          for (int c = 0; c < kc; ++c) acc += S[(int64_t)c * kr + r] * st[it.a_off[0] + c];
+          st[it.b_off[0] + r] = acc;
+        }
+      else
+        for (int c = 0; c < kc; ++c) {
+          cplx acc = 0.0;
+          for (int r = 0; r < kr; ++r) acc += std::conj(S[(int64_t)c * kr + r]) * st[it.b_off[0] + r];
+          st[it.a_off[0] + c] = acc;
+        }
+      return;
+    }
+    bool to_b = (it.type == 0) != adj;
+    if (to_b) {
+      for (int s = 0; s < 2; ++s)
+        vlike(it.blk[s], &st[it.a_off[0]], it.a_k[0], &st[it.a_off[1]], &st[it.b_off[s]], it.type == 2);
+    } else {
+      int c = it.a_k[0] + it.a_k[1];
+      std::vector<cplx> out(c);
+      for (int r = 0; r < c; ++r)
+        out[r] = row(it.blk[0], &st[it.b_off[0]], r, it.type == 0) + row(it.blk[1], &st[it.b_off[1]], r, it.type == 0);
+      for (int r = 0; r < c; ++r) st[r < it.a_k[0] ? it.a_off[0] + r : it.a_off[1] + r - it.a_k[0]] = out[r];
+    }
+  }
+  // leaf matrices are row-major [r][c] on the host
+  void leaf_mv(const std::vector<cplx>& M, int64_t leaf, const cplx* x, cplx* y, bool adj) const {
+    const int64_t n0 = ph.n0;
+    const cplx* A = &M[leaf * n0 * n0];
+    for (int64_t r = 0; r < n0; ++r) {
+      cplx acc = 0.0;
+      for (int64_t c = 0; c < n0; ++c) acc += (adj ? std::conj(A[c * n0 + r]) : A[r * n0 + c]) * x[c];
+      y[r] = acc;
+    }
+  }
+
+  void apply(bool adj, const cplx* x, cplx* y) {
+    const int D = ph.depth;
+    const int64_t n0 = ph.n0;
+    const std::vector<DOuter>& enter = adj ? ph.uout : ph.vout;
+    const std::vector<DOuter>& exitv = adj ? ph.vout : ph.uout;
+    for (int64_t l = 0; l < ph.m; ++l)
+      for (int v = 0; v < D; ++v) {
+        const DOuter& o = enter[l * D + v];
+        vlike(o.blk, x + l * n0, (int)n0, x + l * n0, &st[o.seg_off], adj);
+      }
+    const std::vector<int32_t>& ptr = adj ? ph.astep_ptr : ph.step_ptr;
+    const std::vector<int32_t>& ix = adj ? ph.astep_idx : ph.step_idx;
+    for (size_t s = 0; s + 1 < ptr.size(); ++s)
+      for (int32_t e = ptr[s]; e < ptr[s + 1]; ++e) item(ph.items[ix[e]], adj);
+    std::vector<cplx> tmp(n0);
+    for (int64_t l = 0; l < ph.m; ++l) {
+      for (int64_t r = 0; r < n0; ++r) {
+        cplx acc = 0.0;
+        for (int v = 0; v < D; ++v) {
+          const DOuter& o = exitv[l * D + v];
+          acc += row(o.blk, &st[o.seg_off], (int)r, adj);
+        }
+        y[l * n0 + r] = acc;
+      }
+      leaf_mv(hf.leaf, l, x + l * n0, tmp.data(), adj);
+      for (int64_t r = 0; r < n0; ++r) y[l * n0 + r] += tmp[r];
+    }
+  }
+
+  void sweep(int which, cplx* vec) {
+    const std::vector<DPhase>& prog = which == 0 ? ph.prog_lower : which == 1 ? ph.prog_upper
+                                    : which == 2 ? ph.prog_lower_adj : ph.prog_upper_adj;
+    const std::vector<cplx>& tinv = (which == 0 || which == 2) ? hf.linv : hf.uinv;
+    const int64_t n0 = ph.n0;
+    std::vector<cplx> tmp(n0);
+    for (const DPhase& P : prog) {
+      if (P.kind == PH_LEAF) {
+        leaf_mv(tinv, P.arg0, vec + (int64_t)P.arg0 * n0, tmp.data(), P.adj != 0);
+        std::copy(tmp.begin(), tmp.end(), vec + (int64_t)P.arg0 * n0);
+      } else if (P.kind == PH_ENTER) {
+        const DOuter* ops = P.adj ? &ph.buout[ph.bf_uout0[P.arg0]] : &ph.bvout[ph.bf_vout0[P.arg0]];
+        for (int o = 0; o < P.count; ++o) {
+          const cplx* xl = vec + (int64_t)ops[o].leaf * n0;
+          vlike(ops[o].blk, xl, (int)n0, xl, &st[ops[o].seg_off], P.adj != 0);
+        }
+      } else if (P.kind == PH_ITEMS) {
+        for (int o = 0; o < P.count; ++o) item(ph.items[P.arg0 + o], P.adj != 0);
+      } else {
+        const DOuter* ops = P.adj ? &ph.bvout[ph.bf_vout0[P.arg0]] : &ph.buout[ph.bf_uout0[P.arg0]];
+        for (int o = 0; o < P.count; ++o) {
+          cplx* bl = vec + (int64_t)ops[o].leaf * n0;
+          for (int64_t r = 0; r < n0; ++r) bl[r] -= row(ops[o].blk, &st[ops[o].seg_off], (int)r, P.adj != 0);
+        }
+      }
+    }
+  }
+};
+}  // namespace
+
+void host_apply(const PackedHost& ph, const HostFactor& hf, bool adj, const cplx* x, cplx* y) {
+  HostExec ex(ph, hf);
+  ex.apply(adj, x, y);
+}
+void host_sweep(const PackedHost& ph, const HostFactor& hf, int which, cplx* vec) {
+  HostExec ex(ph, hf);
+  ex.sweep(which, vec);
+}
+
+}  // namespace hb

@@ -1,0 +1,177 @@
+// Internal data structures of libhb: host-side H-IDBF (Alg. 1) and its
+// level-packed device image.  Not part of the public ABI (include/hb.h).
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "../../include/hb.h"
+
+namespace hb {
+
+using cplx = std::complex<double>;
+
+void set_error(const char* fmt, ...);
+
+// ---------------------------------------------------------------------------
+// Geometry: N pulse segments (Sec. 3.1), geometric order.
+// ---------------------------------------------------------------------------
+struct Geometry {
+  int kind = 0;
+  std::vector<double> params;
+  int64_t n = 0;
+  std::vector<double> cx, cy, w;   // centres and lengths
+};
+
+// ---------------------------------------------------------------------------
+// Host H-IDBF.
+//
+// One interpolative decomposition over a candidate list of c indices keeps
+// k skeletons q[0..k) and expresses the c-k others p[0..c-k) through the
+// k x (c-k) matrix T (row-major, T[i*(c-k)+j]):
+//   column ID (V side):  K(:, p_j) ~ sum_i K(:, q_i) T[i][j]
+//                        => z_i = cand[q_i] + sum_j T[i][j] cand[p_j]
+//   row ID (U side):     K(p_j, :) ~ sum_i T[i][j] K(q_i, :)
+//                        => out[q_i] = y_i, out[p_j] = sum_i T[i][j] y_i
+// ---------------------------------------------------------------------------
+struct IdBlock {
+  int k = 0, c = 0;
+  std::vector<int> q, p;            // positions in the candidate list
+  std::vector<cplx> t;              // k x (c-k), row-major
+  std::vector<int64_t> skel;        // global row/column indices of the skeletons
+};
+
+// Butterfly of one off-diagonal block (IDBF, Appendix), canonical reading:
+//  column stage l (0..hc-1): pair (a at row level l, b at column level L-l),
+//      stored at g = a * 2^(L-l) + b;
+//  row stage l (0..hr-1): pair (a at row level L-l, b at column level l),
+//      stored at g = b * 2^(L-l) + a;
+//  middle: S(g) = K(rskel, cskel) for the column-stage-(hc-1) pairs g.
+struct Butterfly {
+  int depth = 0;          // hierarchical depth v of the parent node
+  int64_t node = 0;       // node index p at depth v
+  int kind = 0;           // 0 = F12 (upper-right), 1 = F21 (lower-left)
+  int64_t row0 = 0, col0 = 0, n = 0;
+  int L = 0, hc = 0, hr = 0;
+  std::vector<std::vector<IdBlock>> col, row;
+  std::vector<std::vector<cplx>> mid;   // k_r x k_c, row-major
+  int rebuilt = 0;
+};
+
+struct HostFactor {
+  int64_t n = 0, n0 = 0, m = 0;
+  int depth = 0;
+  double scale = 1.0, eps = 0.0, kappa = 0.0, eta0 = 0.0, gamma = 0.0;
+  std::vector<Butterfly> bf;            // index = butterfly id (see bf_id)
+  std::vector<cplx> leaf;               // m blocks, n0 x n0 row-major (scaled A)
+  std::vector<cplx> linv, uinv;         // leaf triangle inverses, row-major
+  double build_seconds = 0.0;
+};
+
+// butterfly id of (depth v, node p, kind) : 2*(2^v - 1 + p) + kind
+inline int64_t bf_id(int v, int64_t p, int kind) { return 2 * (((int64_t)1 << v) - 1 + p) + kind; }
+
+int build_geometry(int kind, const double* params, int nparams, int64_t n, Geometry& g);
+int build_factor(const Geometry& g, double wavelength, double eta0, double gamma, int64_t leaf, double eps,
+                 uint64_t seed, HostFactor& hf);
+
+// ---------------------------------------------------------------------------
+// Level-packed device image (built on the host, uploaded as flat arrays).
+// ---------------------------------------------------------------------------
+
+// One ID block on the device.  Matrix layout:
+//   V-type (column ID): M[j*k + i] = T[i][j]   (output index i fastest)
+//   U-type (row ID):    M[i*(c-k) + j] = T[i][j] (output index j fastest)
+// Index pool at ioff: q[k], p[c-k], map[c] (map[r] = i if r = q_i, -1-j if r = p_j).
+struct DBlk {
+  int64_t moff;
+  int32_t ioff;
+  int16_t k, c;
+};
+
+// Inner-stage work item.  "A side": the candidate vector, two segments
+// (a0: a_k[0] entries, a1: a_k[1] entries, concatenated).  "B side": two
+// skeleton vectors, one per ID block blk[s] (b_k[s] = blk[s].k).
+//   type 0 (V stage):  forward A -> B (gather + T), adjoint B -> A
+//   type 2 (U stage):  forward B -> A (scatter + T), adjoint A -> B
+//   type 1 (middle):   forward y(b_off[0]) = S z(a_off[0]); S at blk[0].moff,
+//                      k_r = b_k[0], k_c = a_k[0]; adjoint z = S^H y.
+struct DItem {
+  int32_t type;
+  int32_t a_off[2];
+  int32_t b_off[2];
+  int16_t a_k[2];
+  int16_t b_k[2];
+  DBlk blk[2];
+};
+
+// Outer op of one butterfly on one leaf: V0 (column leaf -> z_0 pair) or
+// U0 (y_0 pair -> row leaf).  seg_off = offset of the pair vector in the
+// state buffer; leaf = global leaf index of the rows/columns.
+struct DOuter {
+  DBlk blk;
+  int32_t seg_off;
+  int32_t leaf;
+};
+
+// A phase of a sweep program: `count` independent ops of one kind.
+// Forward sweeps enter a butterfly through its V0 ops (PH_ENTER reads the
+// solved x of the column leaves) and leave through its U0 ops (PH_EXIT
+// subtracts from b on the row leaves).  Adjoint sweeps enter through U0^H
+// (row leaves) and leave through V0^H (column leaves).
+enum PhaseKind : int32_t {
+  PH_LEAF = 0,       // arg0 = leaf index: x_leaf = Tinv_leaf b_leaf (or Tinv^H)
+  PH_ENTER = 1,      // arg0 = butterfly id
+  PH_ITEMS = 2,      // arg0 = first DItem index, count = #items (one stage of one butterfly)
+  PH_EXIT = 3,       // arg0 = butterfly id
+};
+struct DPhase {
+  int32_t kind;
+  int32_t arg0;
+  int32_t count;
+  int32_t adj;       // 1 = adjoint direction of the ops
+};
+
+struct PackedHost {
+  int64_t n = 0, n0 = 0, m = 0;
+  int depth = 0;
+  int kmax = 0;
+  std::vector<cplx> fpool;          // factor matrices (ID T blocks + middle S), padded to even length
+  std::vector<int16_t> ipool;       // indices
+  int64_t state_len = 0;            // entries of the butterfly state buffer (per RHS)
+  // apply (forward)
+  std::vector<DOuter> vout;         // [m][D]: column leaf j, depth v (index j*D + v)
+  std::vector<DOuter> uout;         // [m][D]: row leaf i, depth v
+  std::vector<DItem> items;         // all inner items, ordered by (butterfly, step, pair)
+  std::vector<int32_t> step_ptr;    // forward apply: items of step s at step_idx[step_ptr[s]..step_ptr[s+1])
+  std::vector<int32_t> step_idx;
+  std::vector<int32_t> astep_ptr;   // adjoint apply step lists
+  std::vector<int32_t> astep_idx;
+  int nsteps = 0;
+  // per-butterfly ops for the sweeps
+  std::vector<DOuter> bvout;        // per butterfly, its m_b V0 ops (contiguous)
+  std::vector<DOuter> buout;        // per butterfly, its m_b U0 ops
+  std::vector<int32_t> bf_vout0, bf_uout0, bf_mb;  // first op index / op count per butterfly
+  // per butterfly b: forward inner step s (1..L+1) owns items
+  // [bf_steps[bf_step_base[b] + s - 1], bf_steps[bf_step_base[b] + s]); the adjoint
+  // runs the same ranges in reverse step order.
+  std::vector<int32_t> bf_step_base, bf_steps, bf_L;
+  // sweep programs
+  std::vector<DPhase> prog_lower, prog_upper, prog_lower_adj, prog_upper_adj;
+  // statistics
+  int64_t nnz_bf = 0;
+  int32_t kmax_depth[32] = {0};
+  double kavg_depth[32] = {0};
+  double kavg = 0;
+};
+
+void pack_factor(const HostFactor& hf, PackedHost& ph);
+
+// FP64 host execution of the packed program (verification without a GPU).
+void host_apply(const PackedHost& ph, const HostFactor& hf, bool adj, const cplx* x, cplx* y);
+void host_sweep(const PackedHost& ph, const HostFactor& hf, int which, cplx* vec);
+
+}  // namespace hb

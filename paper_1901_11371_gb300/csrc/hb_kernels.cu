@@ -1,0 +1,484 @@
+// Hot-path CUDA kernels (sm_103a): H-IDBF apply (Alg. 2) and the L~ / U~
+// triangular sweeps (Algs. 3, 4), forward and adjoint.
+//
+// Every butterfly factor is a set of small ID blocks (Sec. 2 / Appendix).  A
+// warp owns one block op; lanes run over the op's OUTPUT entries and loop over
+// its inputs, so factor loads are coalesced (the packer stores every matrix
+// with the output index fastest) and input entries are warp-wide broadcasts.
+//   vlike  (V stage, column ID):  z_i  = cand[q_i] + sum_j T_ij cand[p_j]
+//   ulike  (U stage, row ID):     out_r = y_{map r}            (r skeleton)
+//                                 out_r = sum_i T_i,j(r) y_i   (r redundant)
+//   middle:                       y = S z
+// Adjoint ops swap the two shapes and conjugate the entries.
+// Vectors and the butterfly state use the layout [entry][R] (RHS fastest);
+// one op handles RC right-hand sides per pass.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hb_device.h"
+
+namespace hb {
+
+template <class T> struct C2;
+template <> struct C2<float> { using t = float2; };
+template <> struct C2<double> { using t = double2; };
+
+template <class T> __device__ __forceinline__ typename C2<T>::t mk(T a, T b) { return {a, b}; }
+
+template <class T, class F>
+__device__ __forceinline__ typename C2<T>::t ldf(const F* p) {
+  F v = __ldg(p);
+  return mk<T>((T)v.x, (T)v.y);
+}
+template <class T, class F>
+__device__ __forceinline__ typename C2<T>::t ldf_conj(const F* p) {
+  F v = __ldg(p);
+  return mk<T>((T)v.x, -(T)v.y);
+}
+// acc += a * b
+template <class C>
+__device__ __forceinline__ void cfma(C& acc, const C& a, const C& b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+template <class C>
+__device__ __forceinline__ void cadd(C& acc, const C& a) {
+  acc.x += a.x;
+  acc.y += a.y;
+}
+
+// ---------------------------------------------------------------------------
+// Block ops (one warp).  R = row stride of the [entry][R] layout, r0 = first
+// RHS of this pass, rc = number of valid RHS in the pass (<= RC).
+// ---------------------------------------------------------------------------
+
+// B side (k outputs) = gather + T * rest of the candidate vector cand =
+// concat(a0[0..ka0), a1[..]).  UTYPE_ADJ: the block is a row ID used in
+// adjoint (entries conj(T_ij) read from the U-type layout M[i*(c-k)+j]);
+// otherwise a column ID (V-type layout M[j*k+i]).
+template <class T, class F, int RC, bool UTYPE_ADJ>
+__device__ __forceinline__ void op_vlike(const F* __restrict__ M, const int16_t* __restrict__ idx, int k, int c,
+                                         const typename C2<T>::t* a0, int ka0, const typename C2<T>::t* a1,
+                                         typename C2<T>::t* out, int64_t R, int64_t r0, int rc, int lane) {
+  using C = typename C2<T>::t;
+  const int nr = c - k;
+  for (int i = lane; i < k; i += 32) {
+    C acc[RC];
+    const int qi = idx[i];
+    const C* src = (qi < ka0) ? a0 + (int64_t)qi * R : a1 + (int64_t)(qi - ka0) * R;
+#pragma unroll
+    for (int rr = 0; rr < RC; ++rr) acc[rr] = (rr < rc) ? src[r0 + rr] : mk<T>(0, 0);
+#pragma unroll 4
+    for (int j = 0; j < nr; ++j) {
+      C mij = UTYPE_ADJ ? ldf_conj<T>(M + (int64_t)i * nr + j) : ldf<T>(M + (int64_t)j * k + i);
+      const int pj = idx[k + j];
+      const C* s = (pj < ka0) ? a0 + (int64_t)pj * R : a1 + (int64_t)(pj - ka0) * R;
+#pragma unroll
+      for (int rr = 0; rr < RC; ++rr)
+        if (rr < rc) cfma(acc[rr], mij, s[r0 + rr]);
+    }
+#pragma unroll
+    for (int rr = 0; rr < RC; ++rr)
+      if (rr < rc) out[(int64_t)i * R + r0 + rr] = acc[rr];
+  }
+}
+
+// Contribution of one block to candidate entry r: VTYPE_ADJ: the block is a
+// column ID used in adjoint (conj(T_ij) from M[j*k+i]); otherwise a row ID
+// (U-type layout M[i*(c-k)+j]).
+template <class T, class F, int RC, bool VTYPE_ADJ>
+__device__ __forceinline__ void row_contrib(typename C2<T>::t (&acc)[RC], const F* __restrict__ M,
+                                            const int16_t* __restrict__ idx, int k, int c,
+                                            const typename C2<T>::t* y, int64_t R, int64_t r0, int rc, int r) {
+  using C = typename C2<T>::t;
+  const int code = idx[c + r];
+  if (code >= 0) {
+    const C* s = y + (int64_t)code * R + r0;
+#pragma unroll
+    for (int rr = 0; rr < RC; ++rr)
+      if (rr < rc) cadd(acc[rr], s[rr]);
+  } else {
+    const int j = -1 - code;
+    const int nr = c - k;
+#pragma unroll 4
+    for (int i = 0; i < k; ++i) {
+      C mij = VTYPE_ADJ ? ldf_conj<T>(M + (int64_t)j * k + i) : ldf<T>(M + (int64_t)i * nr + j);
+      const C* s = y + (int64_t)i * R + r0;
+#pragma unroll
+      for (int rr = 0; rr < RC; ++rr)
+        if (rr < rc) cfma(acc[rr], mij, s[rr]);
+    }
+  }
+}
+
+template <class T, class F, int RC>
+__device__ __forceinline__ void op_middle(const F* __restrict__ S, int kr, int kc, bool adj,
+                                          const typename C2<T>::t* in, typename C2<T>::t* out, int64_t R,
+                                          int64_t r0, int rc, int lane) {
+  using C = typename C2<T>::t;
+  const int nout = adj ? kc : kr, nin = adj ? kr : kc;
+  for (int o = lane; o < nout; o += 32) {
+    C acc[RC];
+#pragma unroll
+    for (int rr = 0; rr < RC; ++rr) acc[rr] = mk<T>(0, 0);
+#pragma unroll 4
+    for (int i = 0; i < nin; ++i) {
+      C s = adj ? ldf_conj<T>(S + (int64_t)o * kr + i) : ldf<T>(S + (int64_t)i * kr + o);
+      const C* v = in + (int64_t)i * R + r0;
+#pragma unroll
+      for (int rr = 0; rr < RC; ++rr)
+        if (rr < rc) cfma(acc[rr], s, v[rr]);
+    }
+#pragma unroll
+    for (int rr = 0; rr < RC; ++rr)
+      if (rr < rc) out[(int64_t)o * R + r0 + rr] = acc[rr];
+  }
+}
+
+// One inner item (two ID blocks or one middle block), one warp.
+template <class T, class F, int RC, bool ADJ>
+__device__ __forceinline__ void op_item(const DItem& it, const F* __restrict__ fp, const int16_t* __restrict__ ip,
+                                        typename C2<T>::t* st, int64_t R, int64_t r0, int rc, int lane) {
+  using C = typename C2<T>::t;
+  if (it.type == 1) {
+    const F* S = fp + it.blk[0].moff;
+    if (!ADJ) op_middle<T, F, RC>(S, it.b_k[0], it.a_k[0], false, st + (int64_t)it.a_off[0] * R, st + (int64_t)it.b_off[0] * R, R, r0, rc, lane);
+    else op_middle<T, F, RC>(S, it.b_k[0], it.a_k[0], true, st + (int64_t)it.b_off[0] * R, st + (int64_t)it.a_off[0] * R, R, r0, rc, lane);
+    return;
+  }
+  const bool to_b = (it.type == 0) != ADJ;   // V forward or U adjoint: A (candidates) -> B (skeletons)
+  if (to_b) {
+    const C* a0 = st + (int64_t)it.a_off[0] * R;
+    const C* a1 = st + (int64_t)it.a_off[1] * R;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const DBlk& b = it.blk[s];
+      if (it.type == 0)
+        op_vlike<T, F, RC, false>(fp + b.moff, ip + b.ioff, b.k, b.c, a0, it.a_k[0], a1, st + (int64_t)it.b_off[s] * R, R, r0, rc, lane);
+      else
+        op_vlike<T, F, RC, true>(fp + b.moff, ip + b.ioff, b.k, b.c, a0, it.a_k[0], a1, st + (int64_t)it.b_off[s] * R, R, r0, rc, lane);
+    }
+  } else {
+    const int c = it.a_k[0] + it.a_k[1];
+    for (int r = lane; r < c; r += 32) {
+      C acc[RC];
+#pragma unroll
+      for (int rr = 0; rr < RC; ++rr) acc[rr] = mk<T>(0, 0);
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const DBlk& b = it.blk[s];
+        if (it.type == 2)
+          row_contrib<T, F, RC, false>(acc, fp + b.moff, ip + b.ioff, b.k, b.c, st + (int64_t)it.b_off[s] * R, R, r0, rc, r);
+        else
+          row_contrib<T, F, RC, true>(acc, fp + b.moff, ip + b.ioff, b.k, b.c, st + (int64_t)it.b_off[s] * R, R, r0, rc, r);
+      }
+      C* dst = (r < it.a_k[0]) ? st + (int64_t)(it.a_off[0] + r) * R : st + (int64_t)(it.a_off[1] + r - it.a_k[0]) * R;
+#pragma unroll
+      for (int rr = 0; rr < RC; ++rr)
+        if (rr < rc) dst[r0 + rr] = acc[rr];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Apply kernels (Alg. 2): entry, D inner steps, exit.
+// ---------------------------------------------------------------------------
+
+// Forward: block = column leaf j; warp w handles depths v = w, w+W, ...:
+// z_0 = V0 x_j.  Adjoint: block = row leaf i; y_0 = U0^H x_i.
+template <class T, class F, int RC, bool ADJ>
+__global__ void __launch_bounds__(256) k_apply_enter(const DOuter* __restrict__ ops, int D, int64_t n0,
+                                                     const F* __restrict__ fp, const int16_t* __restrict__ ip,
+                                                     const typename C2<T>::t* __restrict__ x,
+                                                     typename C2<T>::t* st, int64_t R) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t leaf = blockIdx.x;
+  const typename C2<T>::t* xl = x + leaf * n0 * R;
+  for (int v = warp; v < D; v += nw) {
+    const DOuter o = ops[leaf * D + v];
+    for (int64_t r0 = 0; r0 < R; r0 += RC) {
+      int rc = (int)(R - r0 < (int64_t)RC ? R - r0 : (int64_t)RC);
+      op_vlike<T, F, RC, ADJ>(fp + o.blk.moff, ip + o.blk.ioff, o.blk.k, o.blk.c, xl, (int)n0, xl,
+                              st + (int64_t)o.seg_off * R, R, r0, rc, lane);
+    }
+  }
+}
+
+template <class T, class F, int RC, bool ADJ>
+__global__ void __launch_bounds__(256) k_apply_items(const DItem* __restrict__ items, const int32_t* __restrict__ idx,
+                                                     int count, const F* __restrict__ fp,
+                                                     const int16_t* __restrict__ ip, typename C2<T>::t* st,
+                                                     int64_t R) {
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= count) return;
+  const DItem it = items[idx[w]];
+  for (int64_t r0 = 0; r0 < R; r0 += RC) {
+    int rc = (int)(R - r0 < (int64_t)RC ? R - r0 : (int64_t)RC);
+    op_item<T, F, RC, ADJ>(it, fp, ip, st, R, r0, rc, lane);
+  }
+}
+
+// Forward: block = row leaf i, thread = row r: y_r = sum_v (U0 y_0)_r + (A_leaf x_i)_r,
+// summed in the fixed order v = 0..D-1 then the dense leaf.  Adjoint: block =
+// column leaf j: (A^H x)_j = sum_v (V0^H z_0) + A_leaf^H x_j.
+template <class T, class F, int RC, bool ADJ>
+__global__ void __launch_bounds__(256) k_apply_exit(const DOuter* __restrict__ ops, int D, int64_t n0,
+                                                    const F* __restrict__ fp, const int16_t* __restrict__ ip,
+                                                    const F* __restrict__ leafm,
+                                                    const typename C2<T>::t* __restrict__ x,
+                                                    const typename C2<T>::t* st, typename C2<T>::t* y,
+                                                    int64_t R) {
+  using C = typename C2<T>::t;
+  const int64_t leaf = blockIdx.x;
+  const F* A = leafm + leaf * n0 * n0;
+  const C* xl = x + leaf * n0 * R;
+  for (int r = threadIdx.x; r < n0; r += blockDim.x) {
+    for (int64_t r0 = 0; r0 < R; r0 += RC) {
+      int rc = (int)(R - r0 < (int64_t)RC ? R - r0 : (int64_t)RC);
+      C acc[RC];
+#pragma unroll
+      for (int rr = 0; rr < RC; ++rr) acc[rr] = mk<T>(0, 0);
+      for (int v = 0; v < D; ++v) {
+        const DOuter o = ops[leaf * D + v];
+        row_contrib<T, F, RC, ADJ>(acc, fp + o.blk.moff, ip + o.blk.ioff, o.blk.k, o.blk.c,
+                                   st + (int64_t)o.seg_off * R, R, r0, rc, r);
+      }
+#pragma unroll 4
+      for (int cc = 0; cc < n0; ++cc) {
+        C a = ADJ ? ldf_conj<T>(A + (int64_t)r * n0 + cc) : ldf<T>(A + (int64_t)cc * n0 + r);
+        const C* s = xl + (int64_t)cc * R + r0;
+#pragma unroll
+        for (int rr = 0; rr < RC; ++rr)
+          if (rr < rc) cfma(acc[rr], a, s[rr]);
+      }
+      C* dst = y + (leaf * n0 + r) * R + r0;
+#pragma unroll
+      for (int rr = 0; rr < RC; ++rr)
+        if (rr < rc) dst[rr] = acc[rr];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Sweep kernel (Algs. 3, 4 and adjoints): one CTA walks the whole recursion
+// as a program of phases; ops inside a phase are independent and spread over
+// the CTA's warps; __syncthreads separates dependent phases.  CTA g handles
+// RHS columns [g*RC, g*RC + RC).
+// ---------------------------------------------------------------------------
+template <class T, class F, int RC>
+__global__ void __launch_bounds__(512) k_sweep(const DPhase* __restrict__ prog, int nphase, int64_t n0,
+                                               const DOuter* __restrict__ bvout, const DOuter* __restrict__ buout,
+                                               const int32_t* __restrict__ bf_vout0,
+                                               const int32_t* __restrict__ bf_uout0,
+                                               const DItem* __restrict__ items, const F* __restrict__ fp,
+                                               const int16_t* __restrict__ ip, const F* __restrict__ tinv,
+                                               typename C2<T>::t* vec, typename C2<T>::t* st, int64_t R) {
+  using C = typename C2<T>::t;
+  extern __shared__ unsigned char smem_raw[];
+  C* sb = reinterpret_cast<C*>(smem_raw);   // n0 * RC staging for leaf solves
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t r0 = (int64_t)blockIdx.x * RC;
+  if (r0 >= R) return;
+  const int rc = (int)(R - r0 < (int64_t)RC ? R - r0 : (int64_t)RC);
+  for (int ph = 0; ph < nphase; ++ph) {
+    const DPhase P = prog[ph];
+    if (P.kind == PH_LEAF) {
+      const int64_t leaf = P.arg0;
+      C* v = vec + leaf * n0 * R;
+      for (int e = threadIdx.x; e < n0 * RC; e += blockDim.x) {
+        int rr = e % RC, cc = e / RC;
+        sb[e] = (rr < rc) ? v[(int64_t)cc * R + r0 + rr] : mk<T>(0, 0);
+      }
+      __syncthreads();
+      const F* Ti = tinv + leaf * n0 * n0;
+      for (int r = threadIdx.x; r < n0; r += blockDim.x) {
+        C acc[RC];
+#pragma unroll
+        for (int rr = 0; rr < RC; ++rr) acc[rr] = mk<T>(0, 0);
+#pragma unroll 4
+        for (int cc = 0; cc < n0; ++cc) {
+          C a = P.adj ? ldf_conj<T>(Ti + (int64_t)r * n0 + cc) : ldf<T>(Ti + (int64_t)cc * n0 + r);
+#pragma unroll
+          for (int rr = 0; rr < RC; ++rr) cfma(acc[rr], a, sb[cc * RC + rr]);
+        }
+#pragma unroll
+        for (int rr = 0; rr < RC; ++rr)
+          if (rr < rc) v[(int64_t)r * R + r0 + rr] = acc[rr];
+      }
+    } else if (P.kind == PH_ENTER) {
+      // forward: z_0 = V0 x(column leaf); adjoint: y_0 = U0^H x(row leaf)
+      const DOuter* ops = P.adj ? buout + bf_uout0[P.arg0] : bvout + bf_vout0[P.arg0];
+      for (int o = warp; o < P.count; o += nw) {
+        const DOuter op = ops[o];
+        const C* xl = vec + (int64_t)op.leaf * n0 * R;
+        if (P.adj)
+          op_vlike<T, F, RC, true>(fp + op.blk.moff, ip + op.blk.ioff, op.blk.k, op.blk.c, xl, (int)n0, xl,
+                                   st + (int64_t)op.seg_off * R, R, r0, rc, lane);
+        else
+          op_vlike<T, F, RC, false>(fp + op.blk.moff, ip + op.blk.ioff, op.blk.k, op.blk.c, xl, (int)n0, xl,
+                                    st + (int64_t)op.seg_off * R, R, r0, rc, lane);
+      }
+    } else if (P.kind == PH_ITEMS) {
+      for (int o = warp; o < P.count; o += nw) {
+        const DItem it = items[P.arg0 + o];
+        if (P.adj) op_item<T, F, RC, true>(it, fp, ip, st, R, r0, rc, lane);
+        else op_item<T, F, RC, false>(it, fp, ip, st, R, r0, rc, lane);
+      }
+    } else {   // PH_EXIT: b(leaf) -= U0 y_0 (forward) or V0^H z_0 (adjoint)
+      const DOuter* ops = P.adj ? bvout + bf_vout0[P.arg0] : buout + bf_uout0[P.arg0];
+      for (int o = warp; o < P.count; o += nw) {
+        const DOuter op = ops[o];
+        C* bl = vec + (int64_t)op.leaf * n0 * R;
+        for (int r = lane; r < n0; r += 32) {
+          C acc[RC];
+#pragma unroll
+          for (int rr = 0; rr < RC; ++rr) acc[rr] = mk<T>(0, 0);
+          if (P.adj)
+            row_contrib<T, F, RC, true>(acc, fp + op.blk.moff, ip + op.blk.ioff, op.blk.k, op.blk.c,
+                                        st + (int64_t)op.seg_off * R, R, r0, rc, r);
+          else
+            row_contrib<T, F, RC, false>(acc, fp + op.blk.moff, ip + op.blk.ioff, op.blk.k, op.blk.c,
+                                         st + (int64_t)op.seg_off * R, R, r0, rc, r);
+          C* d = bl + (int64_t)r * R + r0;
+#pragma unroll
+          for (int rr = 0; rr < RC; ++rr)
+            if (rr < rc) { d[rr].x -= acc[rr].x; d[rr].y -= acc[rr].y; }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Layout conversion kernels
+// ---------------------------------------------------------------------------
+template <class S, class D>
+__global__ void k_gather_cols(const S* __restrict__ src, int64_t ld, int64_t n, int64_t R, D* __restrict__ dst,
+                              double scale) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t total = n * R;
+  for (; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t row = e / R, r = e % R;
+    S v = src[r * ld + row];
+    dst[e].x = (decltype(dst[e].x))(scale * (double)v.x);
+    dst[e].y = (decltype(dst[e].y))(scale * (double)v.y);
+  }
+}
+template <class S, class D>
+__global__ void k_scatter_cols(const S* __restrict__ src, int64_t n, int64_t R, D* __restrict__ dst, int64_t ld,
+                               double scale) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t total = n * R;
+  for (; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t row = e / R, r = e % R;
+    S v = src[e];
+    dst[r * ld + row].x = (decltype(dst[0].x))(scale * (double)v.x);
+    dst[r * ld + row].y = (decltype(dst[0].y))(scale * (double)v.y);
+  }
+}
+
+static inline int grid_for(int64_t total, int threads) {
+  int64_t g = (total + threads - 1) / threads;
+  if (g > 152 * 32) g = 152 * 32;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+int launch_gather_cols(const void* src, int src_t, int64_t ld, int64_t n, int64_t R, void* dst, int dst_t,
+                       double scale, cudaStream_t st) {
+  int g = grid_for(n * R, 256);
+  if (src_t == 0 && dst_t == 0) k_gather_cols<<<g, 256, 0, st>>>((const double2*)src, ld, n, R, (double2*)dst, scale);
+  else if (src_t == 0 && dst_t == 1) k_gather_cols<<<g, 256, 0, st>>>((const double2*)src, ld, n, R, (float2*)dst, scale);
+  else if (src_t == 1 && dst_t == 0) k_gather_cols<<<g, 256, 0, st>>>((const float2*)src, ld, n, R, (double2*)dst, scale);
+  else k_gather_cols<<<g, 256, 0, st>>>((const float2*)src, ld, n, R, (float2*)dst, scale);
+  return cudaGetLastError() == cudaSuccess ? HB_OK : HB_ECUDA;
+}
+int launch_scatter_cols(const void* src, int src_t, int64_t n, int64_t R, void* dst, int dst_t, int64_t ld,
+                        double scale, cudaStream_t st) {
+  int g = grid_for(n * R, 256);
+  if (src_t == 0 && dst_t == 0) k_scatter_cols<<<g, 256, 0, st>>>((const double2*)src, n, R, (double2*)dst, ld, scale);
+  else if (src_t == 0 && dst_t == 1) k_scatter_cols<<<g, 256, 0, st>>>((const double2*)src, n, R, (float2*)dst, ld, scale);
+  else if (src_t == 1 && dst_t == 0) k_scatter_cols<<<g, 256, 0, st>>>((const float2*)src, n, R, (double2*)dst, ld, scale);
+  else k_scatter_cols<<<g, 256, 0, st>>>((const float2*)src, n, R, (float2*)dst, ld, scale);
+  return cudaGetLastError() == cudaSuccess ? HB_OK : HB_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <class T, class F, int RC>
+static int apply_impl(const DevFactor& df, bool adj, const void* xv, void* yv, int64_t R, void* stv,
+                      cudaStream_t s) {
+  using C = typename C2<T>::t;
+  const F* fp = (const F*)df.fpool;
+  const C* x = (const C*)xv;
+  C* y = (C*)yv;
+  C* st = (C*)stv;
+  int wpb = df.D < 8 ? df.D : 8;
+  if (!adj) k_apply_enter<T, F, RC, false><<<(unsigned)df.m, 32 * wpb, 0, s>>>(df.vout, df.D, df.n0, fp, df.ipool, x, st, R);
+  else k_apply_enter<T, F, RC, true><<<(unsigned)df.m, 32 * wpb, 0, s>>>(df.uout, df.D, df.n0, fp, df.ipool, x, st, R);
+  const std::vector<int32_t>& ptr = adj ? df.astep_ptr : df.step_ptr;
+  const int32_t* idx = adj ? df.astep_idx : df.step_idx;
+  for (int stp = 0; stp + 1 < (int)ptr.size(); ++stp) {
+    int cnt = ptr[stp + 1] - ptr[stp];
+    if (cnt <= 0) continue;
+    int blocks = (cnt + 7) / 8;
+    if (!adj) k_apply_items<T, F, RC, false><<<blocks, 256, 0, s>>>(df.items, idx + ptr[stp], cnt, fp, df.ipool, st, R);
+    else k_apply_items<T, F, RC, true><<<blocks, 256, 0, s>>>(df.items, idx + ptr[stp], cnt, fp, df.ipool, st, R);
+  }
+  int thr = (int)((df.n0 + 31) / 32 * 32);
+  if (thr > 256) thr = 256;
+  if (!adj) k_apply_exit<T, F, RC, false><<<(unsigned)df.m, thr, 0, s>>>(df.uout, df.D, df.n0, fp, df.ipool, (const F*)df.leaf, x, st, y, R);
+  else k_apply_exit<T, F, RC, true><<<(unsigned)df.m, thr, 0, s>>>(df.vout, df.D, df.n0, fp, df.ipool, (const F*)df.leaf, x, st, y, R);
+  return cudaGetLastError() == cudaSuccess ? HB_OK : HB_ECUDA;
+}
+
+template <class T, class F, int RC>
+static int sweep_impl(const DevFactor& df, int which, void* vecv, int64_t R, void* stv, cudaStream_t s) {
+  using C = typename C2<T>::t;
+  const F* tinv = (const F*)((which == 0 || which == 2) ? df.linv : df.uinv);
+  int grid = (int)((R + RC - 1) / RC);
+  size_t smem = (size_t)df.n0 * RC * sizeof(C);
+  int threads = 256;
+  k_sweep<T, F, RC><<<grid, threads, smem, s>>>(df.prog[which], df.nprog[which], df.n0, df.bvout, df.buout,
+                                                df.bf_vout0, df.bf_uout0, df.items, (const F*)df.fpool, df.ipool,
+                                                tinv, (C*)vecv, (C*)stv, R);
+  return cudaGetLastError() == cudaSuccess ? HB_OK : HB_ECUDA;
+}
+
+template <class T, class F>
+static int apply_dispatch(const DevFactor& df, bool adj, const void* x, void* y, int64_t R, void* st,
+                          cudaStream_t s) {
+  if (R == 1) return apply_impl<T, F, 1>(df, adj, x, y, R, st, s);
+  if (R <= 4) return apply_impl<T, F, 4>(df, adj, x, y, R, st, s);
+  return apply_impl<T, F, 8>(df, adj, x, y, R, st, s);
+}
+
+int launch_apply(const DevFactor& df, Prec p, bool adjoint, const void* x, void* y, int64_t R, void* state,
+                 cudaStream_t st) {
+  if (p == PREC_F64) return apply_dispatch<double, double2>(df, adjoint, x, y, R, state, st);
+  if (p == PREC_F32) return apply_dispatch<float, float2>(df, adjoint, x, y, R, state, st);
+  return apply_dispatch<double, float2>(df, adjoint, x, y, R, state, st);
+}
+
+int launch_sweep(const DevFactor& df, Prec p, int which, void* vec, int64_t R, void* state, cudaStream_t st) {
+  if (which < 0 || which > 3) return HB_EINVAL;
+  int rpc = df.sweep_rhs_per_cta;
+  if (rpc <= 0) rpc = 1;
+  if (p == PREC_F64) {
+    if (rpc >= 4 && R >= 4) return sweep_impl<double, double2, 4>(df, which, vec, R, state, st);
+    return sweep_impl<double, double2, 1>(df, which, vec, R, state, st);
+  }
+  if (p == PREC_F32) {
+    if (rpc >= 8 && R >= 8) return sweep_impl<float, float2, 8>(df, which, vec, R, state, st);
+    if (rpc >= 4 && R >= 4) return sweep_impl<float, float2, 4>(df, which, vec, R, state, st);
+    return sweep_impl<float, float2, 1>(df, which, vec, R, state, st);
+  }
+  return sweep_impl<double, float2, 1>(df, which, vec, R, state, st);
+}
+
+}  // namespace hb

@@ -1,0 +1,584 @@
+// Krylov solvers of libhb (Eqs. (Axb2), (Axb3); solver settings of Sec. 4)
+// and the excitation / far-field kernels.
+//
+//  HB_C128:  GMRES(restart) on  L~^{-1} A U~^{-1} y = L~^{-1} b,  x = U~^{-1} y,
+//            all FP64; the true residual ||b - A x|| is checked at every restart.
+//  HB_C64:   FP64 iterative refinement; each refinement step is one cycle of
+//            FP64 flexible GMRES right-preconditioned by U~^{-1} L~^{-1} with
+//            the preconditioner and the operator applied in complex FP32; the
+//            residual b - A x between steps is computed in FP64 arithmetic on
+//            the stored factors.
+// Right-hand sides are solved together in lockstep (one Krylov space per
+// column); reductions run in a fixed order, so results are bitwise repeatable.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "hb_api_internal.h"
+
+namespace hb {
+
+using zc = std::complex<double>;
+
+// ---------------------------------------------------------------------------
+// BLAS-1 style kernels on [row][R] blocks (double2)
+// ---------------------------------------------------------------------------
+static constexpr int kRedBlocks = 304;   // 2 x 152 SMs
+static constexpr int kRedThreads = 256;
+
+// partial[v][blk][r] = sum over this block's rows of conj(V_v[row][r]) * w[row][r]
+__global__ void k_dots_partial(const double2* __restrict__ V, int64_t vstride, int nvec,
+                               const double2* __restrict__ w, int64_t n, int64_t R, double2* __restrict__ partial) {
+  __shared__ double2 red[kRedThreads];
+  const int v = blockIdx.y;
+  const double2* Vv = V + (int64_t)v * vstride;
+  const int64_t rows_per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t row0 = (int64_t)blockIdx.x * rows_per, row1 = min(n, row0 + rows_per);
+  const int G = (R >= kRedThreads) ? 1 : kRedThreads / (int)R;   // row groups
+  for (int64_t rbase = 0; rbase < R; rbase += kRedThreads) {
+    const int t = threadIdx.x;
+    int64_t r = (R >= kRedThreads) ? rbase + t : t % R;
+    int g = (R >= kRedThreads) ? 0 : t / (int)R;
+    double2 acc = {0.0, 0.0};
+    if (g < G && r < R) {
+      for (int64_t row = row0 + g; row < row1; row += G) {
+        double2 a = Vv[row * R + r], b = w[row * R + r];
+        acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
+        acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
+      }
+    }
+    red[t] = acc;
+    __syncthreads();
+    if (R >= kRedThreads) {
+      if (r < R) partial[((int64_t)v * gridDim.x + blockIdx.x) * R + r] = red[t];
+    } else if (t < R) {
+      double2 s = {0.0, 0.0};
+      for (int gg = 0; gg < G; ++gg) { s.x += red[gg * R + t].x; s.y += red[gg * R + t].y; }
+      partial[((int64_t)v * gridDim.x + blockIdx.x) * R + t] = s;
+    }
+    __syncthreads();
+    if (R < kRedThreads) break;
+  }
+}
+
+// out[v][r] = sum_blk partial[v][blk][r] (fixed order)
+__global__ void k_dots_final(const double2* __restrict__ partial, int nblk, int nvec, int64_t R, double2* out) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)nvec * R) return;
+  int v = (int)(e / R);
+  int64_t r = e % R;
+  double2 s = {0.0, 0.0};
+  for (int b = 0; b < nblk; ++b) {
+    double2 p = partial[((int64_t)v * nblk + b) * R + r];
+    s.x += p.x;
+    s.y += p.y;
+  }
+  out[e] = s;
+}
+
+// w[row][r] -= sum_v V_v[row][r] h[v][r]
+__global__ void k_sub_combo(const double2* __restrict__ V, int64_t vstride, int nvec, const double2* __restrict__ h,
+                            double2* __restrict__ w, int64_t n, int64_t R, double sign) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e < n * R; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = e % R;
+    double2 acc = w[e];
+    for (int v = 0; v < nvec; ++v) {
+      double2 a = V[(int64_t)v * vstride + e], c = h[(int64_t)v * R + r];
+      acc.x -= sign * (a.x * c.x - a.y * c.y);
+      acc.y -= sign * (a.x * c.y + a.y * c.x);
+    }
+    w[e] = acc;
+  }
+}
+
+// dst[row][r] = src[row][r] * s[r]  (s real)
+__global__ void k_scale_cols(const double2* __restrict__ src, const double* __restrict__ s, double2* dst, int64_t n,
+                             int64_t R) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e < n * R; e += (int64_t)gridDim.x * blockDim.x) {
+    double f = s[e % R];
+    dst[e] = {src[e].x * f, src[e].y * f};
+  }
+}
+
+// y[e] += x[e] (optionally x converted from float2)
+template <class S>
+__global__ void k_axpy1(const S* __restrict__ x, double2* __restrict__ y, int64_t total) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    y[e].x += (double)x[e].x;
+    y[e].y += (double)x[e].y;
+  }
+}
+
+// y[row][r] += sum_v Z_v[row][r] c[v][r]  (Z double2 or float2)
+template <class S>
+__global__ void k_add_combo(const S* __restrict__ Z, int64_t zstride, int nvec, const double2* __restrict__ c,
+                            double2* __restrict__ y, int64_t n, int64_t R) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e < n * R; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = e % R;
+    double2 acc = y[e];
+    for (int v = 0; v < nvec; ++v) {
+      S a = Z[(int64_t)v * zstride + e];
+      double2 cc = c[(int64_t)v * R + r];
+      acc.x += (double)a.x * cc.x - (double)a.y * cc.y;
+      acc.y += (double)a.x * cc.y + (double)a.y * cc.x;
+    }
+    y[e] = acc;
+  }
+}
+
+__global__ void k_sub_into(const double2* __restrict__ a, const double2* __restrict__ b, double2* out, int64_t total) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e < total; e += (int64_t)gridDim.x * blockDim.x) out[e] = {a[e].x - b[e].x, a[e].y - b[e].y};
+}
+
+__global__ void k_to_f32(const double2* __restrict__ a, float2* __restrict__ b, int64_t total) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e < total; e += (int64_t)gridDim.x * blockDim.x) b[e] = {(float)a[e].x, (float)a[e].y};
+}
+__global__ void k_to_f64(const float2* __restrict__ a, double2* __restrict__ b, int64_t total) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e < total; e += (int64_t)gridDim.x * blockDim.x) b[e] = {(double)a[e].x, (double)a[e].y};
+}
+
+__global__ void k_nonfinite(const double2* __restrict__ a, int64_t ld, int64_t n, int64_t R, int* flag) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e < n * R; e += (int64_t)gridDim.x * blockDim.x) {
+    double2 v = a[(e / n) * ld + e % n];
+    if (!isfinite(v.x) || !isfinite(v.y)) atomicExch(flag, 1);
+  }
+}
+
+// r(col-major) = b(col-major) - y([row][R])
+__global__ void k_residual_cols(const double2* __restrict__ b, int64_t ld, const double2* __restrict__ y, int64_t n,
+                                int64_t R, double2* __restrict__ r) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e < n * R; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t row = e / R, c = e % R;
+    double2 bb = b[c * ld + row], yy = y[e];
+    r[c * ld + row] = {bb.x - yy.x, bb.y - yy.y};
+  }
+}
+
+static inline int gsz(int64_t total) {
+  int64_t g = (total + 255) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
+}
+
+int launch_residual_cols(const void* b, int64_t ld, const void* y, int64_t n, int64_t R, void* r, cudaStream_t st) {
+  k_residual_cols<<<gsz(n * R), 256, 0, st>>>((const double2*)b, ld, (const double2*)y, n, R, (double2*)r);
+  return cudaGetLastError() == cudaSuccess ? HB_OK : HB_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Excitation and far field
+// ---------------------------------------------------------------------------
+__global__ void k_plane_wave(const double* __restrict__ cx, const double* __restrict__ cy, int64_t n,
+                             const double* __restrict__ cphi, const double* __restrict__ sphi, int64_t R,
+                             double kappa, double2* __restrict__ b, int64_t ld) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e < n * R; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = e / n, i = e % n;
+    double ph = -kappa * (cx[i] * cphi[r] + cy[i] * sphi[r]);
+    double s, c;
+    sincos(ph, &s, &c);
+    b[r * ld + i] = {c, s};
+  }
+}
+
+// out[r][q] = C * sum_n w_n x_n exp(+i k (x_n cos phi_q + y_n sin phi_q)); one block per (q, r),
+// fixed-order block reduction.
+__global__ void k_far_field(const double* __restrict__ cx, const double* __restrict__ cy,
+                            const double* __restrict__ w, int64_t n, const double2* __restrict__ x, int64_t ld,
+                            const double* __restrict__ cphi, const double* __restrict__ sphi, int64_t nobs,
+                            double kappa, double2 C, double2* __restrict__ out, int mono_sign) {
+  __shared__ double2 red[256];
+  const int64_t q = blockIdx.x, r = blockIdx.y;
+  const double2* xr = x + r * ld;
+  const int64_t qq = mono_sign ? r : q;
+  double2 acc = {0.0, 0.0};
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    double ph = kappa * (cx[i] * cphi[qq] + cy[i] * sphi[qq]);
+    if (mono_sign) ph = -ph;   // backscatter: steering vector equals b_n
+    double s, c;
+    sincos(ph, &s, &c);
+    double2 v = xr[i];
+    acc.x += w[i] * (v.x * c - v.y * s);
+    acc.y += w[i] * (v.x * s + v.y * c);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) {
+      red[threadIdx.x].x += red[threadIdx.x + off].x;
+      red[threadIdx.x].y += red[threadIdx.x + off].y;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double2 s = red[0];
+    out[r * (mono_sign ? 1 : nobs) + (mono_sign ? 0 : q)] = {C.x * s.x - C.y * s.y, C.x * s.y + C.y * s.x};
+  }
+}
+
+// ---------------------------------------------------------------------------
+// GMRES machinery
+// ---------------------------------------------------------------------------
+struct Dev {
+  hb_factor_t f;
+  cudaStream_t st;
+  int64_t n, R;
+  double2* red_partial;
+  double2* red_out;
+  double* scal;
+};
+
+// h[v][r] = <V_v, w>_r for v < nvec (host copy returned in hh[v*R + r])
+static int dots(Dev& d, const double2* V, int64_t vstride, int nvec, const double2* w, std::vector<zc>& hh) {
+  dim3 grid(kRedBlocks, nvec);
+  k_dots_partial<<<grid, kRedThreads, 0, d.st>>>(V, vstride, nvec, w, d.n, d.R, d.red_partial); count_launch(d.f, 1);
+  int64_t tot = (int64_t)nvec * d.R;
+  k_dots_final<<<(unsigned)((tot + 255) / 256), 256, 0, d.st>>>(d.red_partial, kRedBlocks, nvec, d.R, d.red_out); count_launch(d.f, 1);
+  hh.resize(tot);
+  if (cudaMemcpyAsync(hh.data(), d.red_out, tot * sizeof(double2), cudaMemcpyDeviceToHost, d.st) != cudaSuccess)
+    return HB_ECUDA;
+  if (cudaStreamSynchronize(d.st) != cudaSuccess) return HB_ECUDA;
+  return HB_OK;
+}
+
+// CGS2: orthogonalise w against V_0..V_{nvec-1}; returns h (nvec x R) and ||w|| (R).
+static int cgs2(Dev& d, const double2* V, int64_t vstride, int nvec, double2* w, std::vector<zc>& h,
+                std::vector<double>& nrm) {
+  std::vector<zc> h1, h2;
+  int rc;
+  h.assign((size_t)nvec * d.R, zc(0.0));
+  for (int pass = 0; pass < 2; ++pass) {
+    if ((rc = dots(d, V, vstride, nvec, w, pass ? h2 : h1))) return rc;
+    std::vector<zc>& hp = pass ? h2 : h1;
+    for (size_t i = 0; i < h.size(); ++i) h[i] += hp[i];
+    if (cudaMemcpyAsync(d.red_out, hp.data(), hp.size() * sizeof(double2), cudaMemcpyHostToDevice, d.st) != cudaSuccess)
+      return HB_ECUDA;
+    k_sub_combo<<<gsz(d.n * d.R), 256, 0, d.st>>>(V, vstride, nvec, d.red_out, w, d.n, d.R, 1.0); count_launch(d.f, 1);
+  }
+  std::vector<zc> nn;
+  if ((rc = dots(d, w, 0, 1, w, nn))) return rc;
+  nrm.resize(d.R);
+  for (int64_t r = 0; r < d.R; ++r) nrm[r] = std::sqrt(std::max(nn[r].real(), 0.0));
+  return HB_OK;
+}
+
+static int norms(Dev& d, const double2* w, std::vector<double>& nrm) {
+  std::vector<zc> nn;
+  int rc = dots(d, w, 0, 1, w, nn);
+  if (rc) return rc;
+  nrm.resize(d.R);
+  for (int64_t r = 0; r < d.R; ++r) nrm[r] = std::sqrt(std::max(nn[r].real(), 0.0));
+  return HB_OK;
+}
+
+// dst = src / nrm (per column; zero-norm columns copied unchanged)
+static void normalise(Dev& d, const double2* src, const std::vector<double>& nrm, double2* dst) {
+  std::vector<double> inv(d.R);
+  for (int64_t r = 0; r < d.R; ++r) inv[r] = nrm[r] > 0 ? 1.0 / nrm[r] : 1.0;
+  cudaMemcpyAsync(d.scal, inv.data(), d.R * sizeof(double), cudaMemcpyHostToDevice, d.st);
+  k_scale_cols<<<gsz(d.n * d.R), 256, 0, d.st>>>(src, d.scal, dst, d.n, d.R); count_launch(d.f, 1);
+}
+
+// Per-RHS Givens state of one restart cycle.
+struct Givens {
+  int m;
+  std::vector<zc> H, cs, sn, g;    // H column-major (m+1) x m
+  void reset(int mm, double beta) {
+    m = mm;
+    H.assign((size_t)(m + 1) * m, zc(0.0));
+    cs.assign(m, zc(0.0));
+    sn.assign(m, zc(0.0));
+    g.assign(m + 1, zc(0.0));
+    g[0] = beta;
+  }
+  // insert column j (entries h[0..j], hnext) and return |g_{j+1}|
+  double push(int j, const zc* h, double hnext) {
+    for (int i = 0; i <= j; ++i) H[(size_t)j * (m + 1) + i] = h[i];
+    H[(size_t)j * (m + 1) + j + 1] = hnext;
+    zc* col = &H[(size_t)j * (m + 1)];
+    for (int i = 0; i < j; ++i) {   // G_i = [[c*, s*], [-s, c]]
+      zc t = std::conj(cs[i]) * col[i] + std::conj(sn[i]) * col[i + 1];
+      col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+      col[i] = t;
+    }
+    zc a = col[j], b = col[j + 1];
+    double den = std::sqrt(std::norm(a) + std::norm(b));
+    cs[j] = den > 0 ? a / den : zc(1.0);
+    sn[j] = den > 0 ? b / den : zc(0.0);
+    col[j] = std::conj(cs[j]) * a + std::conj(sn[j]) * b;
+    col[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = std::conj(cs[j]) * g[j];
+    return std::abs(g[j + 1]);
+  }
+  void solve(int k, zc* coef) const {
+    for (int i = k - 1; i >= 0; --i) {
+      zc acc = g[i];
+      for (int l = i + 1; l < k; ++l) acc -= H[(size_t)l * (m + 1) + i] * coef[l];
+      coef[i] = acc / H[(size_t)i * (m + 1) + i];
+    }
+  }
+};
+
+}  // namespace hb
+
+using namespace hb;
+
+extern "C" int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int64_t nrhs, int64_t ld, int restart,
+                        double rtol, int maxit, hb_gmres_info* info, void* stream) {
+  int rc = check_vec_args(f, b_phys, x, nrhs, ld, "hb_gmres");
+  if (rc) return rc;
+  if (op != HB_OP_N && op != HB_OP_H) { set_error("hb_gmres: bad op"); return HB_EINVAL; }
+  if (restart < 1 || restart > 512 || !(rtol > 0) || maxit < 1) { set_error("hb_gmres: bad restart/rtol/maxit"); return HB_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  auto t0 = std::chrono::steady_clock::now();
+  if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("hb_gmres: stream error"); return HB_ECUDA; }
+  const DevFactor& df = f->df;
+  const int64_t n = df.n, R = nrhs;
+  const bool adj = op == HB_OP_H;
+  const bool mixed = df.form != HB_C128;
+  const int m = restart;
+  const size_t vbytes = (size_t)n * R * sizeof(double2);
+  Workspace& ws = f->ws;
+  double2* bh = (double2*)ws.get(WS_VEC2, vbytes);            // scaled b (internal layout)
+  double2* xv = (double2*)ws.get(WS_VEC3, vbytes);            // x (split form: y) iterate
+  double2* V = (double2*)ws.get(WS_BASIS, vbytes * (m + 1));  // Krylov basis
+  double2* red = (double2*)ws.get(WS_RED, (size_t)kRedBlocks * (m + 2) * R * sizeof(double2) + (size_t)(m + 2) * R * sizeof(double2) + R * sizeof(double));
+  void* zb = mixed ? ws.get(WS_ZBASIS, (size_t)n * R * sizeof(float2) * (m + 1)) : nullptr;   // FGMRES Z (float2) + f32 scratch
+  int* flag = (int*)ws.get(WS_SMALL, 256);
+  if (!bh || !xv || !V || !red || !flag || (mixed && !zb)) { set_error("hb_gmres: workspace allocation failed"); return HB_ENOMEM; }
+  double2* tmp = (double2*)ws.get(WS_VEC0, vbytes);
+  double2* tmp2 = (double2*)ws.get(WS_VEC1, vbytes);
+  if (!tmp || !tmp2) { set_error("hb_gmres: workspace allocation failed"); return HB_ENOMEM; }
+  Dev d{f, st, n, R, red, red + (size_t)kRedBlocks * (m + 2) * R, (double*)(red + (size_t)kRedBlocks * (m + 2) * R + (size_t)(m + 2) * R)};
+
+  // non-finite input check
+  cudaMemsetAsync(flag, 0, sizeof(int), st);
+  k_nonfinite<<<gsz(n * R), 256, 0, st>>>((const double2*)b_phys, ld, n, R, flag); count_launch(f, 1);
+  int hflag = 0;
+  cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("hb_gmres: CUDA error"); return HB_ECUDA; }
+  if (hflag) { set_error("hb_gmres: right-hand side contains NaN/Inf"); return HB_ENAN; }
+
+  if ((rc = launch_gather_cols(b_phys, 0, ld, n, R, bh, 0, df.scale, st))) return rc;
+  cudaMemsetAsync(xv, 0, vbytes, st);
+  std::vector<double> bnorm;
+  if ((rc = norms(d, bh, bnorm))) return rc;
+
+  const Prec pres = mixed ? PREC_F32_ACC64 : PREC_F64;    // true residual precision
+  const int lo = adj ? 3 : 0, up = adj ? 2 : 1;            // first / second sweep of M^{-1} (op N: L then U)
+  // split form for op H solves A^H x = b: (U~^H)^{-1}... with A^H = U~^H... the split
+  // system uses  L' = U~^H (lower) and U' = L~^H (upper):  U~^{-H} A^H L~^{-H}.
+  int iters = 0, cycles = 0, nconv = 0;
+  std::vector<int32_t> it_r(R, 0);
+  std::vector<double> res_r(R, 1.0), pres_r(R, 0.0), tscale(R, 1.0);
+  std::vector<char> done(R, 0);
+  std::vector<Givens> gv(R);
+  std::vector<zc> h;
+  std::vector<double> hn;
+  std::vector<int> kuse(R, 0);
+  std::vector<zc> coef((size_t)m * R);
+  float2* zf = (float2*)zb;                                     // Z_0..Z_{m-1} then a float2 scratch at Z_m
+  float2* f32s = mixed ? zf + (size_t)m * n * R : nullptr;
+
+  // r = b^ - A^ x  (FP64); returns per-column relative norms in res_r
+  auto true_residual = [&](const double2* xx, double2* r) -> int {
+    int e;
+    if ((e = apply_internal(f, pres, adj, xx, tmp2, R, st))) return e;
+    k_sub_into<<<gsz(n * R), 256, 0, st>>>(bh, tmp2, r, n * R); count_launch(f, 1);
+    std::vector<double> rn;
+    if ((e = norms(d, r, rn))) return e;
+    for (int64_t c = 0; c < R; ++c) res_r[c] = bnorm[c] > 0 ? rn[c] / bnorm[c] : 0.0;
+    return HB_OK;
+  };
+
+  // split form: x = U'^{-1} y ; preconditioned residual L'^{-1} r
+  double2* r = tmp;   // residual / work vector
+  if ((rc = true_residual(xv, r))) return rc;   // x = 0: r = b^
+  while (iters < maxit) {
+    nconv = 0;
+    for (int64_t c = 0; c < R; ++c) { done[c] = res_r[c] <= rtol; nconv += done[c]; }
+    if (nconv == R) break;
+    // ---- start vector
+    std::vector<double> beta;
+    if (!mixed) {
+      if ((rc = sweep_internal(f, PREC_F64, lo, r, R, st))) return rc;   // r <- L'^{-1} r
+    }
+    if ((rc = norms(d, r, beta))) return rc;
+    normalise(d, r, beta, V);
+    std::vector<double> target(R);
+    for (int64_t c = 0; c < R; ++c) {
+      gv[c].reset(m, beta[c]);
+      kuse[c] = 0;
+      // aim the inner estimate at the final tolerance (scaled back when the true residual missed)
+      double want = rtol * bnorm[c] * tscale[c];
+      if (mixed) want = std::max(want, 2e-7 * beta[c]);
+      else want = rtol * tscale[c] * beta[c] / std::max(res_r[c] * bnorm[c], 1e-300) * bnorm[c];
+      target[c] = want;
+    }
+    int j = 0;
+    for (; j < m && iters < maxit; ++j) {
+      double2* vj = V + (size_t)j * n * R;
+      double2* w = V + (size_t)(j + 1) * n * R;
+      if (!mixed) {
+        // w = L'^{-1} A U'^{-1} v_j
+        cudaMemcpyAsync(w, vj, vbytes, cudaMemcpyDeviceToDevice, st);
+        if ((rc = sweep_internal(f, PREC_F64, up, w, R, st))) return rc;
+        if ((rc = apply_internal(f, PREC_F64, adj, w, tmp2, R, st))) return rc;
+        cudaMemcpyAsync(w, tmp2, vbytes, cudaMemcpyDeviceToDevice, st);
+        if ((rc = sweep_internal(f, PREC_F64, lo, w, R, st))) return rc;
+      } else {
+        // z_j = M^{-1} v_j (FP32), w = A z_j (FP32), promoted to FP64
+        float2* zj = zf + (size_t)j * n * R;
+        k_to_f32<<<gsz(n * R), 256, 0, st>>>(vj, zj, n * R); count_launch(f, 1);
+        if ((rc = sweep_internal(f, PREC_F32, lo, zj, R, st))) return rc;
+        if ((rc = sweep_internal(f, PREC_F32, up, zj, R, st))) return rc;
+        if ((rc = apply_internal(f, PREC_F32, adj, zj, f32s, R, st))) return rc;
+        k_to_f64<<<gsz(n * R), 256, 0, st>>>(f32s, w, n * R); count_launch(f, 1);
+      }
+      if ((rc = cgs2(d, V, (int64_t)n * R, j + 1, w, h, hn))) return rc;
+      normalise(d, w, hn, w);
+      ++iters;
+      int active = 0;
+      for (int64_t c = 0; c < R; ++c) {
+        if (done[c] || kuse[c] < 0) continue;
+        std::vector<zc> col(j + 1);
+        for (int i = 0; i <= j; ++i) col[i] = h[(size_t)i * R + c];
+        double est = gv[c].push(j, col.data(), hn[c]);
+        pres_r[c] = bnorm[c] > 0 ? est / bnorm[c] : 0.0;
+        it_r[c]++;
+        if (est <= target[c]) kuse[c] = -(j + 1);   // converged in this cycle after j+1 steps
+        else active++;
+      }
+      if (active == 0) { ++j; break; }
+    }
+    // ---- update the iterate with each column's own step count
+    int kcyc = j;
+    std::fill(coef.begin(), coef.end(), zc(0.0));
+    for (int64_t c = 0; c < R; ++c) {
+      if (done[c]) continue;
+      int k = kuse[c] < 0 ? -kuse[c] : kcyc;
+      std::vector<zc> cf(k);
+      gv[c].solve(k, cf.data());
+      for (int i = 0; i < k; ++i) coef[(size_t)i * R + c] = cf[i];
+    }
+    cudaMemcpyAsync(d.red_out, coef.data(), (size_t)kcyc * R * sizeof(double2), cudaMemcpyHostToDevice, st);
+    if (!mixed) {
+      // y += V c;  x = U'^{-1} y is formed for the residual check
+      k_add_combo<double2><<<gsz(n * R), 256, 0, st>>>(V, (int64_t)n * R, kcyc, d.red_out, xv, n, R); count_launch(f, 1);
+      cudaMemcpyAsync(tmp2, xv, vbytes, cudaMemcpyDeviceToDevice, st);
+      double2* xs = tmp2;
+      if ((rc = sweep_internal(f, PREC_F64, up, xs, R, st))) return rc;
+      // r = b^ - A^ x (uses tmp2 as scratch: keep x in r first)
+      cudaMemcpyAsync(r, xs, vbytes, cudaMemcpyDeviceToDevice, st);
+      if ((rc = apply_internal(f, PREC_F64, adj, r, tmp2, R, st))) return rc;
+      k_sub_into<<<gsz(n * R), 256, 0, st>>>(bh, tmp2, r, n * R); count_launch(f, 1);
+      std::vector<double> rn;
+      if ((rc = norms(d, r, rn))) return rc;
+      for (int64_t c = 0; c < R; ++c) {
+        double nr = bnorm[c] > 0 ? rn[c] / bnorm[c] : 0.0;
+        if (!done[c] && nr > rtol) tscale[c] *= std::min(0.5, rtol / nr);
+        res_r[c] = nr;
+      }
+    } else {
+      // x += Z c  (Z in FP32), then the FP64 residual
+      k_add_combo<float2><<<gsz(n * R), 256, 0, st>>>(zf, (int64_t)n * R, kcyc, d.red_out, xv, n, R); count_launch(f, 1);
+      if ((rc = true_residual(xv, r))) return rc;
+    }
+    ++cycles;
+  }
+  // final solution in the caller's layout (physical x: unaffected by the rescaling)
+  if (!mixed) {
+    cudaMemcpyAsync(tmp2, xv, vbytes, cudaMemcpyDeviceToDevice, st);
+    if ((rc = sweep_internal(f, PREC_F64, up, tmp2, R, st))) return rc;
+    if ((rc = launch_scatter_cols(tmp2, 0, n, R, x, 0, ld, 1.0, st))) return rc;
+  } else {
+    if ((rc = launch_scatter_cols(xv, 0, n, R, x, 0, ld, 1.0, st))) return rc;
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("hb_gmres: CUDA error"); return HB_ECUDA; }
+  nconv = 0;
+  double worst = 0.0, worst_p = 0.0;
+  for (int64_t c = 0; c < R; ++c) {
+    nconv += res_r[c] <= rtol;
+    worst = std::max(worst, res_r[c]);
+    worst_p = std::max(worst_p, pres_r[c]);
+  }
+  if (info) {
+    int32_t* ipr = info->iters_per_rhs;
+    double* rpr = info->res_per_rhs;
+    info->iters = iters;
+    info->restarts = cycles;
+    info->ir_steps = mixed ? cycles : 0;
+    info->converged = nconv;
+    info->true_rel_res = worst;
+    info->precond_rel_res = worst_p;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (ipr) for (int64_t c = 0; c < R; ++c) ipr[c] = it_r[c];
+    if (rpr) for (int64_t c = 0; c < R; ++c) rpr[c] = res_r[c];
+  }
+  if (nconv < R) { set_error("hb_gmres: %d of %lld columns did not reach rtol in %d iterations", (int)(R - nconv), (long long)R, iters); return HB_ENOCONV; }
+  return HB_OK;
+}
+
+extern "C" int hb_rhs_plane_wave(hb_factor_t f, const double* phi_deg, int64_t nrhs, void* b, int64_t ld, void* stream) {
+  if (!f || !phi_deg || !b || nrhs < 1 || ld < f->df.n) { set_error("hb_rhs_plane_wave: bad argument"); return HB_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<double> cs(2 * nrhs);
+  for (int64_t r = 0; r < nrhs; ++r) {
+    double ph = phi_deg[r] * M_PI / 180.0;
+    cs[r] = std::cos(ph);
+    cs[nrhs + r] = std::sin(ph);
+  }
+  double* d = (double*)f->ws.get(WS_SMALL, std::max<size_t>(256, cs.size() * sizeof(double)));
+  if (!d) { set_error("hb_rhs_plane_wave: allocation failed"); return HB_ENOMEM; }
+  cudaMemcpyAsync(d, cs.data(), cs.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  k_plane_wave<<<gsz(f->df.n * nrhs), 256, 0, st>>>(f->df.cx, f->df.cy, f->df.n, d, d + nrhs, nrhs, f->df.kappa,
+                                                    (double2*)b, ld); count_launch(f, 1);
+  if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("hb_rhs_plane_wave: CUDA error"); return HB_ECUDA; }
+  return HB_OK;
+}
+
+static int far_common(hb_factor_t f, const void* x, int64_t nrhs, int64_t ld, const double* phi, int64_t nang,
+                      void* out, void* stream, bool mono) {
+  if (!f || !x || !phi || !out || nrhs < 1 || ld < f->df.n || nang < 1) { set_error("hb_far_field: bad argument"); return HB_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<double> cs(2 * nang);
+  for (int64_t q = 0; q < nang; ++q) {
+    double ph = phi[q] * M_PI / 180.0;
+    cs[q] = std::cos(ph);
+    cs[nang + q] = std::sin(ph);
+  }
+  double* d = (double*)f->ws.get(WS_SMALL, std::max<size_t>(256, cs.size() * sizeof(double)));
+  if (!d) { set_error("hb_far_field: allocation failed"); return HB_ENOMEM; }
+  cudaMemcpyAsync(d, cs.data(), cs.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  const double k = f->df.kappa;
+  // C = -(k eta0 / 4) sqrt(2i / (pi k))
+  std::complex<double> C = -(k * f->df.eta0 / 4.0) * std::sqrt(std::complex<double>(0.0, 2.0 / (M_PI * k)));
+  dim3 grid((unsigned)(mono ? 1 : nang), (unsigned)nrhs);
+  k_far_field<<<grid, 256, 0, st>>>(f->df.cx, f->df.cy, f->df.w, f->df.n, (const double2*)x, ld, d, d + nang, nang, k,
+                                    double2{C.real(), C.imag()}, (double2*)out, mono ? 1 : 0); count_launch(f, 1);
+  if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("hb_far_field: CUDA error"); return HB_ECUDA; }
+  return HB_OK;
+}
+
+extern "C" int hb_far_field(hb_factor_t f, const void* x, int64_t nrhs, int64_t ld, const double* phi_obs_deg,
+                            int64_t nobs, void* out, void* stream) {
+  return far_common(f, x, nrhs, ld, phi_obs_deg, nobs, out, stream, false);
+}
+
+extern "C" int hb_monostatic(hb_factor_t f, const void* x, int64_t nrhs, int64_t ld, const double* phi_deg, void* out,
+                             void* stream) {
+  return far_common(f, x, nrhs, ld, phi_deg, nrhs, out, stream, true);
+}

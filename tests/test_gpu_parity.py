@@ -1,0 +1,230 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (stated per test):
+* FP64 compressed apply vs the oracle's dense Z: 10 eps relative (eps = 1e-6).
+* With eps = 1e-10 the sampled construction reaches ~1e-8 (its floor, the same
+  on the host interpreter); the bound 1e-7 pins every kernel path (a dropped
+  or mis-indexed term shows at O(1e-4) or more).
+* Sweeps at eps = 1e-10 vs the oracle's exact entry-wise triangular solves: 1e-7.
+* GMRES solutions vs the oracle's dense LU solve: 1e-5 relative (N <= 4096).
+* FP32 forms: the FP32 storage adds ~1e-7 per entry; apply bound 10 eps + 2e-6.
+"""
+import ctypes as C
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import dense, efie, farfield
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hb():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_11371_gb300 import build
+    build.build()
+    import paper_1901_11371_gb300 as hb
+    return hb
+
+
+def _t(a, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return t if dtype is None else t.to(dtype)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def strip(hb):
+    wl = W.CONFIG1
+    g = hb.hb_geometry(wl.kind, wl.params, wl.n)
+    p = efie.Problem.from_workload(wl)
+    a = p.dense()
+    f64 = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C128)
+    f32 = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C64)
+    ftight = hb.hb_factor(g, wl.leaf, 1e-10, form=hb.HB_C128)
+    return dict(wl=wl, g=g, p=p, a=a, f64=f64, f32=f32, ftight=ftight)
+
+
+def test_apply_fp64_within_10eps(hb, strip):
+    a, f = strip["a"], strip["f64"]
+    x = W.complex_gaussian(1024, 21)
+    y = hb.hb_apply(f, _t(x)).cpu().numpy()
+    ref = a @ x
+    assert _rel(y, ref) <= 10 * 1e-6
+    assert np.max(np.abs(y - ref)) <= 10 * 1e-6 * np.max(np.abs(ref))
+
+
+def test_apply_tight_compression_pins_kernels(hb, strip):
+    a, f = strip["a"], strip["ftight"]
+    x = W.complex_gaussian(1024, 22)
+    y = hb.hb_apply(f, _t(x)).cpu().numpy()
+    assert _rel(y, a @ x) <= 1e-7
+    yh = hb.hb_apply(f, _t(x), hb.HB_OP_H).cpu().numpy()
+    assert _rel(yh, a.conj().T @ x) <= 1e-7
+
+
+def test_apply_adjoint_within_10eps(hb, strip):
+    a, f = strip["a"], strip["f64"]
+    x = W.complex_gaussian(1024, 23)
+    y = hb.hb_apply_adjoint(f, _t(x)).cpu().numpy()
+    assert _rel(y, a.conj().T @ x) <= 10 * 1e-6
+
+
+@pytest.mark.parametrize("R", [2, 5, 9])
+def test_apply_multi_rhs_ragged(hb, strip, R):
+    a, f = strip["a"], strip["ftight"]
+    x = W.complex_gaussian(1024, 24, R).T.copy()          # (R, N)
+    y = hb.hb_apply(f, _t(x)).cpu().numpy()
+    ref = (a @ x.T).T
+    for r in range(R):
+        assert _rel(y[r], ref[r]) <= 1e-7
+    np.testing.assert_allclose(y, ref, rtol=0, atol=2e-6 * np.abs(ref).max())
+
+
+def test_apply_leading_dimension(hb, strip):
+    import torch
+    a, f = strip["a"], strip["ftight"]
+    n, R, ld = 1024, 3, 1024 + 40
+    x = W.complex_gaussian(n, 25, R).T.copy()
+    xb = torch.zeros((R, ld), dtype=torch.complex128, device="cuda")
+    xb[:, :n] = _t(x)
+    yb = torch.full((R, ld), 7.0 + 0j, dtype=torch.complex128, device="cuda")
+    rc = hb.lib().hb_apply(f._h, 0, C.c_void_p(xb.data_ptr()), C.c_void_p(yb.data_ptr()), R, ld,
+                           C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0
+    y = yb.cpu().numpy()
+    ref = (a @ x.T).T
+    for r in range(R):
+        assert _rel(y[r, :n], ref[r]) <= 1e-7
+    assert np.all(y[:, n:] == 7.0)                      # padding untouched
+
+
+def test_apply_fp32(hb, strip):
+    import torch
+    a, f = strip["a"], strip["f32"]
+    x = W.complex_gaussian(1024, 26)
+    y = hb.hb_apply(f, _t(x, torch.complex64)).cpu().numpy().astype(np.complex128)
+    assert _rel(y, a @ x) <= 10 * 1e-6 + 2e-6
+
+
+def test_precond_tight_vs_exact_triangles(hb, strip):
+    a, f = strip["a"], strip["ftight"]
+    b = W.complex_gaussian(1024, 27)
+    x = hb.hb_precond_solve(f, _t(b)).cpu().numpy()
+    assert _rel(x, dense.precond_solve(a, b)) <= 1e-7
+    xl = hb.hb_lower_solve(f, _t(b)).cpu().numpy()
+    assert _rel(xl, dense.forward_subst(dense.l_tilde(a), b, unit=True)) <= 1e-7
+    xu = hb.hb_upper_solve(f, _t(b)).cpu().numpy()
+    assert _rel(xu, dense.back_subst(dense.u_tilde(a), b)) <= 1e-7
+    # adjoint: x = L~^{-H} U~^{-H} b
+    xh = hb.hb_precond_solve(f, _t(b), hb.HB_OP_H).cpu().numpy()
+    ref = dense.back_subst(dense.l_tilde(a).conj().T, dense.forward_subst(dense.u_tilde(a).conj().T, b), unit=True)
+    assert _rel(xh, ref) <= 1e-7
+
+
+def test_precond_eps_vs_exact_triangles(hb, strip):
+    a, f = strip["a"], strip["f64"]
+    b = W.complex_gaussian(1024, 28)
+    x = hb.hb_precond_solve(f, _t(b)).cpu().numpy()
+    assert _rel(x, dense.precond_solve(a, b)) <= 1e-4
+
+
+def test_sweeps_match_host_interpreter(hb, strip):
+    # same factors, FP64 on both sides: only the summation order differs
+    wl, g = strip["wl"], strip["g"]
+    fh = hb.hb_factor_host(g, wl.leaf, wl.eps)
+    f = strip["f64"]
+    b = W.complex_gaussian(1024, 29)
+    for which, fn, op in ((0, hb.hb_lower_solve, 0), (1, hb.hb_upper_solve, 0), (2, hb.hb_lower_solve, 1),
+                          (3, hb.hb_upper_solve, 1)):
+        x = fn(f, _t(b), op).cpu().numpy()
+        assert _rel(x, hb.hb_host_sweep(fh, b, which)) <= 1e-12, which
+
+
+def test_gmres_fp64_config1_vs_dense_lu(hb, strip):
+    p, a, f = strip["p"], strip["a"], strip["f64"]
+    b = hb.hb_rhs_plane_wave(f, [30.0])
+    b_np = p.plane_wave(30.0)[:, 0]
+    np.testing.assert_allclose(b.cpu().numpy()[0], b_np, atol=1e-12)
+    x, info = hb.hb_gmres(f, b, rtol=1e-6, restart=30, maxit=500)
+    x_lu = dense.solve(a, b_np * p.scale)
+    assert info["true_rel_res"] <= 1e-6
+    assert _rel(x.cpu().numpy()[0], x_lu) <= 1e-5
+    assert info["iters"] < 60
+
+
+def test_gmres_fp64_adjoint(hb, strip):
+    p, a, f = strip["p"], strip["a"], strip["f64"]
+    b = W.complex_gaussian(1024, 30)
+    x, info = hb.hb_gmres(f, _t(b[None, :]), op=hb.HB_OP_H, rtol=1e-8, maxit=500)
+    x_ref = dense.solve(a.conj().T, b * p.scale)
+    assert _rel(x.cpu().numpy()[0], x_ref) <= 1e-5
+
+
+def test_gmres_mixed_small_semicircle_vs_dense_lu(hb):
+    # semicircle (the non-resonant geometry family of the batching workload) at N = 4096
+    wl = W.arc(4096, 64, 1e-6, radius=4096 / 20.0 / math.pi)
+    g = hb.hb_geometry(wl.kind, wl.params, wl.n)
+    f = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C64)
+    p = efie.Problem.from_workload(wl)
+    a = p.dense()
+    phis = [10.0, 77.0, 145.0]
+    b = hb.hb_rhs_plane_wave(f, phis)
+    x, info = hb.hb_gmres(f, b, rtol=1e-6, restart=30, maxit=600)
+    assert info["converged"] == 3 and info["true_rel_res"] <= 1e-6
+    xs = x.cpu().numpy()
+    bb = p.plane_wave(phis) * p.scale
+    x_lu = dense.solve(a, bb)
+    for r in range(3):
+        assert _rel(xs[r], x_lu[:, r]) <= 1e-5
+
+
+def test_far_field_and_monostatic(hb, strip):
+    p, f = strip["p"], strip["f64"]
+    x = W.complex_gaussian(1024, 31, 2).T.copy()
+    phi = W.observation_angles_deg(64)
+    ff = hb.hb_far_field(f, _t(x), phi).cpu().numpy()
+    for r in range(2):
+        np.testing.assert_allclose(ff[r], farfield.far_field(p, x[r], phi), rtol=1e-11, atol=1e-11 * np.abs(ff).max())
+    mono = hb.hb_monostatic(f, _t(x), [20.0, 60.0]).cpu().numpy()
+    np.testing.assert_allclose(mono, farfield.monostatic(p, x.T, [20.0, 60.0]), rtol=1e-11)
+
+
+def test_error_codes(hb, strip):
+    import torch
+    f = strip["f64"]
+    lib = hb.lib()
+    b = torch.zeros((1, 1024), dtype=torch.complex128, device="cuda")
+    b[0, 5] = float("nan")
+    x = torch.empty_like(b)
+    info = hb._lib.GmresInfo()
+    rc = lib.hb_gmres(f._h, 0, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), 1, 1024, 30, 1e-6, 100,
+                      C.byref(info), None)
+    assert rc == hb._lib.HB_ENAN
+    rc = lib.hb_apply(f._h, 0, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), 1, 1000, None)
+    assert rc == hb._lib.HB_EINVAL                        # ld < N
+    rc = lib.hb_apply(f._h, 0, C.c_void_p(b.data_ptr()), C.c_void_p(b.data_ptr()), 1, 1024, None)
+    assert rc == hb._lib.HB_EINVAL                        # aliasing
+    rc = lib.hb_apply(f._h, 7, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), 1, 1024, None)
+    assert rc == hb._lib.HB_EINVAL                        # bad op
+
+
+def test_repeatable_bitwise(hb, strip):
+    f = strip["f64"]
+    x = _t(W.complex_gaussian(1024, 32))
+    y1 = hb.hb_apply(f, x).cpu().numpy()
+    y2 = hb.hb_apply(f, x).cpu().numpy()
+    assert np.array_equal(y1, y2)
+    b = hb.hb_rhs_plane_wave(f, [40.0])
+    s1, _ = hb.hb_gmres(f, b)
+    s2, _ = hb.hb_gmres(f, b)
+    assert np.array_equal(s1.cpu().numpy(), s2.cpu().numpy())
