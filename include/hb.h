@@ -183,9 +183,19 @@ int hb_far_field(hb_factor_t f, const void* x, int64_t nrhs, int64_t ld, const d
 int hb_monostatic(hb_factor_t f, const void* x, int64_t nrhs, int64_t ld, const double* phi_deg, void* out,
                   void* stream);
 
-/* hb_set_sweep_rhs_per_cta -- tuning knob: RHS columns handled by one CTA of
- * the sweep kernels (0 = library default).  Returns the previous value. */
-int hb_set_sweep_rhs_per_cta(hb_factor_t f, int rhs_per_cta);
+/* hb_set_sweep_grid_min -- tuning knob of the cooperative sweep kernel:
+ * program phases with at least grid_min independent ops are spread over all
+ * CTAs, smaller ones run inside one CTA (default 16).  Synchronises the
+ * legacy default stream.  Returns the previous value (>= 1) or an error code. */
+int hb_set_sweep_grid_min(hb_factor_t f, int grid_min);
+
+/* hb_set_wait_limit -- iteration limit of every bounded device-side wait
+ * (the sweep kernel's grid barrier; default 2^24 polls, about a second).
+ * hb_status -- synchronise `stream`, then return HB_ETIMEOUT (and clear the
+ * flag) if a bounded wait expired since the last call, else HB_OK.  A timed
+ * out sweep leaves its output undefined; the device stays usable. */
+int hb_set_wait_limit(hb_factor_t f, long long spins);
+int hb_status(hb_factor_t f, void* stream);
 
 /* hb_profile -- enable (1) / disable (0) timing of the hot-path kernels of
  * this factor.  While enabled, every apply launch sequence and every sweep

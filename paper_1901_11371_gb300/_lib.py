@@ -64,7 +64,9 @@ SIGNATURES = {
     "hb_rhs_plane_wave": (_INT, [_VP, C.POINTER(C.c_double), _I64, _VP, _I64, _VP]),
     "hb_far_field": (_INT, [_VP, _VP, _I64, _I64, C.POINTER(C.c_double), _I64, _VP, _VP]),
     "hb_monostatic": (_INT, [_VP, _VP, _I64, _I64, C.POINTER(C.c_double), _VP, _VP]),
-    "hb_set_sweep_rhs_per_cta": (_INT, [_VP, _INT]),
+    "hb_set_sweep_grid_min": (_INT, [_VP, _INT]),
+    "hb_set_wait_limit": (_INT, [_VP, C.c_longlong]),
+    "hb_status": (_INT, [_VP, _VP]),
     "hb_profile": (_INT, [_VP, _INT]),
     "hb_profile_read": (_INT, [_VP, _INT, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "hb_host_apply": (_INT, [_VP, _INT, C.POINTER(C.c_double), C.POINTER(C.c_double)]),

@@ -98,6 +98,9 @@ int upload_factor(const PackedHost& ph, const HostFactor& hf, const Geometry& g,
     if ((rc = up(*progs[i], &df.prog[i], st, df.device_bytes))) return rc;
     df.nprog[i] = (int)progs[i]->size();
   }
+  HB_CU(cudaMalloc(&df.bar, 64));
+  HB_CU(cudaMemsetAsync(df.bar, 0, 64, st));
+  if ((rc = set_grid_min(df, ph, 16, st))) return rc;
   if ((rc = up(g.cx, &df.cx, st, df.device_bytes))) return rc;
   if ((rc = up(g.cy, &df.cy, st, df.device_bytes))) return rc;
   if ((rc = up(g.w, &df.w, st, df.device_bytes))) return rc;
@@ -105,10 +108,27 @@ int upload_factor(const PackedHost& ph, const HostFactor& hf, const Geometry& g,
   return HB_OK;
 }
 
+int set_grid_min(DevFactor& df, const PackedHost& ph, int grid_min, cudaStream_t st) {
+  const std::vector<DPhase>* progs[4] = {&ph.prog_lower, &ph.prog_upper, &ph.prog_lower_adj, &ph.prog_upper_adj};
+  HB_CU(cudaStreamSynchronize(st));
+  for (int i = 0; i < 4; ++i) {
+    std::vector<DSeg> segs = segment_program(*progs[i], grid_min);
+    if (df.segs[i]) { cudaFree(df.segs[i]); df.segs[i] = nullptr; }
+    int64_t dummy = 0;
+    int rc = up(segs, &df.segs[i], st, dummy);
+    if (rc) return rc;
+    df.nsegs[i] = (int)segs.size();
+  }
+  HB_CU(cudaStreamSynchronize(st));
+  df.grid_min = grid_min;
+  return HB_OK;
+}
+
 void free_factor(DevFactor& df) {
   void* ptrs[] = {df.fpool, df.leaf, df.linv, df.uinv, df.ipool, df.vout, df.uout, df.bvout, df.buout,
                   df.bf_vout0, df.bf_uout0, df.items, df.step_idx, df.astep_idx, df.prog[0], df.prog[1],
-                  df.prog[2], df.prog[3], df.cx, df.cy, df.w};
+                  df.prog[2], df.prog[3], df.segs[0], df.segs[1], df.segs[2], df.segs[3], df.bar,
+                  df.cx, df.cy, df.w};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   df = DevFactor();
@@ -319,11 +339,25 @@ int hb_tree(hb_factor_t f, int64_t* node_begin, int64_t* node_end) {
   return HB_OK;
 }
 
-int hb_set_sweep_rhs_per_cta(hb_factor_t f, int rhs_per_cta) {
-  if (!f) return HB_EINVAL;
-  int old = f->df.sweep_rhs_per_cta;
-  f->df.sweep_rhs_per_cta = rhs_per_cta < 0 ? 0 : rhs_per_cta;
-  return old;
+int hb_set_sweep_grid_min(hb_factor_t f, int grid_min) {
+  if (!f || f->host_only || grid_min < 1) { set_error("hb_set_sweep_grid_min: bad argument"); return HB_EINVAL; }
+  int old = f->df.grid_min;
+  int rc = set_grid_min(f->df, f->ph, grid_min, nullptr);
+  return rc ? rc : old;
+}
+
+int hb_set_wait_limit(hb_factor_t f, long long spins) {
+  if (!f || f->host_only || spins < 1) { set_error("hb_set_wait_limit: bad argument"); return HB_EINVAL; }
+  f->df.spin_limit = spins;
+  return HB_OK;
+}
+
+int hb_status(hb_factor_t f, void* stream) {
+  if (!f || f->host_only) { set_error("hb_status: bad argument"); return HB_EINVAL; }
+  int err = 0;
+  if (read_grid_error(f->df.bar, (cudaStream_t)stream, &err)) { set_error("hb_status: CUDA error"); return HB_ECUDA; }
+  if (err) { set_error("a bounded device-side wait expired in a sweep kernel"); return HB_ETIMEOUT; }
+  return HB_OK;
 }
 
 }  // extern "C"
@@ -364,7 +398,7 @@ int sweep_internal(hb_factor_t f, Prec p, int which, void* vec, int64_t R, cudaS
   if (!state) { set_error("sweep: cannot allocate state workspace"); return HB_ENOMEM; }
   cudaEvent_t e;
   f->prof.begin(1, st, e);
-  int rc = launch_sweep(f->df, p, which, vec, R, state, st);
+  int rc = launch_sweep_coop(f->df, p, which, vec, R, state, f->df.bar, st, f->df.spin_limit);
   f->prof.end(1, st, e);
   count_launch(f, 1);
   return rc;

@@ -34,13 +34,17 @@ struct DevFactor {
   std::vector<int32_t> step_ptr, astep_ptr;   // host copies (launch sizes)
   DPhase* prog[4] = {nullptr, nullptr, nullptr, nullptr};   // lower, upper, lower^H, upper^H
   int nprog[4] = {0, 0, 0, 0};
+  DSeg* segs[4] = {nullptr, nullptr, nullptr, nullptr};     // cooperative-kernel segments of each program
+  int nsegs[4] = {0, 0, 0, 0};
+  int grid_min = 0;                                         // phases with >= grid_min ops run grid-wide
+  void* bar = nullptr;                                      // grid barrier state + error flag
+  long long spin_limit = 1LL << 24;                         // bounded waits of the grid barrier
   // geometry on the device (far field, plane waves)
   double* cx = nullptr;
   double* cy = nullptr;
   double* w = nullptr;
   double kappa = 0, eta0 = 0, scale = 1;
   int64_t device_bytes = 0;
-  int sweep_rhs_per_cta = 0;
 };
 
 // Upload a packed host image in `form`; returns HB_OK or an error code.
@@ -59,9 +63,15 @@ enum Prec { PREC_F64 = 0,        // double factors, double arithmetic (HB_C128)
 // `state` holds df.state_len * R complex entries of the same type.
 int launch_apply(const DevFactor& df, Prec p, bool adjoint, const void* x, void* y, int64_t R, void* state,
                  cudaStream_t st);
-// In-place sweep: vec holds b on entry and x on exit.  which: 0 = L~^{-1},
-// 1 = U~^{-1}, 2 = L~^{-H}, 3 = U~^{-H}.
-int launch_sweep(const DevFactor& df, Prec p, int which, void* vec, int64_t R, void* state, cudaStream_t st);
+// Cooperative sweep, in place: vec holds b on entry and x on exit.  which:
+// 0 = L~^{-1}, 1 = U~^{-1}, 2 = L~^{-H}, 3 = U~^{-H}.  One launch per sweep,
+// grid barriers between segments.
+int launch_sweep_coop(const DevFactor& df, Prec p, int which, void* vec, int64_t R, void* state, void* bar,
+                      cudaStream_t st, long long spin_limit);
+// Read the barrier error flag (synchronises st).  *err != 0: a bounded wait expired.
+int read_grid_error(void* bar, cudaStream_t st, int* err);
+// (Re)build the cooperative segments of the four programs for threshold grid_min.
+int set_grid_min(DevFactor& df, const PackedHost& ph, int grid_min, cudaStream_t st);
 
 // Layout conversion between the ABI's column-major [R][ld] blocks and the
 // internal [row][R] layout, with optional precision change and scaling.

@@ -474,6 +474,7 @@ struct Packer {
         if (vtype) m[(size_t)j * b.k + i] = t; else m[(size_t)i * nr + j] = t;
       }
     d.moff = push_mat(m.data(), (int64_t)m.size());
+    while (ph.ipool.size() % 8) ph.ipool.push_back(0);     // 16-byte aligned index blocks
     d.ioff = (int32_t)ph.ipool.size();
     for (int i = 0; i < b.k; ++i) ph.ipool.push_back((int16_t)b.q[i]);
     for (int j = 0; j < nr; ++j) ph.ipool.push_back((int16_t)b.p[j]);
@@ -651,6 +652,9 @@ void pack_factor(const HostFactor& hf, PackedHost& ph) {
   rec(0, 0, ph.prog_upper, 1);
   rec(0, 0, ph.prog_lower_adj, 2);
   rec(0, 0, ph.prog_upper_adj, 3);
+  // tail padding so 16-byte bulk copies of the last block stay inside the pools
+  for (int i = 0; i < 4; ++i) ph.fpool.push_back(cplx(0.0));
+  for (int i = 0; i < 16; ++i) ph.ipool.push_back(0);
   ph.kmax = kmax;
   ph.kavg = kcnt ? (double)ksum / (double)kcnt : 0.0;
   for (int v = 0; v < D && v < 32; ++v) {
@@ -801,6 +805,25 @@ struct HostExec {
   }
 };
 }  // namespace
+
+std::vector<DSeg> segment_program(const std::vector<DPhase>& prog, int grid_min) {
+  std::vector<DSeg> segs;
+  int n = (int)prog.size();
+  int i = 0;
+  while (i < n) {
+    bool big = prog[i].kind != PH_LEAF && prog[i].count >= grid_min;
+    if (big) {
+      segs.push_back(DSeg{1, i, 1, 0});
+      ++i;
+    } else {
+      int j = i;
+      while (j < n && !(prog[j].kind != PH_LEAF && prog[j].count >= grid_min)) ++j;
+      segs.push_back(DSeg{0, i, j - i, 0});
+      i = j;
+    }
+  }
+  return segs;
+}
 
 void host_apply(const PackedHost& ph, const HostFactor& hf, bool adj, const cplx* x, cplx* y) {
   HostExec ex(ph, hf);

@@ -135,6 +135,19 @@ struct DPhase {
   int32_t adj;       // 1 = adjoint direction of the ops
 };
 
+// A segment of a sweep program for the cooperative sweep kernel: either one
+// grid-wide phase (its ops spread over every CTA) or a run of consecutive
+// small phases executed by a single CTA; a grid barrier follows each segment.
+struct DSeg {
+  int32_t grid;      // 1 = grid-wide phase, 0 = single-CTA run
+  int32_t first;     // first phase index
+  int32_t count;     // number of phases
+  int32_t pad;
+};
+
+// Split a program into segments: phases with at least grid_min ops run grid-wide.
+std::vector<DSeg> segment_program(const std::vector<DPhase>& prog, int grid_min);
+
 struct PackedHost {
   int64_t n = 0, n0 = 0, m = 0;
   int depth = 0;

@@ -1,5 +1,5 @@
-// Hot-path CUDA kernels (sm_103a): H-IDBF apply (Alg. 2) and the L~ / U~
-// triangular sweeps (Algs. 3, 4), forward and adjoint.
+// Hot-path CUDA kernels (sm_103a): H-IDBF apply (Alg. 2), forward and adjoint.
+// (The L~ / U~ sweeps of Algs. 3, 4 live in hb_sweep.cu.)
 //
 // Every butterfly factor is a set of small ID blocks (Sec. 2 / Appendix).  A
 // warp owns one block op; lanes run over the op's OUTPUT entries and loop over
@@ -263,97 +263,6 @@ __global__ void __launch_bounds__(256) k_apply_exit(const DOuter* __restrict__ o
 }
 
 // ---------------------------------------------------------------------------
-// Sweep kernel (Algs. 3, 4 and adjoints): one CTA walks the whole recursion
-// as a program of phases; ops inside a phase are independent and spread over
-// the CTA's warps; __syncthreads separates dependent phases.  CTA g handles
-// RHS columns [g*RC, g*RC + RC).
-// ---------------------------------------------------------------------------
-template <class T, class F, int RC>
-__global__ void __launch_bounds__(512) k_sweep(const DPhase* __restrict__ prog, int nphase, int64_t n0,
-                                               const DOuter* __restrict__ bvout, const DOuter* __restrict__ buout,
-                                               const int32_t* __restrict__ bf_vout0,
-                                               const int32_t* __restrict__ bf_uout0,
-                                               const DItem* __restrict__ items, const F* __restrict__ fp,
-                                               const int16_t* __restrict__ ip, const F* __restrict__ tinv,
-                                               typename C2<T>::t* vec, typename C2<T>::t* st, int64_t R) {
-  using C = typename C2<T>::t;
-  extern __shared__ unsigned char smem_raw[];
-  C* sb = reinterpret_cast<C*>(smem_raw);   // n0 * RC staging for leaf solves
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int64_t r0 = (int64_t)blockIdx.x * RC;
-  if (r0 >= R) return;
-  const int rc = (int)(R - r0 < (int64_t)RC ? R - r0 : (int64_t)RC);
-  for (int ph = 0; ph < nphase; ++ph) {
-    const DPhase P = prog[ph];
-    if (P.kind == PH_LEAF) {
-      const int64_t leaf = P.arg0;
-      C* v = vec + leaf * n0 * R;
-      for (int e = threadIdx.x; e < n0 * RC; e += blockDim.x) {
-        int rr = e % RC, cc = e / RC;
-        sb[e] = (rr < rc) ? v[(int64_t)cc * R + r0 + rr] : mk<T>(0, 0);
-      }
-      __syncthreads();
-      const F* Ti = tinv + leaf * n0 * n0;
-      for (int r = threadIdx.x; r < n0; r += blockDim.x) {
-        C acc[RC];
-#pragma unroll
-        for (int rr = 0; rr < RC; ++rr) acc[rr] = mk<T>(0, 0);
-#pragma unroll 4
-        for (int cc = 0; cc < n0; ++cc) {
-          C a = P.adj ? ldf_conj<T>(Ti + (int64_t)r * n0 + cc) : ldf<T>(Ti + (int64_t)cc * n0 + r);
-#pragma unroll
-          for (int rr = 0; rr < RC; ++rr) cfma(acc[rr], a, sb[cc * RC + rr]);
-        }
-#pragma unroll
-        for (int rr = 0; rr < RC; ++rr)
-          if (rr < rc) v[(int64_t)r * R + r0 + rr] = acc[rr];
-      }
-    } else if (P.kind == PH_ENTER) {
-      // forward: z_0 = V0 x(column leaf); adjoint: y_0 = U0^H x(row leaf)
-      const DOuter* ops = P.adj ? buout + bf_uout0[P.arg0] : bvout + bf_vout0[P.arg0];
-      for (int o = warp; o < P.count; o += nw) {
-        const DOuter op = ops[o];
-        const C* xl = vec + (int64_t)op.leaf * n0 * R;
-        if (P.adj)
-          op_vlike<T, F, RC, true>(fp + op.blk.moff, ip + op.blk.ioff, op.blk.k, op.blk.c, xl, (int)n0, xl,
-                                   st + (int64_t)op.seg_off * R, R, r0, rc, lane);
-        else
-          op_vlike<T, F, RC, false>(fp + op.blk.moff, ip + op.blk.ioff, op.blk.k, op.blk.c, xl, (int)n0, xl,
-                                    st + (int64_t)op.seg_off * R, R, r0, rc, lane);
-      }
-    } else if (P.kind == PH_ITEMS) {
-      for (int o = warp; o < P.count; o += nw) {
-        const DItem it = items[P.arg0 + o];
-        if (P.adj) op_item<T, F, RC, true>(it, fp, ip, st, R, r0, rc, lane);
-        else op_item<T, F, RC, false>(it, fp, ip, st, R, r0, rc, lane);
-      }
-    } else {   // PH_EXIT: b(leaf) -= U0 y_0 (forward) or V0^H z_0 (adjoint)
-      const DOuter* ops = P.adj ? bvout + bf_vout0[P.arg0] : buout + bf_uout0[P.arg0];
-      for (int o = warp; o < P.count; o += nw) {
-        const DOuter op = ops[o];
-        C* bl = vec + (int64_t)op.leaf * n0 * R;
-        for (int r = lane; r < n0; r += 32) {
-          C acc[RC];
-#pragma unroll
-          for (int rr = 0; rr < RC; ++rr) acc[rr] = mk<T>(0, 0);
-          if (P.adj)
-            row_contrib<T, F, RC, true>(acc, fp + op.blk.moff, ip + op.blk.ioff, op.blk.k, op.blk.c,
-                                        st + (int64_t)op.seg_off * R, R, r0, rc, r);
-          else
-            row_contrib<T, F, RC, false>(acc, fp + op.blk.moff, ip + op.blk.ioff, op.blk.k, op.blk.c,
-                                         st + (int64_t)op.seg_off * R, R, r0, rc, r);
-          C* d = bl + (int64_t)r * R + r0;
-#pragma unroll
-          for (int rr = 0; rr < RC; ++rr)
-            if (rr < rc) { d[rr].x -= acc[rr].x; d[rr].y -= acc[rr].y; }
-        }
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Layout conversion kernels
 // ---------------------------------------------------------------------------
 template <class S, class D>
@@ -437,19 +346,6 @@ static int apply_impl(const DevFactor& df, bool adj, const void* xv, void* yv, i
   return cudaGetLastError() == cudaSuccess ? HB_OK : HB_ECUDA;
 }
 
-template <class T, class F, int RC>
-static int sweep_impl(const DevFactor& df, int which, void* vecv, int64_t R, void* stv, cudaStream_t s) {
-  using C = typename C2<T>::t;
-  const F* tinv = (const F*)((which == 0 || which == 2) ? df.linv : df.uinv);
-  int grid = (int)((R + RC - 1) / RC);
-  size_t smem = (size_t)df.n0 * RC * sizeof(C);
-  int threads = 256;
-  k_sweep<T, F, RC><<<grid, threads, smem, s>>>(df.prog[which], df.nprog[which], df.n0, df.bvout, df.buout,
-                                                df.bf_vout0, df.bf_uout0, df.items, (const F*)df.fpool, df.ipool,
-                                                tinv, (C*)vecv, (C*)stv, R);
-  return cudaGetLastError() == cudaSuccess ? HB_OK : HB_ECUDA;
-}
-
 template <class T, class F>
 static int apply_dispatch(const DevFactor& df, bool adj, const void* x, void* y, int64_t R, void* st,
                           cudaStream_t s) {
@@ -463,22 +359,6 @@ int launch_apply(const DevFactor& df, Prec p, bool adjoint, const void* x, void*
   if (p == PREC_F64) return apply_dispatch<double, double2>(df, adjoint, x, y, R, state, st);
   if (p == PREC_F32) return apply_dispatch<float, float2>(df, adjoint, x, y, R, state, st);
   return apply_dispatch<double, float2>(df, adjoint, x, y, R, state, st);
-}
-
-int launch_sweep(const DevFactor& df, Prec p, int which, void* vec, int64_t R, void* state, cudaStream_t st) {
-  if (which < 0 || which > 3) return HB_EINVAL;
-  int rpc = df.sweep_rhs_per_cta;
-  if (rpc <= 0) rpc = 1;
-  if (p == PREC_F64) {
-    if (rpc >= 4 && R >= 4) return sweep_impl<double, double2, 4>(df, which, vec, R, state, st);
-    return sweep_impl<double, double2, 1>(df, which, vec, R, state, st);
-  }
-  if (p == PREC_F32) {
-    if (rpc >= 8 && R >= 8) return sweep_impl<float, float2, 8>(df, which, vec, R, state, st);
-    if (rpc >= 4 && R >= 4) return sweep_impl<float, float2, 4>(df, which, vec, R, state, st);
-    return sweep_impl<float, float2, 1>(df, which, vec, R, state, st);
-  }
-  return sweep_impl<double, float2, 1>(df, which, vec, R, state, st);
 }
 
 }  // namespace hb
