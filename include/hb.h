@@ -133,6 +133,22 @@ int hb_tree(hb_factor_t f, int64_t* node_begin, int64_t* node_end);
  * top).  Errors: HB_EINVAL (null, nrhs < 1, ld < N), HB_ECUDA. */
 int hb_apply(hb_factor_t f, int op, const void* x, void* y, int64_t nrhs, int64_t ld, void* stream);
 
+/* hb_apply_noalloc -- the same product as hb_apply (same kernels, same
+ * arguments, same result), for callers that must not let the library
+ * allocate device memory: for instance a framework whose caching allocator
+ * owns the whole device-memory budget, or a service that may not allocate
+ * after start-up.  The paper has no counterpart; this is an interface
+ * convenience.  Scratch comes from one fixed 16 MiB device array that every
+ * GPU loading the library holds until the process exits; the call performs
+ * no cudaMalloc / cudaFree.  The first call on each device looks up that
+ * array's device address (cudaGetSymbolAddress, with the device current);
+ * make that first call before any stream capture.  All calls share the
+ * array: calls that may overlap on the GPU (other streams, other threads)
+ * race and must be serialised by the caller.  Requests needing more than
+ * 16 MiB of scratch (butterfly state, plus two reordered blocks when
+ * nrhs > 1) return HB_EINVAL with the required size in hb_last_error(). */
+int hb_apply_noalloc(hb_factor_t f, int op, const void* x, void* y, int64_t nrhs, int64_t ld, void* stream);
+
 /* hb_apply_adjoint -- y = A^_F^H x: conjugate-transposed factors applied in
  * reverse stage order (no counterpart in the paper; same as hb_apply with HB_OP_H). */
 int hb_apply_adjoint(hb_factor_t f, const void* x, void* y, int64_t nrhs, int64_t ld, void* stream);

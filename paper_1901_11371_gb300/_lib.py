@@ -56,6 +56,7 @@ SIGNATURES = {
     "hb_tree": (_INT, [_VP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "hb_apply": (_INT, [_VP, _INT, _VP, _VP, _I64, _I64, _VP]),
     "hb_apply_adjoint": (_INT, [_VP, _VP, _VP, _I64, _I64, _VP]),
+    "hb_apply_noalloc": (_INT, [_VP, _INT, _VP, _VP, _I64, _I64, _VP]),
     "hb_precond_solve": (_INT, [_VP, _INT, _VP, _VP, _I64, _I64, _VP]),
     "hb_lower_solve": (_INT, [_VP, _INT, _VP, _VP, _I64, _I64, _VP]),
     "hb_upper_solve": (_INT, [_VP, _INT, _VP, _VP, _I64, _I64, _VP]),

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["hb_kernels.cu", "hb_sweep.cu", "hb_api.cu", "hb_solver.cu"]
+CU_SOURCES = ["hb_kernels.cu", "hb_sweep.cu", "hb_api.cu", "hb_solver.cu", "hb_noalloc.cu"]
 CPP_SOURCES = ["hb_host.cpp"]
 
 
