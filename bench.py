@@ -169,6 +169,7 @@ def run_gpu(args, rank, world):
     f32 = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C64, seed=0)
     t_build = time.perf_counter() - t0
     st = hb.hb_factor_info(f32)
+    tuned = hb.hb_autotune(f32, NRHS)
     phis = W.incidence_angles_deg(3) + (rank * 180.0 / NRHS / max(world, 1) if world > 1 else 0.0)
     b = hb.hb_rhs_plane_wave(f32, phis)
     x = torch.empty_like(b)
@@ -224,12 +225,13 @@ def run_gpu(args, rank, world):
     e2e = {"value": args.steps * NRHS / e_s, "unit": UNIT, "h2d_bytes_per_step": int(b.numel() * 16),
            "d2h_bytes_per_step": int(x.numel() * 16)}
 
-    out = dict(value=value, ms=ms_max, iters=iters, res=res, st=st, t_build=t_build, clocks=clk, e2e=e2e,
+    out = dict(value=value, ms=ms_max, iters=iters, res=res, st=st, t_build=t_build, clocks=clk, e2e=e2e, tuned=tuned,
                n_apply=n_apply, ms_apply=ms_apply, n_sweep=n_sweep, ms_sweep=ms_sweep, n_launch=n_launch,
                x=x)
     # ---- plain FP64 GPU form on the same workload (rank 0 only, untimed by the contract)
     if rank == 0 and not args.no_plain:
         f64 = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C128, seed=0)
+        hb.hb_autotune(f64, PLAIN_NRHS)
         bp = b[:PLAIN_NRHS].contiguous()
         x64 = torch.empty_like(bp)
         _, i64 = solve(f64, bp, x64)
@@ -249,8 +251,59 @@ def run_gpu(args, rank, world):
     return out
 
 
+def run_kernels(args):
+    """Kernel timings (no Krylov loop): hb_apply, one L~ sweep and one U~ sweep on one workload,
+    with algorithmic bytes per launch and the fraction of the measured HBM copy bandwidth."""
+    import torch
+
+    import paper_1901_11371_gb300 as hb
+    from paper_1901_11371_gb300 import build as hb_build
+    hb_build.build()
+    wl = {"spiral": W.CONFIG2, "semicircle": W.CONFIG3, "strips": W.CONFIG4, "strip": W.CONFIG1}[args.workload]
+    R = args.nrhs
+    g = hb.hb_geometry(wl.kind, wl.params, wl.n)
+    f = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C64 if args.form == "c64" else hb.HB_C128)
+    if args.grid_min:
+        hb.lib().hb_set_sweep_grid_min(f._h, args.grid_min)
+    st = hb.hb_factor_info(f)
+    dt = torch.complex64 if args.form == "c64" else torch.complex128
+    x = torch.randn((R, wl.n) if R > 1 else (wl.n,), dtype=dt, device="cuda")
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    hbm, src = _peaks()
+    ms_a = timed(lambda: hb.hb_apply(f, x), args.steps)
+    ms_l = timed(lambda: hb.hb_lower_solve(f, x), args.steps)
+    ms_u = timed(lambda: hb.hb_upper_solve(f, x), args.steps)
+    eb = 8 if args.form == "c64" else 16
+    vec_extra = 2 * wl.n * (R - 1) * eb
+    out = {"mode": "kernels", "workload": wl.name, "nrhs": R, "form": args.form, "grid_min": args.grid_min or 16,
+           "apply_ms": ms_a, "lower_ms": ms_l, "upper_ms": ms_u,
+           "apply_GBps": (st["apply_bytes"] + vec_extra) / ms_a / 1e6,
+           "lower_GBps": (st["lower_bytes"] + vec_extra) / ms_l / 1e6,
+           "apply_frac": (st["apply_bytes"] + vec_extra) / ms_a / 1e6 / hbm, "peak_GBps": hbm, "peak_source": src,
+           "apply_bytes": st["apply_bytes"], "lower_bytes": st["lower_bytes"], "kmax": st["kmax"],
+           "kavg": st["kavg"], "device_bytes": st["device_bytes"]}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--mode", default="solve", choices=["solve", "kernels"])
+    ap.add_argument("--workload", default="spiral", choices=["spiral", "semicircle", "strips", "strip"])
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--form", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--grid-min", type=int, default=0)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -260,6 +313,9 @@ def main():
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.mode == "kernels":
+        run_kernels(args)
+        return
 
     if args.impl == "reference":
         if rank != 0:
@@ -311,7 +367,7 @@ def main():
         "config": {"workload": "semicircle_N262144: R = 6553.6/pi lambda, phi in [0, pi], N=262144, leaf 64, "
                                "eps 1e-6, 256 plane waves phi_i = 180 i/256 deg per step",
                    "form": f"FP64 FGMRES({RESTART}) + IR around complex-FP32 U~^-1 L~^-1 and A_F (CUDA cores)",
-                   "rhs_per_step": NRHS,
+                   "rhs_per_step": NRHS, "sweep_grid_min": out["tuned"],
                    "l2": f"inputs larger than L2: factor {st['device_bytes'] / 1e6:.0f} MB",
                    "kmax": st["kmax"], "kavg": round(st["kavg"], 2), "build_s": round(out["t_build"], 2)},
         "iters_per_solve": out["iters"], "true_rel_res": out["res"],

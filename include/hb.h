@@ -205,6 +205,15 @@ int hb_monostatic(hb_factor_t f, const void* x, int64_t nrhs, int64_t ld, const 
  * legacy default stream.  Returns the previous value (>= 1) or an error code. */
 int hb_set_sweep_grid_min(hb_factor_t f, int grid_min);
 
+/* hb_autotune -- time the sweep kernel for nrhs right-hand sides under each
+ * candidate split between grid-wide and single-CTA phases (thresholds 4, 8,
+ * 16, 32, 64 ops, and "all single-CTA"), keep the fastest for calls with one
+ * right-hand side (nrhs == 1) or with several (nrhs > 1), and report the
+ * chosen threshold in *chosen (may be NULL).  Synchronises `stream`; uses the
+ * factor's workspace.  hb_set_sweep_grid_min clears the tuned choice.
+ * Not in the paper: launch-configuration tuning. */
+int hb_autotune(hb_factor_t f, int64_t nrhs, void* stream, int* chosen);
+
 /* hb_set_wait_limit -- iteration limit of every bounded device-side wait
  * (the sweep kernel's grid barrier; default 2^24 polls, about a second).
  * hb_status -- synchronise `stream`, then return HB_ETIMEOUT (and clear the

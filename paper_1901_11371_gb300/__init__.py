@@ -22,7 +22,7 @@ __all__ = ["HB_STRIP", "HB_SPIRAL", "HB_ARC", "HB_PARALLEL_STRIPS", "HB_C128", "
            "HB_OP_N", "HB_OP_H", "HBError", "Geometry", "Factor", "hb_geometry", "hb_factor", "hb_factor_host",
            "hb_factor_info", "hb_tree", "hb_apply", "hb_apply_adjoint", "hb_precond_solve", "hb_lower_solve",
            "hb_upper_solve", "hb_residual", "hb_gmres", "hb_rhs_plane_wave", "hb_far_field", "hb_monostatic",
-           "hb_host_apply", "hb_host_sweep", "hb_profile", "hb_profile_read", "lib"]
+           "hb_host_apply", "hb_host_sweep", "hb_profile", "hb_profile_read", "hb_autotune", "lib"]
 
 
 def lib():
@@ -221,6 +221,13 @@ def hb_monostatic(f, x, phi_deg, stream=None):
     _lib.check(lib().hb_monostatic(f._h, C.c_void_p(x.data_ptr()), R, f.n, phi.ctypes.data_as(C.POINTER(C.c_double)),
                                    C.c_void_p(out.data_ptr()), _stream(stream)))
     return out
+
+
+def hb_autotune(f, nrhs, stream=None):
+    """Pick the fastest sweep segmentation for `nrhs` right-hand sides; returns the chosen threshold."""
+    ch = C.c_int()
+    _lib.check(lib().hb_autotune(f._h, int(nrhs), _stream(stream), C.byref(ch)))
+    return ch.value
 
 
 def hb_profile(f, enable=True):

@@ -67,6 +67,7 @@ SIGNATURES = {
     "hb_monostatic": (_INT, [_VP, _VP, _I64, _I64, C.POINTER(C.c_double), _VP, _VP]),
     "hb_set_sweep_grid_min": (_INT, [_VP, _INT]),
     "hb_set_wait_limit": (_INT, [_VP, C.c_longlong]),
+    "hb_autotune": (_INT, [_VP, _I64, _VP, C.POINTER(C.c_int)]),
     "hb_status": (_INT, [_VP, _VP]),
     "hb_profile": (_INT, [_VP, _INT]),
     "hb_profile_read": (_INT, [_VP, _INT, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),

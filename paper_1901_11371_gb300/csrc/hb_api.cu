@@ -97,10 +97,24 @@ int upload_factor(const PackedHost& ph, const HostFactor& hf, const Geometry& g,
   for (int i = 0; i < 4; ++i) {
     if ((rc = up(*progs[i], &df.prog[i], st, df.device_bytes))) return rc;
     df.nprog[i] = (int)progs[i]->size();
+    FlatProgram fpg = flatten_program(ph, *progs[i], ph.n0);
+    if ((rc = up(fpg.ops, &df.flat[i], st, df.device_bytes))) return rc;
+    if ((rc = up(fpg.base, &df.flat_base[i], st, df.device_bytes))) return rc;
+    HB_CU(cudaStreamSynchronize(st));
   }
   HB_CU(cudaMalloc(&df.bar, 64));
   HB_CU(cudaMemsetAsync(df.bar, 0, 64, st));
   if ((rc = set_grid_min(df, ph, 16, st))) return rc;
+  for (int i = 0; i < 4; ++i) {
+    FlatProgram fpg = flatten_program(ph, *progs[i], ph.n0);
+    for (int c = 0; c < DevFactor::kNCand; ++c) {
+      std::vector<DSeg> segs = segment_program(*progs[i], DevFactor::kCand[c]);
+      annotate_segments(segs, fpg);
+      if ((rc = up(segs, &df.cand_segs[i][c], st, df.device_bytes))) return rc;
+      df.cand_nsegs[i][c] = (int)segs.size();
+    }
+    HB_CU(cudaStreamSynchronize(st));
+  }
   if ((rc = up(g.cx, &df.cx, st, df.device_bytes))) return rc;
   if ((rc = up(g.cy, &df.cy, st, df.device_bytes))) return rc;
   if ((rc = up(g.w, &df.w, st, df.device_bytes))) return rc;
@@ -113,6 +127,7 @@ int set_grid_min(DevFactor& df, const PackedHost& ph, int grid_min, cudaStream_t
   HB_CU(cudaStreamSynchronize(st));
   for (int i = 0; i < 4; ++i) {
     std::vector<DSeg> segs = segment_program(*progs[i], grid_min);
+    annotate_segments(segs, flatten_program(ph, *progs[i], ph.n0));
     if (df.segs[i]) { cudaFree(df.segs[i]); df.segs[i] = nullptr; }
     int64_t dummy = 0;
     int rc = up(segs, &df.segs[i], st, dummy);
@@ -128,6 +143,13 @@ void free_factor(DevFactor& df) {
   void* ptrs[] = {df.fpool, df.leaf, df.linv, df.uinv, df.ipool, df.vout, df.uout, df.bvout, df.buout,
                   df.bf_vout0, df.bf_uout0, df.items, df.step_idx, df.astep_idx, df.prog[0], df.prog[1],
                   df.prog[2], df.prog[3], df.segs[0], df.segs[1], df.segs[2], df.segs[3], df.bar,
+                  df.flat[0], df.flat[1], df.flat[2], df.flat[3], df.flat_base[0], df.flat_base[1],
+                  df.flat_base[2], df.flat_base[3],
+                  df.cand_segs[0][0], df.cand_segs[0][1], df.cand_segs[0][2], df.cand_segs[0][3], df.cand_segs[0][4],
+                  df.cand_segs[0][5], df.cand_segs[1][0], df.cand_segs[1][1], df.cand_segs[1][2], df.cand_segs[1][3],
+                  df.cand_segs[1][4], df.cand_segs[1][5], df.cand_segs[2][0], df.cand_segs[2][1], df.cand_segs[2][2],
+                  df.cand_segs[2][3], df.cand_segs[2][4], df.cand_segs[2][5], df.cand_segs[3][0], df.cand_segs[3][1],
+                  df.cand_segs[3][2], df.cand_segs[3][3], df.cand_segs[3][4], df.cand_segs[3][5],
                   df.cx, df.cy, df.w};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -341,9 +363,44 @@ int hb_tree(hb_factor_t f, int64_t* node_begin, int64_t* node_end) {
 
 int hb_set_sweep_grid_min(hb_factor_t f, int grid_min) {
   if (!f || f->host_only || grid_min < 1) { set_error("hb_set_sweep_grid_min: bad argument"); return HB_EINVAL; }
+  f->df.tuned[0] = f->df.tuned[1] = -1;
   int old = f->df.grid_min;
   int rc = set_grid_min(f->df, f->ph, grid_min, nullptr);
   return rc ? rc : old;
+}
+
+int hb_autotune(hb_factor_t f, int64_t nrhs, void* stream, int* chosen) {
+  if (!f || f->host_only || nrhs < 1) { set_error("hb_autotune: bad argument"); return HB_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  DevFactor& df = f->df;
+  const Prec p = df.form == HB_C128 ? PREC_F64 : PREC_F32;
+  const size_t es = p == PREC_F32 ? 8 : 16;
+  void* v = f->ws.get(WS_VEC0, (size_t)df.n * nrhs * es);
+  if (!v) { set_error("hb_autotune: workspace allocation failed"); return HB_ENOMEM; }
+  if (cudaMemsetAsync(v, 0, (size_t)df.n * nrhs * es, st) != cudaSuccess) return HB_ECUDA;
+  const int cls = nrhs > 1 ? 1 : 0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int bestc = -1;
+  for (int c = 0; c < DevFactor::kNCand; ++c) {
+    df.tuned[cls] = c;
+    int rc = sweep_internal(f, p, 0, v, nrhs, st);   // warm
+    if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 2; ++r) sweep_internal(f, p, 0, v, nrhs, st);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; bestc = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  df.tuned[cls] = bestc;
+  if (chosen) *chosen = DevFactor::kCand[bestc];
+  return hb_status(f, stream);
 }
 
 int hb_set_wait_limit(hb_factor_t f, long long spins) {

@@ -34,9 +34,17 @@ struct DevFactor {
   std::vector<int32_t> step_ptr, astep_ptr;   // host copies (launch sizes)
   DPhase* prog[4] = {nullptr, nullptr, nullptr, nullptr};   // lower, upper, lower^H, upper^H
   int nprog[4] = {0, 0, 0, 0};
+  FlatOp* flat[4] = {nullptr, nullptr, nullptr, nullptr};   // resolved op records of each program
+  int32_t* flat_base[4] = {nullptr, nullptr, nullptr, nullptr};
   DSeg* segs[4] = {nullptr, nullptr, nullptr, nullptr};     // cooperative-kernel segments of each program
   int nsegs[4] = {0, 0, 0, 0};
   int grid_min = 0;                                         // phases with >= grid_min ops run grid-wide
+  // autotuner: segmentations of each program for the candidate thresholds
+  static constexpr int kNCand = 6;
+  static constexpr int kCand[kNCand] = {4, 8, 16, 32, 64, 1 << 30};
+  DSeg* cand_segs[4][kNCand] = {};
+  int cand_nsegs[4][kNCand] = {};
+  int tuned[2] = {-1, -1};                                  // chosen candidate for 1 RHS / several RHS (-1: grid_min)
   void* bar = nullptr;                                      // grid barrier state + error flag
   long long spin_limit = 1LL << 24;                         // bounded waits of the grid barrier
   // geometry on the device (far field, plane waves)

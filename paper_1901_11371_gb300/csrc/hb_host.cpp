@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <climits>
 #include <numeric>
 
 #ifdef _OPENMP
@@ -508,17 +509,41 @@ void pack_factor(const HostFactor& hf, PackedHost& ph) {
   std::vector<int> kmax_d(D, 0);
   // per step item lists for the apply
   std::vector<std::vector<int32_t>> fsteps(D + 2), asteps(D + 2);
+  // butterfly state in post-order of the cluster tree (both subtrees, then the
+  // node's F12 and F21), so the state of every subtree is one contiguous range
+  std::vector<int64_t> st_base(nbf, 0);
+  {
+    int64_t cur = 0;
+    std::function<void(int, int64_t)> alloc = [&](int v, int64_t p) {
+      if (v == D) return;
+      alloc(v + 1, 2 * p);
+      alloc(v + 1, 2 * p + 1);
+      for (int kind = 0; kind < 2; ++kind) {
+        int64_t id = bf_id(v, p, kind);
+        const Butterfly& B = hf.bf[id];
+        st_base[id] = cur;
+        const int64_t np = (int64_t)1 << B.L;
+        for (int l = 0; l < B.hc; ++l)
+          for (int64_t g = 0; g < np; ++g) cur += B.col[l][g].k;
+        for (int l = 0; l < B.hr; ++l)
+          for (int64_t g = 0; g < np; ++g) cur += B.row[l][g].k;
+      }
+    };
+    alloc(0, 0);
+    state = cur;
+  }
   for (int64_t id = 0; id < nbf; ++id) {
     const Butterfly& B = hf.bf[id];
     const int L = B.L;
     const int64_t np = (int64_t)1 << L;
     ph.bf_L[id] = L;
+    int64_t sb = st_base[id];
     // state offsets of every pair vector
     std::vector<std::vector<int32_t>> zoff(B.hc, std::vector<int32_t>(np)), yoff(B.hr, std::vector<int32_t>(np));
     for (int l = 0; l < B.hc; ++l)
-      for (int64_t g = 0; g < np; ++g) { zoff[l][g] = (int32_t)state; state += B.col[l][g].k; }
+      for (int64_t g = 0; g < np; ++g) { zoff[l][g] = (int32_t)sb; sb += B.col[l][g].k; }
     for (int l = 0; l < B.hr; ++l)
-      for (int64_t g = 0; g < np; ++g) { yoff[l][g] = (int32_t)state; state += B.row[l][g].k; }
+      for (int64_t g = 0; g < np; ++g) { yoff[l][g] = (int32_t)sb; sb += B.row[l][g].k; }
     // rank statistics
     for (int l = 0; l < B.hc; ++l)
       for (auto& b : B.col[l]) { ksum += b.k; kcnt++; kmax = std::max(kmax, b.k); ksum_d[B.depth] += b.k; kcnt_d[B.depth]++; kmax_d[B.depth] = std::max(kmax_d[B.depth], b.k); }
@@ -625,21 +650,48 @@ void pack_factor(const HostFactor& hf, PackedHost& ph) {
     ph.astep_ptr.push_back((int32_t)ph.astep_idx.size());
   }
   // sweep programs (recursion of Algs. 3 and 4, and their adjoints)
+  auto blk_bytes = [](const DBlk& b) { return (int64_t)b.k * (b.c - b.k) * 16 + (int64_t)4 * b.c + 32; };
+  auto outer_phase = [&](int kind, int64_t id, bool adj) {
+    bool use_u = ((kind == PH_ENTER) == adj);
+    const DOuter* ops = use_u ? &ph.buout[ph.bf_uout0[id]] : &ph.bvout[ph.bf_vout0[id]];
+    int64_t mb = 0;
+    int vm = 0;
+    for (int o = 0; o < ph.bf_mb[id]; ++o) {
+      mb = std::max(mb, blk_bytes(ops[o].blk));
+      vm = std::max(vm, kind == PH_ENTER ? (int)ops[o].blk.c : (int)ops[o].blk.k);
+    }
+    return DPhase{kind, (int32_t)id, ph.bf_mb[id], adj ? 1 : 0, (int32_t)std::min<int64_t>(mb, INT32_MAX), vm};
+  };
   auto emit_bf = [&](std::vector<DPhase>& prog, int64_t id, bool adj) {
     int L = ph.bf_L[id];
     int base = ph.bf_step_base[id];
-    prog.push_back(DPhase{PH_ENTER, (int32_t)id, ph.bf_mb[id], adj ? 1 : 0});
+    prog.push_back(outer_phase(PH_ENTER, id, adj));
     for (int t = 1; t <= L + 1; ++t) {
       int s = adj ? (L + 2 - t) : t;
       int32_t b0 = ph.bf_steps[base + s - 1], b1 = ph.bf_steps[base + s];
-      prog.push_back(DPhase{PH_ITEMS, b0, b1 - b0, adj ? 1 : 0});
+      int64_t mb = 0;
+      int vm = 0;
+      for (int32_t e = b0; e < b1; ++e) {
+        const DItem& it = ph.items[e];
+        if (it.type == 1) {
+          mb = std::max(mb, (int64_t)it.a_k[0] * it.b_k[0] * 16 + 32);
+          vm = std::max(vm, (int)std::max(it.a_k[0], it.b_k[0]));
+        } else {
+          mb = std::max(mb, blk_bytes(it.blk[0]) + blk_bytes(it.blk[1]));
+          vm = std::max(vm, std::max(it.a_k[0] + it.a_k[1], it.b_k[0] + it.b_k[1]));
+        }
+      }
+      prog.push_back(DPhase{PH_ITEMS, b0, b1 - b0, adj ? 1 : 0, (int32_t)std::min<int64_t>(mb, INT32_MAX), vm});
     }
-    prog.push_back(DPhase{PH_EXIT, (int32_t)id, ph.bf_mb[id], adj ? 1 : 0});
+    prog.push_back(outer_phase(PH_EXIT, id, adj));
   };
   ph.prog_lower.clear(); ph.prog_upper.clear(); ph.prog_lower_adj.clear(); ph.prog_upper_adj.clear();
   // lower: left child, F21, right child
   std::function<void(int, int64_t, std::vector<DPhase>&, int)> rec = [&](int v, int64_t p, std::vector<DPhase>& prog, int mode) {
-    if (v == D) { prog.push_back(DPhase{PH_LEAF, (int32_t)p, 1, (mode >= 2) ? 1 : 0}); return; }
+    if (v == D) {
+      prog.push_back(DPhase{PH_LEAF, (int32_t)p, 1, (mode >= 2) ? 1 : 0, (int32_t)(hf.n0 * hf.n0 * 16), (int32_t)hf.n0});
+      return;
+    }
     int64_t lo = 2 * p, hi = 2 * p + 1;
     switch (mode) {
       case 0:  rec(v + 1, lo, prog, mode); emit_bf(prog, bf_id(v, p, 1), false); rec(v + 1, hi, prog, mode); break;  // L~^{-1}
@@ -806,19 +858,134 @@ struct HostExec {
 };
 }  // namespace
 
+FlatProgram flatten_program(const PackedHost& ph, const std::vector<DPhase>& prog, int64_t n0) {
+  FlatProgram fp;
+  fp.base.reserve(prog.size() + 1);
+  auto blkm = [](const DBlk& b) { return (int64_t)b.k * (b.c - b.k); };
+  for (const DPhase& P : prog) {
+    fp.base.push_back((int32_t)fp.ops.size());
+    const bool adj = P.adj != 0;
+    for (int o = 0; o < P.count; ++o) {
+      FlatOp f{};
+      if (P.kind == PH_LEAF) {
+        f.kind = FK_LEAF;
+        f.flags = (int16_t)(adj ? FF_ADJ : 0);
+        f.moff = (int64_t)P.arg0 * n0 * n0;
+        f.melems = (int32_t)(n0 * n0);
+        f.ioff = -1;
+        f.c0 = (int16_t)n0;
+        f.src0 = (int32_t)(P.arg0 * n0);
+        f.n_s0 = (int32_t)n0;
+        f.out0 = f.src0;
+      } else if (P.kind == PH_ENTER || P.kind == PH_EXIT) {
+        const bool enter = P.kind == PH_ENTER;
+        const bool use_u = (enter == adj);
+        const DOuter& op = use_u ? ph.buout[ph.bf_uout0[P.arg0] + o] : ph.bvout[ph.bf_vout0[P.arg0] + o];
+        f.moff = op.blk.moff;
+        f.melems = (int32_t)blkm(op.blk);
+        f.ioff = op.blk.ioff;
+        f.ielems = 2 * op.blk.c;
+        f.k0 = op.blk.k;
+        f.c0 = op.blk.c;
+        if (enter) {
+          f.kind = FK_GATHER;
+          f.flags = (int16_t)((adj ? FF_CONJ : 0) | FF_SRC_VEC);
+          f.src0 = (int32_t)(op.leaf * n0);
+          f.n_s0 = op.blk.c;
+          f.out0 = op.seg_off;
+        } else {
+          f.kind = FK_SCATTER;
+          f.flags = (int16_t)((adj ? FF_CONJ : 0) | FF_SUB | FF_OUT_VEC);
+          f.src0 = op.seg_off;
+          f.n_s0 = op.blk.k;
+          f.out0 = (int32_t)(op.leaf * n0);
+          f.split = op.blk.c;
+        }
+      } else {
+        const DItem& it = ph.items[P.arg0 + o];
+        if (it.type == 1) {
+          f.kind = FK_MIDDLE;
+          f.flags = (int16_t)(adj ? FF_ADJ : 0);
+          f.moff = it.blk[0].moff;
+          f.melems = it.a_k[0] * it.b_k[0];
+          f.ioff = -1;
+          f.k0 = it.b_k[0];
+          f.c0 = it.a_k[0];
+          f.src0 = adj ? it.b_off[0] : it.a_off[0];
+          f.n_s0 = adj ? it.b_k[0] : it.a_k[0];
+          f.out0 = adj ? it.a_off[0] : it.b_off[0];
+        } else {
+          const DBlk& b0 = it.blk[0];
+          const DBlk& b1 = it.blk[1];
+          f.moff = b0.moff;
+          f.m1 = (int32_t)(b1.moff - b0.moff);
+          f.melems = (int32_t)(f.m1 + blkm(b1));
+          f.ioff = b0.ioff;
+          f.i1 = b1.ioff - b0.ioff;
+          f.ielems = f.i1 + 2 * b1.c;
+          f.k0 = b0.k; f.c0 = b0.c; f.k1 = b1.k; f.c1 = b1.c;
+          const bool to_b = (it.type == 0) != adj;
+          if (to_b) {
+            f.kind = FK_GATHER;
+            f.flags = (int16_t)(FF_TWO | (it.type == 2 ? FF_CONJ : 0));
+            f.src0 = it.a_off[0]; f.n_s0 = it.a_k[0];
+            f.src1 = it.a_off[1]; f.n_s1 = it.a_k[1];
+            f.out0 = it.b_off[0]; f.out1 = it.b_off[1];
+          } else {
+            f.kind = FK_SCATTER;
+            f.flags = (int16_t)(FF_TWO | (it.type == 0 ? FF_CONJ : 0));
+            f.src0 = it.b_off[0]; f.n_s0 = it.b_k[0];
+            f.src1 = it.b_off[1]; f.n_s1 = it.b_k[1];
+            f.out0 = it.a_off[0]; f.out1 = it.a_off[1];
+            f.split = it.a_k[0];
+          }
+        }
+      }
+      fp.ops.push_back(f);
+    }
+  }
+  fp.base.push_back((int32_t)fp.ops.size());
+  return fp;
+}
+
+void annotate_segments(std::vector<DSeg>& segs, const FlatProgram& fp) {
+  for (DSeg& sg : segs) {
+    sg.row_lo = sg.st_lo = INT32_MAX;
+    sg.row_hi = sg.st_hi = 0;
+    if (sg.grid) { sg.row_lo = sg.st_lo = 0; continue; }
+    for (int32_t o = fp.base[sg.first]; o < fp.base[sg.first + sg.count]; ++o) {
+      const FlatOp& f = fp.ops[o];
+      auto row = [&](int32_t a, int32_t n) { sg.row_lo = std::min(sg.row_lo, a); sg.row_hi = std::max(sg.row_hi, a + n); };
+      auto stt = [&](int32_t a, int32_t n) { if (n > 0) { sg.st_lo = std::min(sg.st_lo, a); sg.st_hi = std::max(sg.st_hi, a + n); } };
+      const int n_out0 = (f.kind == FK_GATHER) ? f.k0 : (f.kind == FK_SCATTER) ? ((f.flags & FF_TWO) ? f.split : f.c0)
+                       : (f.kind == FK_MIDDLE) ? ((f.flags & FF_ADJ) ? f.c0 : f.k0) : f.c0;
+      const int n_out1 = (f.kind == FK_GATHER && (f.flags & FF_TWO)) ? f.k1
+                       : (f.kind == FK_SCATTER && (f.flags & FF_TWO)) ? f.c0 - f.split : 0;
+      if (f.kind == FK_LEAF) { row(f.src0, f.n_s0); continue; }
+      if (f.flags & FF_SRC_VEC) row(f.src0, f.n_s0); else stt(f.src0, f.n_s0);
+      stt(f.src1, f.n_s1);
+      if (f.flags & FF_OUT_VEC) row(f.out0, n_out0); else stt(f.out0, n_out0);
+      stt(f.out1, n_out1);
+    }
+    if (sg.row_lo > sg.row_hi) sg.row_lo = sg.row_hi = 0;
+    if (sg.st_lo > sg.st_hi) sg.st_lo = sg.st_hi = 0;
+  }
+}
+
 std::vector<DSeg> segment_program(const std::vector<DPhase>& prog, int grid_min) {
   std::vector<DSeg> segs;
   int n = (int)prog.size();
   int i = 0;
+  // grid-wide: many ops, or vector operands too wide for a warp's staging slice
+  auto big = [&](const DPhase& P) { return P.kind != PH_LEAF && (P.count >= grid_min || P.vmax > 128); };
   while (i < n) {
-    bool big = prog[i].kind != PH_LEAF && prog[i].count >= grid_min;
-    if (big) {
-      segs.push_back(DSeg{1, i, 1, 0});
+    if (big(prog[i])) {
+      segs.push_back(DSeg{1, i, 1, 0, 0, 0, 0, 0});
       ++i;
     } else {
       int j = i;
-      while (j < n && !(prog[j].kind != PH_LEAF && prog[j].count >= grid_min)) ++j;
-      segs.push_back(DSeg{0, i, j - i, 0});
+      while (j < n && !big(prog[j])) ++j;
+      segs.push_back(DSeg{0, i, j - i, 0, 0, 0, 0, 0});
       i = j;
     }
   }

@@ -133,6 +133,8 @@ struct DPhase {
   int32_t arg0;
   int32_t count;
   int32_t adj;       // 1 = adjoint direction of the ops
+  int32_t mbytes;    // largest factor bytes (matrices + indices) of one op, complex128 storage
+  int32_t vmax;      // largest vector operand (entries per right-hand side) of one op
 };
 
 // A segment of a sweep program for the cooperative sweep kernel: either one
@@ -143,6 +145,34 @@ struct DSeg {
   int32_t first;     // first phase index
   int32_t count;     // number of phases
   int32_t pad;
+  // single-CTA runs: the vector rows and butterfly-state entries the run
+  // touches ([row_lo, row_hi), [st_lo, st_hi)); the kernel keeps them in
+  // shared memory for the whole run when they fit.
+  int32_t row_lo, row_hi, st_lo, st_hi;
+};
+
+// A fully resolved sweep op (built on the host per program, in program order),
+// so the kernel needs a single record per op.  Element offsets/counts refer to
+// the factor pool (or, for leaf ops, the leaf-inverse array) in elements of the
+// storage type and to the index pool in int16 entries.
+enum FlatKind : int16_t { FK_GATHER = 0, FK_SCATTER = 1, FK_MIDDLE = 2, FK_LEAF = 3 };
+enum FlatFlag : int16_t { FF_CONJ = 1, FF_SUB = 2, FF_ADJ = 4, FF_SRC_VEC = 8, FF_OUT_VEC = 16, FF_TWO = 32 };
+struct FlatOp {
+  int64_t moff;      // first element to stage
+  int32_t melems;    // elements to stage (both blocks and the gap between them)
+  int32_t m1;        // element offset of block 1 inside the staged matrices
+  int32_t ioff;      // first index entry to stage (-1: none)
+  int32_t ielems;    // index entries to stage
+  int32_t i1;        // offset of block 1's indices
+  int16_t kind, flags;
+  int16_t k0, c0, k1, c1;   // FK_MIDDLE: k0 = k_r, c0 = k_c; FK_LEAF: c0 = n0
+  int32_t src0, n_s0, src1, n_s1;   // vector operand segments (state entries or vec rows)
+  int32_t out0, out1, split;        // outputs (state entries or vec rows), scatter split row
+  int32_t pad;
+};
+struct FlatProgram {
+  std::vector<FlatOp> ops;
+  std::vector<int32_t> base;   // base[ph] = first op of phase ph; base[nphase] = total
 };
 
 // Split a program into segments: phases with at least grid_min ops run grid-wide.
@@ -182,6 +212,9 @@ struct PackedHost {
 };
 
 void pack_factor(const HostFactor& hf, PackedHost& ph);
+FlatProgram flatten_program(const PackedHost& ph, const std::vector<DPhase>& prog, int64_t n0);
+// fill the row / state ranges of the single-CTA runs
+void annotate_segments(std::vector<DSeg>& segs, const FlatProgram& fp);
 
 // FP64 host execution of the packed program (verification without a GPU).
 void host_apply(const PackedHost& ph, const HostFactor& hf, bool adj, const cplx* x, cplx* y);

@@ -117,7 +117,7 @@ __device__ bool grid_sync(GridBar* gb, unsigned& my_gen, long long spin_limit) {
 // B side = gather + T * rest (V-type layout M[j*k+i]; or U-type adjoint conj(M[i*nr+j]))
 template <class T, class F, int RC, bool UADJ>
 __device__ __forceinline__ void vlike(const F* M, const int16_t* idx, int k, int c,
-                                      const typename CT<T>::t* cand /* [c][RC] smem */,
+                                      const typename CT<T>::t* cand /* [c][vs] smem */, int vs,
                                       typename CT<T>::t* out, int64_t R, int64_t r0, int rc, const Grp& g) {
   using C = typename CT<T>::t;
   const int nr = c - k;
@@ -125,11 +125,11 @@ __device__ __forceinline__ void vlike(const F* M, const int16_t* idx, int k, int
     C acc[RC];
     const int qi = idx[i];
 #pragma unroll
-    for (int rr = 0; rr < RC; ++rr) acc[rr] = cand[qi * RC + rr];
+    for (int rr = 0; rr < RC; ++rr) acc[rr] = cand[qi * vs + rr];
 #pragma unroll 8
     for (int j = 0; j < nr; ++j) {
       C m = UADJ ? cvc<T>(M[(int64_t)i * nr + j]) : cv<T>(M[(int64_t)j * k + i]);
-      const C* s = cand + idx[k + j] * RC;
+      const C* s = cand + idx[k + j] * vs;
 #pragma unroll
       for (int rr = 0; rr < RC; ++rr) fma2(acc[rr], m, s[rr]);
     }
@@ -142,29 +142,44 @@ __device__ __forceinline__ void vlike(const F* M, const int16_t* idx, int k, int
 // candidate entry r of one block (U-type layout M[i*nr+j]; or V-type adjoint conj(M[j*k+i]))
 template <class T, class F, int RC, bool VADJ>
 __device__ __forceinline__ void rowc(typename CT<T>::t (&acc)[RC], const F* M, const int16_t* idx, int k, int c,
-                                     const typename CT<T>::t* y /* [k][RC] smem */, int r) {
+                                     const typename CT<T>::t* y /* [k][vs] smem */, int vs, int r) {
   using C = typename CT<T>::t;
   const int code = idx[c + r];
   if (code >= 0) {
 #pragma unroll
-    for (int rr = 0; rr < RC; ++rr) { acc[rr].x += y[code * RC + rr].x; acc[rr].y += y[code * RC + rr].y; }
+    for (int rr = 0; rr < RC; ++rr) { acc[rr].x += y[code * vs + rr].x; acc[rr].y += y[code * vs + rr].y; }
   } else {
     const int j = -1 - code, nr = c - k;
 #pragma unroll 8
     for (int i = 0; i < k; ++i) {
       C m = VADJ ? cvc<T>(M[(int64_t)j * k + i]) : cv<T>(M[(int64_t)i * nr + j]);
 #pragma unroll
-      for (int rr = 0; rr < RC; ++rr) fma2(acc[rr], m, y[i * RC + rr]);
+      for (int rr = 0; rr < RC; ++rr) fma2(acc[rr], m, y[i * vs + rr]);
     }
   }
 }
 
-// load `cnt` vector entries (stride R, RHS r0..r0+rc) into smem [cnt][RC] (zero padded)
-template <class C, int RC>
-__device__ __forceinline__ void load_vec(C* dst, const C* src, int cnt, int64_t R, int64_t r0, int rc, const Grp& g) {
-  for (int e = g.t; e < cnt * RC; e += g.nt) {
-    int i = e / RC, rr = e % RC;
-    dst[e] = (rr < rc) ? ldcg2(src + (int64_t)i * R + r0 + rr) : C{0, 0};
+// Stage `cnt` vector entries, right-hand sides [r0, r0+width), from global
+// (row stride R) into shared memory rows of stride W (>= width).  Rows that
+// are 16-byte aligned and sized go through cp.async (asynchronous; completed by
+// cp_commit_wait), other rows through L1-bypassing loads.
+template <class C>
+__device__ __forceinline__ void stage_vec(C* dst, const C* src, int cnt, int64_t R, int64_t r0, int width, int W,
+                                          const Grp& g, bool noasync = false) {
+  const int64_t rowb = (int64_t)width * sizeof(C);
+  const bool vec16 = !noasync && ((rowb & 15) == 0) && ((((uintptr_t)(src + r0)) & 15) == 0) && (((R * sizeof(C)) & 15) == 0) &&
+                     ((((int64_t)W * sizeof(C)) & 15) == 0);
+  if (vec16) {
+    const int per = (int)(rowb >> 4);
+    for (int e = g.t; e < cnt * per; e += g.nt) {
+      const int i = e / per, q = e % per;
+      cp16((char*)(dst + (int64_t)i * W) + 16 * q, (const char*)(src + (int64_t)i * R + r0) + 16 * q);
+    }
+  } else {
+    for (int e = g.t; e < cnt * width; e += g.nt) {
+      const int i = e / width, rr = e % width;
+      dst[(int64_t)i * W + rr] = ldcg2(src + (int64_t)i * R + r0 + rr);
+    }
   }
 }
 
@@ -172,6 +187,8 @@ struct SweepArgs {
   const DSeg* segs;
   int nseg;
   const DPhase* prog;
+  const FlatOp* flat;
+  const int32_t* flat_base;
   int64_t n0;
   const DOuter* bvout;
   const DOuter* buout;
@@ -187,239 +204,465 @@ struct SweepArgs {
   GridBar* bar;
   int smem_bytes;
   long long spin_limit;
+  int use_pf;
 };
 
 // ---------------------------------------------------------------------------
-// one op of a phase, executed by group g (warp or CTA) with staging area buf
+// one op of a phase, executed by group g (warp or CTA) with staging area buf.
+// The op's factor blocks are staged once; its vector operands for the RHS
+// range [rb, re) are staged in one pass when they fit next to them (else one
+// RC-wide chunk at a time), and the op is computed chunk by chunk from shared
+// memory.
 // ---------------------------------------------------------------------------
+// Vector operand plan of one op for the RHS range [rb, re): either the whole
+// range is staged at once in rows of stride W = nch*RC, or one RC-wide chunk
+// at a time (stride RC).
+template <class C, int RC>
+struct VecPlan {
+  int64_t rb, re, nch;
+  bool once;
+  int W;
+  __device__ VecPlan(int64_t rb_, int64_t re_, int64_t base_bytes, int vcnt, int64_t buf_bytes) : rb(rb_), re(re_) {
+    nch = (re - rb + RC - 1) / RC;
+    once = base_bytes + nch * RC * (int64_t)vcnt * (int64_t)sizeof(C) <= buf_bytes;
+    W = once ? (int)(nch * RC) : RC;
+  }
+  __device__ int rc(int64_t ch) const {
+    int64_t r0 = rb + ch * RC;
+    return (int)((re - r0) < RC ? (re - r0) : RC);
+  }
+};
+
+// stage the vector operand segments (up to two, concatenated) for RHS [r0, r0+width)
+template <class C>
+__device__ __forceinline__ void load_segs(C* dst, const C* s0, int n0s, const C* s1, int n1s, int64_t R, int64_t r0,
+                                          int width, int W, const Grp& g, bool noasync = false) {
+  stage_vec<C>(dst, s0, n0s, R, r0, width, W, g, noasync);
+  if (n1s > 0) stage_vec<C>(dst + (int64_t)n0s * W, s1, n1s, R, r0, width, W, g, noasync);
+}
+
 template <class T, class F, int RC>
-__device__ void do_op(const SweepArgs& a, const DPhase& P, int o, char* buf, int64_t buf_bytes, const Grp& g,
-                      int64_t rb, int64_t re) {
+__device__ void do_op(const SweepArgs& a, const FlatOp& f, char* buf, int64_t buf_bytes, const Grp& g, int64_t rb,
+                      int64_t re, bool pre = false) {
   using C = typename CT<T>::t;
-  const F* fp = (const F*)a.fp;
   C* vec = (C*)a.vec;
   C* st = (C*)a.st;
-  const int64_t R = a.R, n0 = a.n0;
-  if (P.kind == PH_ENTER || P.kind == PH_EXIT) {
-    const bool enter = P.kind == PH_ENTER;
-    // forward: enter = V0 (bvout), exit = U0 (buout); adjoint: enter = U0^H, exit = V0^H
-    const bool use_u = (enter == (P.adj != 0));
-    const DOuter op = use_u ? a.buout[a.bf_uout0[P.arg0] + o] : a.bvout[a.bf_vout0[P.arg0] + o];
-    const int k = op.blk.k, c = op.blk.c;
-    const int64_t mb = align16((int64_t)k * (c - k) * sizeof(F));
-    const int64_t ib = align16((int64_t)2 * c * sizeof(int16_t));
-    const int vcnt = enter ? c : k;
-    const int64_t need = mb + ib + (int64_t)vcnt * RC * sizeof(C);
-    const F* M;
-    const int16_t* idx;
-    C* v;
-    if (need <= buf_bytes) {
-      stage(buf, fp + op.blk.moff, mb, g);
-      stage(buf + mb, a.ip + op.blk.ioff, ib, g);
-      M = (const F*)buf;
-      idx = (const int16_t*)(buf + mb);
-      v = (C*)(buf + mb + ib);
-    } else {
-      M = fp + op.blk.moff;
-      idx = a.ip + op.blk.ioff;
-      v = (C*)buf;
+  const int64_t R = a.R;
+  const int kind = f.kind;
+  const bool conj_layout = (f.flags & FF_CONJ) != 0;
+  const bool subtract = (f.flags & FF_SUB) != 0;
+  const bool adj = (f.flags & FF_ADJ) != 0;
+  const int nblk = (f.flags & FF_TWO) ? 2 : 1;
+  const int k0 = f.k0, c0 = f.c0, k1 = f.k1, c1 = f.c1;
+  const C* src0 = ((f.flags & FF_SRC_VEC) ? vec : st) + (int64_t)f.src0 * R;
+  const C* src1 = st + (int64_t)f.src1 * R;
+  const int n_s0 = f.n_s0, n_s1 = f.n_s1;
+  C* out0 = ((f.flags & FF_OUT_VEC) ? vec : st) + (int64_t)f.out0 * R;
+  C* out1 = st + (int64_t)f.out1 * R;
+  const int split_r = f.split;
+  const int kr = f.k0, kc = f.c0;
+  const F* mstart = (const F*)a.fp + f.moff;
+  const int16_t* istart = f.ioff >= 0 ? a.ip + f.ioff : nullptr;
+  const int64_t mbytes = align16((int64_t)f.melems * (int64_t)sizeof(F));
+  const int64_t ibytes = f.ioff >= 0 ? align16((int64_t)f.ielems * (int64_t)sizeof(int16_t)) : 0;
+  // ---- staging
+  const int vcnt = n_s0 + n_s1;
+  const bool fit = pre || mbytes + ibytes + (int64_t)vcnt * RC * (int64_t)sizeof(C) <= buf_bytes;
+  const F* Ms = mstart;
+  const int16_t* Is = istart;
+  C* v = (C*)buf;
+  int64_t base = 0;
+  if (fit) {
+    if (!pre) {
+      stage(buf, mstart, mbytes, g);
+      if (ibytes) stage(buf + mbytes, istart, ibytes, g);
     }
-    const C* src = enter ? vec + (int64_t)op.leaf * n0 * R : st + (int64_t)op.seg_off * R;
-    for (int64_t r0 = rb; r0 < re; r0 += RC) {
-    const int rc = (int)((re - r0) < RC ? (re - r0) : RC);
-    load_vec<C, RC>(v, src, vcnt, R, r0, rc, g);
-    cp_commit_wait();
+    Ms = (const F*)buf;
+    Is = (const int16_t*)(buf + mbytes);
+    base = mbytes + ibytes;
+    v = (C*)(buf + base);
+  }
+  const F* M0 = Ms;
+  const int16_t* I0 = Is;
+  const F* M1 = Ms + f.m1;
+  const int16_t* I1 = Is ? Is + f.i1 : nullptr;
+  VecPlan<C, RC> pl(rb, re, base, vcnt, buf_bytes);
+  const int W = pl.W;
+  if (pl.once) {
+    load_segs<C>(v, src0, n_s0, src1, n_s1, R, rb, (int)(re - rb), W, g, pre);
+    if (!pre) cp_commit_wait();
     g.sync();
-    if (enter) {
-      C* out = st + (int64_t)op.seg_off * R;
-      if (P.adj) vlike<T, F, RC, true>(M, idx, k, c, v, out, R, r0, rc, g);
-      else vlike<T, F, RC, false>(M, idx, k, c, v, out, R, r0, rc, g);
-    } else {
-      C* bl = vec + (int64_t)op.leaf * n0 * R;
-      for (int r = g.t; r < c; r += g.nt) {
+  }
+  for (int64_t ch = 0; ch < pl.nch; ++ch) {
+    const int64_t r0 = rb + ch * RC;
+    const int rc = pl.rc(ch);
+    C* vv = pl.once ? v + ch * RC : v;
+    if (!pl.once) {
+      load_segs<C>(vv, src0, n_s0, src1, n_s1, R, r0, rc, W, g, pre);
+      if (!pre) cp_commit_wait();
+      g.sync();
+    }
+    if (kind == 0) {
+      if (conj_layout) {
+        vlike<T, F, RC, true>(M0, I0, k0, c0, vv, W, out0, R, r0, rc, g);
+        if (nblk == 2) vlike<T, F, RC, true>(M1, I1, k1, c1, vv, W, out1, R, r0, rc, g);
+      } else {
+        vlike<T, F, RC, false>(M0, I0, k0, c0, vv, W, out0, R, r0, rc, g);
+        if (nblk == 2) vlike<T, F, RC, false>(M1, I1, k1, c1, vv, W, out1, R, r0, rc, g);
+      }
+    } else if (kind == 1) {
+      const int nrows = c0;   // candidate entries (both blocks of an item share the candidate list)
+      const C* y0 = vv;
+      const C* y1 = vv + (int64_t)n_s0 * W;
+      for (int r = g.t; r < nrows; r += g.nt) {
         C acc[RC];
 #pragma unroll
         for (int rr = 0; rr < RC; ++rr) acc[rr] = z2<T>();
-        if (P.adj) rowc<T, F, RC, true>(acc, M, idx, k, c, v, r);
-        else rowc<T, F, RC, false>(acc, M, idx, k, c, v, r);
-        C* d = bl + (int64_t)r * R + r0;
+        if (conj_layout) {
+          rowc<T, F, RC, true>(acc, M0, I0, k0, c0, y0, W, r);
+          if (nblk == 2) rowc<T, F, RC, true>(acc, M1, I1, k1, c1, y1, W, r);
+        } else {
+          rowc<T, F, RC, false>(acc, M0, I0, k0, c0, y0, W, r);
+          if (nblk == 2) rowc<T, F, RC, false>(acc, M1, I1, k1, c1, y1, W, r);
+        }
+        C* d = (nblk == 1 || r < split_r) ? out0 + (int64_t)r * R + r0 : out1 + (int64_t)(r - split_r) * R + r0;
 #pragma unroll
         for (int rr = 0; rr < RC; ++rr)
           if (rr < rc) {
-            C cur = ldcg2(d + rr);
-            d[rr] = C{cur.x - acc[rr].x, cur.y - acc[rr].y};
+            if (subtract) {
+              C cur = ldcg2(d + rr);
+              d[rr] = C{cur.x - acc[rr].x, cur.y - acc[rr].y};
+            } else {
+              d[rr] = acc[rr];
+            }
           }
       }
-    }
-    g.sync();
-    }
-    return;
-  }
-  // ---- inner item
-  const DItem it = a.items[P.arg0 + o];
-  const bool adj = P.adj != 0;
-  if (it.type == 1) {
-    const int kr = it.b_k[0], kc = it.a_k[0];
-    const int64_t mb = align16((int64_t)kr * kc * sizeof(F));
-    const int nin = adj ? kr : kc, nout = adj ? kc : kr;
-    const F* S;
-    C* v;
-    if (mb + (int64_t)nin * RC * sizeof(C) <= buf_bytes) {
-      stage(buf, fp + it.blk[0].moff, mb, g);
-      S = (const F*)buf;
-      v = (C*)(buf + mb);
     } else {
-      S = fp + it.blk[0].moff;
-      v = (C*)buf;
-    }
-    C* out = st + (int64_t)(adj ? it.a_off[0] : it.b_off[0]) * R;
-    for (int64_t r0 = rb; r0 < re; r0 += RC) {
-    const int rc = (int)((re - r0) < RC ? (re - r0) : RC);
-    load_vec<C, RC>(v, st + (int64_t)(adj ? it.b_off[0] : it.a_off[0]) * R, nin, R, r0, rc, g);
-    cp_commit_wait();
-    g.sync();
-    for (int oo = g.t; oo < nout; oo += g.nt) {
-      C acc[RC];
+      const int nin = adj ? kr : kc, nout = adj ? kc : kr;
+      for (int oo = g.t; oo < nout; oo += g.nt) {
+        C acc[RC];
 #pragma unroll
-      for (int rr = 0; rr < RC; ++rr) acc[rr] = z2<T>();
+        for (int rr = 0; rr < RC; ++rr) acc[rr] = z2<T>();
 #pragma unroll 8
-      for (int i = 0; i < nin; ++i) {
-        C s = adj ? cvc<T>(S[(int64_t)oo * kr + i]) : cv<T>(S[(int64_t)i * kr + oo]);
+        for (int i = 0; i < nin; ++i) {
+          C sv = adj ? cvc<T>(Ms[(int64_t)oo * kr + i]) : cv<T>(Ms[(int64_t)i * kr + oo]);
 #pragma unroll
-        for (int rr = 0; rr < RC; ++rr) fma2(acc[rr], s, v[i * RC + rr]);
+          for (int rr = 0; rr < RC; ++rr) fma2(acc[rr], sv, vv[(int64_t)i * W + rr]);
+        }
+#pragma unroll
+        for (int rr = 0; rr < RC; ++rr)
+          if (rr < rc) out0[(int64_t)oo * R + r0 + rr] = acc[rr];
       }
-#pragma unroll
-      for (int rr = 0; rr < RC; ++rr)
-        if (rr < rc) out[(int64_t)oo * R + r0 + rr] = acc[rr];
     }
-    g.sync();
-    }
-    return;
+    if (!pl.once) g.sync();
   }
-  // two ID blocks: matrices and index arrays are contiguous in their pools
-  const DBlk& b0 = it.blk[0];
-  const DBlk& b1 = it.blk[1];
-  const int64_t m1off = (b1.moff - b0.moff) * (int64_t)sizeof(F);
-  const int64_t mb = align16(m1off + (int64_t)b1.k * (b1.c - b1.k) * sizeof(F));
-  const int64_t i1off = (int64_t)(b1.ioff - b0.ioff) * (int64_t)sizeof(int16_t);
-  const int64_t ib = align16(i1off + (int64_t)2 * b1.c * sizeof(int16_t));
-  const int ca = it.a_k[0] + it.a_k[1];
-  const bool to_b = (it.type == 0) != adj;
-  const int vcnt = to_b ? ca : (it.b_k[0] + it.b_k[1]);
-  const int64_t need = mb + ib + (int64_t)vcnt * RC * sizeof(C);
-  const F *M0, *M1;
-  const int16_t *I0, *I1;
-  C* v;
-  if (need <= buf_bytes) {
-    stage(buf, fp + b0.moff, mb, g);
-    stage(buf + mb, a.ip + b0.ioff, ib, g);
-    M0 = (const F*)buf;
-    M1 = (const F*)(buf + m1off);
-    I0 = (const int16_t*)(buf + mb);
-    I1 = (const int16_t*)(buf + mb + i1off);
-    v = (C*)(buf + mb + ib);
-  } else {
-    M0 = fp + b0.moff;
-    M1 = fp + b1.moff;
-    I0 = a.ip + b0.ioff;
-    I1 = a.ip + b1.ioff;
-    v = (C*)buf;
-  }
-  for (int64_t r0 = rb; r0 < re; r0 += RC) {
-  const int rc = (int)((re - r0) < RC ? (re - r0) : RC);
-  if (to_b) {
-    load_vec<C, RC>(v, st + (int64_t)it.a_off[0] * R, it.a_k[0], R, r0, rc, g);
-    load_vec<C, RC>(v + it.a_k[0] * RC, st + (int64_t)it.a_off[1] * R, it.a_k[1], R, r0, rc, g);
-  } else {
-    load_vec<C, RC>(v, st + (int64_t)it.b_off[0] * R, it.b_k[0], R, r0, rc, g);
-    load_vec<C, RC>(v + it.b_k[0] * RC, st + (int64_t)it.b_off[1] * R, it.b_k[1], R, r0, rc, g);
-  }
-  cp_commit_wait();
-  g.sync();
-  if (to_b) {
-    C* o0 = st + (int64_t)it.b_off[0] * R;
-    C* o1 = st + (int64_t)it.b_off[1] * R;
-    if (it.type == 0) {
-      vlike<T, F, RC, false>(M0, I0, b0.k, b0.c, v, o0, R, r0, rc, g);
-      vlike<T, F, RC, false>(M1, I1, b1.k, b1.c, v, o1, R, r0, rc, g);
-    } else {
-      vlike<T, F, RC, true>(M0, I0, b0.k, b0.c, v, o0, R, r0, rc, g);
-      vlike<T, F, RC, true>(M1, I1, b1.k, b1.c, v, o1, R, r0, rc, g);
-    }
-  } else {
-    const C* y0 = v;
-    const C* y1 = v + it.b_k[0] * RC;
-    for (int r = g.t; r < ca; r += g.nt) {
-      C acc[RC];
-#pragma unroll
-      for (int rr = 0; rr < RC; ++rr) acc[rr] = z2<T>();
-      if (it.type == 2) {
-        rowc<T, F, RC, false>(acc, M0, I0, b0.k, b0.c, y0, r);
-        rowc<T, F, RC, false>(acc, M1, I1, b1.k, b1.c, y1, r);
-      } else {
-        rowc<T, F, RC, true>(acc, M0, I0, b0.k, b0.c, y0, r);
-        rowc<T, F, RC, true>(acc, M1, I1, b1.k, b1.c, y1, r);
-      }
-      C* d = (r < it.a_k[0]) ? st + (int64_t)(it.a_off[0] + r) * R : st + (int64_t)(it.a_off[1] + r - it.a_k[0]) * R;
-#pragma unroll
-      for (int rr = 0; rr < RC; ++rr)
-        if (rr < rc) d[r0 + rr] = acc[rr];
-    }
-  }
-  g.sync();
-  }
+  if (pl.once) g.sync();
 }
 
 // leaf solve x_leaf = Tinv b_leaf (or Tinv^H b_leaf), whole CTA
 template <class T, class F, int RC>
-__device__ void do_leaf(const SweepArgs& a, const DPhase& P, char* buf, int64_t buf_bytes, int64_t rb, int64_t re) {
+__device__ void do_leaf(const SweepArgs& a, const FlatOp& f, char* buf, int64_t buf_bytes, int64_t rb, int64_t re,
+                        const F* pre_m = nullptr) {
   using C = typename CT<T>::t;
   const int64_t n0 = a.n0, R = a.R;
   const Grp g{(int)threadIdx.x, (int)blockDim.x, true};
-  const F* Tg = (const F*)a.tinv + (int64_t)P.arg0 * n0 * n0;
-  C* v = (C*)a.vec + (int64_t)P.arg0 * n0 * R;
+  const F* Tg = (const F*)a.tinv + f.moff;
+  C* v = (C*)a.vec + (int64_t)f.src0 * R;
+  const bool ladj = (f.flags & FF_ADJ) != 0;
   const int64_t mb = align16(n0 * n0 * (int64_t)sizeof(F));
   const int ngrp = (int)(blockDim.x / n0) > 0 ? (int)(blockDim.x / n0) : 1;
-  const int64_t need = mb + n0 * RC * (int64_t)sizeof(C) + (int64_t)ngrp * n0 * RC * sizeof(C);
-  const F* Tm;
-  C* bv;
-  C* part;
-  if (need <= buf_bytes) {
+  const int64_t partb = align16((int64_t)ngrp * n0 * RC * sizeof(C));
+  const F* Tm = Tg;
+  char* area = buf;
+  int64_t area_bytes = buf_bytes;
+  if (pre_m) {
+    Tm = pre_m;
+  } else if (mb + partb + n0 * RC * (int64_t)sizeof(C) <= buf_bytes) {
     stage(buf, Tg, mb, g);
     Tm = (const F*)buf;
-    bv = (C*)(buf + mb);
-  } else {
-    Tm = Tg;
-    bv = (C*)buf;
+    area = buf + mb;
+    area_bytes = buf_bytes - mb;
   }
-  part = bv + n0 * RC;
-  for (int64_t r0 = rb; r0 < re; r0 += RC) {
-  const int rc = (int)((re - r0) < RC ? (re - r0) : RC);
-  load_vec<C, RC>(bv, v, (int)n0, R, r0, rc, g);
-  cp_commit_wait();
+  C* part = (C*)area;
+  C* bv = (C*)(area + partb);
+  VecPlan<C, RC> pl(rb, re, partb, (int)n0, area_bytes);
+  const int W = pl.W;
+  const bool noasync = pre_m != nullptr;
+  if (pl.once) stage_vec<C>(bv, v, (int)n0, R, rb, (int)(re - rb), W, g, noasync);
+  if (!noasync) cp_commit_wait();
   __syncthreads();
-  // thread (row r, column group q): partial sums over columns cc = q, q+ngrp, ...
-  for (int e = threadIdx.x; e < ngrp * n0; e += blockDim.x) {
-    const int r = e % n0, q = e / n0;
-    C acc[RC];
-#pragma unroll
-    for (int rr = 0; rr < RC; ++rr) acc[rr] = z2<T>();
-    for (int cc = q; cc < n0; cc += ngrp) {
-      C m = P.adj ? cvc<T>(Tm[(int64_t)r * n0 + cc]) : cv<T>(Tm[(int64_t)cc * n0 + r]);
-#pragma unroll
-      for (int rr = 0; rr < RC; ++rr) fma2(acc[rr], m, bv[cc * RC + rr]);
+  for (int64_t ch = 0; ch < pl.nch; ++ch) {
+    const int64_t r0 = rb + ch * RC;
+    const int rc = pl.rc(ch);
+    C* bb = pl.once ? bv + ch * RC : bv;
+    if (!pl.once) {
+      stage_vec<C>(bb, v, (int)n0, R, r0, rc, W, g, noasync);
+      if (!noasync) cp_commit_wait();
+      __syncthreads();
     }
+    for (int e = threadIdx.x; e < ngrp * n0; e += blockDim.x) {
+      const int r = e % n0, q = e / n0;
+      C acc[RC];
 #pragma unroll
-    for (int rr = 0; rr < RC; ++rr) part[(q * n0 + r) * RC + rr] = acc[rr];
+      for (int rr = 0; rr < RC; ++rr) acc[rr] = z2<T>();
+      for (int cc = q; cc < n0; cc += ngrp) {
+        C m = ladj ? cvc<T>(Tm[(int64_t)r * n0 + cc]) : cv<T>(Tm[(int64_t)cc * n0 + r]);
+#pragma unroll
+        for (int rr = 0; rr < RC; ++rr) fma2(acc[rr], m, bb[(int64_t)cc * W + rr]);
+      }
+#pragma unroll
+      for (int rr = 0; rr < RC; ++rr) part[(q * n0 + r) * RC + rr] = acc[rr];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n0 * RC; e += blockDim.x) {
+      const int r = e / RC, rr = e % RC;
+      C sum = z2<T>();
+      for (int q = 0; q < ngrp; ++q) { sum.x += part[(q * n0 + r) * RC + rr].x; sum.y += part[(q * n0 + r) * RC + rr].y; }
+      if (rr < rc) v[(int64_t)r * R + r0 + rr] = sum;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < n0 * RC; e += blockDim.x) {
-    const int r = e / RC, rr = e % RC;
-    C s = z2<T>();
-    for (int q = 0; q < ngrp; ++q) { s.x += part[(q * n0 + r) * RC + rr].x; s.y += part[(q * n0 + r) * RC + rr].y; }
-    if (rr < rc) v[(int64_t)r * R + r0 + rr] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Local runs with prefetch (complex FP32 factors, n0 <= 64): the factor data
+// of phase p+1 is copied (cp.async, one group per phase) into the other half
+// of each warp's slice -- or into the other leaf buffer -- while phase p
+// computes, so only the data-dependent vector loads remain on the chain.
+// Shared-memory map: [leaf buffer 0 | leaf buffer 1 | leaf scratch | warp
+// halves (warp w, parity h) of kPfHalf bytes].
+// ---------------------------------------------------------------------------
+constexpr int kPfLeaf = 32 * 1024;
+constexpr int kPfAux = 8 * 1024;
+constexpr int kPfHalf = 6 * 1024;
+constexpr int kPfRes = 56 * 1024;                                               // resident vectors + state
+constexpr int kSmemBytes = 2 * kPfLeaf + kPfAux + 8 * 2 * kPfHalf + kPfRes;    // 224 KB
+
+__device__ __forceinline__ char* pf_half(char* smem, int w, int h) {
+  return smem + 2 * kPfLeaf + kPfAux + (w * 2 + h) * kPfHalf;
+}
+
+template <class F>
+__device__ __forceinline__ int64_t op_stage_bytes(const FlatOp& f) {
+  return align16((int64_t)f.melems * (int64_t)sizeof(F)) +
+         (f.ioff >= 0 ? align16((int64_t)f.ielems * (int64_t)sizeof(int16_t)) : 0);
+}
+
+// issue the factor-data copies of phase ph into parity h, then commit one group
+template <class F>
+__device__ void pf_issue(const SweepArgs& a, int ph, int h, char* smem, int warp, int lane) {
+  const int32_t ob = __ldg(a.flat_base + ph), oe = __ldg(a.flat_base + ph + 1);
+  const FlatOp* ops = a.flat + ob;
+  if (ops[0].kind == FK_LEAF) {
+    const Grp g{(int)threadIdx.x, (int)blockDim.x, true};
+    stage(smem + h * kPfLeaf, (const F*)a.tinv + ops[0].moff, align16((int64_t)ops[0].melems * (int64_t)sizeof(F)), g);
+  } else if (warp < oe - ob) {
+    const FlatOp& f = ops[warp];
+    const Grp g{lane, 32, false};
+    if (op_stage_bytes<F>(f) <= kPfHalf) {
+      char* d = pf_half(smem, warp, h);
+      const int64_t mb = align16((int64_t)f.melems * (int64_t)sizeof(F));
+      stage(d, (const F*)a.fp + f.moff, mb, g);
+      if (f.ioff >= 0) stage(d + mb, a.ip + f.ioff, align16((int64_t)f.ielems * (int64_t)sizeof(int16_t)), g);
+    }
   }
-  __syncthreads();
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// An op of a resident run: operands and results live in shared memory (rows
+// of stride Wr, columns = the CTA's right-hand sides), the factor data is
+// either prefetched into `half` (pre) or read from global memory.
+template <class T, class F, int RC>
+__device__ void do_op_res(const SweepArgs& a, const FlatOp& f, const char* half, bool pre,
+                          typename CT<T>::t* rvec, int row_lo, typename CT<T>::t* rst, int st_lo, int Wr, int ncol,
+                          const Grp& g) {
+  using C = typename CT<T>::t;
+  const bool conj_layout = (f.flags & FF_CONJ) != 0;
+  const bool subtract = (f.flags & FF_SUB) != 0;
+  const bool adj = (f.flags & FF_ADJ) != 0;
+  const int nblk = (f.flags & FF_TWO) ? 2 : 1;
+  const C* src0 = (f.flags & FF_SRC_VEC) ? rvec + (int64_t)(f.src0 - row_lo) * Wr : rst + (int64_t)(f.src0 - st_lo) * Wr;
+  const C* src1 = rst + (int64_t)(f.src1 - st_lo) * Wr;
+  C* out0 = (f.flags & FF_OUT_VEC) ? rvec + (int64_t)(f.out0 - row_lo) * Wr : rst + (int64_t)(f.out0 - st_lo) * Wr;
+  C* out1 = rst + (int64_t)(f.out1 - st_lo) * Wr;
+  const int64_t mbytes = align16((int64_t)f.melems * (int64_t)sizeof(F));
+  const F* Ms = pre ? (const F*)half : (const F*)a.fp + f.moff;
+  const int16_t* Is = pre ? (const int16_t*)(half + mbytes) : (f.ioff >= 0 ? a.ip + f.ioff : nullptr);
+  const F* M1 = Ms + f.m1;
+  const int16_t* I1 = Is ? Is + f.i1 : nullptr;
+  for (int r0 = 0; r0 < ncol; r0 += RC) {
+    const int rc = (ncol - r0) < RC ? (ncol - r0) : RC;
+    if (f.kind == FK_GATHER) {
+      if (conj_layout) {
+        vlike<T, F, RC, true>(Ms, Is, f.k0, f.c0, src0 + r0, Wr, out0, Wr, r0, rc, g);
+        if (nblk == 2) vlike<T, F, RC, true>(M1, I1, f.k1, f.c1, src0 + r0, Wr, out1, Wr, r0, rc, g);
+      } else {
+        vlike<T, F, RC, false>(Ms, Is, f.k0, f.c0, src0 + r0, Wr, out0, Wr, r0, rc, g);
+        if (nblk == 2) vlike<T, F, RC, false>(M1, I1, f.k1, f.c1, src0 + r0, Wr, out1, Wr, r0, rc, g);
+      }
+    } else if (f.kind == FK_SCATTER) {
+      const int split_r = f.split;
+      for (int r = g.t; r < f.c0; r += g.nt) {
+        C acc[RC];
+#pragma unroll
+        for (int rr = 0; rr < RC; ++rr) acc[rr] = z2<T>();
+        if (conj_layout) {
+          rowc<T, F, RC, true>(acc, Ms, Is, f.k0, f.c0, src0 + r0, Wr, r);
+          if (nblk == 2) rowc<T, F, RC, true>(acc, M1, I1, f.k1, f.c1, src1 + r0, Wr, r);
+        } else {
+          rowc<T, F, RC, false>(acc, Ms, Is, f.k0, f.c0, src0 + r0, Wr, r);
+          if (nblk == 2) rowc<T, F, RC, false>(acc, M1, I1, f.k1, f.c1, src1 + r0, Wr, r);
+        }
+        C* d = (nblk == 1 || r < split_r) ? out0 + (int64_t)r * Wr + r0 : out1 + (int64_t)(r - split_r) * Wr + r0;
+#pragma unroll
+        for (int rr = 0; rr < RC; ++rr)
+          if (rr < rc) {
+            if (subtract) d[rr] = C{d[rr].x - acc[rr].x, d[rr].y - acc[rr].y};
+            else d[rr] = acc[rr];
+          }
+      }
+    } else {   // middle
+      const int kr = f.k0, kc = f.c0;
+      const int nin = adj ? kr : kc, nout = adj ? kc : kr;
+      for (int oo = g.t; oo < nout; oo += g.nt) {
+        C acc[RC];
+#pragma unroll
+        for (int rr = 0; rr < RC; ++rr) acc[rr] = z2<T>();
+#pragma unroll 8
+        for (int i = 0; i < nin; ++i) {
+          C sv = adj ? cvc<T>(Ms[(int64_t)oo * kr + i]) : cv<T>(Ms[(int64_t)i * kr + oo]);
+#pragma unroll
+          for (int rr = 0; rr < RC; ++rr) fma2(acc[rr], sv, src0[(int64_t)i * Wr + r0 + rr]);
+        }
+#pragma unroll
+        for (int rr = 0; rr < RC; ++rr)
+          if (rr < rc) out0[(int64_t)oo * Wr + r0 + rr] = acc[rr];
+      }
+    }
+  }
+  g.sync();
+}
+
+// leaf solve of a resident run: rows in shared memory, inverse prefetched
+template <class T, class F, int RC>
+__device__ void do_leaf_res(const SweepArgs& a, const FlatOp& f, const F* Tm, typename CT<T>::t* rvec, int row_lo,
+                            int Wr, int ncol, typename CT<T>::t* part) {
+  using C = typename CT<T>::t;
+  const int n0 = (int)a.n0;
+  const bool ladj = (f.flags & FF_ADJ) != 0;
+  C* v = rvec + (int64_t)(f.src0 - row_lo) * Wr;
+  const int ngrp = (int)(blockDim.x / n0) > 0 ? (int)(blockDim.x / n0) : 1;
+  for (int r0 = 0; r0 < ncol; r0 += RC) {
+    const int rc = (ncol - r0) < RC ? (ncol - r0) : RC;
+    for (int e = threadIdx.x; e < ngrp * n0; e += blockDim.x) {
+      const int r = e % n0, q = e / n0;
+      C acc[RC];
+#pragma unroll
+      for (int rr = 0; rr < RC; ++rr) acc[rr] = z2<T>();
+#pragma unroll 4
+      for (int cc = q; cc < n0; cc += ngrp) {
+        C m = ladj ? cvc<T>(Tm[(int64_t)r * n0 + cc]) : cv<T>(Tm[(int64_t)cc * n0 + r]);
+#pragma unroll
+        for (int rr = 0; rr < RC; ++rr) fma2(acc[rr], m, v[(int64_t)cc * Wr + r0 + rr]);
+      }
+#pragma unroll
+      for (int rr = 0; rr < RC; ++rr) part[(q * n0 + r) * RC + rr] = acc[rr];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n0 * RC; e += blockDim.x) {
+      const int r = e / RC, rr = e % RC;
+      C sum = z2<T>();
+      for (int q = 0; q < ngrp; ++q) { sum.x += part[(q * n0 + r) * RC + rr].x; sum.y += part[(q * n0 + r) * RC + rr].y; }
+      if (rr < rc) v[(int64_t)r * Wr + r0 + rr] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+template <class T, class F, int RC>
+__device__ void local_run_pf(const SweepArgs& a, const DSeg& sg, char* smem, int64_t lb, int64_t le) {
+  using C = typename CT<T>::t;
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+  const int end = sg.first + sg.count;
+  // records of this run into L1 (static data)
+  {
+    const int32_t o_first = __ldg(a.flat_base + sg.first), o_last = __ldg(a.flat_base + end);
+    const char* p0 = (const char*)(a.flat + o_first);
+    const int64_t nb = (int64_t)(o_last - o_first) * (int64_t)sizeof(FlatOp);
+    for (int64_t e = (int64_t)threadIdx.x * 128; e < nb; e += (int64_t)blockDim.x * 128)
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(p0 + e));
+    const char* p1 = (const char*)(a.flat_base + sg.first);
+    for (int64_t e = (int64_t)threadIdx.x * 128; e < (int64_t)(sg.count + 1) * 4; e += (int64_t)blockDim.x * 128)
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(p1 + e));
+  }
+  // resident operands: this CTA's columns of the run's vector rows and state
+  const int ncol = (int)(le - lb);
+  const int Wr = ((ncol + RC - 1) / RC) * RC;
+  const int64_t res_need = ((int64_t)(sg.row_hi - sg.row_lo) + (sg.st_hi - sg.st_lo)) * Wr * (int64_t)sizeof(C);
+  const bool resident = res_need <= kPfRes;
+  C* rvec = (C*)(smem + 2 * kPfLeaf + kPfAux + 16 * kPfHalf);
+  C* rst = rvec + (int64_t)(sg.row_hi - sg.row_lo) * Wr;
+  C* vecg = (C*)a.vec;
+  if (resident) {
+    const int nrow = sg.row_hi - sg.row_lo;
+    for (int e = threadIdx.x; e < nrow * ncol; e += blockDim.x) {
+      const int r = e / ncol, c = e % ncol;
+      rvec[(int64_t)r * Wr + c] = ldcg2(vecg + (int64_t)(sg.row_lo + r) * a.R + lb + c);
+    }
+  }
+  pf_issue<F>(a, sg.first, 0, smem, warp, lane);
+  int h = 0;
+  for (int ph = sg.first; ph < end; ++ph) {
+    if (ph + 1 < end) {
+      pf_issue<F>(a, ph + 1, h ^ 1, smem, warp, lane);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncthreads();
+    const int32_t ob = __ldg(a.flat_base + ph), oe = __ldg(a.flat_base + ph + 1);
+    const FlatOp* ops = a.flat + ob;
+    if (resident) {
+      if (ops[0].kind == FK_LEAF) {
+        do_leaf_res<T, F, RC>(a, ops[0], (const F*)(smem + h * kPfLeaf), rvec, sg.row_lo, Wr, ncol,
+                              (C*)(smem + 2 * kPfLeaf));
+      } else {
+        const Grp g{lane, 32, false};
+        for (int o = warp; o < oe - ob; o += nw) {
+          const FlatOp f = ops[o];
+          const bool pre = (o == warp) && op_stage_bytes<F>(f) <= kPfHalf;
+          do_op_res<T, F, RC>(a, f, pf_half(smem, warp, h), pre, rvec, sg.row_lo, rst, sg.st_lo, Wr, ncol, g);
+        }
+      }
+    } else if (ops[0].kind == FK_LEAF) {
+      do_leaf<T, F, RC>(a, ops[0], smem + 2 * kPfLeaf, kPfAux, lb, le, (const F*)(smem + h * kPfLeaf));
+    } else {
+      const Grp g{lane, 32, false};
+      for (int o = warp; o < oe - ob; o += nw) {
+        const FlatOp f = ops[o];
+        const int64_t sb = op_stage_bytes<F>(f);
+        const int64_t vb = (int64_t)(f.n_s0 + f.n_s1) * (((le - lb + RC - 1) / RC) * RC) * (int64_t)sizeof(C);
+        char* half = pf_half(smem, warp, h);
+        if (o == warp && sb <= kPfHalf && sb + vb <= kPfHalf) {
+          do_op<T, F, RC>(a, f, half, kPfHalf, g, lb, le, true);
+        } else if (o == warp && sb <= kPfHalf) {
+          // prefetched, but the vectors do not fit beside it: read the matrices from global
+          do_op<T, F, RC>(a, f, half, 0, g, lb, le);
+        } else {
+          do_op<T, F, RC>(a, f, half, kPfHalf, g, lb, le);
+        }
+      }
+    }
+    __syncthreads();
+    h ^= 1;
+  }
+  if (resident) {
+    const int nrow = sg.row_hi - sg.row_lo;
+    for (int e = threadIdx.x; e < nrow * ncol; e += blockDim.x) {
+      const int r = e / ncol, c = e % ncol;
+      vecg[(int64_t)(sg.row_lo + r) * a.R + lb + c] = rvec[(int64_t)r * Wr + c];
+    }
+    __syncthreads();
   }
 }
 
@@ -429,26 +672,47 @@ __global__ void __launch_bounds__(256, 1) k_sweep_coop(SweepArgs a) {
   const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
   unsigned my_gen = 0;
   const int64_t slice = (a.smem_bytes / nw) & ~(int64_t)15;
-  // local runs: the right-hand sides are split over the CTAs (chunks of RC);
-  // CTA b owns [lb, le).  With a single chunk only CTA 0 works.
-  const int64_t nchunk = (a.R + RC - 1) / RC;
-  const int64_t cper = (nchunk + gridDim.x - 1) / gridDim.x;
-  const int64_t lb = (int64_t)blockIdx.x * cper * RC;
-  const int64_t le = (lb + cper * RC < a.R) ? lb + cper * RC : a.R;
+  // local runs: the right-hand sides are split over the CTAs; CTA b owns
+  // [lb, le) (q = ceil(R / #CTAs) columns).  With one right-hand side only CTA 0 works.
+  const int64_t q = (a.R + gridDim.x - 1) / gridDim.x;
+  const int64_t lb = (int64_t)blockIdx.x * q;
+  const int64_t le = (lb + q < a.R) ? lb + q : a.R;
   for (int s = 0; s < a.nseg; ++s) {
     const DSeg sg = a.segs[s];
     if (sg.grid) {
       const DPhase P = a.prog[sg.first];
-      const Grp g{(int)threadIdx.x, (int)blockDim.x, true};
-      for (int o = blockIdx.x; o < P.count; o += gridDim.x) do_op<T, F, RC>(a, P, o, smem, a.smem_bytes, g, 0, a.R);
+      const FlatOp* ops = a.flat + a.flat_base[sg.first];
+      if (a.R <= 4 && (int64_t)P.mbytes / (16 / (int)sizeof(F)) + (int64_t)P.vmax * RC * (int64_t)sizeof(typename CT<T>::t) <= slice) {
+        // few right-hand sides and ops that fit a warp's slice: one op per warp over the whole grid
+        const Grp g{lane, 32, false};
+        const int gw = blockIdx.x * nw + warp, tw = gridDim.x * nw;
+        for (int o = gw; o < P.count; o += tw) do_op<T, F, RC>(a, ops[o], smem + warp * slice, slice, g, 0, a.R);
+      } else {
+        const Grp g{(int)threadIdx.x, (int)blockDim.x, true};
+        for (int o = blockIdx.x; o < P.count; o += gridDim.x) do_op<T, F, RC>(a, ops[o], smem, a.smem_bytes, g, 0, a.R);
+      }
+    } else if (lb < le && a.use_pf) {
+      local_run_pf<T, F, RC>(a, sg, smem, lb, le);
     } else if (lb < le) {
+      // bring this run's op and phase records into L1 (static data, one round trip)
+      const int32_t o_first = __ldg(a.flat_base + sg.first), o_last = __ldg(a.flat_base + sg.first + sg.count);
+      {
+        const char* p0 = (const char*)(a.flat + o_first);
+        const int64_t nb = (int64_t)(o_last - o_first) * (int64_t)sizeof(FlatOp);
+        for (int64_t e = (int64_t)threadIdx.x * 128; e < nb; e += (int64_t)blockDim.x * 128)
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(p0 + e));
+        const char* p1 = (const char*)(a.flat_base + sg.first);
+        for (int64_t e = (int64_t)threadIdx.x * 128; e < (int64_t)(sg.count + 1) * 4; e += (int64_t)blockDim.x * 128)
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(p1 + e));
+      }
       for (int ph = sg.first; ph < sg.first + sg.count; ++ph) {
-        const DPhase P = a.prog[ph];
-        if (P.kind == PH_LEAF) {
-          do_leaf<T, F, RC>(a, P, smem, a.smem_bytes, lb, le);
+        const int32_t ob = __ldg(a.flat_base + ph), oe = __ldg(a.flat_base + ph + 1);
+        const FlatOp* ops = a.flat + ob;
+        if (ops[0].kind == FK_LEAF) {
+          do_leaf<T, F, RC>(a, ops[0], smem, a.smem_bytes, lb, le);
         } else {
           const Grp g{lane, 32, false};
-          for (int o = warp; o < P.count; o += nw) do_op<T, F, RC>(a, P, o, smem + warp * slice, slice, g, lb, le);
+          for (int o = warp; o < oe - ob; o += nw) do_op<T, F, RC>(a, ops[o], smem + warp * slice, slice, g, lb, le);
           __syncthreads();
         }
       }
@@ -481,7 +745,7 @@ static int sweep_coop_impl(const DevFactor& df, int which, void* vec, int64_t R,
                            cudaStream_t s, long long spin_limit) {
   int grid = 0;
   coop_launch_dims(grid);
-  const int smem = 192 * 1024;
+  const int smem = kSmemBytes;
   auto kern = k_sweep_coop<T, F, RC>;
   static bool attr_done = false;
   if (!attr_done) {
@@ -489,9 +753,17 @@ static int sweep_coop_impl(const DevFactor& df, int which, void* vec, int64_t R,
     attr_done = true;
   }
   SweepArgs a;
-  a.segs = df.segs[which];
-  a.nseg = df.nsegs[which];
+  const int cls = R > 1 ? 1 : 0;
+  if (df.tuned[cls] >= 0) {
+    a.segs = df.cand_segs[which][df.tuned[cls]];
+    a.nseg = df.cand_nsegs[which][df.tuned[cls]];
+  } else {
+    a.segs = df.segs[which];
+    a.nseg = df.nsegs[which];
+  }
   a.prog = df.prog[which];
+  a.flat = df.flat[which];
+  a.flat_base = df.flat_base[which];
   a.n0 = df.n0;
   a.bvout = df.bvout;
   a.buout = df.buout;
@@ -505,8 +777,12 @@ static int sweep_coop_impl(const DevFactor& df, int which, void* vec, int64_t R,
   a.st = st;
   a.R = R;
   a.bar = (GridBar*)bar;
-  a.smem_bytes = smem;
+  a.smem_bytes = 192 * 1024;
   a.spin_limit = spin_limit;
+  // prefetching runs: complex FP32 factors, leaf inverses within one leaf
+  // buffer, and leaf partial sums (256 threads x RC columns) within the scratch
+  a.use_pf = (sizeof(F) == 8 && df.n0 * df.n0 * (int64_t)sizeof(F) <= kPfLeaf &&
+              (256 + df.n0) * RC * (int64_t)sizeof(typename CT<T>::t) <= kPfAux) ? 1 : 0;
   // reset count and generation; the error flag stays set until hb_status reads it
   if (cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s) != cudaSuccess) return HB_ECUDA;
   void* args[] = {&a};
@@ -521,15 +797,22 @@ static int sweep_coop_impl(const DevFactor& df, int which, void* vec, int64_t R,
 int launch_sweep_coop(const DevFactor& df, Prec p, int which, void* vec, int64_t R, void* state, void* bar,
                       cudaStream_t st, long long spin_limit) {
   if (which < 0 || which > 3) return HB_EINVAL;
+  int grid = 0;
+  coop_launch_dims(grid);
+  // RHS chunk width: the per-CTA share of the local runs, rounded up to 1, 2, 4 or 8
+  const int64_t q = (R + grid - 1) / grid;
   if (p == PREC_F64) {
-    if (R >= 4) return sweep_coop_impl<double, double2, 4>(df, which, vec, R, state, bar, st, spin_limit);
+    if (q >= 3) return sweep_coop_impl<double, double2, 4>(df, which, vec, R, state, bar, st, spin_limit);
+    if (q == 2) return sweep_coop_impl<double, double2, 2>(df, which, vec, R, state, bar, st, spin_limit);
     return sweep_coop_impl<double, double2, 1>(df, which, vec, R, state, bar, st, spin_limit);
   }
   if (p == PREC_F32) {
-    if (R >= 8) return sweep_coop_impl<float, float2, 8>(df, which, vec, R, state, bar, st, spin_limit);
-    if (R >= 4) return sweep_coop_impl<float, float2, 4>(df, which, vec, R, state, bar, st, spin_limit);
+    if (q >= 5) return sweep_coop_impl<float, float2, 8>(df, which, vec, R, state, bar, st, spin_limit);
+    if (q >= 3) return sweep_coop_impl<float, float2, 4>(df, which, vec, R, state, bar, st, spin_limit);
+    if (q == 2) return sweep_coop_impl<float, float2, 2>(df, which, vec, R, state, bar, st, spin_limit);
     return sweep_coop_impl<float, float2, 1>(df, which, vec, R, state, bar, st, spin_limit);
   }
+  if (q >= 2) return sweep_coop_impl<double, float2, 2>(df, which, vec, R, state, bar, st, spin_limit);
   return sweep_coop_impl<double, float2, 1>(df, which, vec, R, state, bar, st, spin_limit);
 }
 

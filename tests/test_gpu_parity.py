@@ -267,3 +267,17 @@ def test_bounded_wait_reports_timeout(hb, strip):
     assert lib.hb_status(f._h, C.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
     fh = hb.hb_factor_host(g, wl.leaf, wl.eps)
     assert _rel(x, hb.hb_host_sweep(fh, b.cpu().numpy(), 0)) <= 1e-12
+
+
+def test_autotune_keeps_results(hb, strip):
+    wl, g = strip["wl"], strip["g"]
+    fh = hb.hb_factor_host(g, wl.leaf, wl.eps)
+    f = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C128)
+    b = W.complex_gaussian(1024, 35, 3).T.copy()
+    for R in (1, 3):
+        chosen = hb.hb_autotune(f, R)
+        assert chosen >= 4
+        xb = b[0] if R == 1 else b
+        x = hb.hb_lower_solve(f, _t(xb)).cpu().numpy().reshape(R, -1)
+        for r in range(R):
+            assert _rel(x[r], hb.hb_host_sweep(fh, b[r], 0)) <= 1e-12
