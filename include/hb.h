@@ -194,6 +194,14 @@ int hb_rhs_plane_wave(hb_factor_t f, const double* phi_deg, int64_t nrhs, void* 
 int hb_far_field(hb_factor_t f, const void* x, int64_t nrhs, int64_t ld, const double* phi_obs_deg, int64_t nobs,
                  void* out, void* stream);
 
+/* hb_far_field_adjoint -- the conjugate transpose of hb_far_field:
+ * out[:, r] = sum_q conj(C) w_n exp(-i k (x_n cos phi_q + y_n sin phi_q)) g[r][q]
+ * for g a complex128 device array [nrhs][nobs]; out is a complex128 device
+ * block [nrhs][ld].  Used by the gradient of far-field losses (no counterpart
+ * in the paper). */
+int hb_far_field_adjoint(hb_factor_t f, const void* g, int64_t nrhs, const double* phi_obs_deg, int64_t nobs,
+                         void* out, int64_t ld, void* stream);
+
 /* hb_monostatic -- backscatter for column r of x at its own incidence angle
  * phi_deg[r]: C sum_n w_n b_n(phi_r) x_n.  out: complex128 device [nrhs]. */
 int hb_monostatic(hb_factor_t f, const void* x, int64_t nrhs, int64_t ld, const double* phi_deg, void* out,

@@ -35,3 +35,27 @@ def monostatic(problem, x, phi_inc_deg):
     k = problem.kappa
     c = -(k * problem.eta0 / 4.0) * np.sqrt(2j / (math.pi * k))
     return c * np.sum(problem.lengths[:, None] * b * np.asarray(x).reshape(b.shape), axis=0)
+
+
+def far_field_matrix(problem, phi_obs_deg):
+    """Dense F with E_far = F x: F[q, n] = C w_n exp(+i kappa (x_n cos phi_q + y_n sin phi_q))."""
+    phi = np.asarray(phi_obs_deg, dtype=np.float64) * math.pi / 180.0
+    k = problem.kappa
+    c = -(k * problem.eta0 / 4.0) * np.sqrt(2j / (math.pi * k))
+    cx = problem.centres[:, 0]
+    cy = problem.centres[:, 1]
+    return c * problem.lengths[None, :] * np.exp(
+        1j * k * (cx[None, :] * np.cos(phi)[:, None] + cy[None, :] * np.sin(phi)[:, None]))
+
+
+def loss_gradient(a_unscaled, problem, b, target, phi_obs_deg):
+    """Far-field loss L(b) = sum_q |(F A^{-1} b)_q - t_q|^2 and its gradient
+    dL/dRe b + i dL/dIm b = A^{-H} 2 F^H (F x - t) (dense solves written out)."""
+    from . import dense
+    f = far_field_matrix(problem, phi_obs_deg)
+    x = dense.solve(a_unscaled, b)
+    e = f @ x
+    loss = float(np.sum(np.abs(e - target) ** 2))
+    g = 2.0 * f.conj().T @ (e - target)
+    lam = dense.solve(a_unscaled.conj().T, g)
+    return loss, lam

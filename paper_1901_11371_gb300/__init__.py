@@ -22,7 +22,7 @@ __all__ = ["HB_STRIP", "HB_SPIRAL", "HB_ARC", "HB_PARALLEL_STRIPS", "HB_C128", "
            "HB_OP_N", "HB_OP_H", "HBError", "Geometry", "Factor", "hb_geometry", "hb_factor", "hb_factor_host",
            "hb_factor_info", "hb_tree", "hb_apply", "hb_apply_adjoint", "hb_precond_solve", "hb_lower_solve",
            "hb_upper_solve", "hb_residual", "hb_gmres", "hb_rhs_plane_wave", "hb_far_field", "hb_monostatic",
-           "hb_host_apply", "hb_host_sweep", "hb_profile", "hb_profile_read", "hb_autotune", "lib"]
+           "hb_host_apply", "hb_host_sweep", "hb_far_field_adjoint", "hb_profile", "hb_profile_read", "hb_autotune", "lib"]
 
 
 def lib():
@@ -210,6 +210,20 @@ def hb_far_field(f, x, phi_obs_deg, stream=None):
     out = torch.empty((R, phi.shape[0]), dtype=torch.complex128, device="cuda")
     _lib.check(lib().hb_far_field(f._h, C.c_void_p(x.data_ptr()), R, f.n, phi.ctypes.data_as(C.POINTER(C.c_double)),
                                   phi.shape[0], C.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def hb_far_field_adjoint(f, g, phi_obs_deg, stream=None):
+    """out = F^H g for g of shape (R, nobs) (complex128); returns (R, N)."""
+    import torch
+    if not (isinstance(g, torch.Tensor) and g.is_cuda and g.dtype == torch.complex128 and g.dim() == 2):
+        raise HBError(_lib.HB_EINVAL, "expected a complex128 CUDA tensor of shape (R, nobs)")
+    g = g.contiguous()
+    phi = np.ascontiguousarray(np.atleast_1d(np.asarray(phi_obs_deg, dtype=np.float64)))
+    out = torch.empty((g.shape[0], f.n), dtype=torch.complex128, device="cuda")
+    _lib.check(lib().hb_far_field_adjoint(f._h, C.c_void_p(g.data_ptr()), g.shape[0],
+                                          phi.ctypes.data_as(C.POINTER(C.c_double)), phi.shape[0],
+                                          C.c_void_p(out.data_ptr()), f.n, _stream(stream)))
     return out
 
 

@@ -64,6 +64,7 @@ SIGNATURES = {
     "hb_gmres": (_INT, [_VP, _INT, _VP, _VP, _I64, _I64, _INT, _DBL, _INT, C.POINTER(GmresInfo), _VP]),
     "hb_rhs_plane_wave": (_INT, [_VP, C.POINTER(C.c_double), _I64, _VP, _I64, _VP]),
     "hb_far_field": (_INT, [_VP, _VP, _I64, _I64, C.POINTER(C.c_double), _I64, _VP, _VP]),
+    "hb_far_field_adjoint": (_INT, [_VP, _VP, _I64, C.POINTER(C.c_double), _I64, _VP, _I64, _VP]),
     "hb_monostatic": (_INT, [_VP, _VP, _I64, _I64, C.POINTER(C.c_double), _VP, _VP]),
     "hb_set_sweep_grid_min": (_INT, [_VP, _INT]),
     "hb_set_wait_limit": (_INT, [_VP, C.c_longlong]),

@@ -244,7 +244,103 @@ static void sample_positions(int64_t M, int s, uint64_t seed, std::vector<int64_
   std::sort(out.begin(), out.end());
 }
 
-static inline int sample_count(int c) { return 2 * c + 8; }
+static inline int sample_count(int c) { return 2 * c + 16; }
+
+// Sample positions of `pool` for an ID over the candidate points `cand`: half
+// of the sample is the pool entries geometrically nearest to the candidates
+// (the near field across block boundaries and between adjacent turns, which a
+// uniform or Chebyshev sample of a long pool can miss), the rest a Mock-
+// Chebyshev + uniform sample of the remaining entries.
+static void sample_near(const Geometry& g, const std::vector<int64_t>& pool, const std::vector<int64_t>& cand,
+                        int s, uint64_t seed, std::vector<int64_t>& out) {
+  const int64_t M = (int64_t)pool.size();
+  if (M <= s) {
+    out.resize(M);
+    std::iota(out.begin(), out.end(), 0);
+    return;
+  }
+  // distance of each pool point to (up to 8 evenly spaced) candidate points
+  const int nc = (int)cand.size();
+  const int nref = std::min(nc, 8);
+  std::vector<std::pair<double, int64_t>> dist(M);
+  for (int64_t e = 0; e < M; ++e) {
+    const double px = g.cx[pool[e]], py = g.cy[pool[e]];
+    double dmin = 1e300;
+    for (int r = 0; r < nref; ++r) {
+      const int64_t c = cand[(int64_t)r * (nc - 1) / std::max(1, nref - 1)];
+      const double dx = px - g.cx[c], dy = py - g.cy[c];
+      dmin = std::min(dmin, dx * dx + dy * dy);
+    }
+    dist[e] = {dmin, e};
+  }
+  const int nn = s / 2;
+  std::nth_element(dist.begin(), dist.begin() + nn, dist.end());
+  std::vector<char> used(M, 0);
+  out.clear();
+  for (int i = 0; i < nn; ++i) { used[dist[i].second] = 1; out.push_back(dist[i].second); }
+  // Chebyshev-spaced and uniform picks among the rest
+  const int nrest = s - nn;
+  const int ncheb = nrest / 2;
+  for (int i = 0; i < ncheb; ++i) {
+    double x = 0.5 * (1.0 - std::cos(M_PI * (2.0 * i + 1.0) / (2.0 * ncheb)));
+    int64_t idx = std::min<int64_t>(M - 1, (int64_t)std::llround(x * (double)(M - 1)));
+    if (!used[idx]) { used[idx] = 1; out.push_back(idx); }
+  }
+  uint64_t st = seed;
+  while ((int)out.size() < s) {
+    int64_t idx = (int64_t)(splitmix(st) % (uint64_t)M);
+    if (!used[idx]) { used[idx] = 1; out.push_back(idx); }
+  }
+  std::sort(out.begin(), out.end());
+}
+
+// ---------------------------------------------------------------------------
+// Adaptive sampled ID.  cand: the c candidate indices; pool: indices of the
+// other dimension to sample; ent(pool_idx, cand_idx) gives the entry.  The ID
+// is computed on a sample (sample_near), then checked on a probe of unsampled
+// pool entries (nearest first, then uniform); while the probe residual
+// ||M_P(:,p) - M_P(:,q) T||_F exceeds 10 tol ||M_P||_F the sample is doubled.
+// ---------------------------------------------------------------------------
+template <class Ent>
+static void adaptive_id(const Geometry& geo, const std::vector<int64_t>& pool, const std::vector<int64_t>& cand,
+                        double tol, uint64_t seed, const Ent& ent, IdBlock& blk) {
+  const int c = (int)cand.size();
+  const int64_t M = (int64_t)pool.size();
+  int s = sample_count(c);
+  std::vector<int64_t> pos;
+  for (int attempt = 0;; ++attempt) {
+    sample_near(geo, pool, cand, s, seed + 0x51ull * attempt, pos);
+    const int ns = (int)pos.size();
+    std::vector<cplx> Mt((size_t)ns * c);
+    for (int cc = 0; cc < c; ++cc)
+      for (int r = 0; r < ns; ++r) Mt[(size_t)cc * ns + r] = ent(pool[pos[r]], cand[cc]);
+    column_id(Mt, ns, c, tol, blk);
+    if (ns >= M || blk.k >= c) return;          // whole pool used, or no compression: exact on the sample
+    // probe: up to 16 + c/2 unsampled entries, the nearest half first
+    std::vector<char> used(M, 0);
+    for (int64_t e : pos) used[e] = 1;
+    std::vector<int64_t> rest;
+    rest.reserve(M - ns);
+    for (int64_t e = 0; e < M; ++e)
+      if (!used[e]) rest.push_back(pool[e]);
+    std::vector<int64_t> ppos;
+    sample_near(geo, rest, cand, std::min<int64_t>((int64_t)rest.size(), 16 + c / 2), seed ^ 0xFEEDull, ppos);
+    const int np = (int)ppos.size();
+    double num = 0.0, den = 0.0;
+    const int nr = c - blk.k;
+    for (int r = 0; r < np; ++r) {
+      std::vector<cplx> row(c);
+      for (int cc = 0; cc < c; ++cc) { row[cc] = ent(rest[ppos[r]], cand[cc]); den += std::norm(row[cc]); }
+      for (int j = 0; j < nr; ++j) {
+        cplx acc = row[blk.p[j]];
+        for (int i = 0; i < blk.k; ++i) acc -= row[blk.q[i]] * blk.t[(size_t)i * nr + j];
+        num += std::norm(acc);
+      }
+    }
+    if (num <= 100.0 * tol * tol * den || s >= M || attempt >= 6) return;
+    s = (int)std::min<int64_t>(M, 2 * (int64_t)s);
+  }
+}
 
 // ---------------------------------------------------------------------------
 // One butterfly: interleaved row / column stages (complementary
@@ -252,6 +348,7 @@ static inline int sample_count(int c) { return 2 * c + 8; }
 // same level, row IDs sample the column skeletons of the previous level).
 // ---------------------------------------------------------------------------
 static void build_butterfly(Butterfly& B, const Entries& K, int64_t n0, double tol, uint64_t seed, bool par) {
+  const Geometry& geo = *K.g;
   const int L = B.L;
   const int64_t npairs = (int64_t)1 << L;
   B.col.assign(B.hc, std::vector<IdBlock>(npairs));
@@ -291,15 +388,9 @@ static void build_butterfly(Butterfly& B, const Entries& K, int64_t n0, double t
             pool.insert(pool.end(), cb.skel.begin(), cb.skel.end());
           }
         }
-        int c = (int)cand.size();
-        std::vector<int64_t> pos;
         uint64_t sd = seed ^ (0x1000003ull * (uint64_t)(d + 1)) ^ (0x9E37ull * (uint64_t)g) ^ 0xABCDull;
-        sample_positions((int64_t)pool.size(), sample_count(c), sd, pos);
-        int s = (int)pos.size();
-        std::vector<cplx> M((size_t)s * c);
-        for (int cc = 0; cc < c; ++cc)
-          for (int r = 0; r < s; ++r) M[(size_t)cc * s + r] = K(cand[cc], pool[pos[r]]);
-        column_id(M, s, c, tol, blk);
+        // row ID: entries K(candidate row, sampled column)
+        adaptive_id(geo, pool, cand, tol, sd, [&](int64_t col, int64_t row) { return K(row, col); }, blk);
         blk.skel.resize(blk.k);
         for (int i = 0; i < blk.k; ++i) blk.skel[i] = cand[blk.q[i]];
       }
@@ -331,15 +422,9 @@ static void build_butterfly(Butterfly& B, const Entries& K, int64_t n0, double t
           const IdBlock& rb = B.row[d][bp * na2 + aa];
           pool.insert(pool.end(), rb.skel.begin(), rb.skel.end());
         }
-        int c = (int)cand.size();
-        std::vector<int64_t> pos;
         uint64_t sd = seed ^ (0x2000011ull * (uint64_t)(d + 1)) ^ (0x7F4Aull * (uint64_t)g) ^ 0x1234ull;
-        sample_positions((int64_t)pool.size(), sample_count(c), sd, pos);
-        int s = (int)pos.size();
-        std::vector<cplx> M((size_t)s * c);
-        for (int cc = 0; cc < c; ++cc)
-          for (int r = 0; r < s; ++r) M[(size_t)cc * s + r] = K(pool[pos[r]], cand[cc]);
-        column_id(M, s, c, tol, blk);
+        // column ID: entries K(sampled row, candidate column)
+        adaptive_id(geo, pool, cand, tol, sd, [&](int64_t row, int64_t col) { return K(row, col); }, blk);
         blk.skel.resize(blk.k);
         for (int i = 0; i < blk.k; ++i) blk.skel[i] = cand[blk.q[i]];
       }
@@ -381,6 +466,11 @@ static void triangle_inverse(const cplx* A, int n0, bool lower, cplx* X) {
     }
   }
 }
+
+// The sampled IDs truncate at eps / 10 (the tightened tolerance of the reading of
+// Eq. (req)): per-ID errors of the sampled construction accumulate over the
+// L + 3 factors of a butterfly and over the H-IDBF levels.
+static constexpr double kIdTolFactor = 0.1;
 
 int build_factor(const Geometry& g, double wavelength, double eta0, double gamma, int64_t leaf, double eps,
                  uint64_t seed, HostFactor& hf) {
@@ -444,7 +534,7 @@ int build_factor(const Geometry& g, double wavelength, double eta0, double gamma
     uint64_t sdv = seed * 0x100000001B3ull;
 #pragma omp parallel for schedule(dynamic, 1) if (outer)
     for (int64_t i = 0; i < cnt; ++i)
-      build_butterfly(hf.bf[first + i], K, leaf, eps, sdv ^ (uint64_t)(first + i) * 0xC2B2AE35ull, !outer);
+      build_butterfly(hf.bf[first + i], K, leaf, eps * kIdTolFactor, sdv ^ (uint64_t)(first + i) * 0xC2B2AE35ull, !outer);
   }
   hf.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return HB_OK;

@@ -228,6 +228,29 @@ __global__ void k_far_field(const double* __restrict__ cx, const double* __restr
   }
 }
 
+// out[r][n] (col-major, ld) = conj(C) w_n sum_q exp(-i k (x_n cos phi_q + y_n sin phi_q)) g[r][q]
+// (the conjugate transpose of the far-field map), one thread per (n, r), fixed-order sum over q.
+__global__ void k_far_field_adj(const double* __restrict__ cx, const double* __restrict__ cy,
+                                const double* __restrict__ w, int64_t n, const double2* __restrict__ g, int64_t nobs,
+                                const double* __restrict__ cphi, const double* __restrict__ sphi, int64_t R,
+                                double kappa, double2 Cc, double2* __restrict__ out, int64_t ld) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e < n * R; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % n, r = e / n;
+    double2 acc = {0.0, 0.0};
+    for (int64_t q = 0; q < nobs; ++q) {
+      double ph = -kappa * (cx[i] * cphi[q] + cy[i] * sphi[q]);
+      double s, c;
+      sincos(ph, &s, &c);
+      double2 gv = g[r * nobs + q];
+      acc.x += gv.x * c - gv.y * s;
+      acc.y += gv.x * s + gv.y * c;
+    }
+    acc = {w[i] * acc.x, w[i] * acc.y};
+    out[r * ld + i] = {Cc.x * acc.x - Cc.y * acc.y, Cc.x * acc.y + Cc.y * acc.x};
+  }
+}
+
 // ---------------------------------------------------------------------------
 // GMRES machinery
 // ---------------------------------------------------------------------------
@@ -576,6 +599,33 @@ static int far_common(hb_factor_t f, const void* x, int64_t nrhs, int64_t ld, co
 extern "C" int hb_far_field(hb_factor_t f, const void* x, int64_t nrhs, int64_t ld, const double* phi_obs_deg,
                             int64_t nobs, void* out, void* stream) {
   return far_common(f, x, nrhs, ld, phi_obs_deg, nobs, out, stream, false);
+}
+
+extern "C" int hb_far_field_adjoint(hb_factor_t f, const void* g, int64_t nrhs, const double* phi_obs_deg,
+                                    int64_t nobs, void* out, int64_t ld, void* stream) {
+  if (!f || f->host_only || !g || !phi_obs_deg || !out || nrhs < 1 || nobs < 1 || ld < f->df.n) {
+    set_error("hb_far_field_adjoint: bad argument");
+    return HB_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<double> cs(2 * nobs);
+  for (int64_t q = 0; q < nobs; ++q) {
+    double ph = phi_obs_deg[q] * M_PI / 180.0;
+    cs[q] = std::cos(ph);
+    cs[nobs + q] = std::sin(ph);
+  }
+  double* d = (double*)f->ws.get(WS_SMALL, std::max<size_t>(256, cs.size() * sizeof(double)));
+  if (!d) { set_error("hb_far_field_adjoint: allocation failed"); return HB_ENOMEM; }
+  cudaMemcpyAsync(d, cs.data(), cs.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  const double k = f->df.kappa;
+  std::complex<double> C = -(k * f->df.eta0 / 4.0) * std::sqrt(std::complex<double>(0.0, 2.0 / (M_PI * k)));
+  std::complex<double> Cc = std::conj(C);
+  k_far_field_adj<<<gsz(f->df.n * nrhs), 256, 0, st>>>(f->df.cx, f->df.cy, f->df.w, f->df.n, (const double2*)g, nobs,
+                                                       d, d + nobs, nrhs, k, double2{Cc.real(), Cc.imag()},
+                                                       (double2*)out, ld);
+  count_launch(f, 1);
+  if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("hb_far_field_adjoint: CUDA error"); return HB_ECUDA; }
+  return HB_OK;
 }
 
 extern "C" int hb_monostatic(hb_factor_t f, const void* x, int64_t nrhs, int64_t ld, const double* phi_deg, void* out,

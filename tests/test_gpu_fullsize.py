@@ -1,0 +1,74 @@
+"""Full-size parity on the benchmark workload (semicircle, N = 262,144, 256 plane waves,
+complex-FP32 form, autotuned sweep, FGMRES(30) + IR), checked on sampled outputs that the
+oracle computes one row at a time with its own Hankel function.
+
+For S sampled rows i and a right-hand side b, the oracle forms the exact residual
+r_i = b^_i - sum_j A^_ij x_j.  The solve stops at ||b^ - A^_F x|| <= 1e-6 ||b^|| and the
+compressed operator differs from A^ by at most 10 eps, so the sampled estimate of the
+exact relative residual, sqrt(N/S sum |r_i|^2) / ||b^||, must stay below 2 (10 eps + rtol)
+(factor 2: sampling noise).  The same bound (10 eps, x2) applies to sampled rows of
+hb_apply against exact rows of A^ x.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import efie
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def big():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_11371_gb300 import build
+    build.build()
+    import paper_1901_11371_gb300 as hb
+    wl = W.CONFIG3
+    g = hb.hb_geometry(wl.kind, wl.params, wl.n)
+    f = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C64)
+    hb.hb_autotune(f, 256)
+    p = efie.Problem.from_workload(wl)
+    return torch, hb, wl, f, p
+
+
+def _exact_rows(p, rows, xs):
+    """Exact A^ rows (oracle Hankel) applied to the columns xs [n, R]."""
+    cols = np.arange(p.n)
+    out = []
+    for i in rows:
+        a_row = p.entries(np.array([i]), cols)[0] * p.scale
+        out.append(a_row @ xs)
+    return np.array(out)
+
+
+def test_fullsize_apply_sampled_rows(big):
+    torch, hb, wl, f, p = big
+    x = W.complex_gaussian(wl.n, 70)
+    y = hb.hb_apply(f, torch.from_numpy(x).to(torch.complex64).cuda()).cpu().numpy().astype(np.complex128)
+    rows = W.sample_rows(wl.n, 16, W.SEED_ROWS)
+    exact = _exact_rows(p, rows, x.astype(np.complex64).astype(np.complex128)[:, None])[:, 0]
+    est = math.sqrt(wl.n / len(rows) * np.sum(np.abs(y[rows] - exact) ** 2)) / np.linalg.norm(y)
+    assert est <= 2 * 10 * wl.eps, est
+
+
+def test_fullsize_batched_solve_sampled_residual(big):
+    torch, hb, wl, f, p = big
+    phis = W.incidence_angles_deg(3)
+    b = hb.hb_rhs_plane_wave(f, phis)
+    x, info = hb.hb_gmres(f, b, rtol=1e-6, restart=30, maxit=600)
+    assert info["converged"] == 256 and info["true_rel_res"] <= 1e-6
+    assert info["iters"] < 60
+    cols = [0, 77, 128, 255]
+    xs = x.cpu().numpy()[cols].T                           # [n, 4]
+    bs = p.plane_wave(phis[cols]) * p.scale                # oracle's own excitation
+    rows = W.sample_rows(wl.n, 16, W.SEED_ROWS + 1)
+    ax = _exact_rows(p, rows, xs)                          # [16, 4]
+    for j in range(len(cols)):
+        r = bs[rows, j] - ax[:, j]
+        est = math.sqrt(wl.n / len(rows) * np.sum(np.abs(r) ** 2)) / np.linalg.norm(bs[:, j])
+        assert est <= 2 * (10 * wl.eps + 1e-6), (cols[j], est)
