@@ -177,8 +177,14 @@ def run_gpu(args, rank, world):
     def solve(fac, bb, out):
         return hb.hb_gmres(fac, bb, restart=RESTART, rtol=RTOL, maxit=MAXIT, out=out)
 
+    def step(bb, out):
+        # one step: batched solve, then the monostatic far field at every incidence angle
+        _, inf = solve(f32, bb, out)
+        mono = hb.hb_monostatic(f32, out, phis)
+        return inf, mono
+
     for _ in range(args.warmup):
-        _, info = solve(f32, b, x)
+        info, mono = step(b, x)
     # ---- timed region: device events on the launching stream
     hb.hb_profile(f32, True)
     clocks = ClockSampler(dev)
@@ -190,7 +196,7 @@ def run_gpu(args, rank, world):
     ev0.record(stream)
     infos = []
     for _ in range(args.steps):
-        _, info = solve(f32, b, x)
+        info, mono = step(b, x)
         infos.append(info)
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -218,14 +224,17 @@ def run_gpu(args, rank, world):
     e0 = time.perf_counter()
     for _ in range(args.steps):
         b_dev.copy_(b_host, non_blocking=True)
-        solve(f32, b_dev, x)
+        _, mono = step(b_dev, x)
         x_host.copy_(x, non_blocking=True)
+        mono_host = mono.cpu()
         torch.cuda.synchronize()
     e_s = time.perf_counter() - e0
     e2e = {"value": args.steps * NRHS / e_s, "unit": UNIT, "h2d_bytes_per_step": int(b.numel() * 16),
-           "d2h_bytes_per_step": int(x.numel() * 16)}
+           "d2h_bytes_per_step": int(x.numel() * 16 + NRHS * 16)}
 
+    mono_np = mono.cpu().numpy()
     out = dict(value=value, ms=ms_max, iters=iters, res=res, st=st, t_build=t_build, clocks=clk, e2e=e2e, tuned=tuned,
+               mono_db=[float(v) for v in 20 * np.log10(np.abs(mono_np[::32]) + 1e-300)],
                n_apply=n_apply, ms_apply=ms_apply, n_sweep=n_sweep, ms_sweep=ms_sweep, n_launch=n_launch,
                x=x)
     # ---- plain FP64 GPU form on the same workload (rank 0 only, untimed by the contract)
@@ -371,6 +380,7 @@ def main():
                    "l2": f"inputs larger than L2: factor {st['device_bytes'] / 1e6:.0f} MB",
                    "kmax": st["kmax"], "kavg": round(st["kavg"], 2), "build_s": round(out["t_build"], 2)},
         "iters_per_solve": out["iters"], "true_rel_res": out["res"],
+        "monostatic_dB_every_32nd_angle": out["mono_db"],
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "algorithmic_bytes_per_launch": algo,
                      "avg_launch_ms": avg_ms, "peak_source": peak_kind,
