@@ -170,6 +170,7 @@ def run_gpu(args, rank, world):
     t_build = time.perf_counter() - t0
     st = hb.hb_factor_info(f32)
     tuned = hb.hb_autotune(f32, NRHS)
+    tune_ms = hb.hb_autotune_times(f32, NRHS)
     phis = W.incidence_angles_deg(3) + (rank * 180.0 / NRHS / max(world, 1) if world > 1 else 0.0)
     b = hb.hb_rhs_plane_wave(f32, phis)
     x = torch.empty_like(b)
@@ -233,7 +234,7 @@ def run_gpu(args, rank, world):
            "d2h_bytes_per_step": int(x.numel() * 16 + NRHS * 16)}
 
     mono_np = mono.cpu().numpy()
-    out = dict(value=value, ms=ms_max, iters=iters, res=res, st=st, t_build=t_build, clocks=clk, e2e=e2e, tuned=tuned,
+    out = dict(value=value, ms=ms_max, iters=iters, res=res, st=st, t_build=t_build, clocks=clk, e2e=e2e, tuned=tuned, tune_ms=tune_ms,
                mono_db=[float(v) for v in 20 * np.log10(np.abs(mono_np[::32]) + 1e-300)],
                n_apply=n_apply, ms_apply=ms_apply, n_sweep=n_sweep, ms_sweep=ms_sweep, n_launch=n_launch,
                x=x)
@@ -272,8 +273,12 @@ def run_kernels(args):
     R = args.nrhs
     g = hb.hb_geometry(wl.kind, wl.params, wl.n)
     f = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C64 if args.form == "c64" else hb.HB_C128)
+    tuned, times = None, {}
     if args.grid_min:
         hb.lib().hb_set_sweep_grid_min(f._h, args.grid_min)
+    else:
+        tuned = hb.hb_autotune(f, R)
+        times = hb.hb_autotune_times(f, R)
     st = hb.hb_factor_info(f)
     dt = torch.complex64 if args.form == "c64" else torch.complex128
     x = torch.randn((R, wl.n) if R > 1 else (wl.n,), dtype=dt, device="cuda")
@@ -296,7 +301,8 @@ def run_kernels(args):
     ms_u = timed(lambda: hb.hb_upper_solve(f, x), args.steps)
     eb = 8 if args.form == "c64" else 16
     vec_extra = 2 * wl.n * (R - 1) * eb
-    out = {"mode": "kernels", "workload": wl.name, "nrhs": R, "form": args.form, "grid_min": args.grid_min or 16,
+    out = {"mode": "kernels", "workload": wl.name, "nrhs": R, "form": args.form,
+           "grid_min": args.grid_min or tuned, "autotune_ms": times,
            "apply_ms": ms_a, "lower_ms": ms_l, "upper_ms": ms_u,
            "apply_GBps": (st["apply_bytes"] + vec_extra) / ms_a / 1e6,
            "lower_GBps": (st["lower_bytes"] + vec_extra) / ms_l / 1e6,
@@ -377,6 +383,7 @@ def main():
                                "eps 1e-6, 256 plane waves phi_i = 180 i/256 deg per step",
                    "form": f"FP64 FGMRES({RESTART}) + IR around complex-FP32 U~^-1 L~^-1 and A_F (CUDA cores)",
                    "rhs_per_step": NRHS, "sweep_grid_min": out["tuned"],
+                   "sweep_autotune_ms": {str(k): round(v, 3) for k, v in out["tune_ms"].items()},
                    "l2": f"inputs larger than L2: factor {st['device_bytes'] / 1e6:.0f} MB",
                    "kmax": st["kmax"], "kavg": round(st["kavg"], 2), "build_s": round(out["t_build"], 2)},
         "iters_per_solve": out["iters"], "true_rel_res": out["res"],

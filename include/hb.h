@@ -222,6 +222,13 @@ int hb_set_sweep_grid_min(hb_factor_t f, int grid_min);
  * Not in the paper: launch-configuration tuning. */
 int hb_autotune(hb_factor_t f, int64_t nrhs, void* stream, int* chosen);
 
+/* hb_autotune_times -- the per-candidate sweep times (ms per sweep) of the
+ * last hb_autotune call of the class of nrhs (one / several right-hand
+ * sides), with the candidates' thresholds (2^30 = all single-CTA).  Writes
+ * min(max, 6) entries to ms_out / grid_min_out (host arrays) and returns the
+ * number written, 0 if that class was never tuned, or HB_EINVAL. */
+int hb_autotune_times(hb_factor_t f, int64_t nrhs, float* ms_out, int* grid_min_out, int max);
+
 /* hb_set_wait_limit -- iteration limit of every bounded device-side wait
  * (the sweep kernel's grid barrier; default 2^24 polls, about a second).
  * hb_status -- synchronise `stream`, then return HB_ETIMEOUT (and clear the

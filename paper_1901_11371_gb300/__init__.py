@@ -22,7 +22,7 @@ __all__ = ["HB_STRIP", "HB_SPIRAL", "HB_ARC", "HB_PARALLEL_STRIPS", "HB_C128", "
            "HB_OP_N", "HB_OP_H", "HBError", "Geometry", "Factor", "hb_geometry", "hb_factor", "hb_factor_host",
            "hb_factor_info", "hb_tree", "hb_apply", "hb_apply_adjoint", "hb_precond_solve", "hb_lower_solve",
            "hb_upper_solve", "hb_residual", "hb_gmres", "hb_rhs_plane_wave", "hb_far_field", "hb_monostatic",
-           "hb_host_apply", "hb_host_sweep", "hb_far_field_adjoint", "hb_profile", "hb_profile_read", "hb_autotune", "lib"]
+           "hb_host_apply", "hb_host_sweep", "hb_far_field_adjoint", "hb_profile", "hb_profile_read", "hb_autotune", "hb_autotune_times", "lib"]
 
 
 def lib():
@@ -242,6 +242,16 @@ def hb_autotune(f, nrhs, stream=None):
     ch = C.c_int()
     _lib.check(lib().hb_autotune(f._h, int(nrhs), _stream(stream), C.byref(ch)))
     return ch.value
+
+
+def hb_autotune_times(f, nrhs):
+    """{threshold: ms per sweep} of the last hb_autotune for the class of `nrhs` ({} if untuned)."""
+    ms = (C.c_float * 6)()
+    gm = (C.c_int * 6)()
+    n = lib().hb_autotune_times(f._h, int(nrhs), ms, gm, 6)
+    if n < 0:
+        _lib.check(n)
+    return {int(gm[i]): float(ms[i]) for i in range(n)}
 
 
 def hb_profile(f, enable=True):

@@ -69,6 +69,7 @@ SIGNATURES = {
     "hb_set_sweep_grid_min": (_INT, [_VP, _INT]),
     "hb_set_wait_limit": (_INT, [_VP, C.c_longlong]),
     "hb_autotune": (_INT, [_VP, _I64, _VP, C.POINTER(C.c_int)]),
+    "hb_autotune_times": (_INT, [_VP, _I64, C.POINTER(C.c_float), C.POINTER(C.c_int), C.c_int]),
     "hb_status": (_INT, [_VP, _VP]),
     "hb_profile": (_INT, [_VP, _INT]),
     "hb_profile_read": (_INT, [_VP, _INT, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),

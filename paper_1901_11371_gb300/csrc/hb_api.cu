@@ -98,23 +98,20 @@ int upload_factor(const PackedHost& ph, const HostFactor& hf, const Geometry& g,
     if ((rc = up(*progs[i], &df.prog[i], st, df.device_bytes))) return rc;
     df.nprog[i] = (int)progs[i]->size();
     FlatProgram fpg = flatten_program(ph, *progs[i], ph.n0);
+    if (!fpg.ok) {
+      set_error("sweep program: an op does not fit the 64-byte record");
+      return HB_EUNSUPPORTED;
+    }
     if ((rc = up(fpg.ops, &df.flat[i], st, df.device_bytes))) return rc;
     if ((rc = up(fpg.base, &df.flat_base[i], st, df.device_bytes))) return rc;
+    if ((rc = up(fpg.pbytes, &df.flat_pbytes[i], st, df.device_bytes))) return rc;
     HB_CU(cudaStreamSynchronize(st));
   }
   HB_CU(cudaMalloc(&df.bar, 64));
   HB_CU(cudaMemsetAsync(df.bar, 0, 64, st));
   if ((rc = set_grid_min(df, ph, 16, st))) return rc;
-  for (int i = 0; i < 4; ++i) {
-    FlatProgram fpg = flatten_program(ph, *progs[i], ph.n0);
-    for (int c = 0; c < DevFactor::kNCand; ++c) {
-      std::vector<DSeg> segs = segment_program(*progs[i], DevFactor::kCand[c]);
-      annotate_segments(segs, fpg);
-      if ((rc = up(segs, &df.cand_segs[i][c], st, df.device_bytes))) return rc;
-      df.cand_nsegs[i][c] = (int)segs.size();
-    }
-    HB_CU(cudaStreamSynchronize(st));
-  }
+  if ((rc = build_candidates(df, ph, 0, 1, st))) return rc;
+  if ((rc = build_candidates(df, ph, 1, 2, st))) return rc;
   if ((rc = up(g.cx, &df.cx, st, df.device_bytes))) return rc;
   if ((rc = up(g.cy, &df.cy, st, df.device_bytes))) return rc;
   if ((rc = up(g.w, &df.w, st, df.device_bytes))) return rc;
@@ -122,12 +119,19 @@ int upload_factor(const PackedHost& ph, const HostFactor& hf, const Geometry& g,
   return HB_OK;
 }
 
+int64_t resident_budget(int64_t cols, size_t es) {
+  const int64_t wr = cols <= 2 ? (cols < 1 ? 1 : cols) : (cols <= 4 ? 4 : (cols + 7) / 8 * 8);
+  return (int64_t)kResidentBytes / (wr * (int64_t)es);
+}
+
+static size_t vec_elem_bytes(const DevFactor& df) { return df.form == HB_C128 ? 16 : 8; }
+
 int set_grid_min(DevFactor& df, const PackedHost& ph, int grid_min, cudaStream_t st) {
   const std::vector<DPhase>* progs[4] = {&ph.prog_lower, &ph.prog_upper, &ph.prog_lower_adj, &ph.prog_upper_adj};
   HB_CU(cudaStreamSynchronize(st));
+  const int64_t budget = resident_budget(1, vec_elem_bytes(df));
   for (int i = 0; i < 4; ++i) {
-    std::vector<DSeg> segs = segment_program(*progs[i], grid_min);
-    annotate_segments(segs, flatten_program(ph, *progs[i], ph.n0));
+    std::vector<DSeg> segs = segment_program(*progs[i], flatten_program(ph, *progs[i], ph.n0), grid_min, budget);
     if (df.segs[i]) { cudaFree(df.segs[i]); df.segs[i] = nullptr; }
     int64_t dummy = 0;
     int rc = up(segs, &df.segs[i], st, dummy);
@@ -139,20 +143,40 @@ int set_grid_min(DevFactor& df, const PackedHost& ph, int grid_min, cudaStream_t
   return HB_OK;
 }
 
+int build_candidates(DevFactor& df, const PackedHost& ph, int cls, int64_t cols, cudaStream_t st) {
+  const std::vector<DPhase>* progs[4] = {&ph.prog_lower, &ph.prog_upper, &ph.prog_lower_adj, &ph.prog_upper_adj};
+  const int64_t budget = resident_budget(cols, vec_elem_bytes(df));
+  if (df.cand_segs[cls][0][0] && df.cand_budget[cls] == budget) return HB_OK;
+  HB_CU(cudaStreamSynchronize(st));
+  for (int i = 0; i < 4; ++i) {
+    FlatProgram fpg = flatten_program(ph, *progs[i], ph.n0);
+    for (int c = 0; c < DevFactor::kNCand; ++c) {
+      std::vector<DSeg> segs = segment_program(*progs[i], fpg, DevFactor::kCand[c], budget);
+      if (df.cand_segs[cls][i][c]) { cudaFree(df.cand_segs[cls][i][c]); df.cand_segs[cls][i][c] = nullptr; }
+      int64_t dummy = 0;
+      int rc = up(segs, &df.cand_segs[cls][i][c], st, dummy);
+      if (rc) return rc;
+      df.cand_nsegs[cls][i][c] = (int)segs.size();
+    }
+  }
+  HB_CU(cudaStreamSynchronize(st));
+  df.cand_budget[cls] = budget;
+  return HB_OK;
+}
+
 void free_factor(DevFactor& df) {
   void* ptrs[] = {df.fpool, df.leaf, df.linv, df.uinv, df.ipool, df.vout, df.uout, df.bvout, df.buout,
                   df.bf_vout0, df.bf_uout0, df.items, df.step_idx, df.astep_idx, df.prog[0], df.prog[1],
                   df.prog[2], df.prog[3], df.segs[0], df.segs[1], df.segs[2], df.segs[3], df.bar,
                   df.flat[0], df.flat[1], df.flat[2], df.flat[3], df.flat_base[0], df.flat_base[1],
-                  df.flat_base[2], df.flat_base[3],
-                  df.cand_segs[0][0], df.cand_segs[0][1], df.cand_segs[0][2], df.cand_segs[0][3], df.cand_segs[0][4],
-                  df.cand_segs[0][5], df.cand_segs[1][0], df.cand_segs[1][1], df.cand_segs[1][2], df.cand_segs[1][3],
-                  df.cand_segs[1][4], df.cand_segs[1][5], df.cand_segs[2][0], df.cand_segs[2][1], df.cand_segs[2][2],
-                  df.cand_segs[2][3], df.cand_segs[2][4], df.cand_segs[2][5], df.cand_segs[3][0], df.cand_segs[3][1],
-                  df.cand_segs[3][2], df.cand_segs[3][3], df.cand_segs[3][4], df.cand_segs[3][5],
-                  df.cx, df.cy, df.w};
+                  df.flat_base[2], df.flat_base[3], df.flat_pbytes[0], df.flat_pbytes[1], df.flat_pbytes[2],
+                  df.flat_pbytes[3], df.cx, df.cy, df.w};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (auto& per_cls : df.cand_segs)
+    for (auto& per_prog : per_cls)
+      for (DSeg* p : per_prog)
+        if (p) cudaFree(p);
   df = DevFactor();
 }
 
@@ -379,6 +403,15 @@ int hb_autotune(hb_factor_t f, int64_t nrhs, void* stream, int* chosen) {
   if (!v) { set_error("hb_autotune: workspace allocation failed"); return HB_ENOMEM; }
   if (cudaMemsetAsync(v, 0, (size_t)df.n * nrhs * es, st) != cudaSuccess) return HB_ECUDA;
   const int cls = nrhs > 1 ? 1 : 0;
+  {
+    // candidate segmentations cut for this many columns per CTA
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t cols = (nrhs + std::max(sms, 1) - 1) / std::max(sms, 1);
+    int rc = build_candidates(df, f->ph, cls, cols, st);
+    if (rc) return rc;
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -394,6 +427,7 @@ int hb_autotune(hb_factor_t f, int64_t nrhs, void* stream, int* chosen) {
     cudaEventSynchronize(e1);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
+    df.cand_ms[cls][c] = ms / 2;
     if (ms < best) { best = ms; bestc = c; }
   }
   cudaEventDestroy(e0);
@@ -401,6 +435,21 @@ int hb_autotune(hb_factor_t f, int64_t nrhs, void* stream, int* chosen) {
   df.tuned[cls] = bestc;
   if (chosen) *chosen = DevFactor::kCand[bestc];
   return hb_status(f, stream);
+}
+
+int hb_autotune_times(hb_factor_t f, int64_t nrhs, float* ms_out, int* grid_min_out, int max) {
+  if (!f || f->host_only || nrhs < 1 || max < 0 || (max > 0 && (!ms_out || !grid_min_out))) {
+    set_error("hb_autotune_times: bad argument");
+    return HB_EINVAL;
+  }
+  const int cls = nrhs > 1 ? 1 : 0;
+  if (f->df.tuned[cls] < 0) return 0;
+  const int n = std::min(max, DevFactor::kNCand);
+  for (int c = 0; c < n; ++c) {
+    ms_out[c] = f->df.cand_ms[cls][c];
+    grid_min_out[c] = DevFactor::kCand[c];
+  }
+  return n;
 }
 
 int hb_set_wait_limit(hb_factor_t f, long long spins) {

@@ -36,14 +36,19 @@ struct DevFactor {
   int nprog[4] = {0, 0, 0, 0};
   FlatOp* flat[4] = {nullptr, nullptr, nullptr, nullptr};   // resolved op records of each program
   int32_t* flat_base[4] = {nullptr, nullptr, nullptr, nullptr};
+  int32_t* flat_pbytes[4] = {nullptr, nullptr, nullptr, nullptr};   // staging bytes per phase
   DSeg* segs[4] = {nullptr, nullptr, nullptr, nullptr};     // cooperative-kernel segments of each program
   int nsegs[4] = {0, 0, 0, 0};
   int grid_min = 0;                                         // phases with >= grid_min ops run grid-wide
-  // autotuner: segmentations of each program for the candidate thresholds
+  // autotuner: segmentations of each program for the candidate thresholds,
+  // one set per class (0: one right-hand side, 1: several), each cut for the
+  // shared-memory budget of that class's columns per CTA
   static constexpr int kNCand = 6;
   static constexpr int kCand[kNCand] = {4, 8, 16, 32, 64, 1 << 30};
-  DSeg* cand_segs[4][kNCand] = {};
-  int cand_nsegs[4][kNCand] = {};
+  DSeg* cand_segs[2][4][kNCand] = {};
+  int cand_nsegs[2][4][kNCand] = {};
+  int64_t cand_budget[2] = {0, 0};                          // residency budget (entries) of each set
+  float cand_ms[2][kNCand] = {};                            // last autotune timings
   int tuned[2] = {-1, -1};                                  // chosen candidate for 1 RHS / several RHS (-1: grid_min)
   void* bar = nullptr;                                      // grid barrier state + error flag
   long long spin_limit = 1LL << 24;                         // bounded waits of the grid barrier
@@ -78,8 +83,17 @@ int launch_sweep_coop(const DevFactor& df, Prec p, int which, void* vec, int64_t
                       cudaStream_t st, long long spin_limit);
 // Read the barrier error flag (synchronises st).  *err != 0: a bounded wait expired.
 int read_grid_error(void* bar, cudaStream_t st, int* err);
+// Shared memory that a single-CTA run may use to keep its vector rows and
+// butterfly state resident (bytes; the sweep kernel's layout holds this much).
+constexpr int kResidentBytes = 56 * 1024;
+// Residency budget in entries per right-hand side for `cols` columns per CTA
+// of element size `es` bytes (the kernel rounds the columns up to its chunk).
+int64_t resident_budget(int64_t cols, size_t es);
 // (Re)build the cooperative segments of the four programs for threshold grid_min.
 int set_grid_min(DevFactor& df, const PackedHost& ph, int grid_min, cudaStream_t st);
+// (Re)build the autotuner's candidate segmentations of class cls for
+// `cols` columns per CTA.
+int build_candidates(DevFactor& df, const PackedHost& ph, int cls, int64_t cols, cudaStream_t st);
 
 // Layout conversion between the ABI's column-major [R][ld] blocks and the
 // internal [row][R] layout, with optional precision change and scaling.

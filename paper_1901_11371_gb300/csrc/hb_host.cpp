@@ -965,7 +965,8 @@ FlatProgram flatten_program(const PackedHost& ph, const std::vector<DPhase>& pro
         f.ioff = -1;
         f.c0 = (int16_t)n0;
         f.src0 = (int32_t)(P.arg0 * n0);
-        f.n_s0 = (int32_t)n0;
+        f.n_s0 = (int16_t)n0;
+        if (n0 > INT16_MAX) fp.ok = false;
         f.out0 = f.src0;
       } else if (P.kind == PH_ENTER || P.kind == PH_EXIT) {
         const bool enter = P.kind == PH_ENTER;
@@ -974,7 +975,7 @@ FlatProgram flatten_program(const PackedHost& ph, const std::vector<DPhase>& pro
         f.moff = op.blk.moff;
         f.melems = (int32_t)blkm(op.blk);
         f.ioff = op.blk.ioff;
-        f.ielems = 2 * op.blk.c;
+        f.ielems = (int16_t)(2 * op.blk.c);
         f.k0 = op.blk.k;
         f.c0 = op.blk.c;
         if (enter) {
@@ -1011,8 +1012,10 @@ FlatProgram flatten_program(const PackedHost& ph, const std::vector<DPhase>& pro
           f.m1 = (int32_t)(b1.moff - b0.moff);
           f.melems = (int32_t)(f.m1 + blkm(b1));
           f.ioff = b0.ioff;
-          f.i1 = b1.ioff - b0.ioff;
-          f.ielems = f.i1 + 2 * b1.c;
+          const int64_t i1 = (int64_t)b1.ioff - b0.ioff, ie = i1 + 2 * (int64_t)b1.c;
+          if (i1 < 0 || ie > INT16_MAX) fp.ok = false;   // index blocks of an item must be adjacent
+          f.i1 = (int16_t)i1;
+          f.ielems = (int16_t)ie;
           f.k0 = b0.k; f.c0 = b0.c; f.k1 = b1.k; f.c1 = b1.c;
           const bool to_b = (it.type == 0) != adj;
           if (to_b) {
@@ -1033,36 +1036,108 @@ FlatProgram flatten_program(const PackedHost& ph, const std::vector<DPhase>& pro
       }
       fp.ops.push_back(f);
     }
+    // staging offsets of the phase's ops (one contiguous area per phase)
+    int32_t off = 0;
+    for (int32_t o = fp.base.back(); o < (int32_t)fp.ops.size(); ++o) {
+      fp.ops[o].soff = off;
+      off += flat_stage_bytes32(fp.ops[o]);
+    }
+    fp.pbytes.push_back(off);
   }
   fp.base.push_back((int32_t)fp.ops.size());
   return fp;
 }
 
+namespace {
+// outputs (state entries or vector rows) of one op: [out0, out0+n0) and [out1, out1+n1)
+void op_outputs(const FlatOp& f, int& n_out0, int& n_out1) {
+  n_out0 = (f.kind == FK_GATHER) ? f.k0 : (f.kind == FK_SCATTER) ? ((f.flags & FF_TWO) ? f.split : f.c0)
+         : (f.kind == FK_MIDDLE) ? ((f.flags & FF_ADJ) ? f.c0 : f.k0) : f.c0;
+  n_out1 = (f.kind == FK_GATHER && (f.flags & FF_TWO)) ? f.k1
+         : (f.kind == FK_SCATTER && (f.flags & FF_TWO)) ? f.c0 - f.split : 0;
+}
+
+// vector-row and state spans [lo, hi) touched by one phase (empty: lo = hi = 0)
+struct Span { int32_t row_lo, row_hi, st_lo, st_hi; };
+Span phase_span(const FlatProgram& fp, int ph) {
+  Span sp{INT32_MAX, 0, INT32_MAX, 0};
+  for (int32_t o = fp.base[ph]; o < fp.base[ph + 1]; ++o) {
+    const FlatOp& f = fp.ops[o];
+    auto row = [&](int32_t a, int32_t n) { sp.row_lo = std::min(sp.row_lo, a); sp.row_hi = std::max(sp.row_hi, a + n); };
+    auto stt = [&](int32_t a, int32_t n) { if (n > 0) { sp.st_lo = std::min(sp.st_lo, a); sp.st_hi = std::max(sp.st_hi, a + n); } };
+    int n_out0, n_out1;
+    op_outputs(f, n_out0, n_out1);
+    if (f.kind == FK_LEAF) { row(f.src0, f.n_s0); continue; }
+    if (f.flags & FF_SRC_VEC) row(f.src0, f.n_s0); else stt(f.src0, f.n_s0);
+    stt(f.src1, f.n_s1);
+    if (f.flags & FF_OUT_VEC) row(f.out0, n_out0); else stt(f.out0, n_out0);
+    stt(f.out1, n_out1);
+  }
+  if (sp.row_lo > sp.row_hi) sp.row_lo = sp.row_hi = 0;
+  if (sp.st_lo > sp.st_hi) sp.st_lo = sp.st_hi = 0;
+  return sp;
+}
+}  // namespace
+
 void annotate_segments(std::vector<DSeg>& segs, const FlatProgram& fp) {
-  for (DSeg& sg : segs) {
-    sg.row_lo = sg.st_lo = INT32_MAX;
-    sg.row_hi = sg.st_hi = 0;
-    if (sg.grid) { sg.row_lo = sg.st_lo = 0; continue; }
-    for (int32_t o = fp.base[sg.first]; o < fp.base[sg.first + sg.count]; ++o) {
-      const FlatOp& f = fp.ops[o];
-      auto row = [&](int32_t a, int32_t n) { sg.row_lo = std::min(sg.row_lo, a); sg.row_hi = std::max(sg.row_hi, a + n); };
-      auto stt = [&](int32_t a, int32_t n) { if (n > 0) { sg.st_lo = std::min(sg.st_lo, a); sg.st_hi = std::max(sg.st_hi, a + n); } };
-      const int n_out0 = (f.kind == FK_GATHER) ? f.k0 : (f.kind == FK_SCATTER) ? ((f.flags & FF_TWO) ? f.split : f.c0)
-                       : (f.kind == FK_MIDDLE) ? ((f.flags & FF_ADJ) ? f.c0 : f.k0) : f.c0;
-      const int n_out1 = (f.kind == FK_GATHER && (f.flags & FF_TWO)) ? f.k1
-                       : (f.kind == FK_SCATTER && (f.flags & FF_TWO)) ? f.c0 - f.split : 0;
-      if (f.kind == FK_LEAF) { row(f.src0, f.n_s0); continue; }
-      if (f.flags & FF_SRC_VEC) row(f.src0, f.n_s0); else stt(f.src0, f.n_s0);
-      stt(f.src1, f.n_s1);
-      if (f.flags & FF_OUT_VEC) row(f.out0, n_out0); else stt(f.out0, n_out0);
-      stt(f.out1, n_out1);
+  // st_cross: a single-CTA run that keeps its state in shared memory must
+  // produce every state entry it reads and consume every entry it writes.
+  {
+    int32_t st_len = 0;
+    for (const FlatOp& f : fp.ops) {
+      if (f.kind == FK_LEAF) continue;
+      int n0o, n1o;
+      op_outputs(f, n0o, n1o);
+      if (!(f.flags & FF_SRC_VEC)) st_len = std::max(st_len, f.src0 + f.n_s0);
+      if (f.n_s1 > 0) st_len = std::max(st_len, f.src1 + f.n_s1);
+      if (!(f.flags & FF_OUT_VEC)) st_len = std::max(st_len, f.out0 + n0o);
+      if (n1o > 0) st_len = std::max(st_len, f.out1 + n1o);
     }
-    if (sg.row_lo > sg.row_hi) sg.row_lo = sg.row_hi = 0;
-    if (sg.st_lo > sg.st_hi) sg.st_lo = sg.st_hi = 0;
+    std::vector<int32_t> writer((size_t)st_len, -1);   // segment that last wrote each state entry
+    for (size_t si = 0; si < segs.size(); ++si) segs[si].st_cross = 0;
+    for (size_t si = 0; si < segs.size(); ++si) {
+      DSeg& sg = segs[si];
+      for (int32_t o = fp.base[sg.first]; o < fp.base[sg.first + sg.count]; ++o) {
+        const FlatOp& f = fp.ops[o];
+        if (f.kind == FK_LEAF) continue;
+        auto rd = [&](int32_t a, int32_t n) {
+          for (int32_t e = a; e < a + n; ++e) {
+            const int32_t w = writer[(size_t)e];
+            if (w != (int32_t)si) {
+              sg.st_cross = 1;
+              if (w >= 0) segs[(size_t)w].st_cross = 1;
+            }
+          }
+        };
+        if (!(f.flags & FF_SRC_VEC)) rd(f.src0, f.n_s0);
+        if (f.n_s1 > 0) rd(f.src1, f.n_s1);
+        int n0o, n1o;
+        op_outputs(f, n0o, n1o);
+        if (!(f.flags & FF_OUT_VEC)) for (int32_t e = f.out0; e < f.out0 + n0o; ++e) writer[(size_t)e] = (int32_t)si;
+        for (int32_t e = f.out1; e < f.out1 + n1o; ++e) writer[(size_t)e] = (int32_t)si;
+      }
+    }
+  }
+  for (DSeg& sg : segs) {
+    sg.row_lo = sg.st_lo = sg.row_hi = sg.st_hi = 0;
+    if (sg.grid) continue;
+    bool rows = false, st = false;
+    for (int ph = sg.first; ph < sg.first + sg.count; ++ph) {
+      const Span v = phase_span(fp, ph);
+      if (v.row_hi > v.row_lo) {
+        if (!rows) { sg.row_lo = v.row_lo; sg.row_hi = v.row_hi; rows = true; }
+        else { sg.row_lo = std::min(sg.row_lo, v.row_lo); sg.row_hi = std::max(sg.row_hi, v.row_hi); }
+      }
+      if (v.st_hi > v.st_lo) {
+        if (!st) { sg.st_lo = v.st_lo; sg.st_hi = v.st_hi; st = true; }
+        else { sg.st_lo = std::min(sg.st_lo, v.st_lo); sg.st_hi = std::max(sg.st_hi, v.st_hi); }
+      }
+    }
   }
 }
 
-std::vector<DSeg> segment_program(const std::vector<DPhase>& prog, int grid_min) {
+std::vector<DSeg> segment_program(const std::vector<DPhase>& prog, const FlatProgram& fp, int grid_min,
+                                  int64_t res_entries) {
   std::vector<DSeg> segs;
   int n = (int)prog.size();
   int i = 0;
@@ -1072,13 +1147,76 @@ std::vector<DSeg> segment_program(const std::vector<DPhase>& prog, int grid_min)
     if (big(prog[i])) {
       segs.push_back(DSeg{1, i, 1, 0, 0, 0, 0, 0});
       ++i;
-    } else {
-      int j = i;
-      while (j < n && !big(prog[j])) ++j;
+      continue;
+    }
+    int j = i;
+    while (j < n && !big(prog[j])) ++j;
+    if (res_entries <= 0) {
       segs.push_back(DSeg{0, i, j - i, 0, 0, 0, 0, 0});
       i = j;
+      continue;
     }
+    // cut the run so that each piece's rows + state entries fit the budget;
+    // cuts fall between atoms (a leaf solve, or a butterfly from its entry
+    // phase to its exit phase), so that a piece holds whole butterflies (an
+    // atom that alone exceeds the budget forms a piece of its own)
+    auto atom_end = [&](int p) {
+      if (prog[p].kind != PH_ENTER) return p + 1;
+      int q = p + 1;
+      while (q < j && !(prog[q].kind == PH_EXIT && prog[q].arg0 == prog[p].arg0)) ++q;
+      return q < j ? q + 1 : j;
+    };
+    auto atom_span = [&](int p, int e) {
+      Span u = phase_span(fp, p);
+      for (int q = p + 1; q < e; ++q) {
+        Span v = phase_span(fp, q);
+        if (v.row_hi > v.row_lo) {
+          if (u.row_hi <= u.row_lo) { u.row_lo = v.row_lo; u.row_hi = v.row_hi; }
+          else { u.row_lo = std::min(u.row_lo, v.row_lo); u.row_hi = std::max(u.row_hi, v.row_hi); }
+        }
+        if (v.st_hi > v.st_lo) {
+          if (u.st_hi <= u.st_lo) { u.st_lo = v.st_lo; u.st_hi = v.st_hi; }
+          else { u.st_lo = std::min(u.st_lo, v.st_lo); u.st_hi = std::max(u.st_hi, v.st_hi); }
+        }
+      }
+      return u;
+    };
+    int s0 = i;
+    int ae = atom_end(i);
+    Span cur = atom_span(i, ae);
+    for (int p = ae; p <= j; p = ae) {
+      bool cut = (p == j);
+      Span nx{};
+      if (!cut) {
+        ae = atom_end(p);
+        nx = atom_span(p, ae);
+        auto lo = [](int32_t a, int32_t b, int32_t ha, int32_t hb) {
+          if (ha <= a) return b;           // empty span a
+          if (hb <= b) return a;
+          return std::min(a, b);
+        };
+        auto hi = [](int32_t a, int32_t b, int32_t la, int32_t lb) {
+          if (a <= la) return b;
+          if (b <= lb) return a;
+          return std::max(a, b);
+        };
+        Span u{lo(cur.row_lo, nx.row_lo, cur.row_hi, nx.row_hi), hi(cur.row_hi, nx.row_hi, cur.row_lo, nx.row_lo),
+               lo(cur.st_lo, nx.st_lo, cur.st_hi, nx.st_hi), hi(cur.st_hi, nx.st_hi, cur.st_lo, nx.st_lo)};
+        const int64_t foot = (int64_t)(u.row_hi - u.row_lo) + (int64_t)(u.st_hi - u.st_lo);
+        const int64_t nops = (int64_t)fp.base[ae] - fp.base[s0];
+        if (foot > res_entries || nops > kRunMaxOps || ae - s0 > kRunMaxPhases) cut = true;
+        else cur = u;
+      }
+      if (cut) {
+        segs.push_back(DSeg{0, s0, p - s0, 0, 0, 0, 0, 0});
+        s0 = p;
+        if (p < j) cur = nx;
+      }
+      if (p == j) break;
+    }
+    i = j;
   }
+  annotate_segments(segs, fp);
   return segs;
 }
 

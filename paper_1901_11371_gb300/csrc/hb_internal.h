@@ -139,12 +139,15 @@ struct DPhase {
 
 // A segment of a sweep program for the cooperative sweep kernel: either one
 // grid-wide phase (its ops spread over every CTA) or a run of consecutive
-// small phases executed by a single CTA; a grid barrier follows each segment.
+// small phases executed by a single CTA per group of right-hand sides; a grid
+// barrier separates two segments unless both are single-CTA runs (a CTA only
+// reads what it wrote itself there).
 struct DSeg {
   int32_t grid;      // 1 = grid-wide phase, 0 = single-CTA run
   int32_t first;     // first phase index
   int32_t count;     // number of phases
-  int32_t pad;
+  int32_t st_cross;  // 1 = the run reads butterfly state written outside it, or
+                     //     writes state read after it: keep it in global memory
   // single-CTA runs: the vector rows and butterfly-state entries the run
   // touches ([row_lo, row_hi), [st_lo, st_hi)); the kernel keeps them in
   // shared memory for the whole run when they fit.
@@ -162,21 +165,31 @@ struct FlatOp {
   int32_t melems;    // elements to stage (both blocks and the gap between them)
   int32_t m1;        // element offset of block 1 inside the staged matrices
   int32_t ioff;      // first index entry to stage (-1: none)
-  int32_t ielems;    // index entries to stage
-  int32_t i1;        // offset of block 1's indices
+  int32_t src0, src1;               // vector operand segments (state entries or vec rows)
+  int32_t out0, out1;               // outputs (state entries or vec rows)
+  int32_t soff;      // byte offset of this op's staged data inside its phase's staging area
+  int16_t ielems;    // index entries to stage
+  int16_t i1;        // offset of block 1's indices
   int16_t kind, flags;
   int16_t k0, c0, k1, c1;   // FK_MIDDLE: k0 = k_r, c0 = k_c; FK_LEAF: c0 = n0
-  int32_t src0, n_s0, src1, n_s1;   // vector operand segments (state entries or vec rows)
-  int32_t out0, out1, split;        // outputs (state entries or vec rows), scatter split row
-  int32_t pad;
+  int16_t n_s0, n_s1;       // lengths of the two operand segments
+  int16_t split;            // scatter: split row between the two outputs
+  int16_t pad;
 };
+static_assert(sizeof(FlatOp) == 64, "one op record is 64 bytes");
 struct FlatProgram {
   std::vector<FlatOp> ops;
-  std::vector<int32_t> base;   // base[ph] = first op of phase ph; base[nphase] = total
+  std::vector<int32_t> base;     // base[ph] = first op of phase ph; base[nphase] = total
+  std::vector<int32_t> pbytes;   // staging bytes of phase ph (complex-FP32 factor storage)
+  bool ok = true;                // false: a field did not fit its record width
 };
+// Staging bytes of one op with complex-FP32 factors: matrices, then indices,
+// each rounded up to 16 bytes.
+inline int32_t flat_stage_bytes32(const FlatOp& f) {
+  auto a16 = [](int64_t b) { return (b + 15) & ~(int64_t)15; };
+  return (int32_t)(a16((int64_t)f.melems * 8) + (f.ioff >= 0 ? a16((int64_t)f.ielems * 2) : 0));
+}
 
-// Split a program into segments: phases with at least grid_min ops run grid-wide.
-std::vector<DSeg> segment_program(const std::vector<DPhase>& prog, int grid_min);
 
 struct PackedHost {
   int64_t n = 0, n0 = 0, m = 0;
@@ -215,6 +228,19 @@ void pack_factor(const HostFactor& hf, PackedHost& ph);
 FlatProgram flatten_program(const PackedHost& ph, const std::vector<DPhase>& prog, int64_t n0);
 // fill the row / state ranges of the single-CTA runs
 void annotate_segments(std::vector<DSeg>& segs, const FlatProgram& fp);
+// Limits of a single-CTA run that the sweep kernel keeps in shared memory
+// (its op records and phase table are staged there as well); the segmenter
+// cuts runs to stay within them when it cuts for residency.
+constexpr int kRunMaxOps = 768;      // 48 KB of op records
+constexpr int kRunMaxPhases = 511;   // (phases + 1) x 8 bytes of phase table <= 4 KB
+// Split a program into segments: phases with at least grid_min ops (or
+// operands too wide for a warp) run grid-wide; the runs of small phases
+// between them go to single CTAs.  res_entries > 0 cuts those runs into
+// pieces whose vector rows + state entries (one right-hand side) stay within
+// res_entries, so that the kernel can keep a piece in shared memory.  The
+// result is annotated (annotate_segments).
+std::vector<DSeg> segment_program(const std::vector<DPhase>& prog, const FlatProgram& fp, int grid_min,
+                                  int64_t res_entries);
 
 // FP64 host execution of the packed program (verification without a GPU).
 void host_apply(const PackedHost& ph, const HostFactor& hf, bool adj, const cplx* x, cplx* y);

@@ -263,6 +263,212 @@ __global__ void __launch_bounds__(256) k_apply_exit(const DOuter* __restrict__ o
 }
 
 // ---------------------------------------------------------------------------
+// Column-parallel apply for many right-hand sides (R >= kWideMin): a CTA owns
+// one op and up to 256 consecutive right-hand sides, one thread per
+// right-hand side.  Vector rows are read as whole coalesced rows of the
+// [entry][R] layout; factor entries are warp-uniform loads (one broadcast per
+// warp, L1-resident across the CTA's warps); each thread keeps KC outputs in
+// registers and walks the op's inputs once per chunk of KC outputs.
+// ---------------------------------------------------------------------------
+constexpr int kWideMin = 32;
+
+template <class T> struct KCw { static constexpr int v = 16; };
+template <> struct KCw<double> { static constexpr int v = 8; };
+
+// B side of a V-type op (or a U-type op in adjoint): out_i = cand[q_i] + sum_j T_ij cand[p_j]
+template <class T, class F, bool UTYPE_ADJ>
+__device__ __forceinline__ void w_vlike(const F* __restrict__ M, const int16_t* __restrict__ idx, int k, int c,
+                                        const typename C2<T>::t* a0, int ka0, const typename C2<T>::t* a1,
+                                        typename C2<T>::t* out, int64_t R, int64_t col) {
+  using C = typename C2<T>::t;
+  constexpr int KC = KCw<T>::v;
+  const int nr = c - k;
+  for (int i0 = 0; i0 < k; i0 += KC) {
+    C acc[KC];
+#pragma unroll
+    for (int ii = 0; ii < KC; ++ii) {
+      acc[ii] = mk<T>(0, 0);
+      if (i0 + ii < k) {
+        const int q = idx[i0 + ii];
+        acc[ii] = (q < ka0) ? a0[(int64_t)q * R + col] : a1[(int64_t)(q - ka0) * R + col];
+      }
+    }
+    for (int j = 0; j < nr; ++j) {
+      const int pj = idx[k + j];
+      const C sv = (pj < ka0) ? a0[(int64_t)pj * R + col] : a1[(int64_t)(pj - ka0) * R + col];
+#pragma unroll
+      for (int ii = 0; ii < KC; ++ii)
+        if (i0 + ii < k) {
+          const C m = UTYPE_ADJ ? ldf_conj<T>(M + (int64_t)(i0 + ii) * nr + j) : ldf<T>(M + (int64_t)j * k + i0 + ii);
+          cfma(acc[ii], m, sv);
+        }
+    }
+#pragma unroll
+    for (int ii = 0; ii < KC; ++ii)
+      if (i0 + ii < k) out[(int64_t)(i0 + ii) * R + col] = acc[ii];
+  }
+}
+
+// Candidate entries r0 .. r0+KC-1 (< c) of one block added to acc: a skeleton
+// entry copies y_{map r}; a redundant one sums T_{i,j(r)} y_i (U-type layout
+// M[i*(c-k)+j]; VTYPE_ADJ: a V-type block in adjoint, conj(M[j*k+i])).
+template <class T, class F, bool VTYPE_ADJ>
+__device__ __forceinline__ void w_rows(typename C2<T>::t (&acc)[KCw<T>::v], const F* __restrict__ M,
+                                       const int16_t* __restrict__ idx, int k, int c, const typename C2<T>::t* y,
+                                       int64_t R, int64_t col, int r0, int nrow) {
+  using C = typename C2<T>::t;
+  constexpr int KC = KCw<T>::v;
+  const int nr = c - k;
+  int code[KC];
+  bool any_red = false;
+#pragma unroll
+  for (int ii = 0; ii < KC; ++ii) {
+    code[ii] = (ii < nrow) ? idx[c + r0 + ii] : 0;
+    if (ii < nrow) {
+      if (code[ii] >= 0) cadd(acc[ii], y[(int64_t)code[ii] * R + col]);
+      else any_red = true;
+    }
+  }
+  if (!any_red) return;
+  for (int i = 0; i < k; ++i) {
+    const C yi = y[(int64_t)i * R + col];
+#pragma unroll
+    for (int ii = 0; ii < KC; ++ii)
+      if (ii < nrow && code[ii] < 0) {
+        const int j = -1 - code[ii];
+        const C m = VTYPE_ADJ ? ldf_conj<T>(M + (int64_t)j * k + i) : ldf<T>(M + (int64_t)i * nr + j);
+        cfma(acc[ii], m, yi);
+      }
+  }
+}
+
+template <class T, class F, bool ADJ>
+__global__ void __launch_bounds__(256) k_wapply_enter(const DOuter* __restrict__ ops, int64_t n0,
+                                                      const F* __restrict__ fp, const int16_t* __restrict__ ip,
+                                                      const typename C2<T>::t* __restrict__ x,
+                                                      typename C2<T>::t* st, int64_t R) {
+  const int64_t col = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+  if (col >= R) return;
+  const DOuter o = ops[blockIdx.x];   // (leaf, depth) = (blockIdx.x / D, blockIdx.x % D)
+  const typename C2<T>::t* xl = x + (int64_t)o.leaf * n0 * R;
+  w_vlike<T, F, ADJ>(fp + o.blk.moff, ip + o.blk.ioff, o.blk.k, o.blk.c, xl, (int)n0, xl,
+                     st + (int64_t)o.seg_off * R, R, col);
+}
+
+template <class T, class F, bool ADJ>
+__global__ void __launch_bounds__(256) k_wapply_items(const DItem* __restrict__ items,
+                                                      const int32_t* __restrict__ idx, const F* __restrict__ fp,
+                                                      const int16_t* __restrict__ ip, typename C2<T>::t* st,
+                                                      int64_t R) {
+  using C = typename C2<T>::t;
+  constexpr int KC = KCw<T>::v;
+  const int64_t col = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+  if (col >= R) return;
+  const DItem it = items[idx[blockIdx.x]];
+  if (it.type == 1) {   // middle: y = S z (or z = S^H y)
+    const F* S = fp + it.blk[0].moff;
+    const int kr = it.b_k[0], kc = it.a_k[0];
+    const int nout = ADJ ? kc : kr, nin = ADJ ? kr : kc;
+    const C* in = st + (int64_t)(ADJ ? it.b_off[0] : it.a_off[0]) * R;
+    C* out = st + (int64_t)(ADJ ? it.a_off[0] : it.b_off[0]) * R;
+    for (int o0 = 0; o0 < nout; o0 += KC) {
+      C acc[KC];
+#pragma unroll
+      for (int ii = 0; ii < KC; ++ii) acc[ii] = mk<T>(0, 0);
+      for (int i = 0; i < nin; ++i) {
+        const C v = in[(int64_t)i * R + col];
+#pragma unroll
+        for (int ii = 0; ii < KC; ++ii)
+          if (o0 + ii < nout) {
+            const C sv = ADJ ? ldf_conj<T>(S + (int64_t)(o0 + ii) * kr + i) : ldf<T>(S + (int64_t)i * kr + o0 + ii);
+            cfma(acc[ii], sv, v);
+          }
+      }
+#pragma unroll
+      for (int ii = 0; ii < KC; ++ii)
+        if (o0 + ii < nout) out[(int64_t)(o0 + ii) * R + col] = acc[ii];
+    }
+    return;
+  }
+  const bool to_b = (it.type == 0) != ADJ;
+  if (to_b) {
+    const C* a0 = st + (int64_t)it.a_off[0] * R;
+    const C* a1 = st + (int64_t)it.a_off[1] * R;
+#pragma unroll
+    for (int sb = 0; sb < 2; ++sb) {
+      const DBlk& b = it.blk[sb];
+      if (it.type == 0)
+        w_vlike<T, F, false>(fp + b.moff, ip + b.ioff, b.k, b.c, a0, it.a_k[0], a1, st + (int64_t)it.b_off[sb] * R, R, col);
+      else
+        w_vlike<T, F, true>(fp + b.moff, ip + b.ioff, b.k, b.c, a0, it.a_k[0], a1, st + (int64_t)it.b_off[sb] * R, R, col);
+    }
+  } else {
+    const int c = it.a_k[0] + it.a_k[1];
+    for (int r0 = 0; r0 < c; r0 += KC) {
+      const int nrow = (c - r0) < KC ? (c - r0) : KC;
+      C acc[KC];
+#pragma unroll
+      for (int ii = 0; ii < KC; ++ii) acc[ii] = mk<T>(0, 0);
+#pragma unroll
+      for (int sb = 0; sb < 2; ++sb) {
+        const DBlk& b = it.blk[sb];
+        if (it.type == 2)
+          w_rows<T, F, false>(acc, fp + b.moff, ip + b.ioff, b.k, b.c, st + (int64_t)it.b_off[sb] * R, R, col, r0, nrow);
+        else
+          w_rows<T, F, true>(acc, fp + b.moff, ip + b.ioff, b.k, b.c, st + (int64_t)it.b_off[sb] * R, R, col, r0, nrow);
+      }
+#pragma unroll
+      for (int ii = 0; ii < KC; ++ii)
+        if (ii < nrow) {
+          const int r = r0 + ii;
+          C* dst = (r < it.a_k[0]) ? st + (int64_t)(it.a_off[0] + r) * R : st + (int64_t)(it.a_off[1] + r - it.a_k[0]) * R;
+          dst[col] = acc[ii];
+        }
+    }
+  }
+}
+
+// y_leaf = sum_v U0_v y_0 + A_leaf x_leaf (fixed order: depths 0..D-1, then the leaf)
+template <class T, class F, bool ADJ>
+__global__ void __launch_bounds__(256) k_wapply_exit(const DOuter* __restrict__ ops, int D, int64_t n0,
+                                                     const F* __restrict__ fp, const int16_t* __restrict__ ip,
+                                                     const F* __restrict__ leafm,
+                                                     const typename C2<T>::t* __restrict__ x,
+                                                     const typename C2<T>::t* st, typename C2<T>::t* y,
+                                                     int64_t R) {
+  using C = typename C2<T>::t;
+  constexpr int KC = KCw<T>::v;
+  const int64_t col = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+  if (col >= R) return;
+  const int64_t leaf = blockIdx.x;
+  const F* A = leafm + leaf * n0 * n0;
+  const C* xl = x + leaf * n0 * R;
+  for (int r0 = 0; r0 < (int)n0; r0 += KC) {
+    const int nrow = ((int)n0 - r0) < KC ? ((int)n0 - r0) : KC;
+    C acc[KC];
+#pragma unroll
+    for (int ii = 0; ii < KC; ++ii) acc[ii] = mk<T>(0, 0);
+    for (int v = 0; v < D; ++v) {
+      const DOuter o = ops[leaf * D + v];
+      w_rows<T, F, ADJ>(acc, fp + o.blk.moff, ip + o.blk.ioff, o.blk.k, o.blk.c, st + (int64_t)o.seg_off * R, R,
+                        col, r0, nrow);
+    }
+    for (int cc = 0; cc < (int)n0; ++cc) {
+      const C xv = xl[(int64_t)cc * R + col];
+#pragma unroll
+      for (int ii = 0; ii < KC; ++ii)
+        if (ii < nrow) {
+          const C a = ADJ ? ldf_conj<T>(A + (int64_t)(r0 + ii) * n0 + cc) : ldf<T>(A + (int64_t)cc * n0 + r0 + ii);
+          cfma(acc[ii], a, xv);
+        }
+    }
+#pragma unroll
+    for (int ii = 0; ii < KC; ++ii)
+      if (ii < nrow) y[(leaf * n0 + r0 + ii) * R + col] = acc[ii];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Layout conversion kernels
 // ---------------------------------------------------------------------------
 template <class S, class D>
@@ -347,8 +553,37 @@ static int apply_impl(const DevFactor& df, bool adj, const void* xv, void* yv, i
 }
 
 template <class T, class F>
+static int apply_wide(const DevFactor& df, bool adj, const void* xv, void* yv, int64_t R, void* stv,
+                      cudaStream_t s) {
+  using C = typename C2<T>::t;
+  const F* fp = (const F*)df.fpool;
+  const C* x = (const C*)xv;
+  C* y = (C*)yv;
+  C* st = (C*)stv;
+  const int thr = (int)(R < 256 ? (R + 31) / 32 * 32 : 256);
+  const unsigned cb = (unsigned)((R + thr - 1) / thr);
+  const dim3 g_enter((unsigned)(df.m * df.D), cb);
+  if (!adj) k_wapply_enter<T, F, false><<<g_enter, thr, 0, s>>>(df.vout, df.n0, fp, df.ipool, x, st, R);
+  else k_wapply_enter<T, F, true><<<g_enter, thr, 0, s>>>(df.uout, df.n0, fp, df.ipool, x, st, R);
+  const std::vector<int32_t>& ptr = adj ? df.astep_ptr : df.step_ptr;
+  const int32_t* idx = adj ? df.astep_idx : df.step_idx;
+  for (int stp = 0; stp + 1 < (int)ptr.size(); ++stp) {
+    int cnt = ptr[stp + 1] - ptr[stp];
+    if (cnt <= 0) continue;
+    const dim3 g((unsigned)cnt, cb);
+    if (!adj) k_wapply_items<T, F, false><<<g, thr, 0, s>>>(df.items, idx + ptr[stp], fp, df.ipool, st, R);
+    else k_wapply_items<T, F, true><<<g, thr, 0, s>>>(df.items, idx + ptr[stp], fp, df.ipool, st, R);
+  }
+  const dim3 g_exit((unsigned)df.m, cb);
+  if (!adj) k_wapply_exit<T, F, false><<<g_exit, thr, 0, s>>>(df.uout, df.D, df.n0, fp, df.ipool, (const F*)df.leaf, x, st, y, R);
+  else k_wapply_exit<T, F, true><<<g_exit, thr, 0, s>>>(df.vout, df.D, df.n0, fp, df.ipool, (const F*)df.leaf, x, st, y, R);
+  return cudaGetLastError() == cudaSuccess ? HB_OK : HB_ECUDA;
+}
+
+template <class T, class F>
 static int apply_dispatch(const DevFactor& df, bool adj, const void* x, void* y, int64_t R, void* st,
                           cudaStream_t s) {
+  if (R >= kWideMin) return apply_wide<T, F>(df, adj, x, y, R, st, s);
   if (R == 1) return apply_impl<T, F, 1>(df, adj, x, y, R, st, s);
   if (R <= 4) return apply_impl<T, F, 4>(df, adj, x, y, R, st, s);
   return apply_impl<T, F, 8>(df, adj, x, y, R, st, s);

@@ -6,11 +6,14 @@
 // exit ops); consecutive phases depend on each other, ops inside a phase do
 // not.  The program is cut into segments:
 //   * a grid segment is one large phase (a stage of a big butterfly); its
-//     ops are spread over all CTAs, one op per CTA at a time;
+//     ops (or, with many right-hand sides, (op, column range) units) are
+//     spread over all CTAs, one unit per CTA at a time;
 //   * a local segment is a run of small phases (a subtree near the leaves);
-//     a single CTA executes it, one op per warp, __syncthreads between phases.
-// A grid barrier (bounded spin; HB_ETIMEOUT instead of a hang) separates the
-// segments.  Every op first stages its factor blocks into shared memory with
+//     each CTA executes it for its own share of the right-hand sides, one op
+//     per warp, __syncthreads between phases.
+// A grid barrier (bounded spin; HB_ETIMEOUT instead of a hang) separates a
+// grid segment from its neighbours; consecutive local segments need none.
+// Every op first stages its factor blocks into shared memory with
 // 16-byte cp.async copies (one memory round trip for the whole op), then
 // computes from shared memory.  Vector and butterfly-state reads bypass L1
 // (ld.global.cg) because other CTAs write them inside the same launch.
@@ -114,28 +117,36 @@ __device__ bool grid_sync(GridBar* gb, unsigned& my_gen, long long spin_limit) {
 // compute kernels of one op from staged operands
 // ---------------------------------------------------------------------------
 
-// B side = gather + T * rest (V-type layout M[j*k+i]; or U-type adjoint conj(M[i*nr+j]))
+// B side = gather + T * rest (V-type layout M[j*k+i]; or U-type adjoint conj(M[i*nr+j])).
+// The group's threads take (output i, RHS chunk ch) pairs: chunk ch holds the
+// right-hand sides r0 + ch*RC .. (< rend) at column ch*RC of the staged rows
+// (row stride vs) and of `out` (row stride R, column offset r0).
 template <class T, class F, int RC, bool UADJ>
 __device__ __forceinline__ void vlike(const F* M, const int16_t* idx, int k, int c,
                                       const typename CT<T>::t* cand /* [c][vs] smem */, int vs,
-                                      typename CT<T>::t* out, int64_t R, int64_t r0, int rc, const Grp& g) {
+                                      typename CT<T>::t* out, int64_t R, int64_t r0, int64_t rend, int nch,
+                                      const Grp& g) {
   using C = typename CT<T>::t;
   const int nr = c - k;
-  for (int i = g.t; i < k; i += g.nt) {
+  for (int e = g.t; e < k * nch; e += g.nt) {
+    const int i = e % k, ch = e / k;
+    const C* cb = cand + ch * RC;
+    const int64_t rs = r0 + (int64_t)ch * RC;
+    const int rc = (rend - rs) < RC ? (int)(rend - rs) : RC;
     C acc[RC];
     const int qi = idx[i];
 #pragma unroll
-    for (int rr = 0; rr < RC; ++rr) acc[rr] = cand[qi * vs + rr];
+    for (int rr = 0; rr < RC; ++rr) acc[rr] = cb[qi * vs + rr];
 #pragma unroll 8
     for (int j = 0; j < nr; ++j) {
       C m = UADJ ? cvc<T>(M[(int64_t)i * nr + j]) : cv<T>(M[(int64_t)j * k + i]);
-      const C* s = cand + idx[k + j] * vs;
+      const C* sv = cb + idx[k + j] * vs;
 #pragma unroll
-      for (int rr = 0; rr < RC; ++rr) fma2(acc[rr], m, s[rr]);
+      for (int rr = 0; rr < RC; ++rr) fma2(acc[rr], m, sv[rr]);
     }
 #pragma unroll
     for (int rr = 0; rr < RC; ++rr)
-      if (rr < rc) out[(int64_t)i * R + r0 + rr] = acc[rr];
+      if (rr < rc) out[(int64_t)i * R + rs + rr] = acc[rr];
   }
 }
 
@@ -189,6 +200,7 @@ struct SweepArgs {
   const DPhase* prog;
   const FlatOp* flat;
   const int32_t* flat_base;
+  const int32_t* flat_pbytes;
   int64_t n0;
   const DOuter* bvout;
   const DOuter* buout;
@@ -293,28 +305,34 @@ __device__ void do_op(const SweepArgs& a, const FlatOp& f, char* buf, int64_t bu
     if (!pre) cp_commit_wait();
     g.sync();
   }
-  for (int64_t ch = 0; ch < pl.nch; ++ch) {
-    const int64_t r0 = rb + ch * RC;
-    const int rc = pl.rc(ch);
-    C* vv = pl.once ? v + ch * RC : v;
+  // Whole range staged: the threads take (output, chunk) pairs over all
+  // chunks in one pass.  Otherwise one chunk per pass.
+  const int nst = pl.once ? (int)pl.nch : 1;
+  const int npass = pl.once ? 1 : (int)pl.nch;
+  for (int ps = 0; ps < npass; ++ps) {
+    const int64_t r0 = rb + (int64_t)ps * RC;
+    C* vv = v;
     if (!pl.once) {
-      load_segs<C>(vv, src0, n_s0, src1, n_s1, R, r0, rc, W, g, pre);
+      load_segs<C>(vv, src0, n_s0, src1, n_s1, R, r0, pl.rc(ps), W, g, pre);
       if (!pre) cp_commit_wait();
       g.sync();
     }
     if (kind == 0) {
       if (conj_layout) {
-        vlike<T, F, RC, true>(M0, I0, k0, c0, vv, W, out0, R, r0, rc, g);
-        if (nblk == 2) vlike<T, F, RC, true>(M1, I1, k1, c1, vv, W, out1, R, r0, rc, g);
+        vlike<T, F, RC, true>(M0, I0, k0, c0, vv, W, out0, R, r0, re, nst, g);
+        if (nblk == 2) vlike<T, F, RC, true>(M1, I1, k1, c1, vv, W, out1, R, r0, re, nst, g);
       } else {
-        vlike<T, F, RC, false>(M0, I0, k0, c0, vv, W, out0, R, r0, rc, g);
-        if (nblk == 2) vlike<T, F, RC, false>(M1, I1, k1, c1, vv, W, out1, R, r0, rc, g);
+        vlike<T, F, RC, false>(M0, I0, k0, c0, vv, W, out0, R, r0, re, nst, g);
+        if (nblk == 2) vlike<T, F, RC, false>(M1, I1, k1, c1, vv, W, out1, R, r0, re, nst, g);
       }
     } else if (kind == 1) {
       const int nrows = c0;   // candidate entries (both blocks of an item share the candidate list)
-      const C* y0 = vv;
-      const C* y1 = vv + (int64_t)n_s0 * W;
-      for (int r = g.t; r < nrows; r += g.nt) {
+      for (int e = g.t; e < nrows * nst; e += g.nt) {
+        const int r = e % nrows, ch = e / nrows;
+        const int64_t rs = r0 + (int64_t)ch * RC;
+        const int rc = (re - rs) < RC ? (int)(re - rs) : RC;
+        const C* y0 = vv + ch * RC;
+        const C* y1 = vv + (int64_t)n_s0 * W + ch * RC;
         C acc[RC];
 #pragma unroll
         for (int rr = 0; rr < RC; ++rr) acc[rr] = z2<T>();
@@ -325,7 +343,7 @@ __device__ void do_op(const SweepArgs& a, const FlatOp& f, char* buf, int64_t bu
           rowc<T, F, RC, false>(acc, M0, I0, k0, c0, y0, W, r);
           if (nblk == 2) rowc<T, F, RC, false>(acc, M1, I1, k1, c1, y1, W, r);
         }
-        C* d = (nblk == 1 || r < split_r) ? out0 + (int64_t)r * R + r0 : out1 + (int64_t)(r - split_r) * R + r0;
+        C* d = (nblk == 1 || r < split_r) ? out0 + (int64_t)r * R + rs : out1 + (int64_t)(r - split_r) * R + rs;
 #pragma unroll
         for (int rr = 0; rr < RC; ++rr)
           if (rr < rc) {
@@ -339,7 +357,11 @@ __device__ void do_op(const SweepArgs& a, const FlatOp& f, char* buf, int64_t bu
       }
     } else {
       const int nin = adj ? kr : kc, nout = adj ? kc : kr;
-      for (int oo = g.t; oo < nout; oo += g.nt) {
+      for (int e = g.t; e < nout * nst; e += g.nt) {
+        const int oo = e % nout, ch = e / nout;
+        const int64_t rs = r0 + (int64_t)ch * RC;
+        const int rc = (re - rs) < RC ? (int)(re - rs) : RC;
+        const C* vb = vv + ch * RC;
         C acc[RC];
 #pragma unroll
         for (int rr = 0; rr < RC; ++rr) acc[rr] = z2<T>();
@@ -347,11 +369,11 @@ __device__ void do_op(const SweepArgs& a, const FlatOp& f, char* buf, int64_t bu
         for (int i = 0; i < nin; ++i) {
           C sv = adj ? cvc<T>(Ms[(int64_t)oo * kr + i]) : cv<T>(Ms[(int64_t)i * kr + oo]);
 #pragma unroll
-          for (int rr = 0; rr < RC; ++rr) fma2(acc[rr], sv, vv[(int64_t)i * W + rr]);
+          for (int rr = 0; rr < RC; ++rr) fma2(acc[rr], sv, vb[(int64_t)i * W + rr]);
         }
 #pragma unroll
         for (int rr = 0; rr < RC; ++rr)
-          if (rr < rc) out0[(int64_t)oo * R + r0 + rr] = acc[rr];
+          if (rr < rc) out0[(int64_t)oo * R + rs + rr] = acc[rr];
       }
     }
     if (!pl.once) g.sync();
@@ -425,48 +447,51 @@ __device__ void do_leaf(const SweepArgs& a, const FlatOp& f, char* buf, int64_t 
 }
 
 // ---------------------------------------------------------------------------
-// Local runs with prefetch (complex FP32 factors, n0 <= 64): the factor data
-// of phase p+1 is copied (cp.async, one group per phase) into the other half
-// of each warp's slice -- or into the other leaf buffer -- while phase p
-// computes, so only the data-dependent vector loads remain on the chain.
-// Shared-memory map: [leaf buffer 0 | leaf buffer 1 | leaf scratch | warp
-// halves (warp w, parity h) of kPfHalf bytes].
+// Resident single-CTA runs with a staging ring (complex FP32 factors,
+// n0 <= 64).  The run's vector rows and butterfly state live in shared memory
+// for the whole run.  The factor data of the coming phases (each phase's ops
+// packed into one contiguous area, offsets precomputed on the host) is copied
+// into a ring buffer with cp.async, up to kLook phases ahead of the phase being
+// computed and as far as the ring has room, one commit group per phase; so
+// only shared-memory work and barriers remain on the dependency chain.
+// Shared-memory map: [ring | leaf partial sums | resident rows + state].
 // ---------------------------------------------------------------------------
-constexpr int kPfLeaf = 32 * 1024;
-constexpr int kPfAux = 8 * 1024;
-constexpr int kPfHalf = 6 * 1024;
-constexpr int kPfRes = 56 * 1024;                                               // resident vectors + state
-constexpr int kSmemBytes = 2 * kPfLeaf + kPfAux + 8 * 2 * kPfHalf + kPfRes;    // 224 KB
+constexpr int kSmemBytes = 224 * 1024;
+constexpr int kAuxBytes = 8 * 1024;                                     // leaf partial sums
+constexpr int kRecBytes = kRunMaxOps * 64;                              // the run's op records (48 KB)
+constexpr int kPhBytes = (kRunMaxPhases + 1) * 8;                       // the run's phase table (4 KB)
+constexpr int kRingBytes = kSmemBytes - kAuxBytes - kResidentBytes - kRecBytes - kPhBytes;   // 108 KB
+constexpr int kLook = 7;                                                // phases in flight beyond the current one
 
-__device__ __forceinline__ char* pf_half(char* smem, int w, int h) {
-  return smem + 2 * kPfLeaf + kPfAux + (w * 2 + h) * kPfHalf;
+__device__ __forceinline__ void cp_wait_n(int n) {
+  switch (n) {
+    case 0: asm volatile("cp.async.wait_group 0;\n" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;\n" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;\n" ::: "memory"); break;
+    case 3: asm volatile("cp.async.wait_group 3;\n" ::: "memory"); break;
+    case 4: asm volatile("cp.async.wait_group 4;\n" ::: "memory"); break;
+    case 5: asm volatile("cp.async.wait_group 5;\n" ::: "memory"); break;
+    case 6: asm volatile("cp.async.wait_group 6;\n" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 7;\n" ::: "memory"); break;
+  }
 }
 
+// issue the copies of one phase's factor data (ops[0 .. nops)) into dst (no commit)
 template <class F>
-__device__ __forceinline__ int64_t op_stage_bytes(const FlatOp& f) {
-  return align16((int64_t)f.melems * (int64_t)sizeof(F)) +
-         (f.ioff >= 0 ? align16((int64_t)f.ielems * (int64_t)sizeof(int16_t)) : 0);
-}
-
-// issue the factor-data copies of phase ph into parity h, then commit one group
-template <class F>
-__device__ void pf_issue(const SweepArgs& a, int ph, int h, char* smem, int warp, int lane) {
-  const int32_t ob = __ldg(a.flat_base + ph), oe = __ldg(a.flat_base + ph + 1);
-  const FlatOp* ops = a.flat + ob;
+__device__ void ring_issue(const SweepArgs& a, const FlatOp* ops, int nops, char* dst, int warp, int nw, int lane) {
   if (ops[0].kind == FK_LEAF) {
     const Grp g{(int)threadIdx.x, (int)blockDim.x, true};
-    stage(smem + h * kPfLeaf, (const F*)a.tinv + ops[0].moff, align16((int64_t)ops[0].melems * (int64_t)sizeof(F)), g);
-  } else if (warp < oe - ob) {
-    const FlatOp& f = ops[warp];
-    const Grp g{lane, 32, false};
-    if (op_stage_bytes<F>(f) <= kPfHalf) {
-      char* d = pf_half(smem, warp, h);
-      const int64_t mb = align16((int64_t)f.melems * (int64_t)sizeof(F));
-      stage(d, (const F*)a.fp + f.moff, mb, g);
-      if (f.ioff >= 0) stage(d + mb, a.ip + f.ioff, align16((int64_t)f.ielems * (int64_t)sizeof(int16_t)), g);
-    }
+    stage(dst, (const F*)a.tinv + ops[0].moff, align16((int64_t)ops[0].melems * (int64_t)sizeof(F)), g);
+    return;
   }
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  const Grp g{lane, 32, false};
+  for (int o = warp; o < nops; o += nw) {
+    const FlatOp& f = ops[o];
+    char* d = dst + f.soff;
+    const int64_t mb = align16((int64_t)f.melems * (int64_t)sizeof(F));
+    stage(d, (const F*)a.fp + f.moff, mb, g);
+    if (f.ioff >= 0) stage(d + mb, a.ip + f.ioff, align16((int64_t)f.ielems * (int64_t)sizeof(int16_t)), g);
+  }
 }
 
 // An op of a resident run: operands and results live in shared memory (rows
@@ -490,54 +515,58 @@ __device__ void do_op_res(const SweepArgs& a, const FlatOp& f, const char* half,
   const int16_t* Is = pre ? (const int16_t*)(half + mbytes) : (f.ioff >= 0 ? a.ip + f.ioff : nullptr);
   const F* M1 = Ms + f.m1;
   const int16_t* I1 = Is ? Is + f.i1 : nullptr;
-  for (int r0 = 0; r0 < ncol; r0 += RC) {
-    const int rc = (ncol - r0) < RC ? (ncol - r0) : RC;
-    if (f.kind == FK_GATHER) {
+  const int nch = (ncol + RC - 1) / RC;
+  if (f.kind == FK_GATHER) {
+    if (conj_layout) {
+      vlike<T, F, RC, true>(Ms, Is, f.k0, f.c0, src0, Wr, out0, Wr, 0, ncol, nch, g);
+      if (nblk == 2) vlike<T, F, RC, true>(M1, I1, f.k1, f.c1, src0, Wr, out1, Wr, 0, ncol, nch, g);
+    } else {
+      vlike<T, F, RC, false>(Ms, Is, f.k0, f.c0, src0, Wr, out0, Wr, 0, ncol, nch, g);
+      if (nblk == 2) vlike<T, F, RC, false>(M1, I1, f.k1, f.c1, src0, Wr, out1, Wr, 0, ncol, nch, g);
+    }
+  } else if (f.kind == FK_SCATTER) {
+    const int split_r = f.split;
+    for (int e = g.t; e < f.c0 * nch; e += g.nt) {
+      const int r = e % f.c0, ch = e / f.c0;
+      const int r0 = ch * RC;
+      const int rc = (ncol - r0) < RC ? (ncol - r0) : RC;
+      C acc[RC];
+#pragma unroll
+      for (int rr = 0; rr < RC; ++rr) acc[rr] = z2<T>();
       if (conj_layout) {
-        vlike<T, F, RC, true>(Ms, Is, f.k0, f.c0, src0 + r0, Wr, out0, Wr, r0, rc, g);
-        if (nblk == 2) vlike<T, F, RC, true>(M1, I1, f.k1, f.c1, src0 + r0, Wr, out1, Wr, r0, rc, g);
+        rowc<T, F, RC, true>(acc, Ms, Is, f.k0, f.c0, src0 + r0, Wr, r);
+        if (nblk == 2) rowc<T, F, RC, true>(acc, M1, I1, f.k1, f.c1, src1 + r0, Wr, r);
       } else {
-        vlike<T, F, RC, false>(Ms, Is, f.k0, f.c0, src0 + r0, Wr, out0, Wr, r0, rc, g);
-        if (nblk == 2) vlike<T, F, RC, false>(M1, I1, f.k1, f.c1, src0 + r0, Wr, out1, Wr, r0, rc, g);
+        rowc<T, F, RC, false>(acc, Ms, Is, f.k0, f.c0, src0 + r0, Wr, r);
+        if (nblk == 2) rowc<T, F, RC, false>(acc, M1, I1, f.k1, f.c1, src1 + r0, Wr, r);
       }
-    } else if (f.kind == FK_SCATTER) {
-      const int split_r = f.split;
-      for (int r = g.t; r < f.c0; r += g.nt) {
-        C acc[RC];
+      C* d = (nblk == 1 || r < split_r) ? out0 + (int64_t)r * Wr + r0 : out1 + (int64_t)(r - split_r) * Wr + r0;
 #pragma unroll
-        for (int rr = 0; rr < RC; ++rr) acc[rr] = z2<T>();
-        if (conj_layout) {
-          rowc<T, F, RC, true>(acc, Ms, Is, f.k0, f.c0, src0 + r0, Wr, r);
-          if (nblk == 2) rowc<T, F, RC, true>(acc, M1, I1, f.k1, f.c1, src1 + r0, Wr, r);
-        } else {
-          rowc<T, F, RC, false>(acc, Ms, Is, f.k0, f.c0, src0 + r0, Wr, r);
-          if (nblk == 2) rowc<T, F, RC, false>(acc, M1, I1, f.k1, f.c1, src1 + r0, Wr, r);
+      for (int rr = 0; rr < RC; ++rr)
+        if (rr < rc) {
+          if (subtract) d[rr] = C{d[rr].x - acc[rr].x, d[rr].y - acc[rr].y};
+          else d[rr] = acc[rr];
         }
-        C* d = (nblk == 1 || r < split_r) ? out0 + (int64_t)r * Wr + r0 : out1 + (int64_t)(r - split_r) * Wr + r0;
+    }
+  } else {   // middle
+    const int kr = f.k0, kc = f.c0;
+    const int nin = adj ? kr : kc, nout = adj ? kc : kr;
+    for (int e = g.t; e < nout * nch; e += g.nt) {
+      const int oo = e % nout, ch = e / nout;
+      const int r0 = ch * RC;
+      const int rc = (ncol - r0) < RC ? (ncol - r0) : RC;
+      C acc[RC];
 #pragma unroll
-        for (int rr = 0; rr < RC; ++rr)
-          if (rr < rc) {
-            if (subtract) d[rr] = C{d[rr].x - acc[rr].x, d[rr].y - acc[rr].y};
-            else d[rr] = acc[rr];
-          }
-      }
-    } else {   // middle
-      const int kr = f.k0, kc = f.c0;
-      const int nin = adj ? kr : kc, nout = adj ? kc : kr;
-      for (int oo = g.t; oo < nout; oo += g.nt) {
-        C acc[RC];
-#pragma unroll
-        for (int rr = 0; rr < RC; ++rr) acc[rr] = z2<T>();
+      for (int rr = 0; rr < RC; ++rr) acc[rr] = z2<T>();
 #pragma unroll 8
-        for (int i = 0; i < nin; ++i) {
-          C sv = adj ? cvc<T>(Ms[(int64_t)oo * kr + i]) : cv<T>(Ms[(int64_t)i * kr + oo]);
+      for (int i = 0; i < nin; ++i) {
+        C sv = adj ? cvc<T>(Ms[(int64_t)oo * kr + i]) : cv<T>(Ms[(int64_t)i * kr + oo]);
 #pragma unroll
-          for (int rr = 0; rr < RC; ++rr) fma2(acc[rr], sv, src0[(int64_t)i * Wr + r0 + rr]);
-        }
-#pragma unroll
-        for (int rr = 0; rr < RC; ++rr)
-          if (rr < rc) out0[(int64_t)oo * Wr + r0 + rr] = acc[rr];
+        for (int rr = 0; rr < RC; ++rr) fma2(acc[rr], sv, src0[(int64_t)i * Wr + r0 + rr]);
       }
+#pragma unroll
+      for (int rr = 0; rr < RC; ++rr)
+        if (rr < rc) out0[(int64_t)oo * Wr + r0 + rr] = acc[rr];
     }
   }
   g.sync();
@@ -579,90 +608,134 @@ __device__ void do_leaf_res(const SweepArgs& a, const FlatOp& f, const F* Tm, ty
   }
 }
 
-template <class T, class F, int RC>
-__device__ void local_run_pf(const SweepArgs& a, const DSeg& sg, char* smem, int64_t lb, int64_t le) {
-  using C = typename CT<T>::t;
-  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
-  const int end = sg.first + sg.count;
-  // records of this run into L1 (static data)
-  {
-    const int32_t o_first = __ldg(a.flat_base + sg.first), o_last = __ldg(a.flat_base + end);
-    const char* p0 = (const char*)(a.flat + o_first);
-    const int64_t nb = (int64_t)(o_last - o_first) * (int64_t)sizeof(FlatOp);
-    for (int64_t e = (int64_t)threadIdx.x * 128; e < nb; e += (int64_t)blockDim.x * 128)
-      asm volatile("prefetch.global.L1 [%0];" ::"l"(p0 + e));
-    const char* p1 = (const char*)(a.flat_base + sg.first);
-    for (int64_t e = (int64_t)threadIdx.x * 128; e < (int64_t)(sg.count + 1) * 4; e += (int64_t)blockDim.x * 128)
-      asm volatile("prefetch.global.L1 [%0];" ::"l"(p1 + e));
+// bring a run's op and phase records into L1 (static data, one round trip)
+__device__ __forceinline__ void prefetch_records(const SweepArgs& a, const DSeg& sg) {
+  const int32_t o_first = __ldg(a.flat_base + sg.first), o_last = __ldg(a.flat_base + sg.first + sg.count);
+  const char* p0 = (const char*)(a.flat + o_first);
+  const int64_t nb = (int64_t)(o_last - o_first) * (int64_t)sizeof(FlatOp);
+  for (int64_t e = (int64_t)threadIdx.x * 128; e < nb; e += (int64_t)blockDim.x * 128)
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p0 + e));
+  const char* p1 = (const char*)(a.flat_base + sg.first);
+  const char* p2 = (const char*)(a.flat_pbytes + sg.first);
+  for (int64_t e = (int64_t)threadIdx.x * 128; e < (int64_t)(sg.count + 1) * 4; e += (int64_t)blockDim.x * 128) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p1 + e));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p2 + e));
   }
-  // resident operands: this CTA's columns of the run's vector rows and state
+}
+
+// resident run with the staging ring (columns [lb, le) of this CTA); the
+// run's op records and phase table are copied to shared memory first, so no
+// phase waits on a record load from L2
+template <class T, class F, int RC>
+__device__ void local_run_ring(const SweepArgs& a, const DSeg& sg, char* smem, int64_t lb, int64_t le,
+                               int32_t o_first, int32_t o_last) {
+  using C = typename CT<T>::t;
+  __shared__ int s_qoff[kLook + 1];   // ring offset of each phase in flight (-1: read from global memory)
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+  const int np = sg.count;
+  char* ring = smem;
+  FlatOp* recs = (FlatOp*)(smem + kRingBytes);
+  int32_t* sbase = (int32_t*)(smem + kRingBytes + kRecBytes);   // [np + 1] first op of each phase
+  int32_t* spb = sbase + (kRunMaxPhases + 1);                      // [np] staging bytes of each phase
+  C* part = (C*)(smem + kRingBytes + kRecBytes + kPhBytes);
+  C* rvec = (C*)(smem + kRingBytes + kRecBytes + kPhBytes + kAuxBytes);
   const int ncol = (int)(le - lb);
   const int Wr = ((ncol + RC - 1) / RC) * RC;
-  const int64_t res_need = ((int64_t)(sg.row_hi - sg.row_lo) + (sg.st_hi - sg.st_lo)) * Wr * (int64_t)sizeof(C);
-  const bool resident = res_need <= kPfRes;
-  C* rvec = (C*)(smem + 2 * kPfLeaf + kPfAux + 16 * kPfHalf);
   C* rst = rvec + (int64_t)(sg.row_hi - sg.row_lo) * Wr;
   C* vecg = (C*)a.vec;
-  if (resident) {
-    const int nrow = sg.row_hi - sg.row_lo;
-    for (int e = threadIdx.x; e < nrow * ncol; e += blockDim.x) {
-      const int r = e / ncol, c = e % ncol;
-      rvec[(int64_t)r * Wr + c] = ldcg2(vecg + (int64_t)(sg.row_lo + r) * a.R + lb + c);
-    }
+  {
+    const Grp g{(int)threadIdx.x, (int)blockDim.x, true};
+    stage(recs, a.flat + o_first, (int64_t)(o_last - o_first) * (int64_t)sizeof(FlatOp), g);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
-  pf_issue<F>(a, sg.first, 0, smem, warp, lane);
-  int h = 0;
-  for (int ph = sg.first; ph < end; ++ph) {
-    if (ph + 1 < end) {
-      pf_issue<F>(a, ph + 1, h ^ 1, smem, warp, lane);
-      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-    } else {
-      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    }
-    __syncthreads();
-    const int32_t ob = __ldg(a.flat_base + ph), oe = __ldg(a.flat_base + ph + 1);
-    const FlatOp* ops = a.flat + ob;
-    if (resident) {
-      if (ops[0].kind == FK_LEAF) {
-        do_leaf_res<T, F, RC>(a, ops[0], (const F*)(smem + h * kPfLeaf), rvec, sg.row_lo, Wr, ncol,
-                              (C*)(smem + 2 * kPfLeaf));
-      } else {
-        const Grp g{lane, 32, false};
-        for (int o = warp; o < oe - ob; o += nw) {
-          const FlatOp f = ops[o];
-          const bool pre = (o == warp) && op_stage_bytes<F>(f) <= kPfHalf;
-          do_op_res<T, F, RC>(a, f, pf_half(smem, warp, h), pre, rvec, sg.row_lo, rst, sg.st_lo, Wr, ncol, g);
+  for (int p = threadIdx.x; p <= np; p += blockDim.x) {
+    sbase[p] = __ldg(a.flat_base + sg.first + p) - o_first;
+    if (p < np) spb[p] = __ldg(a.flat_pbytes + sg.first + p);
+  }
+  const int nrow = sg.row_hi - sg.row_lo;
+  for (int e = threadIdx.x; e < nrow * ncol; e += blockDim.x) {
+    const int r = e / ncol, c = e % ncol;
+    rvec[(int64_t)r * Wr + c] = ldcg2(vecg + (int64_t)(sg.row_lo + r) * a.R + lb + c);
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+  // ring state (identical in every thread): next phase to issue, allocation
+  // head, start of the oldest staged phase in flight, staged phases in flight
+  int issued = 0, head = 0, tail = 0, live = 0;
+  for (int ph = 0; ph < np; ++ph) {
+    while (issued < np && issued - ph <= kLook) {
+      const int pb = spb[issued];
+      int off = -1;
+      if (pb > 0 && pb <= kRingBytes) {
+        if (live == 0) {
+          head = tail = 0;
+          off = 0;
+        } else if (head > tail) {
+          if (head + pb <= kRingBytes) off = head;
+          else if (pb <= tail) off = 0;
+        } else if (head < tail) {
+          if (head + pb <= tail) off = head;
         }
+        if (off < 0) break;   // ring full: issue later
+        ring_issue<F>(a, recs + sbase[issued], sbase[issued + 1] - sbase[issued], ring + off, warp, nw, lane);
+        head = off + pb;
+        ++live;
       }
-    } else if (ops[0].kind == FK_LEAF) {
-      do_leaf<T, F, RC>(a, ops[0], smem + 2 * kPfLeaf, kPfAux, lb, le, (const F*)(smem + h * kPfLeaf));
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+      if (threadIdx.x == 0) s_qoff[issued % (kLook + 1)] = off;
+      ++issued;
+    }
+    cp_wait_n(issued - ph - 1);
+    __syncthreads();
+    const int myoff = s_qoff[ph % (kLook + 1)];
+    const FlatOp* ops = recs + sbase[ph];
+    const int nops = sbase[ph + 1] - sbase[ph];
+    if (ops[0].kind == FK_LEAF) {
+      const F* Tm = myoff >= 0 ? (const F*)(ring + myoff) : (const F*)a.tinv + ops[0].moff;
+      do_leaf_res<T, F, RC>(a, ops[0], Tm, rvec, sg.row_lo, Wr, ncol, part);
     } else {
       const Grp g{lane, 32, false};
-      for (int o = warp; o < oe - ob; o += nw) {
-        const FlatOp f = ops[o];
-        const int64_t sb = op_stage_bytes<F>(f);
-        const int64_t vb = (int64_t)(f.n_s0 + f.n_s1) * (((le - lb + RC - 1) / RC) * RC) * (int64_t)sizeof(C);
-        char* half = pf_half(smem, warp, h);
-        if (o == warp && sb <= kPfHalf && sb + vb <= kPfHalf) {
-          do_op<T, F, RC>(a, f, half, kPfHalf, g, lb, le, true);
-        } else if (o == warp && sb <= kPfHalf) {
-          // prefetched, but the vectors do not fit beside it: read the matrices from global
-          do_op<T, F, RC>(a, f, half, 0, g, lb, le);
-        } else {
-          do_op<T, F, RC>(a, f, half, kPfHalf, g, lb, le);
-        }
+      for (int o = warp; o < nops; o += nw) {
+        const FlatOp& f = ops[o];
+        do_op_res<T, F, RC>(a, f, ring + (myoff >= 0 ? myoff : 0) + f.soff, myoff >= 0, rvec, sg.row_lo, rst,
+                            sg.st_lo, Wr, ncol, g);
       }
     }
     __syncthreads();
-    h ^= 1;
-  }
-  if (resident) {
-    const int nrow = sg.row_hi - sg.row_lo;
-    for (int e = threadIdx.x; e < nrow * ncol; e += blockDim.x) {
-      const int r = e / ncol, c = e % ncol;
-      vecg[(int64_t)(sg.row_lo + r) * a.R + lb + c] = rvec[(int64_t)r * Wr + c];
+    if (myoff >= 0) {   // release the phase's ring area
+      if (--live == 0) {
+        head = tail = 0;
+      } else {
+        for (int q = ph + 1; q < issued; ++q) {
+          const int o2 = s_qoff[q % (kLook + 1)];
+          if (o2 >= 0) { tail = o2; break; }
+        }
+      }
     }
-    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < nrow * ncol; e += blockDim.x) {
+    const int r = e / ncol, c = e % ncol;
+    vecg[(int64_t)(sg.row_lo + r) * a.R + lb + c] = rvec[(int64_t)r * Wr + c];
+  }
+  __syncthreads();
+}
+
+// run kept in global memory: operands staged per op into warp slices
+template <class T, class F, int RC>
+__device__ void local_run_plain(const SweepArgs& a, const DSeg& sg, char* smem, int64_t slice, int64_t lb,
+                                int64_t le) {
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+  prefetch_records(a, sg);
+  for (int ph = sg.first; ph < sg.first + sg.count; ++ph) {
+    const int32_t ob = __ldg(a.flat_base + ph), oe = __ldg(a.flat_base + ph + 1);
+    const FlatOp* ops = a.flat + ob;
+    if (ops[0].kind == FK_LEAF) {
+      do_leaf<T, F, RC>(a, ops[0], smem, a.smem_bytes, lb, le);
+    } else {
+      const Grp g{lane, 32, false};
+      for (int o = warp; o < oe - ob; o += nw) do_op<T, F, RC>(a, ops[o], smem + warp * slice, slice, g, lb, le);
+      __syncthreads();
+    }
   }
 }
 
@@ -688,36 +761,43 @@ __global__ void __launch_bounds__(256, 1) k_sweep_coop(SweepArgs a) {
         const int gw = blockIdx.x * nw + warp, tw = gridDim.x * nw;
         for (int o = gw; o < P.count; o += tw) do_op<T, F, RC>(a, ops[o], smem + warp * slice, slice, g, 0, a.R);
       } else {
+        // one (op, RHS range) unit per CTA at a time: a phase with fewer ops
+        // than CTAs splits its right-hand sides into ranges of >= 16 columns
         const Grp g{(int)threadIdx.x, (int)blockDim.x, true};
-        for (int o = blockIdx.x; o < P.count; o += gridDim.x) do_op<T, F, RC>(a, ops[o], smem, a.smem_bytes, g, 0, a.R);
-      }
-    } else if (lb < le && a.use_pf) {
-      local_run_pf<T, F, RC>(a, sg, smem, lb, le);
-    } else if (lb < le) {
-      // bring this run's op and phase records into L1 (static data, one round trip)
-      const int32_t o_first = __ldg(a.flat_base + sg.first), o_last = __ldg(a.flat_base + sg.first + sg.count);
-      {
-        const char* p0 = (const char*)(a.flat + o_first);
-        const int64_t nb = (int64_t)(o_last - o_first) * (int64_t)sizeof(FlatOp);
-        for (int64_t e = (int64_t)threadIdx.x * 128; e < nb; e += (int64_t)blockDim.x * 128)
-          asm volatile("prefetch.global.L1 [%0];" ::"l"(p0 + e));
-        const char* p1 = (const char*)(a.flat_base + sg.first);
-        for (int64_t e = (int64_t)threadIdx.x * 128; e < (int64_t)(sg.count + 1) * 4; e += (int64_t)blockDim.x * 128)
-          asm volatile("prefetch.global.L1 [%0];" ::"l"(p1 + e));
-      }
-      for (int ph = sg.first; ph < sg.first + sg.count; ++ph) {
-        const int32_t ob = __ldg(a.flat_base + ph), oe = __ldg(a.flat_base + ph + 1);
-        const FlatOp* ops = a.flat + ob;
-        if (ops[0].kind == FK_LEAF) {
-          do_leaf<T, F, RC>(a, ops[0], smem, a.smem_bytes, lb, le);
-        } else {
-          const Grp g{lane, 32, false};
-          for (int o = warp; o < oe - ob; o += nw) do_op<T, F, RC>(a, ops[o], smem + warp * slice, slice, g, lb, le);
-          __syncthreads();
+        int64_t nu = 1, wg = a.R;
+        if (P.count < (int)gridDim.x && a.R >= 32) {
+          nu = gridDim.x / P.count;
+          const int64_t maxu = a.R / 16;
+          if (nu > maxu) nu = maxu;
+          wg = ((a.R + nu - 1) / nu + RC - 1) / RC * RC;
+          nu = (a.R + wg - 1) / wg;
+        }
+        const int64_t units = (int64_t)P.count * nu;
+        for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+          const int o = (int)(u / nu);
+          const int64_t rb = (u % nu) * wg;
+          const int64_t re = (rb + wg < a.R) ? rb + wg : a.R;
+          do_op<T, F, RC>(a, ops[o], smem, a.smem_bytes, g, rb, re);
         }
       }
+    } else if (lb < le) {
+      const int64_t ncol = le - lb, Wr = (ncol + RC - 1) / RC * RC;
+      const int64_t res_need = ((int64_t)(sg.row_hi - sg.row_lo) + (sg.st_hi - sg.st_lo)) * Wr *
+                               (int64_t)sizeof(typename CT<T>::t);
+      bool ring = a.use_pf && !sg.st_cross && res_need <= kResidentBytes && sg.count <= kRunMaxPhases;
+      int32_t o_first = 0, o_last = 0;
+      if (ring) {
+        o_first = __ldg(a.flat_base + sg.first);
+        o_last = __ldg(a.flat_base + sg.first + sg.count);
+        ring = o_last - o_first <= kRunMaxOps;
+      }
+      if (ring) local_run_ring<T, F, RC>(a, sg, smem, lb, le, o_first, o_last);
+      else local_run_plain<T, F, RC>(a, sg, smem, slice, lb, le);
     }
-    if (!grid_sync(a.bar, my_gen, a.spin_limit)) return;
+    // Two consecutive single-CTA runs need no grid barrier: each CTA only
+    // reads there the columns it wrote itself.  No barrier after the last segment.
+    if (s + 1 < a.nseg && (sg.grid || a.segs[s + 1].grid))
+      if (!grid_sync(a.bar, my_gen, a.spin_limit)) return;
   }
 }
 
@@ -755,8 +835,8 @@ static int sweep_coop_impl(const DevFactor& df, int which, void* vec, int64_t R,
   SweepArgs a;
   const int cls = R > 1 ? 1 : 0;
   if (df.tuned[cls] >= 0) {
-    a.segs = df.cand_segs[which][df.tuned[cls]];
-    a.nseg = df.cand_nsegs[which][df.tuned[cls]];
+    a.segs = df.cand_segs[cls][which][df.tuned[cls]];
+    a.nseg = df.cand_nsegs[cls][which][df.tuned[cls]];
   } else {
     a.segs = df.segs[which];
     a.nseg = df.nsegs[which];
@@ -764,6 +844,7 @@ static int sweep_coop_impl(const DevFactor& df, int which, void* vec, int64_t R,
   a.prog = df.prog[which];
   a.flat = df.flat[which];
   a.flat_base = df.flat_base[which];
+  a.flat_pbytes = df.flat_pbytes[which];
   a.n0 = df.n0;
   a.bvout = df.bvout;
   a.buout = df.buout;
@@ -781,8 +862,8 @@ static int sweep_coop_impl(const DevFactor& df, int which, void* vec, int64_t R,
   a.spin_limit = spin_limit;
   // prefetching runs: complex FP32 factors, leaf inverses within one leaf
   // buffer, and leaf partial sums (256 threads x RC columns) within the scratch
-  a.use_pf = (sizeof(F) == 8 && df.n0 * df.n0 * (int64_t)sizeof(F) <= kPfLeaf &&
-              (256 + df.n0) * RC * (int64_t)sizeof(typename CT<T>::t) <= kPfAux) ? 1 : 0;
+  a.use_pf = (sizeof(F) == 8 && df.n0 <= 64 &&
+              (256 + df.n0) * RC * (int64_t)sizeof(typename CT<T>::t) <= kAuxBytes) ? 1 : 0;
   // reset count and generation; the error flag stays set until hb_status reads it
   if (cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s) != cudaSuccess) return HB_ECUDA;
   void* args[] = {&a};

@@ -90,6 +90,28 @@ def test_apply_multi_rhs_ragged(hb, strip, R):
     np.testing.assert_allclose(y, ref, rtol=0, atol=2e-6 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("R", [40, 300])
+def test_apply_many_rhs_column_parallel(hb, strip, R):
+    # R >= 32 runs the column-parallel apply kernels (one thread per right-hand
+    # side; R = 300 spans two column blocks with a ragged tail).  FP64 tight
+    # factor: 1e-7 per column against the dense Z, forward and adjoint; FP32
+    # factor: 10 eps + 2e-6 per column; mixed FP32 factors with FP64 arithmetic
+    # (hb_residual of the FP32 form) is covered by the full-size batched test.
+    import torch
+    a = strip["a"]
+    x = W.complex_gaussian(1024, 37, R).T.copy()
+    ref = (a @ x.T).T
+    refh = (a.conj().T @ x.T).T
+    y = hb.hb_apply(strip["ftight"], _t(x)).cpu().numpy()
+    yh = hb.hb_apply(strip["ftight"], _t(x), hb.HB_OP_H).cpu().numpy()
+    e = np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    eh = np.linalg.norm(yh - refh, axis=1) / np.linalg.norm(refh, axis=1)
+    assert e.max() <= 1e-7 and eh.max() <= 1e-7, (e.max(), eh.max())
+    y32 = hb.hb_apply(strip["f32"], _t(x, torch.complex64)).cpu().numpy().astype(np.complex128)
+    e32 = np.linalg.norm(y32 - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert e32.max() <= 10 * 1e-6 + 2e-6, e32.max()
+
+
 def test_apply_leading_dimension(hb, strip):
     import torch
     a, f = strip["a"], strip["ftight"]
@@ -258,6 +280,7 @@ def test_bounded_wait_reports_timeout(hb, strip):
     f = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C128)
     lib = hb.lib()
     b = _t(W.complex_gaussian(1024, 34))
+    assert lib.hb_set_sweep_grid_min(f._h, 1) >= 1     # every butterfly stage grid-wide: many barriers
     assert lib.hb_set_wait_limit(f._h, 1) == 0
     hb.hb_lower_solve(f, b)
     rc = lib.hb_status(f._h, C.c_void_p(torch.cuda.current_stream().cuda_stream))
@@ -267,6 +290,35 @@ def test_bounded_wait_reports_timeout(hb, strip):
     assert lib.hb_status(f._h, C.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
     fh = hb.hb_factor_host(g, wl.leaf, wl.eps)
     assert _rel(x, hb.hb_host_sweep(fh, b.cpu().numpy(), 0)) <= 1e-12
+
+
+@pytest.mark.parametrize("R", [40, 300])
+def test_sweeps_many_rhs_fp32(hb, strip, R):
+    # Many right-hand sides: grid-wide phases split their columns into
+    # (op, column range) units over the CTAs, single-CTA runs keep each CTA's
+    # columns (R = 300: two per CTA) resident in shared memory.  Every column
+    # of all four sweeps must match the FP64 host sweep of the same factor to
+    # FP32 accuracy (1e-5 relative; the FP32 storage alone gives ~1e-7 per entry)
+    # under each segmentation, including the autotuned one.
+    import torch
+    wl, g = strip["wl"], strip["g"]
+    fh = hb.hb_factor_host(g, wl.leaf, wl.eps)
+    f = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C64)
+    b = W.complex_gaussian(1024, 36, R).T.copy()
+    calls = [(hb.hb_lower_solve, hb.HB_OP_N), (hb.hb_upper_solve, hb.HB_OP_N),
+             (hb.hb_lower_solve, hb.HB_OP_H), (hb.hb_upper_solve, hb.HB_OP_H)]
+    ref = [np.stack([hb.hb_host_sweep(fh, b[r], w) for r in range(R)]) for w in range(4)]
+    lib = hb.lib()
+    for gm in (1, 8, 1 << 20, None):
+        if gm is None:
+            assert hb.hb_autotune(f, R) >= 4
+            assert len(hb.hb_autotune_times(f, R)) == 6
+        else:
+            assert lib.hb_set_sweep_grid_min(f._h, gm) >= 1
+        for w, (fn, op) in enumerate(calls):
+            x = fn(f, _t(b, torch.complex64), op).cpu().numpy().astype(np.complex128)
+            err = np.linalg.norm(x - ref[w], axis=1) / np.linalg.norm(ref[w], axis=1)
+            assert err.max() <= 1e-5, (gm, w, err.max())
 
 
 def test_autotune_keeps_results(hb, strip):
