@@ -63,13 +63,13 @@ typedef struct {
   double scale;           /* a */
   double eps;             /* compression tolerance */
   int32_t kmax;           /* largest ID rank over all blocks */
-  int32_t pad0;
+  int32_t sweep_leaf;     /* rows s of the dense triangle blocks the sweeps apply (s = n0 2^t) */
   double kavg;            /* mean ID rank over all ID blocks */
   int32_t kmax_depth[32]; /* largest rank per hierarchical depth v */
   double kavg_depth[32];  /* mean rank per depth */
   int64_t nnz_leaf;       /* entries of the dense diagonal leaves (m n0^2) */
   int64_t nnz_butterfly;  /* stored entries of all butterfly factors (ID form) */
-  int64_t nnz_lu_leaf;    /* entries of the leaf triangle inverses (2 m n0^2) */
+  int64_t nnz_lu_leaf;    /* entries of the packed triangle inverses of both sweeps (2 (N/s) s(s+1)/2) */
   int64_t index_bytes;    /* bytes of pivot / map indices on the device */
   int64_t device_bytes;   /* total device bytes held by the factor */
   int64_t apply_bytes;    /* algorithmic bytes one single-RHS hb_apply touches */

@@ -28,7 +28,7 @@ class HBError(RuntimeError):
 class FactorStats(C.Structure):
     _fields_ = [("n", C.c_int64), ("leaf", C.c_int64), ("depth", C.c_int32), ("form", C.c_int32),
                 ("n_butterflies", C.c_int64), ("scale", C.c_double), ("eps", C.c_double),
-                ("kmax", C.c_int32), ("pad0", C.c_int32), ("kavg", C.c_double),
+                ("kmax", C.c_int32), ("sweep_leaf", C.c_int32), ("kavg", C.c_double),
                 ("kmax_depth", C.c_int32 * 32), ("kavg_depth", C.c_double * 32),
                 ("nnz_leaf", C.c_int64), ("nnz_butterfly", C.c_int64), ("nnz_lu_leaf", C.c_int64),
                 ("index_bytes", C.c_int64), ("device_bytes", C.c_int64), ("apply_bytes", C.c_int64),

@@ -62,12 +62,11 @@ static int upload_elems(const PackedHost& ph, const HostFactor& hf, cudaStream_t
   convert(leaves_colmajor(hf.leaf, hf.m, hf.n0), tmp);
   if ((rc = up(tmp, (E**)&df.leaf, st, df.device_bytes))) return rc;
   HB_CU(cudaStreamSynchronize(st));
-  convert(leaves_colmajor(hf.linv, hf.m, hf.n0), tmp);
-  if ((rc = up(tmp, (E**)&df.linv, st, df.device_bytes))) return rc;
-  HB_CU(cudaStreamSynchronize(st));
-  convert(leaves_colmajor(hf.uinv, hf.m, hf.n0), tmp);
-  if ((rc = up(tmp, (E**)&df.uinv, st, df.device_bytes))) return rc;
-  HB_CU(cudaStreamSynchronize(st));
+  for (int w = 0; w < 4; ++w) {
+    convert(ph.sl[w], tmp);
+    if ((rc = up(tmp, (E**)&df.sl[w], st, df.device_bytes))) return rc;
+    HB_CU(cudaStreamSynchronize(st));
+  }
   return HB_OK;
 }
 
@@ -76,6 +75,7 @@ int upload_factor(const PackedHost& ph, const HostFactor& hf, const Geometry& g,
   df.form = form;
   df.n = ph.n; df.n0 = ph.n0; df.m = ph.m; df.D = ph.depth;
   df.state_len = ph.state_len;
+  df.sl_n = ph.sl_n; df.sl_m = ph.sl_m;
   df.fpool_len = (int64_t)ph.fpool.size();
   df.ipool_len = (int64_t)ph.ipool.size();
   df.kappa = hf.kappa; df.eta0 = hf.eta0; df.scale = hf.scale;
@@ -97,10 +97,21 @@ int upload_factor(const PackedHost& ph, const HostFactor& hf, const Geometry& g,
   for (int i = 0; i < 4; ++i) {
     if ((rc = up(*progs[i], &df.prog[i], st, df.device_bytes))) return rc;
     df.nprog[i] = (int)progs[i]->size();
-    FlatProgram fpg = flatten_program(ph, *progs[i], ph.n0);
+    FlatProgram fpg = flatten_program(ph, *progs[i], i);
     if (!fpg.ok) {
       set_error("sweep program: an op does not fit the 64-byte record");
       return HB_EUNSUPPORTED;
+    }
+    df.sweep_elems[i] = df.sweep_idx[i] = 0;
+    for (const FlatOp& o : fpg.ops) {
+      df.sweep_elems[i] += o.melems;
+      if (o.ioff >= 0) df.sweep_idx[i] += o.ielems;
+      // the sweep kernel copies every op's data with 16-byte bulk copies:
+      // matrices must start on an even complex-FP32 entry, indices on a multiple of 8
+      if ((o.moff & 1) || (o.ioff >= 0 && (o.ioff & 7))) {
+        set_error("sweep program: op data not 16-byte aligned");
+        return HB_EUNSUPPORTED;
+      }
     }
     if ((rc = up(fpg.ops, &df.flat[i], st, df.device_bytes))) return rc;
     if ((rc = up(fpg.base, &df.flat_base[i], st, df.device_bytes))) return rc;
@@ -131,7 +142,7 @@ int set_grid_min(DevFactor& df, const PackedHost& ph, int grid_min, cudaStream_t
   HB_CU(cudaStreamSynchronize(st));
   const int64_t budget = resident_budget(1, vec_elem_bytes(df));
   for (int i = 0; i < 4; ++i) {
-    std::vector<DSeg> segs = segment_program(*progs[i], flatten_program(ph, *progs[i], ph.n0), grid_min, budget);
+    std::vector<DSeg> segs = segment_program(*progs[i], flatten_program(ph, *progs[i], i), grid_min, budget);
     if (df.segs[i]) { cudaFree(df.segs[i]); df.segs[i] = nullptr; }
     int64_t dummy = 0;
     int rc = up(segs, &df.segs[i], st, dummy);
@@ -149,7 +160,7 @@ int build_candidates(DevFactor& df, const PackedHost& ph, int cls, int64_t cols,
   if (df.cand_segs[cls][0][0] && df.cand_budget[cls] == budget) return HB_OK;
   HB_CU(cudaStreamSynchronize(st));
   for (int i = 0; i < 4; ++i) {
-    FlatProgram fpg = flatten_program(ph, *progs[i], ph.n0);
+    FlatProgram fpg = flatten_program(ph, *progs[i], i);
     for (int c = 0; c < DevFactor::kNCand; ++c) {
       std::vector<DSeg> segs = segment_program(*progs[i], fpg, DevFactor::kCand[c], budget);
       if (df.cand_segs[cls][i][c]) { cudaFree(df.cand_segs[cls][i][c]); df.cand_segs[cls][i][c] = nullptr; }
@@ -165,7 +176,7 @@ int build_candidates(DevFactor& df, const PackedHost& ph, int cls, int64_t cols,
 }
 
 void free_factor(DevFactor& df) {
-  void* ptrs[] = {df.fpool, df.leaf, df.linv, df.uinv, df.ipool, df.vout, df.uout, df.bvout, df.buout,
+  void* ptrs[] = {df.fpool, df.leaf, df.sl[0], df.sl[1], df.sl[2], df.sl[3], df.ipool, df.vout, df.uout, df.bvout, df.buout,
                   df.bf_vout0, df.bf_uout0, df.items, df.step_idx, df.astep_idx, df.prog[0], df.prog[1],
                   df.prog[2], df.prog[3], df.segs[0], df.segs[1], df.segs[2], df.segs[3], df.bar,
                   df.flat[0], df.flat[1], df.flat[2], df.flat[3], df.flat_base[0], df.flat_base[1],
@@ -281,6 +292,7 @@ int hb_factor(hb_geometry_t g, double wavelength, double eta0, double gamma, int
   f->hf.leaf.clear(); f->hf.leaf.shrink_to_fit();
   f->hf.linv.clear(); f->hf.linv.shrink_to_fit();
   f->hf.uinv.clear(); f->hf.uinv.shrink_to_fit();
+  for (auto& v : f->ph.sl) { v.clear(); v.shrink_to_fit(); }
   *out = f;
   return HB_OK;
 }
@@ -325,16 +337,26 @@ int hb_factor_info(hb_factor_t f, hb_factor_stats* s) {
   for (int v = 0; v < 32; ++v) { s->kmax_depth[v] = ph.kmax_depth[v]; s->kavg_depth[v] = ph.kavg_depth[v]; }
   s->nnz_leaf = ph.m * ph.n0 * ph.n0;
   s->nnz_butterfly = ph.nnz_bf;
-  s->nnz_lu_leaf = 2 * s->nnz_leaf;
+  s->sweep_leaf = (int32_t)ph.sl_n;
+  s->nnz_lu_leaf = 2 * ph.sl_m * packed_tri(ph.sl_n);
   s->index_bytes = f->df.ipool_len * 2;
   s->device_bytes = f->df.device_bytes;
   int64_t eb = (f->df.form == HB_C128) ? 16 : 8;
   // algorithmic bytes of one single-RHS apply: every stored butterfly entry and
   // dense-leaf entry once, the index arrays once, x read and y written.
   s->apply_bytes = (ph.nnz_bf + s->nnz_leaf) * eb + s->index_bytes + 2 * ph.n * eb;
-  // a sweep touches the butterflies of one triangle (about half) and one leaf-inverse set
-  s->lower_bytes = f->lower_nnz * eb + s->nnz_leaf * eb + s->index_bytes / 2 + 2 * ph.n * eb;
-  s->upper_bytes = f->upper_nnz * eb + s->nnz_leaf * eb + s->index_bytes / 2 + 2 * ph.n * eb;
+  // a sweep reads every factor entry and index entry of its program once (the
+  // butterflies of one triangle above the sweep leaves, and one packed
+  // triangle per sweep leaf), reads b and writes x
+  int64_t el[2] = {f->df.sweep_elems[0], f->df.sweep_elems[1]}, ix[2] = {f->df.sweep_idx[0], f->df.sweep_idx[1]};
+  if (f->host_only)
+    for (int w = 0; w < 2; ++w) {
+      FlatProgram fp = flatten_program(ph, w == 0 ? ph.prog_lower : ph.prog_upper, w);
+      el[w] = ix[w] = 0;
+      for (const FlatOp& o : fp.ops) { el[w] += o.melems; if (o.ioff >= 0) ix[w] += o.ielems; }
+    }
+  s->lower_bytes = el[0] * eb + ix[0] * 2 + 2 * ph.n * eb;
+  s->upper_bytes = el[1] * eb + ix[1] * 2 + 2 * ph.n * eb;
   s->rebuilt_blocks = 0;
   s->build_seconds = f->build_seconds;
   return HB_OK;

@@ -18,8 +18,10 @@ struct DevFactor {
   void* fpool = nullptr;
   int64_t fpool_len = 0;
   void* leaf = nullptr;          // [m][c][r]
-  void* linv = nullptr;          // [m][c][r] inverse of the unit-lower leaf triangle
-  void* uinv = nullptr;          // [m][c][r] inverse of the upper leaf triangle
+  void* sl[4] = {nullptr, nullptr, nullptr, nullptr};   // packed sweep-leaf triangles per sweep (PackedHost::sl)
+  int64_t sl_n = 0, sl_m = 0;    // sweep-leaf order and count
+  int64_t sweep_elems[4] = {0, 0, 0, 0};   // factor entries one sweep reads (per program)
+  int64_t sweep_idx[4] = {0, 0, 0, 0};     // index entries one sweep reads
   int16_t* ipool = nullptr;
   int64_t ipool_len = 0;
   DOuter* vout = nullptr;        // [m][D]

@@ -579,6 +579,9 @@ struct Packer {
 };
 }  // namespace
 
+// Dense sweep-leaf triangles (PackedHost::sl) from the subtree programs.
+static void build_sweep_leaves(const HostFactor& hf, PackedHost& ph, const std::vector<std::vector<DPhase>> (&subs)[2]);
+
 void pack_factor(const HostFactor& hf, PackedHost& ph) {
   Packer pk(ph);
   const int D = hf.depth;
@@ -776,10 +779,17 @@ void pack_factor(const HostFactor& hf, PackedHost& ph) {
     prog.push_back(outer_phase(PH_EXIT, id, adj));
   };
   ph.prog_lower.clear(); ph.prog_upper.clear(); ph.prog_lower_adj.clear(); ph.prog_upper_adj.clear();
+  // sweep leaves: merge the lowest sl_t levels while the subtree has at most kSweepLeafMax rows
+  ph.sl_t = 0;
+  while (ph.sl_t < D && (n0 << (ph.sl_t + 1)) <= kSweepLeafMax) ++ph.sl_t;
+  ph.sl_n = n0 << ph.sl_t;
+  ph.sl_m = m >> ph.sl_t;
+  const int vl = D - ph.sl_t;   // depth of the sweep leaves
   // lower: left child, F21, right child
   std::function<void(int, int64_t, std::vector<DPhase>&, int)> rec = [&](int v, int64_t p, std::vector<DPhase>& prog, int mode) {
-    if (v == D) {
-      prog.push_back(DPhase{PH_LEAF, (int32_t)p, 1, (mode >= 2) ? 1 : 0, (int32_t)(hf.n0 * hf.n0 * 16), (int32_t)hf.n0});
+    if (v == vl) {
+      prog.push_back(DPhase{PH_LEAF, (int32_t)p, 1, (mode >= 2) ? 1 : 0,
+                            (int32_t)std::min<int64_t>(packed_tri(ph.sl_n) * 16, INT32_MAX), (int32_t)ph.sl_n});
       return;
     }
     int64_t lo = 2 * p, hi = 2 * p + 1;
@@ -794,6 +804,24 @@ void pack_factor(const HostFactor& hf, PackedHost& ph) {
   rec(0, 0, ph.prog_upper, 1);
   rec(0, 0, ph.prog_lower_adj, 2);
   rec(0, 0, ph.prog_upper_adj, 3);
+  // the full-depth programs (down to the n0 leaves) of every sweep-leaf subtree,
+  // for L~^{-1} (mode 0) and U~^{-1} (mode 1); their results on unit vectors
+  // are the columns of the sweep-leaf triangles
+  std::vector<std::vector<DPhase>> subs[2];
+  std::function<void(int, int64_t, std::vector<DPhase>&, int)> rec_full = [&](int v, int64_t p, std::vector<DPhase>& prog, int mode) {
+    if (v == D) {
+      prog.push_back(DPhase{PH_LEAF, (int32_t)p, 1, 0, 0, (int32_t)n0});
+      return;
+    }
+    const int64_t lo = 2 * p, hi = 2 * p + 1;
+    if (mode == 0) { rec_full(v + 1, lo, prog, mode); emit_bf(prog, bf_id(v, p, 1), false); rec_full(v + 1, hi, prog, mode); }
+    else { rec_full(v + 1, hi, prog, mode); emit_bf(prog, bf_id(v, p, 0), false); rec_full(v + 1, lo, prog, mode); }
+  };
+  for (int mode = 0; mode < 2; ++mode) {
+    subs[mode].resize((size_t)ph.sl_m);
+    for (int64_t p = 0; p < ph.sl_m; ++p) rec_full(vl, p, subs[mode][(size_t)p], mode);
+  }
+  build_sweep_leaves(hf, ph, subs);
   // tail padding so 16-byte bulk copies of the last block stay inside the pools
   for (int i = 0; i < 4; ++i) ph.fpool.push_back(cplx(0.0));
   for (int i = 0; i < 16; ++i) ph.ipool.push_back(0);
@@ -918,16 +946,35 @@ struct HostExec {
     }
   }
 
-  void sweep(int which, cplx* vec) {
-    const std::vector<DPhase>& prog = which == 0 ? ph.prog_lower : which == 1 ? ph.prog_upper
-                                    : which == 2 ? ph.prog_lower_adj : ph.prog_upper_adj;
-    const std::vector<cplx>& tinv = (which == 0 || which == 2) ? hf.linv : hf.uinv;
+  // x = T x for the packed sweep-leaf triangle p of sweep `which`
+  void sl_mv(int which, int64_t p, cplx* x, cplx* y) const {
+    const int64_t s = ph.sl_n;
+    const cplx* T = &ph.sl[which][(size_t)(p * packed_tri(s))];
+    const bool upper = (which == 1 || which == 2);
+    for (int64_t r = 0; r < s; ++r) {
+      cplx acc = 0.0;
+      if (upper) for (int64_t c = r; c < s; ++c) acc += T[tri_off_upper(r, c)] * x[c];
+      else for (int64_t c = 0; c <= r; ++c) acc += T[tri_off_lower(s, r, c)] * x[c];
+      y[r] = acc;
+    }
+    std::copy(y, y + s, x);
+  }
+
+  // Run a sweep program in place.  sweep_leaves: its PH_LEAF phases are sweep
+  // leaves (packed triangles of ph.sl[which]); otherwise n0 leaves (the leaf
+  // triangle inverses, `which` 0 or 1).
+  void run(const std::vector<DPhase>& prog, int which, cplx* vec, bool sweep_leaves) {
     const int64_t n0 = ph.n0;
-    std::vector<cplx> tmp(n0);
+    std::vector<cplx> tmp((size_t)std::max<int64_t>(n0, ph.sl_n));
     for (const DPhase& P : prog) {
       if (P.kind == PH_LEAF) {
-        leaf_mv(tinv, P.arg0, vec + (int64_t)P.arg0 * n0, tmp.data(), P.adj != 0);
-        std::copy(tmp.begin(), tmp.end(), vec + (int64_t)P.arg0 * n0);
+        if (sweep_leaves) {
+          sl_mv(which, P.arg0, vec + (int64_t)P.arg0 * ph.sl_n, tmp.data());
+        } else {
+          const std::vector<cplx>& tinv = (which == 0 || which == 2) ? hf.linv : hf.uinv;
+          leaf_mv(tinv, P.arg0, vec + (int64_t)P.arg0 * n0, tmp.data(), P.adj != 0);
+          std::copy(tmp.begin(), tmp.begin() + n0, vec + (int64_t)P.arg0 * n0);
+        }
       } else if (P.kind == PH_ENTER) {
         const DOuter* ops = P.adj ? &ph.buout[ph.bf_uout0[P.arg0]] : &ph.bvout[ph.bf_vout0[P.arg0]];
         for (int o = 0; o < P.count; ++o) {
@@ -945,11 +992,55 @@ struct HostExec {
       }
     }
   }
+
+  void sweep(int which, cplx* vec) {
+    const std::vector<DPhase>& prog = which == 0 ? ph.prog_lower : which == 1 ? ph.prog_upper
+                                    : which == 2 ? ph.prog_lower_adj : ph.prog_upper_adj;
+    run(prog, which, vec, true);
+  }
 };
 }  // namespace
 
-FlatProgram flatten_program(const PackedHost& ph, const std::vector<DPhase>& prog, int64_t n0) {
+static void build_sweep_leaves(const HostFactor& hf, PackedHost& ph, const std::vector<std::vector<DPhase>> (&subs)[2]) {
+  const int64_t s = ph.sl_n, P = packed_tri(s);
+  for (int w = 0; w < 4; ++w) ph.sl[w].assign((size_t)(ph.sl_m * P), cplx(0.0));
+#pragma omp parallel
+  {
+    HostExec ex(ph, hf);
+    std::vector<cplx> vec((size_t)ph.n, cplx(0.0));
+    std::vector<cplx> dense((size_t)(s * s));
+#pragma omp for schedule(dynamic, 4)
+    for (int64_t p = 0; p < ph.sl_m; ++p) {
+      cplx* v = vec.data() + p * s;
+      for (int mode = 0; mode < 2; ++mode) {
+        // column j of the subtree's inverse triangle = the subtree sweep of e_j
+        for (int64_t j = 0; j < s; ++j) {
+          std::fill(v, v + s, cplx(0.0));
+          v[j] = 1.0;
+          ex.run(subs[mode][(size_t)p], mode, vec.data(), false);
+          for (int64_t r = 0; r < s; ++r) dense[(size_t)(r * s + j)] = v[r];
+        }
+        // mode 0: T lower -> sl[0], T^H upper -> sl[2];  mode 1: T upper -> sl[1], T^H lower -> sl[3]
+        cplx* a = &ph.sl[mode][(size_t)(p * P)];
+        cplx* b = &ph.sl[mode + 2][(size_t)(p * P)];
+        for (int64_t c = 0; c < s; ++c) {
+          if (mode == 0) {
+            for (int64_t r = c; r < s; ++r) a[tri_off_lower(s, r, c)] = dense[(size_t)(r * s + c)];
+            for (int64_t r = 0; r <= c; ++r) b[tri_off_upper(r, c)] = std::conj(dense[(size_t)(c * s + r)]);
+          } else {
+            for (int64_t r = 0; r <= c; ++r) a[tri_off_upper(r, c)] = dense[(size_t)(r * s + c)];
+            for (int64_t r = c; r < s; ++r) b[tri_off_lower(s, r, c)] = std::conj(dense[(size_t)(c * s + r)]);
+          }
+        }
+      }
+    }
+  }
+}
+
+FlatProgram flatten_program(const PackedHost& ph, const std::vector<DPhase>& prog, int which) {
   FlatProgram fp;
+  const int64_t n0 = ph.n0;
+  const bool upper_tri = (which == 1 || which == 2);
   fp.base.reserve(prog.size() + 1);
   auto blkm = [](const DBlk& b) { return (int64_t)b.k * (b.c - b.k); };
   for (const DPhase& P : prog) {
@@ -958,15 +1049,17 @@ FlatProgram flatten_program(const PackedHost& ph, const std::vector<DPhase>& pro
     for (int o = 0; o < P.count; ++o) {
       FlatOp f{};
       if (P.kind == PH_LEAF) {
+        // sweep leaf: packed triangle of order sl_n
+        const int64_t s = ph.sl_n;
         f.kind = FK_LEAF;
-        f.flags = (int16_t)(adj ? FF_ADJ : 0);
-        f.moff = (int64_t)P.arg0 * n0 * n0;
-        f.melems = (int32_t)(n0 * n0);
+        f.flags = (int16_t)(upper_tri ? FF_UPPER : 0);
+        f.moff = (int64_t)P.arg0 * packed_tri(s);
+        f.melems = (int32_t)packed_tri(s);
         f.ioff = -1;
-        f.c0 = (int16_t)n0;
-        f.src0 = (int32_t)(P.arg0 * n0);
-        f.n_s0 = (int16_t)n0;
-        if (n0 > INT16_MAX) fp.ok = false;
+        f.c0 = (int16_t)s;
+        f.src0 = (int32_t)(P.arg0 * s);
+        f.n_s0 = (int16_t)s;
+        if (s > INT16_MAX) fp.ok = false;
         f.out0 = f.src0;
       } else if (P.kind == PH_ENTER || P.kind == PH_EXIT) {
         const bool enter = P.kind == PH_ENTER;

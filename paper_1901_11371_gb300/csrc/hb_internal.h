@@ -159,7 +159,19 @@ struct DSeg {
 // the factor pool (or, for leaf ops, the leaf-inverse array) in elements of the
 // storage type and to the index pool in int16 entries.
 enum FlatKind : int16_t { FK_GATHER = 0, FK_SCATTER = 1, FK_MIDDLE = 2, FK_LEAF = 3 };
-enum FlatFlag : int16_t { FF_CONJ = 1, FF_SUB = 2, FF_ADJ = 4, FF_SRC_VEC = 8, FF_OUT_VEC = 16, FF_TWO = 32 };
+enum FlatFlag : int16_t { FF_CONJ = 1, FF_SUB = 2, FF_ADJ = 4, FF_SRC_VEC = 8, FF_OUT_VEC = 16, FF_TWO = 32,
+                          FF_UPPER = 64 /* leaf op: packed upper triangle */ };
+// Largest sweep leaf (rows) that pack_factor forms by merging subtrees.
+constexpr int kSweepLeafMax = 128;
+#ifdef __CUDACC__
+#define HB_HD __host__ __device__
+#else
+#define HB_HD
+#endif
+HB_HD inline int64_t packed_tri(int64_t s) { return s * (s + 1) / 2; }
+// offset of entry (r, c) in a column-packed triangle of order s
+HB_HD inline int64_t tri_off_lower(int64_t s, int64_t r, int64_t c) { return c * s - c * (c - 1) / 2 + (r - c); }
+HB_HD inline int64_t tri_off_upper(int64_t r, int64_t c) { return c * (c + 1) / 2 + r; }
 struct FlatOp {
   int64_t moff;      // first element to stage
   int32_t melems;    // elements to stage (both blocks and the gap between them)
@@ -217,6 +229,16 @@ struct PackedHost {
   std::vector<int32_t> bf_step_base, bf_steps, bf_L;
   // sweep programs
   std::vector<DPhase> prog_lower, prog_upper, prog_lower_adj, prog_upper_adj;
+  // Sweep leaves ("super-leaves"): the sweeps treat each subtree of
+  // sl_n = n0 2^sl_t rows as one dense triangle, the exact inverse of L~ (or
+  // U~) restricted to that subtree, i.e. what Alg. 3 (Alg. 4) computes on it.
+  // sl[w] holds, for sweep w (0: L~^{-1}, 1: U~^{-1}, 2: L~^{-H}, 3: U~^{-H}),
+  // sl_m packed triangles of sl_n (sl_n + 1) / 2 entries, column by column:
+  // lower triangles (w = 0, 3) store rows c..s-1 of column c, upper ones
+  // (w = 1, 2) rows 0..c.
+  int sl_t = 0;
+  int64_t sl_n = 0, sl_m = 0;
+  std::vector<cplx> sl[4];
   // statistics
   int64_t nnz_bf = 0;
   int32_t kmax_depth[32] = {0};
@@ -225,7 +247,8 @@ struct PackedHost {
 };
 
 void pack_factor(const HostFactor& hf, PackedHost& ph);
-FlatProgram flatten_program(const PackedHost& ph, const std::vector<DPhase>& prog, int64_t n0);
+// Flatten sweep program `which` (0: L~^{-1}, 1: U~^{-1}, 2: L~^{-H}, 3: U~^{-H}).
+FlatProgram flatten_program(const PackedHost& ph, const std::vector<DPhase>& prog, int which);
 // fill the row / state ranges of the single-CTA runs
 void annotate_segments(std::vector<DSeg>& segs, const FlatProgram& fp);
 // Limits of a single-CTA run that the sweep kernel keeps in shared memory

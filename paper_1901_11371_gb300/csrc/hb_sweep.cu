@@ -46,8 +46,10 @@ __device__ __forceinline__ double2 ldcg2(const double2* p) { return __ldcg(p); }
 struct Grp {
   int t, nt;
   bool cta;
+  int bar = 0;   // > 0: a group of whole warps synchronised on named barrier `bar`
   __device__ __forceinline__ void sync() const {
-    if (cta) __syncthreads();
+    if (bar > 0) asm volatile("bar.sync %0, %1;\n" ::"r"(bar), "r"(nt) : "memory");
+    else if (cta) __syncthreads();
     else __syncwarp();
   }
 };
@@ -381,68 +383,91 @@ __device__ void do_op(const SweepArgs& a, const FlatOp& f, char* buf, int64_t bu
   if (pl.once) g.sync();
 }
 
-// leaf solve x_leaf = Tinv b_leaf (or Tinv^H b_leaf), whole CTA
+// Sweep-leaf product x = T b, T the packed triangle of order s of the op
+// (lower, or upper with FF_UPPER), column-packed.  Thread (pair j, group g)
+// owns rows j and s-1-j (together s+1 triangle entries, so every thread has
+// the same share) and sums the columns c = g, g + ngrp, ... of each row inside
+// the triangle; for a fixed column consecutive threads read consecutive
+// entries.  part: ngrp * s * RC partial sums; b: the s input rows (stride W,
+// columns of this pass); results replace the rows of out (stride Wo) after a
+// barrier, so out may alias b.
 template <class T, class F, int RC>
-__device__ void do_leaf(const SweepArgs& a, const FlatOp& f, char* buf, int64_t buf_bytes, int64_t rb, int64_t re,
-                        const F* pre_m = nullptr) {
+__device__ __forceinline__ void tri_pass(const F* Tm, int s, bool upper, const typename CT<T>::t* b, int64_t W,
+                                         typename CT<T>::t* out, int64_t Wo, int rc, typename CT<T>::t* part) {
   using C = typename CT<T>::t;
-  const int64_t n0 = a.n0, R = a.R;
-  const Grp g{(int)threadIdx.x, (int)blockDim.x, true};
-  const F* Tg = (const F*)a.tinv + f.moff;
-  C* v = (C*)a.vec + (int64_t)f.src0 * R;
-  const bool ladj = (f.flags & FF_ADJ) != 0;
-  const int64_t mb = align16(n0 * n0 * (int64_t)sizeof(F));
-  const int ngrp = (int)(blockDim.x / n0) > 0 ? (int)(blockDim.x / n0) : 1;
-  const int64_t partb = align16((int64_t)ngrp * n0 * RC * sizeof(C));
-  const F* Tm = Tg;
-  char* area = buf;
-  int64_t area_bytes = buf_bytes;
-  if (pre_m) {
-    Tm = pre_m;
-  } else if (mb + partb + n0 * RC * (int64_t)sizeof(C) <= buf_bytes) {
-    stage(buf, Tg, mb, g);
-    Tm = (const F*)buf;
-    area = buf + mb;
-    area_bytes = buf_bytes - mb;
-  }
-  C* part = (C*)area;
-  C* bv = (C*)(area + partb);
-  VecPlan<C, RC> pl(rb, re, partb, (int)n0, area_bytes);
-  const int W = pl.W;
-  const bool noasync = pre_m != nullptr;
-  if (pl.once) stage_vec<C>(bv, v, (int)n0, R, rb, (int)(re - rb), W, g, noasync);
-  if (!noasync) cp_commit_wait();
-  __syncthreads();
-  for (int64_t ch = 0; ch < pl.nch; ++ch) {
-    const int64_t r0 = rb + ch * RC;
-    const int rc = pl.rc(ch);
-    C* bb = pl.once ? bv + ch * RC : bv;
-    if (!pl.once) {
-      stage_vec<C>(bb, v, (int)n0, R, r0, rc, W, g, noasync);
-      if (!noasync) cp_commit_wait();
-      __syncthreads();
-    }
-    for (int e = threadIdx.x; e < ngrp * n0; e += blockDim.x) {
-      const int r = e % n0, q = e / n0;
+  const int npair = s > 1 ? s / 2 : 1;
+  const int ngrp = (int)blockDim.x / npair > 0 ? (int)blockDim.x / npair : 1;
+  for (int e = threadIdx.x; e < ngrp * npair; e += blockDim.x) {
+    const int j = e % npair, g = e / npair;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = h == 0 ? j : s - 1 - j;
+      if (h == 1 && r == j) break;   // s == 1
       C acc[RC];
 #pragma unroll
       for (int rr = 0; rr < RC; ++rr) acc[rr] = z2<T>();
-      for (int cc = q; cc < n0; cc += ngrp) {
-        C m = ladj ? cvc<T>(Tm[(int64_t)r * n0 + cc]) : cv<T>(Tm[(int64_t)cc * n0 + r]);
+      if (upper) {
+        // row r: columns r .. s-1, entry (r, c) at c (c + 1) / 2 + r
+        int c = r + ((g - r % ngrp) + ngrp) % ngrp;
+#pragma unroll 4
+        for (; c < s; c += ngrp) {
+          const C m = cv<T>(Tm[(c * (c + 1) >> 1) + r]);
 #pragma unroll
-        for (int rr = 0; rr < RC; ++rr) fma2(acc[rr], m, bb[(int64_t)cc * W + rr]);
+          for (int rr = 0; rr < RC; ++rr) fma2(acc[rr], m, b[(int64_t)c * W + rr]);
+        }
+      } else {
+        // row r: columns 0 .. r, entry (r, c) at c s - c (c - 1) / 2 + r - c
+#pragma unroll 4
+        for (int c = g; c <= r; c += ngrp) {
+          const C m = cv<T>(Tm[c * s - ((c * (c - 1)) >> 1) + r - c]);
+#pragma unroll
+          for (int rr = 0; rr < RC; ++rr) fma2(acc[rr], m, b[(int64_t)c * W + rr]);
+        }
       }
 #pragma unroll
-      for (int rr = 0; rr < RC; ++rr) part[(q * n0 + r) * RC + rr] = acc[rr];
+      for (int rr = 0; rr < RC; ++rr) part[(g * s + r) * RC + rr] = acc[rr];
     }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < s * RC; e += blockDim.x) {
+    const int r = e / RC, rr = e % RC;
+    C sum = z2<T>();
+    for (int g = 0; g < ngrp; ++g) { sum.x += part[(g * s + r) * RC + rr].x; sum.y += part[(g * s + r) * RC + rr].y; }
+    if (rr < rc) out[(int64_t)r * Wo + rr] = sum;
+  }
+  __syncthreads();
+}
+
+// sweep-leaf solve of a run kept in global memory: whole CTA, columns [rb, re)
+template <class T, class F, int RC>
+__device__ void do_leaf(const SweepArgs& a, const FlatOp& f, char* buf, int64_t buf_bytes, int64_t rb, int64_t re) {
+  using C = typename CT<T>::t;
+  const int s = f.c0;
+  const int64_t R = a.R;
+  const Grp g{(int)threadIdx.x, (int)blockDim.x, true};
+  const F* Tg = (const F*)a.tinv + f.moff;
+  C* v = (C*)a.vec + (int64_t)f.src0 * R;
+  const bool upper = (f.flags & FF_UPPER) != 0;
+  const int npair = s > 1 ? s / 2 : 1;
+  const int ngrp = (int)blockDim.x / npair > 0 ? (int)blockDim.x / npair : 1;
+  const int64_t mb = align16((int64_t)f.melems * (int64_t)sizeof(F));
+  const int64_t partb = align16((int64_t)ngrp * s * RC * (int64_t)sizeof(C));
+  const int64_t vb = (int64_t)s * RC * (int64_t)sizeof(C);
+  const F* Tm = Tg;
+  char* area = buf;
+  if (mb + partb + vb <= buf_bytes) {
+    stage(buf, Tg, mb, g);
+    Tm = (const F*)buf;
+    area = buf + mb;
+  }
+  C* part = (C*)area;
+  C* bb = (C*)(area + partb);
+  for (int64_t r0 = rb; r0 < re; r0 += RC) {
+    const int rc = (re - r0) < RC ? (int)(re - r0) : RC;
+    stage_vec<C>(bb, v, s, R, r0, rc, RC, g, true);
+    cp_commit_wait();
     __syncthreads();
-    for (int e = threadIdx.x; e < n0 * RC; e += blockDim.x) {
-      const int r = e / RC, rr = e % RC;
-      C sum = z2<T>();
-      for (int q = 0; q < ngrp; ++q) { sum.x += part[(q * n0 + r) * RC + rr].x; sum.y += part[(q * n0 + r) * RC + rr].y; }
-      if (rr < rc) v[(int64_t)r * R + r0 + rr] = sum;
-    }
-    __syncthreads();
+    tri_pass<T, F, RC>(Tm, s, upper, bb, RC, v + r0, R, rc, part);
   }
 }
 
@@ -457,10 +482,10 @@ __device__ void do_leaf(const SweepArgs& a, const FlatOp& f, char* buf, int64_t 
 // Shared-memory map: [ring | leaf partial sums | resident rows + state].
 // ---------------------------------------------------------------------------
 constexpr int kSmemBytes = 224 * 1024;
-constexpr int kAuxBytes = 8 * 1024;                                     // leaf partial sums
+constexpr int kAuxBytes = 16 * 1024;                                    // sweep-leaf partial sums
 constexpr int kRecBytes = kRunMaxOps * 64;                              // the run's op records (48 KB)
 constexpr int kPhBytes = (kRunMaxPhases + 1) * 8;                       // the run's phase table (4 KB)
-constexpr int kRingBytes = kSmemBytes - kAuxBytes - kResidentBytes - kRecBytes - kPhBytes;   // 108 KB
+constexpr int kRingBytes = kSmemBytes - kAuxBytes - kResidentBytes - kRecBytes - kPhBytes;   // 100 KB
 constexpr int kLook = 7;                                                // phases in flight beyond the current one
 
 __device__ __forceinline__ void cp_wait_n(int n) {
@@ -476,21 +501,51 @@ __device__ __forceinline__ void cp_wait_n(int n) {
   }
 }
 
-// issue the copies of one phase's factor data (ops[0 .. nops)) into dst (no commit)
+// ---- mbarrier + bulk-copy helpers (one thread issues a phase's copies)
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint64_t* b) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* b, unsigned bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(b)),
+               "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
+  unsigned ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(ok) : "r"(smem_u32(b)), "r"(parity) : "memory");
+  return ok != 0;
+}
+// bulk copy of `bytes` (multiple of 16; both addresses 16-byte aligned), completion on mbarrier b
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(b)) : "memory");
+}
+
+// issue the bulk copies of one phase's factor data (ops[0 .. nops), total
+// `bytes`) into dst, completing on mbarrier b (one warp; lane o issues op o)
 template <class F>
-__device__ void ring_issue(const SweepArgs& a, const FlatOp* ops, int nops, char* dst, int warp, int nw, int lane) {
+__device__ void ring_issue(const SweepArgs& a, const FlatOp* ops, int nops, char* dst, unsigned bytes, uint64_t* b,
+                           int lane) {
+  if (lane == 0) {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // earlier generic reads of the area come first
+    mbar_arrive_tx(b, bytes);
+  }
+  __syncwarp();
   if (ops[0].kind == FK_LEAF) {
-    const Grp g{(int)threadIdx.x, (int)blockDim.x, true};
-    stage(dst, (const F*)a.tinv + ops[0].moff, align16((int64_t)ops[0].melems * (int64_t)sizeof(F)), g);
+    if (lane == 0)
+      bulk_g2s(dst, (const F*)a.tinv + ops[0].moff, (unsigned)align16((int64_t)ops[0].melems * (int64_t)sizeof(F)), b);
     return;
   }
-  const Grp g{lane, 32, false};
-  for (int o = warp; o < nops; o += nw) {
+  for (int o = lane; o < nops; o += 32) {
     const FlatOp& f = ops[o];
     char* d = dst + f.soff;
-    const int64_t mb = align16((int64_t)f.melems * (int64_t)sizeof(F));
-    stage(d, (const F*)a.fp + f.moff, mb, g);
-    if (f.ioff >= 0) stage(d + mb, a.ip + f.ioff, align16((int64_t)f.ielems * (int64_t)sizeof(int16_t)), g);
+    const unsigned mb = (unsigned)align16((int64_t)f.melems * (int64_t)sizeof(F));
+    bulk_g2s(d, (const F*)a.fp + f.moff, mb, b);
+    if (f.ioff >= 0) bulk_g2s(d + mb, a.ip + f.ioff, (unsigned)align16((int64_t)f.ielems * (int64_t)sizeof(int16_t)), b);
   }
 }
 
@@ -572,39 +627,18 @@ __device__ void do_op_res(const SweepArgs& a, const FlatOp& f, const char* half,
   g.sync();
 }
 
-// leaf solve of a resident run: rows in shared memory, inverse prefetched
+// sweep-leaf solve of a resident run: rows in shared memory, triangle staged (or global)
 template <class T, class F, int RC>
 __device__ void do_leaf_res(const SweepArgs& a, const FlatOp& f, const F* Tm, typename CT<T>::t* rvec, int row_lo,
                             int Wr, int ncol, typename CT<T>::t* part) {
   using C = typename CT<T>::t;
-  const int n0 = (int)a.n0;
-  const bool ladj = (f.flags & FF_ADJ) != 0;
+  const int s = f.c0;
+  const bool upper = (f.flags & FF_UPPER) != 0;
   C* v = rvec + (int64_t)(f.src0 - row_lo) * Wr;
-  const int ngrp = (int)(blockDim.x / n0) > 0 ? (int)(blockDim.x / n0) : 1;
+  // the pass reads all of b before any row is written (a barrier separates them)
   for (int r0 = 0; r0 < ncol; r0 += RC) {
     const int rc = (ncol - r0) < RC ? (ncol - r0) : RC;
-    for (int e = threadIdx.x; e < ngrp * n0; e += blockDim.x) {
-      const int r = e % n0, q = e / n0;
-      C acc[RC];
-#pragma unroll
-      for (int rr = 0; rr < RC; ++rr) acc[rr] = z2<T>();
-#pragma unroll 4
-      for (int cc = q; cc < n0; cc += ngrp) {
-        C m = ladj ? cvc<T>(Tm[(int64_t)r * n0 + cc]) : cv<T>(Tm[(int64_t)cc * n0 + r]);
-#pragma unroll
-        for (int rr = 0; rr < RC; ++rr) fma2(acc[rr], m, v[(int64_t)cc * Wr + r0 + rr]);
-      }
-#pragma unroll
-      for (int rr = 0; rr < RC; ++rr) part[(q * n0 + r) * RC + rr] = acc[rr];
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < n0 * RC; e += blockDim.x) {
-      const int r = e / RC, rr = e % RC;
-      C sum = z2<T>();
-      for (int q = 0; q < ngrp; ++q) { sum.x += part[(q * n0 + r) * RC + rr].x; sum.y += part[(q * n0 + r) * RC + rr].y; }
-      if (rr < rc) v[(int64_t)r * Wr + r0 + rr] = sum;
-    }
-    __syncthreads();
+    tri_pass<T, F, RC>(Tm, s, upper, v + r0, Wr, v + r0, Wr, rc, part);
   }
 }
 
@@ -627,10 +661,11 @@ __device__ __forceinline__ void prefetch_records(const SweepArgs& a, const DSeg&
 // run's op records and phase table are copied to shared memory first, so no
 // phase waits on a record load from L2
 template <class T, class F, int RC>
-__device__ void local_run_ring(const SweepArgs& a, const DSeg& sg, char* smem, int64_t lb, int64_t le,
+__device__ bool local_run_ring(const SweepArgs& a, const DSeg& sg, char* smem, int64_t lb, int64_t le,
                                int32_t o_first, int32_t o_last) {
   using C = typename CT<T>::t;
   __shared__ int s_qoff[kLook + 1];   // ring offset of each phase in flight (-1: read from global memory)
+  __shared__ __align__(8) uint64_t s_mbar[kLook + 1];   // completion of each phase slot's bulk copies
   const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
   const int np = sg.count;
   char* ring = smem;
@@ -657,12 +692,18 @@ __device__ void local_run_ring(const SweepArgs& a, const DSeg& sg, char* smem, i
     const int r = e / ncol, c = e % ncol;
     rvec[(int64_t)r * Wr + c] = ldcg2(vecg + (int64_t)(sg.row_lo + r) * a.R + lb + c);
   }
+  if (threadIdx.x == 0) {
+    for (int k = 0; k <= kLook; ++k) mbar_init(&s_mbar[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
+  bool ok = true;
   // ring state (identical in every thread): next phase to issue, allocation
   // head, start of the oldest staged phase in flight, staged phases in flight
   int issued = 0, head = 0, tail = 0, live = 0;
-  for (int ph = 0; ph < np; ++ph) {
+  int ph = 0;
+  for (; ph < np; ++ph) {
     while (issued < np && issued - ph <= kLook) {
       const int pb = spb[issued];
       int off = -1;
@@ -677,16 +718,28 @@ __device__ void local_run_ring(const SweepArgs& a, const DSeg& sg, char* smem, i
           if (head + pb <= tail) off = head;
         }
         if (off < 0) break;   // ring full: issue later
-        ring_issue<F>(a, recs + sbase[issued], sbase[issued + 1] - sbase[issued], ring + off, warp, nw, lane);
+        if (warp == 0)
+          ring_issue<F>(a, recs + sbase[issued], sbase[issued + 1] - sbase[issued], ring + off, (unsigned)pb,
+                        &s_mbar[issued % (kLook + 1)], lane);
         head = off + pb;
         ++live;
+      } else if (threadIdx.x == 0) {
+        mbar_arrive_tx(&s_mbar[issued % (kLook + 1)], 0);   // nothing staged: complete the slot's phase
       }
-      asm volatile("cp.async.commit_group;\n" ::: "memory");
       if (threadIdx.x == 0) s_qoff[issued % (kLook + 1)] = off;
       ++issued;
     }
-    cp_wait_n(issued - ph - 1);
     __syncthreads();
+    {
+      // bounded wait for this phase's copies (parity = how often the slot was used before)
+      uint64_t* mb = &s_mbar[ph % (kLook + 1)];
+      const unsigned par = (unsigned)(ph / (kLook + 1)) & 1u;
+      long long spins = 0;
+      while (!mbar_try_wait(mb, par)) {
+        if (++spins > a.spin_limit) { ok = false; break; }
+      }
+    }
+    if (__syncthreads_or(!ok)) { ok = false; break; }
     const int myoff = s_qoff[ph % (kLook + 1)];
     const FlatOp* ops = recs + sbase[ph];
     const int nops = sbase[ph + 1] - sbase[ph];
@@ -713,11 +766,25 @@ __device__ void local_run_ring(const SweepArgs& a, const DSeg& sg, char* smem, i
       }
     }
   }
+  if (!ok) {
+    // a copy did not complete in time: report, then give the copies in flight
+    // a second bounded wait before the shared memory is left
+    if (threadIdx.x == 0) atomicExch(&a.bar->err, 1);
+    for (int q = ph; q < issued; ++q) {
+      long long spins = 0;
+      while (!mbar_try_wait(&s_mbar[q % (kLook + 1)], (unsigned)(q / (kLook + 1)) & 1u) && ++spins < a.spin_limit) {
+      }
+    }
+  }
   for (int e = threadIdx.x; e < nrow * ncol; e += blockDim.x) {
     const int r = e / ncol, c = e % ncol;
     vecg[(int64_t)(sg.row_lo + r) * a.R + lb + c] = rvec[(int64_t)r * Wr + c];
   }
   __syncthreads();
+  if (threadIdx.x == 0)
+    for (int k = 0; k <= kLook; ++k) mbar_inval(&s_mbar[k]);
+  __syncthreads();
+  return ok;
 }
 
 // run kept in global memory: operands staged per op into warp slices
@@ -791,8 +858,11 @@ __global__ void __launch_bounds__(256, 1) k_sweep_coop(SweepArgs a) {
         o_last = __ldg(a.flat_base + sg.first + sg.count);
         ring = o_last - o_first <= kRunMaxOps;
       }
-      if (ring) local_run_ring<T, F, RC>(a, sg, smem, lb, le, o_first, o_last);
-      else local_run_plain<T, F, RC>(a, sg, smem, slice, lb, le);
+      if (ring) {
+        if (!local_run_ring<T, F, RC>(a, sg, smem, lb, le, o_first, o_last)) return;
+      } else {
+        local_run_plain<T, F, RC>(a, sg, smem, slice, lb, le);
+      }
     }
     // Two consecutive single-CTA runs need no grid barrier: each CTA only
     // reads there the columns it wrote itself.  No barrier after the last segment.
@@ -853,7 +923,7 @@ static int sweep_coop_impl(const DevFactor& df, int which, void* vec, int64_t R,
   a.items = df.items;
   a.fp = df.fpool;
   a.ip = df.ipool;
-  a.tinv = (which == 0 || which == 2) ? df.linv : df.uinv;
+  a.tinv = df.sl[which];
   a.vec = vec;
   a.st = st;
   a.R = R;
@@ -862,8 +932,9 @@ static int sweep_coop_impl(const DevFactor& df, int which, void* vec, int64_t R,
   a.spin_limit = spin_limit;
   // prefetching runs: complex FP32 factors, leaf inverses within one leaf
   // buffer, and leaf partial sums (256 threads x RC columns) within the scratch
-  a.use_pf = (sizeof(F) == 8 && df.n0 <= 64 &&
-              (256 + df.n0) * RC * (int64_t)sizeof(typename CT<T>::t) <= kAuxBytes) ? 1 : 0;
+  // (the sweep-leaf product keeps 2 x 256 partial rows of RC columns)
+  a.use_pf = (sizeof(F) == 8 && df.sl_n <= 256 &&
+              2 * 256 * RC * (int64_t)sizeof(typename CT<T>::t) <= kAuxBytes) ? 1 : 0;
   // reset count and generation; the error flag stays set until hb_status reads it
   if (cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s) != cudaSuccess) return HB_ECUDA;
   void* args[] = {&a};
