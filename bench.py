@@ -358,15 +358,20 @@ def main():
     # dominant kernel: the sweep kernel (two per iteration) vs the apply sequence
     sweep_ms = out["ms_sweep"] / max(out["n_sweep"], 1)
     apply_ms = out["ms_apply"] / max(out["n_apply"], 1)
-    sweep_bytes = 0.5 * (st["lower_bytes"] + st["upper_bytes"])
+    # algorithmic bytes of one launch over the NRHS-column block: every factor and
+    # index entry once, every right-hand side's vector read and written once
+    # (hb_factor_info reports the single-column figure)
+    vec_extra = 2 * st["n"] * (NRHS - 1) * 8
+    sweep_bytes = 0.5 * (st["lower_bytes"] + st["upper_bytes"]) + vec_extra
+    apply_bytes = st["apply_bytes"] + vec_extra
     dominant = "k_sweep" if out["ms_sweep"] >= out["ms_apply"] else "apply (k_apply_*)"
     if dominant == "k_sweep":
         achieved = sweep_bytes / (sweep_ms / 1e3) / 1e9
         algo = sweep_bytes
         avg_ms = sweep_ms
     else:
-        achieved = st["apply_bytes"] / (apply_ms / 1e3) / 1e9
-        algo = st["apply_bytes"]
+        achieved = apply_bytes / (apply_ms / 1e3) / 1e9
+        algo = apply_bytes
         avg_ms = apply_ms
     traffic = None
     prof_path = os.path.join(ROOT, "profiles", "traffic.json")

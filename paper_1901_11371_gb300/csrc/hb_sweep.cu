@@ -393,11 +393,12 @@ __device__ void do_op(const SweepArgs& a, const FlatOp& f, char* buf, int64_t bu
 // barrier, so out may alias b.
 template <class T, class F, int RC>
 __device__ __forceinline__ void tri_pass(const F* Tm, int s, bool upper, const typename CT<T>::t* b, int64_t W,
-                                         typename CT<T>::t* out, int64_t Wo, int rc, typename CT<T>::t* part) {
+                                         typename CT<T>::t* out, int64_t Wo, int rc, typename CT<T>::t* part,
+                                         const Grp& gt) {
   using C = typename CT<T>::t;
   const int npair = s > 1 ? s / 2 : 1;
-  const int ngrp = (int)blockDim.x / npair > 0 ? (int)blockDim.x / npair : 1;
-  for (int e = threadIdx.x; e < ngrp * npair; e += blockDim.x) {
+  const int ngrp = gt.nt / npair > 0 ? gt.nt / npair : 1;
+  for (int e = gt.t; e < ngrp * npair; e += gt.nt) {
     const int j = e % npair, g = e / npair;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -428,14 +429,14 @@ __device__ __forceinline__ void tri_pass(const F* Tm, int s, bool upper, const t
       for (int rr = 0; rr < RC; ++rr) part[(g * s + r) * RC + rr] = acc[rr];
     }
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < s * RC; e += blockDim.x) {
+  gt.sync();
+  for (int e = gt.t; e < s * RC; e += gt.nt) {
     const int r = e / RC, rr = e % RC;
     C sum = z2<T>();
     for (int g = 0; g < ngrp; ++g) { sum.x += part[(g * s + r) * RC + rr].x; sum.y += part[(g * s + r) * RC + rr].y; }
     if (rr < rc) out[(int64_t)r * Wo + rr] = sum;
   }
-  __syncthreads();
+  gt.sync();
 }
 
 // sweep-leaf solve of a run kept in global memory: whole CTA, columns [rb, re)
@@ -449,7 +450,7 @@ __device__ void do_leaf(const SweepArgs& a, const FlatOp& f, char* buf, int64_t 
   C* v = (C*)a.vec + (int64_t)f.src0 * R;
   const bool upper = (f.flags & FF_UPPER) != 0;
   const int npair = s > 1 ? s / 2 : 1;
-  const int ngrp = (int)blockDim.x / npair > 0 ? (int)blockDim.x / npair : 1;
+  const int ngrp = g.nt / npair > 0 ? g.nt / npair : 1;
   const int64_t mb = align16((int64_t)f.melems * (int64_t)sizeof(F));
   const int64_t partb = align16((int64_t)ngrp * s * RC * (int64_t)sizeof(C));
   const int64_t vb = (int64_t)s * RC * (int64_t)sizeof(C);
@@ -467,7 +468,7 @@ __device__ void do_leaf(const SweepArgs& a, const FlatOp& f, char* buf, int64_t 
     stage_vec<C>(bb, v, s, R, r0, rc, RC, g, true);
     cp_commit_wait();
     __syncthreads();
-    tri_pass<T, F, RC>(Tm, s, upper, bb, RC, v + r0, R, rc, part);
+    tri_pass<T, F, RC>(Tm, s, upper, bb, RC, v + r0, R, rc, part, g);
   }
 }
 
@@ -518,6 +519,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
   asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
                : "=r"(ok) : "r"(smem_u32(b)), "r"(parity) : "memory");
   return ok != 0;
+}
+// OR of v over the nt threads of named barrier id (also a barrier among them)
+__device__ __forceinline__ bool bar_red_or(bool v, int id, int nt) {
+  unsigned r;
+  asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+               : "=r"(r) : "r"((unsigned)v), "r"(id), "r"(nt) : "memory");
+  return r != 0;
 }
 // bulk copy of `bytes` (multiple of 16; both addresses 16-byte aligned), completion on mbarrier b
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* b) {
@@ -630,7 +638,7 @@ __device__ void do_op_res(const SweepArgs& a, const FlatOp& f, const char* half,
 // sweep-leaf solve of a resident run: rows in shared memory, triangle staged (or global)
 template <class T, class F, int RC>
 __device__ void do_leaf_res(const SweepArgs& a, const FlatOp& f, const F* Tm, typename CT<T>::t* rvec, int row_lo,
-                            int Wr, int ncol, typename CT<T>::t* part) {
+                            int Wr, int ncol, typename CT<T>::t* part, const Grp& gt) {
   using C = typename CT<T>::t;
   const int s = f.c0;
   const bool upper = (f.flags & FF_UPPER) != 0;
@@ -638,7 +646,7 @@ __device__ void do_leaf_res(const SweepArgs& a, const FlatOp& f, const F* Tm, ty
   // the pass reads all of b before any row is written (a barrier separates them)
   for (int r0 = 0; r0 < ncol; r0 += RC) {
     const int rc = (ncol - r0) < RC ? (ncol - r0) : RC;
-    tri_pass<T, F, RC>(Tm, s, upper, v + r0, Wr, v + r0, Wr, rc, part);
+    tri_pass<T, F, RC>(Tm, s, upper, v + r0, Wr, v + r0, Wr, rc, part, gt);
   }
 }
 
@@ -666,6 +674,9 @@ __device__ bool local_run_ring(const SweepArgs& a, const DSeg& sg, char* smem, i
   using C = typename CT<T>::t;
   __shared__ int s_qoff[kLook + 1];   // ring offset of each phase in flight (-1: read from global memory)
   __shared__ __align__(8) uint64_t s_mbar[kLook + 1];   // completion of each phase slot's bulk copies
+  __shared__ int s_done;    // phases finished by the compute warps
+  __shared__ int s_abort;   // a bounded wait gave up
+  __shared__ int s_issued;  // phases the producer issued
   const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
   const int np = sg.count;
   char* ring = smem;
@@ -698,18 +709,32 @@ __device__ bool local_run_ring(const SweepArgs& a, const DSeg& sg, char* smem, i
   }
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
+  if (threadIdx.x == 0) { s_done = 0; s_abort = 0; s_issued = 0; }
+  __syncthreads();
   bool ok = true;
-  // ring state (identical in every thread): next phase to issue, allocation
-  // head, start of the oldest staged phase in flight, staged phases in flight
-  int issued = 0, head = 0, tail = 0, live = 0;
-  int ph = 0;
-  for (; ph < np; ++ph) {
-    while (issued < np && issued - ph <= kLook) {
-      const int pb = spb[issued];
+  const int cw = nw - 1;                 // compute warps; the last warp is the producer
+  if (warp == cw) {
+    // ---- producer: stage phases ahead of the compute warps.  Ring state:
+    // next phase to issue, allocation head; phases [done, issued) are in
+    // flight (their ring areas in use).
+    int issued = 0, head = 0;
+    long long spins = 0;
+    while (issued < np) {
+      const int done = *(volatile int*)&s_done;
+      __threadfence_block();   // pairs with the compute warps' fence before they publish s_done
+      if (*(volatile int*)&s_abort) break;
+      bool go = issued - done <= kLook;
       int off = -1;
-      if (pb > 0 && pb <= kRingBytes) {
-        if (live == 0) {
-          head = tail = 0;
+      const int pb = spb[issued];
+      if (go && pb > 0 && pb <= kRingBytes) {
+        // oldest staged phase still in use
+        int tail = -1;
+        for (int q = done; q < issued; ++q) {
+          const int o2 = s_qoff[q % (kLook + 1)];
+          if (o2 >= 0) { tail = o2; break; }
+        }
+        if (tail < 0) {
+          head = 0;
           off = 0;
         } else if (head > tail) {
           if (head + pb <= kRingBytes) off = head;
@@ -717,60 +742,73 @@ __device__ bool local_run_ring(const SweepArgs& a, const DSeg& sg, char* smem, i
         } else if (head < tail) {
           if (head + pb <= tail) off = head;
         }
-        if (off < 0) break;   // ring full: issue later
-        if (warp == 0)
-          ring_issue<F>(a, recs + sbase[issued], sbase[issued + 1] - sbase[issued], ring + off, (unsigned)pb,
-                        &s_mbar[issued % (kLook + 1)], lane);
-        head = off + pb;
-        ++live;
-      } else if (threadIdx.x == 0) {
-        mbar_arrive_tx(&s_mbar[issued % (kLook + 1)], 0);   // nothing staged: complete the slot's phase
+        go = off >= 0;
       }
-      if (threadIdx.x == 0) s_qoff[issued % (kLook + 1)] = off;
+      if (!go) {   // wait for the compute warps to release a phase (bounded)
+        if (++spins > a.spin_limit) { if (lane == 0) atomicExch(&s_abort, 1); break; }
+        __nanosleep(32);
+        continue;
+      }
+      spins = 0;
+      uint64_t* mb = &s_mbar[issued % (kLook + 1)];
+      if (lane == 0) s_qoff[issued % (kLook + 1)] = off;   // published by the barrier arrive below
+      __syncwarp();
+      if (off >= 0) {
+        ring_issue<F>(a, recs + sbase[issued], sbase[issued + 1] - sbase[issued], ring + off, (unsigned)pb, mb, lane);
+        head = off + pb;
+      } else if (lane == 0) {
+        mbar_arrive_tx(mb, 0);   // nothing staged: complete the slot's phase
+      }
       ++issued;
     }
-    __syncthreads();
-    {
-      // bounded wait for this phase's copies (parity = how often the slot was used before)
+    if (lane == 0) s_issued = issued;
+    __syncwarp();
+  } else {
+    // ---- compute warps (named barrier 1 among them)
+    const Grp gc{(int)threadIdx.x, cw * 32, false, 1};
+    int ph = 0;
+    for (; ph < np; ++ph) {
       uint64_t* mb = &s_mbar[ph % (kLook + 1)];
       const unsigned par = (unsigned)(ph / (kLook + 1)) & 1u;
       long long spins = 0;
       while (!mbar_try_wait(mb, par)) {
-        if (++spins > a.spin_limit) { ok = false; break; }
+        if (++spins > a.spin_limit || *(volatile int*)&s_abort) { ok = false; break; }
       }
-    }
-    if (__syncthreads_or(!ok)) { ok = false; break; }
-    const int myoff = s_qoff[ph % (kLook + 1)];
-    const FlatOp* ops = recs + sbase[ph];
-    const int nops = sbase[ph + 1] - sbase[ph];
-    if (ops[0].kind == FK_LEAF) {
-      const F* Tm = myoff >= 0 ? (const F*)(ring + myoff) : (const F*)a.tinv + ops[0].moff;
-      do_leaf_res<T, F, RC>(a, ops[0], Tm, rvec, sg.row_lo, Wr, ncol, part);
-    } else {
-      const Grp g{lane, 32, false};
-      for (int o = warp; o < nops; o += nw) {
-        const FlatOp& f = ops[o];
-        do_op_res<T, F, RC>(a, f, ring + (myoff >= 0 ? myoff : 0) + f.soff, myoff >= 0, rvec, sg.row_lo, rst,
-                            sg.st_lo, Wr, ncol, g);
+      // uniform decision among the compute warps (the OR-reduction is their barrier)
+      if (bar_red_or(!ok, gc.bar, gc.nt)) {
+        ok = false;
+        if (threadIdx.x == 0) atomicExch(&s_abort, 1);
+        break;
       }
-    }
-    __syncthreads();
-    if (myoff >= 0) {   // release the phase's ring area
-      if (--live == 0) {
-        head = tail = 0;
+      const int myoff = s_qoff[ph % (kLook + 1)];
+      const FlatOp* ops = recs + sbase[ph];
+      const int nops = sbase[ph + 1] - sbase[ph];
+      if (ops[0].kind == FK_LEAF) {
+        const F* Tm = myoff >= 0 ? (const F*)(ring + myoff) : (const F*)a.tinv + ops[0].moff;
+        do_leaf_res<T, F, RC>(a, ops[0], Tm, rvec, sg.row_lo, Wr, ncol, part, gc);
       } else {
-        for (int q = ph + 1; q < issued; ++q) {
-          const int o2 = s_qoff[q % (kLook + 1)];
-          if (o2 >= 0) { tail = o2; break; }
+        const Grp g{lane, 32, false};
+        for (int o = warp; o < nops; o += cw) {
+          const FlatOp& f = ops[o];
+          do_op_res<T, F, RC>(a, f, ring + (myoff >= 0 ? myoff : 0) + f.soff, myoff >= 0, rvec, sg.row_lo, rst,
+                              sg.st_lo, Wr, ncol, g);
         }
+      }
+      gc.sync();
+      if (threadIdx.x == 0) {
+        __threadfence_block();
+        *(volatile int*)&s_done = ph + 1;   // releases the phase's slot and ring area
       }
     }
   }
+  __syncthreads();
+  ok = *(volatile int*)&s_abort == 0;
   if (!ok) {
-    // a copy did not complete in time: report, then give the copies in flight
-    // a second bounded wait before the shared memory is left
+    // a wait gave up: report, then give the copies in flight a second bounded
+    // wait before the shared memory is left
     if (threadIdx.x == 0) atomicExch(&a.bar->err, 1);
-    for (int q = ph; q < issued; ++q) {
+    const int done = s_done, iss = s_issued;
+    for (int q = done; q < iss; ++q) {
       long long spins = 0;
       while (!mbar_try_wait(&s_mbar[q % (kLook + 1)], (unsigned)(q / (kLook + 1)) & 1u) && ++spins < a.spin_limit) {
       }
@@ -828,24 +866,40 @@ __global__ void __launch_bounds__(256, 1) k_sweep_coop(SweepArgs a) {
         const int gw = blockIdx.x * nw + warp, tw = gridDim.x * nw;
         for (int o = gw; o < P.count; o += tw) do_op<T, F, RC>(a, ops[o], smem + warp * slice, slice, g, 0, a.R);
       } else {
-        // one (op, RHS range) unit per CTA at a time: a phase with fewer ops
-        // than CTAs splits its right-hand sides into ranges of >= 16 columns
-        const Grp g{(int)threadIdx.x, (int)blockDim.x, true};
-        int64_t nu = 1, wg = a.R;
-        if (P.count < (int)gridDim.x && a.R >= 32) {
-          nu = gridDim.x / P.count;
+        // (op, column range) units over the workers: with many right-hand
+        // sides each CTA runs kGroups groups of two warps (named barriers,
+        // own shared-memory slice), so several units' staging latencies
+        // overlap; a unit's columns are cut so that its staged operands fit
+        // the slice, and a phase with fewer ops than workers splits its
+        // right-hand sides further (ranges of >= 16 columns)
+        constexpr int kGroups = 4;
+        const int G = a.R >= 32 ? kGroups : 1;
+        const int gsz = (int)blockDim.x / G, gi = (int)threadIdx.x / gsz;
+        const Grp g{(int)threadIdx.x % gsz, gsz, G == 1, G == 1 ? 0 : 1 + gi};
+        const int64_t gslice = ((int64_t)a.smem_bytes / G) & ~(int64_t)15;
+        const int64_t workers = (int64_t)gridDim.x * G;
+        const int64_t mbf = (int64_t)P.mbytes / (16 / (int)sizeof(F)) + 64;
+        const int64_t colb = (int64_t)(P.vmax > 0 ? P.vmax : 1) * (int64_t)sizeof(typename CT<T>::t);
+        int64_t wfit = (gslice - mbf) / colb;
+        wfit = wfit < RC ? RC : wfit / RC * RC;
+        int64_t nu = (a.R + wfit - 1) / wfit;
+        if ((int64_t)P.count * nu < workers && a.R >= 32) {
+          int64_t want = (workers + P.count - 1) / P.count;
           const int64_t maxu = a.R / 16;
-          if (nu > maxu) nu = maxu;
-          wg = ((a.R + nu - 1) / nu + RC - 1) / RC * RC;
-          nu = (a.R + wg - 1) / wg;
+          if (want > maxu) want = maxu;
+          if (want > nu) nu = want;
         }
+        int64_t wg = ((a.R + nu - 1) / nu + RC - 1) / RC * RC;
+        nu = (a.R + wg - 1) / wg;
         const int64_t units = (int64_t)P.count * nu;
-        for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        char* gbuf = smem + gi * gslice;
+        for (int64_t u = (int64_t)blockIdx.x * G + gi; u < units; u += workers) {
           const int o = (int)(u / nu);
           const int64_t rb = (u % nu) * wg;
           const int64_t re = (rb + wg < a.R) ? rb + wg : a.R;
-          do_op<T, F, RC>(a, ops[o], smem, a.smem_bytes, g, rb, re);
+          do_op<T, F, RC>(a, ops[o], gbuf, gslice, g, rb, re);
         }
+        if (G > 1) __syncthreads();
       }
     } else if (lb < le) {
       const int64_t ncol = le - lb, Wr = (ncol + RC - 1) / RC * RC;
