@@ -215,6 +215,7 @@ def run_gpu(args, rank, world):
     ms_max = float(t.item())
     value = world * args.steps * NRHS / (ms_max / 1e3)
     iters = int(np.mean([i["iters"] for i in infos]))
+    ir_steps = int(np.mean([i["ir_steps"] for i in infos]))
     res = max(i["true_rel_res"] for i in infos)
 
     # ---- end-to-end through the public API with host buffers (pinned), copies inside the region
@@ -234,7 +235,7 @@ def run_gpu(args, rank, world):
            "d2h_bytes_per_step": int(x.numel() * 16 + NRHS * 16)}
 
     mono_np = mono.cpu().numpy()
-    out = dict(value=value, ms=ms_max, iters=iters, res=res, st=st, t_build=t_build, clocks=clk, e2e=e2e, tuned=tuned, tune_ms=tune_ms,
+    out = dict(value=value, ms=ms_max, iters=iters, ir_steps=ir_steps, res=res, st=st, t_build=t_build, clocks=clk, e2e=e2e, tuned=tuned, tune_ms=tune_ms,
                mono_db=[float(v) for v in 20 * np.log10(np.abs(mono_np[::32]) + 1e-300)],
                n_apply=n_apply, ms_apply=ms_apply, n_sweep=n_sweep, ms_sweep=ms_sweep, n_launch=n_launch,
                x=x)
@@ -391,7 +392,7 @@ def main():
                    "sweep_autotune_ms": {str(k): round(v, 3) for k, v in out["tune_ms"].items()},
                    "l2": f"inputs larger than L2: factor {st['device_bytes'] / 1e6:.0f} MB",
                    "kmax": st["kmax"], "kavg": round(st["kavg"], 2), "build_s": round(out["t_build"], 2)},
-        "iters_per_solve": out["iters"], "true_rel_res": out["res"],
+        "iters_per_solve": out["iters"], "ir_steps_per_solve": out["ir_steps"], "true_rel_res": out["res"],
         "monostatic_dB_every_32nd_angle": out["mono_db"],
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "algorithmic_bytes_per_launch": algo,

@@ -31,11 +31,15 @@ static constexpr int kRedBlocks = 304;   // 2 x 152 SMs
 static constexpr int kRedThreads = 256;
 
 // partial[v][blk][r] = sum over this block's rows of conj(V_v[row][r]) * w[row][r]
-__global__ void k_dots_partial(const double2* __restrict__ V, int64_t vstride, int nvec,
-                               const double2* __restrict__ w, int64_t n, int64_t R, double2* __restrict__ partial) {
+// (VT = double2: FP64 arithmetic; VT = float2: FP32 products and per-thread
+// sums, FP64 from the block reduction on)
+template <class VT>
+__global__ void k_dots_partial(const VT* __restrict__ V, int64_t vstride, int nvec,
+                               const VT* __restrict__ w, int64_t n, int64_t R, double2* __restrict__ partial) {
+  using S = decltype(VT::x);
   __shared__ double2 red[kRedThreads];
   const int v = blockIdx.y;
-  const double2* Vv = V + (int64_t)v * vstride;
+  const VT* Vv = V + (int64_t)v * vstride;
   const int64_t rows_per = (n + gridDim.x - 1) / gridDim.x;
   const int64_t row0 = (int64_t)blockIdx.x * rows_per, row1 = min(n, row0 + rows_per);
   const int G = (R >= kRedThreads) ? 1 : kRedThreads / (int)R;   // row groups
@@ -43,15 +47,15 @@ __global__ void k_dots_partial(const double2* __restrict__ V, int64_t vstride, i
     const int t = threadIdx.x;
     int64_t r = (R >= kRedThreads) ? rbase + t : t % R;
     int g = (R >= kRedThreads) ? 0 : t / (int)R;
-    double2 acc = {0.0, 0.0};
+    S ax = 0, ay = 0;
     if (g < G && r < R) {
       for (int64_t row = row0 + g; row < row1; row += G) {
-        double2 a = Vv[row * R + r], b = w[row * R + r];
-        acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
-        acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
+        VT a = Vv[row * R + r], b = w[row * R + r];
+        ax = fma(a.x, b.x, fma(a.y, b.y, ax));
+        ay = fma(a.x, b.y, fma(-a.y, b.x, ay));
       }
     }
-    red[t] = acc;
+    red[t] = double2{(double)ax, (double)ay};
     __syncthreads();
     if (R >= kRedThreads) {
       if (r < R) partial[((int64_t)v * gridDim.x + blockIdx.x) * R + r] = red[t];
@@ -80,29 +84,35 @@ __global__ void k_dots_final(const double2* __restrict__ partial, int nblk, int 
   out[e] = s;
 }
 
-// w[row][r] -= sum_v V_v[row][r] h[v][r]
-__global__ void k_sub_combo(const double2* __restrict__ V, int64_t vstride, int nvec, const double2* __restrict__ h,
-                            double2* __restrict__ w, int64_t n, int64_t R, double sign) {
+// w[row][r] -= sum_v V_v[row][r] h[v][r]   (arithmetic in the precision of VT)
+template <class VT>
+__global__ void k_sub_combo(const VT* __restrict__ V, int64_t vstride, int nvec, const double2* __restrict__ h,
+                            VT* __restrict__ w, int64_t n, int64_t R, double sign) {
+  using S = decltype(VT::x);
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (; e < n * R; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t r = e % R;
-    double2 acc = w[e];
+    VT acc = w[e];
     for (int v = 0; v < nvec; ++v) {
-      double2 a = V[(int64_t)v * vstride + e], c = h[(int64_t)v * R + r];
-      acc.x -= sign * (a.x * c.x - a.y * c.y);
-      acc.y -= sign * (a.x * c.y + a.y * c.x);
+      VT a = V[(int64_t)v * vstride + e];
+      double2 cd = h[(int64_t)v * R + r];
+      S cx = (S)(sign * cd.x), cy = (S)(sign * cd.y);
+      acc.x -= a.x * cx - a.y * cy;
+      acc.y -= a.x * cy + a.y * cx;
     }
     w[e] = acc;
   }
 }
 
-// dst[row][r] = src[row][r] * s[r]  (s real)
-__global__ void k_scale_cols(const double2* __restrict__ src, const double* __restrict__ s, double2* dst, int64_t n,
+// dst[row][r] = src[row][r] * s[r]  (s real; src / dst double2 or float2)
+template <class SRC, class DST>
+__global__ void k_scale_cols(const SRC* __restrict__ src, const double* __restrict__ s, DST* dst, int64_t n,
                              int64_t R) {
+  using S = decltype(DST::x);
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (; e < n * R; e += (int64_t)gridDim.x * blockDim.x) {
     double f = s[e % R];
-    dst[e] = {src[e].x * f, src[e].y * f};
+    dst[e] = {(S)(src[e].x * f), (S)(src[e].y * f)};
   }
 }
 
@@ -131,6 +141,15 @@ __global__ void k_add_combo(const S* __restrict__ Z, int64_t zstride, int nvec, 
       acc.y += (double)a.x * cc.y + (double)a.y * cc.x;
     }
     y[e] = acc;
+  }
+}
+
+// r[e] -= a[e]  (a complex FP32, r FP64)
+__global__ void k_sub_f32(const float2* __restrict__ a, double2* __restrict__ r, int64_t total) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    r[e].x -= (double)a[e].x;
+    r[e].y -= (double)a[e].y;
   }
 }
 
@@ -264,9 +283,10 @@ struct Dev {
 };
 
 // h[v][r] = <V_v, w>_r for v < nvec (host copy returned in hh[v*R + r])
-static int dots(Dev& d, const double2* V, int64_t vstride, int nvec, const double2* w, std::vector<zc>& hh) {
+template <class VT>
+static int dots(Dev& d, const VT* V, int64_t vstride, int nvec, const VT* w, std::vector<zc>& hh) {
   dim3 grid(kRedBlocks, nvec);
-  k_dots_partial<<<grid, kRedThreads, 0, d.st>>>(V, vstride, nvec, w, d.n, d.R, d.red_partial); count_launch(d.f, 1);
+  k_dots_partial<VT><<<grid, kRedThreads, 0, d.st>>>(V, vstride, nvec, w, d.n, d.R, d.red_partial); count_launch(d.f, 1);
   int64_t tot = (int64_t)nvec * d.R;
   k_dots_final<<<(unsigned)((tot + 255) / 256), 256, 0, d.st>>>(d.red_partial, kRedBlocks, nvec, d.R, d.red_out); count_launch(d.f, 1);
   hh.resize(tot);
@@ -277,7 +297,8 @@ static int dots(Dev& d, const double2* V, int64_t vstride, int nvec, const doubl
 }
 
 // CGS2: orthogonalise w against V_0..V_{nvec-1}; returns h (nvec x R) and ||w|| (R).
-static int cgs2(Dev& d, const double2* V, int64_t vstride, int nvec, double2* w, std::vector<zc>& h,
+template <class VT>
+static int cgs2(Dev& d, const VT* V, int64_t vstride, int nvec, VT* w, std::vector<zc>& h,
                 std::vector<double>& nrm) {
   std::vector<zc> h1, h2;
   int rc;
@@ -288,7 +309,7 @@ static int cgs2(Dev& d, const double2* V, int64_t vstride, int nvec, double2* w,
     for (size_t i = 0; i < h.size(); ++i) h[i] += hp[i];
     if (cudaMemcpyAsync(d.red_out, hp.data(), hp.size() * sizeof(double2), cudaMemcpyHostToDevice, d.st) != cudaSuccess)
       return HB_ECUDA;
-    k_sub_combo<<<gsz(d.n * d.R), 256, 0, d.st>>>(V, vstride, nvec, d.red_out, w, d.n, d.R, 1.0); count_launch(d.f, 1);
+    k_sub_combo<VT><<<gsz(d.n * d.R), 256, 0, d.st>>>(V, vstride, nvec, d.red_out, w, d.n, d.R, 1.0); count_launch(d.f, 1);
   }
   std::vector<zc> nn;
   if ((rc = dots(d, w, 0, 1, w, nn))) return rc;
@@ -297,7 +318,8 @@ static int cgs2(Dev& d, const double2* V, int64_t vstride, int nvec, double2* w,
   return HB_OK;
 }
 
-static int norms(Dev& d, const double2* w, std::vector<double>& nrm) {
+template <class VT>
+static int norms(Dev& d, const VT* w, std::vector<double>& nrm) {
   std::vector<zc> nn;
   int rc = dots(d, w, 0, 1, w, nn);
   if (rc) return rc;
@@ -307,11 +329,12 @@ static int norms(Dev& d, const double2* w, std::vector<double>& nrm) {
 }
 
 // dst = src / nrm (per column; zero-norm columns copied unchanged)
-static void normalise(Dev& d, const double2* src, const std::vector<double>& nrm, double2* dst) {
+template <class SRC, class DST>
+static void normalise(Dev& d, const SRC* src, const std::vector<double>& nrm, DST* dst) {
   std::vector<double> inv(d.R);
   for (int64_t r = 0; r < d.R; ++r) inv[r] = nrm[r] > 0 ? 1.0 / nrm[r] : 1.0;
   cudaMemcpyAsync(d.scal, inv.data(), d.R * sizeof(double), cudaMemcpyHostToDevice, d.st);
-  k_scale_cols<<<gsz(d.n * d.R), 256, 0, d.st>>>(src, d.scal, dst, d.n, d.R); count_launch(d.f, 1);
+  k_scale_cols<SRC, DST><<<gsz(d.n * d.R), 256, 0, d.st>>>(src, d.scal, dst, d.n, d.R); count_launch(d.f, 1);
 }
 
 // Per-RHS Givens state of one restart cycle.
@@ -377,11 +400,16 @@ extern "C" int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int6
   Workspace& ws = f->ws;
   double2* bh = (double2*)ws.get(WS_VEC2, vbytes);            // scaled b (internal layout)
   double2* xv = (double2*)ws.get(WS_VEC3, vbytes);            // x (split form: y) iterate
-  double2* V = (double2*)ws.get(WS_BASIS, vbytes * (m + 1));  // Krylov basis
+  // Krylov basis: FP64 for HB_C128; complex FP32 for the FP32 forms (the inner
+  // FGMRES of the refinement loop; the residual between steps stays FP64)
+  const size_t vbytes_basis = mixed ? (size_t)n * R * sizeof(float2) : vbytes;
+  void* Vb = ws.get(WS_BASIS, vbytes_basis * (m + 1));
+  double2* V = (double2*)Vb;
+  float2* V32 = (float2*)Vb;
   double2* red = (double2*)ws.get(WS_RED, (size_t)kRedBlocks * (m + 2) * R * sizeof(double2) + (size_t)(m + 2) * R * sizeof(double2) + R * sizeof(double));
   void* zb = mixed ? ws.get(WS_ZBASIS, (size_t)n * R * sizeof(float2) * (m + 1)) : nullptr;   // FGMRES Z (float2) + f32 scratch
   int* flag = (int*)ws.get(WS_SMALL, 256);
-  if (!bh || !xv || !V || !red || !flag || (mixed && !zb)) { set_error("hb_gmres: workspace allocation failed"); return HB_ENOMEM; }
+  if (!bh || !xv || !Vb || !red || !flag || (mixed && !zb)) { set_error("hb_gmres: workspace allocation failed"); return HB_ENOMEM; }
   double2* tmp = (double2*)ws.get(WS_VEC0, vbytes);
   double2* tmp2 = (double2*)ws.get(WS_VEC1, vbytes);
   if (!tmp || !tmp2) { set_error("hb_gmres: workspace allocation failed"); return HB_ENOMEM; }
@@ -429,7 +457,9 @@ extern "C" int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int6
 
   // split form: x = U'^{-1} y ; preconditioned residual L'^{-1} r
   double2* r = tmp;   // residual / work vector
-  if ((rc = true_residual(xv, r))) return rc;   // x = 0: r = b^
+  // x = 0: r = b^ (no operator application needed)
+  cudaMemcpyAsync(r, bh, vbytes, cudaMemcpyDeviceToDevice, st);
+  for (int64_t c = 0; c < R; ++c) res_r[c] = bnorm[c] > 0 ? 1.0 : 0.0;
   while (iters < maxit) {
     nconv = 0;
     for (int64_t c = 0; c < R; ++c) { done[c] = res_r[c] <= rtol; nconv += done[c]; }
@@ -440,7 +470,8 @@ extern "C" int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int6
       if ((rc = sweep_internal(f, PREC_F64, lo, r, R, st))) return rc;   // r <- L'^{-1} r
     }
     if ((rc = norms(d, r, beta))) return rc;
-    normalise(d, r, beta, V);
+    if (mixed) normalise(d, r, beta, V32);
+    else normalise(d, r, beta, V);
     std::vector<double> target(R);
     for (int64_t c = 0; c < R; ++c) {
       gv[c].reset(m, beta[c]);
@@ -453,8 +484,8 @@ extern "C" int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int6
     }
     int j = 0;
     for (; j < m && iters < maxit; ++j) {
-      double2* vj = V + (size_t)j * n * R;
-      double2* w = V + (size_t)(j + 1) * n * R;
+      double2* vj = mixed ? nullptr : V + (size_t)j * n * R;
+      double2* w = mixed ? nullptr : V + (size_t)(j + 1) * n * R;
       if (!mixed) {
         // w = L'^{-1} A U'^{-1} v_j
         cudaMemcpyAsync(w, vj, vbytes, cudaMemcpyDeviceToDevice, st);
@@ -463,16 +494,22 @@ extern "C" int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int6
         cudaMemcpyAsync(w, tmp2, vbytes, cudaMemcpyDeviceToDevice, st);
         if ((rc = sweep_internal(f, PREC_F64, lo, w, R, st))) return rc;
       } else {
-        // z_j = M^{-1} v_j (FP32), w = A z_j (FP32), promoted to FP64
+        // z_j = M^{-1} v_j, w = A z_j, all in complex FP32
         float2* zj = zf + (size_t)j * n * R;
-        k_to_f32<<<gsz(n * R), 256, 0, st>>>(vj, zj, n * R); count_launch(f, 1);
+        float2* w32 = V32 + (size_t)(j + 1) * n * R;
+        cudaMemcpyAsync(zj, V32 + (size_t)j * n * R, (size_t)n * R * sizeof(float2), cudaMemcpyDeviceToDevice, st);
         if ((rc = sweep_internal(f, PREC_F32, lo, zj, R, st))) return rc;
         if ((rc = sweep_internal(f, PREC_F32, up, zj, R, st))) return rc;
-        if ((rc = apply_internal(f, PREC_F32, adj, zj, f32s, R, st))) return rc;
-        k_to_f64<<<gsz(n * R), 256, 0, st>>>(f32s, w, n * R); count_launch(f, 1);
+        if ((rc = apply_internal(f, PREC_F32, adj, zj, w32, R, st))) return rc;
       }
-      if ((rc = cgs2(d, V, (int64_t)n * R, j + 1, w, h, hn))) return rc;
-      normalise(d, w, hn, w);
+      if (mixed) {
+        float2* w32 = V32 + (size_t)(j + 1) * n * R;
+        if ((rc = cgs2(d, V32, (int64_t)n * R, j + 1, w32, h, hn))) return rc;
+        normalise(d, w32, hn, w32);
+      } else {
+        if ((rc = cgs2(d, V, (int64_t)n * R, j + 1, w, h, hn))) return rc;
+        normalise(d, w, hn, w);
+      }
       ++iters;
       int active = 0;
       for (int64_t c = 0; c < R; ++c) {
