@@ -150,6 +150,24 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
+def shard_angles(rank, world):
+    """Incidence angles (deg) of this rank's block: every rank solves NRHS plane waves,
+    rank r's angles offset by r * 180 / (NRHS * world) so that the ranks' sets interleave
+    without overlap (replicas of the factor, right-hand sides sharded; no collective on the
+    data path)."""
+    base = W.incidence_angles_deg(3)
+    return base + (rank * 180.0 / NRHS / world if world > 1 else 0.0)
+
+
+def max_over_ranks(ms, world, device):
+    """Largest timed-region length over the ranks (the job's time)."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_gpu(args, rank, world):
     import torch
 
@@ -171,7 +189,7 @@ def run_gpu(args, rank, world):
     st = hb.hb_factor_info(f32)
     tuned = hb.hb_autotune(f32, NRHS)
     tune_ms = hb.hb_autotune_times(f32, NRHS)
-    phis = W.incidence_angles_deg(3) + (rank * 180.0 / NRHS / max(world, 1) if world > 1 else 0.0)
+    phis = shard_angles(rank, world)
     b = hb.hb_rhs_plane_wave(f32, phis)
     x = torch.empty_like(b)
 
@@ -209,10 +227,7 @@ def run_gpu(args, rank, world):
     n_apply, ms_apply = hb.hb_profile_read(f32, 0)
     n_sweep, ms_sweep = hb.hb_profile_read(f32, 1)
     n_launch, _ = hb.hb_profile_read(f32, 2)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, "cuda")
     value = world * args.steps * NRHS / (ms_max / 1e3)
     iters = int(np.mean([i["iters"] for i in infos]))
     ir_steps = int(np.mean([i["ir_steps"] for i in infos]))

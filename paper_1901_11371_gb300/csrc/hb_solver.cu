@@ -87,21 +87,18 @@ __global__ void k_dots_final(const double2* __restrict__ partial, int nblk, int 
   out[e] = s;
 }
 
-// w[row][r] -= sum_v V_v[row][r] h[v][r]   (arithmetic in the precision of VT)
+// w[row][r] -= sum_v V_v[row][r] h[v][r]   (h and the arithmetic in the precision of VT)
 template <class VT>
-__global__ void k_sub_combo(const VT* __restrict__ V, int64_t vstride, int nvec, const double2* __restrict__ h,
-                            VT* __restrict__ w, int64_t n, int64_t R, double sign) {
-  using S = decltype(VT::x);
+__global__ void k_sub_combo(const VT* __restrict__ V, int64_t vstride, int nvec, const VT* __restrict__ h,
+                            VT* __restrict__ w, int64_t n, int64_t R) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (; e < n * R; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t r = e % R;
     VT acc = w[e];
     for (int v = 0; v < nvec; ++v) {
-      VT a = V[(int64_t)v * vstride + e];
-      double2 cd = h[(int64_t)v * R + r];
-      S cx = (S)(sign * cd.x), cy = (S)(sign * cd.y);
-      acc.x -= a.x * cx - a.y * cy;
-      acc.y -= a.x * cy + a.y * cx;
+      const VT a = V[(int64_t)v * vstride + e], c = h[(int64_t)v * R + r];
+      acc.x -= a.x * c.x - a.y * c.y;
+      acc.y -= a.x * c.y + a.y * c.x;
     }
     w[e] = acc;
   }
@@ -112,10 +109,17 @@ template <class SRC, class DST>
 __global__ void k_scale_cols(const SRC* __restrict__ src, const double* __restrict__ s, DST* dst, int64_t n,
                              int64_t R) {
   using S = decltype(DST::x);
+  using SS = decltype(SRC::x);
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (; e < n * R; e += (int64_t)gridDim.x * blockDim.x) {
-    double f = s[e % R];
-    dst[e] = {(S)(src[e].x * f), (S)(src[e].y * f)};
+    // in the narrower of the two precisions (FP32 vectors stay off the FP64 pipe)
+    if (sizeof(S) < sizeof(SS)) {
+      const S f = (S)s[e % R];
+      dst[e] = {(S)src[e].x * f, (S)src[e].y * f};
+    } else {
+      const SS f = (SS)s[e % R];
+      dst[e] = {(S)(src[e].x * f), (S)(src[e].y * f)};
+    }
   }
 }
 
@@ -129,21 +133,22 @@ __global__ void k_axpy1(const S* __restrict__ x, double2* __restrict__ y, int64_
   }
 }
 
-// y[row][r] += sum_v Z_v[row][r] c[v][r]  (Z double2 or float2)
+// y[row][r] += sum_v Z_v[row][r] c[v][r]  (Z and c double2, or both float2: the
+// combination is then formed in FP32 and added to the FP64 y once)
 template <class S>
-__global__ void k_add_combo(const S* __restrict__ Z, int64_t zstride, int nvec, const double2* __restrict__ c,
+__global__ void k_add_combo(const S* __restrict__ Z, int64_t zstride, int nvec, const S* __restrict__ c,
                             double2* __restrict__ y, int64_t n, int64_t R) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (; e < n * R; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t r = e % R;
-    double2 acc = y[e];
+    S acc = {0, 0};
     for (int v = 0; v < nvec; ++v) {
-      S a = Z[(int64_t)v * zstride + e];
-      double2 cc = c[(int64_t)v * R + r];
-      acc.x += (double)a.x * cc.x - (double)a.y * cc.y;
-      acc.y += (double)a.x * cc.y + (double)a.y * cc.x;
+      const S a = Z[(int64_t)v * zstride + e], cc = c[(int64_t)v * R + r];
+      acc.x += a.x * cc.x - a.y * cc.y;
+      acc.y += a.x * cc.y + a.y * cc.x;
     }
-    y[e] = acc;
+    y[e].x += (double)acc.x;
+    y[e].y += (double)acc.y;
   }
 }
 
@@ -310,9 +315,13 @@ static int cgs2(Dev& d, const VT* V, int64_t vstride, int nvec, VT* w, std::vect
     if ((rc = dots(d, V, vstride, nvec, w, pass ? h2 : h1))) return rc;
     std::vector<zc>& hp = pass ? h2 : h1;
     for (size_t i = 0; i < h.size(); ++i) h[i] += hp[i];
-    if (cudaMemcpyAsync(d.red_out, hp.data(), hp.size() * sizeof(double2), cudaMemcpyHostToDevice, d.st) != cudaSuccess)
+    // the coefficients in the vectors' precision (converted once, on the host)
+    std::vector<VT> hv(hp.size());
+    for (size_t i = 0; i < hp.size(); ++i) hv[i] = VT{(decltype(VT::x))hp[i].real(), (decltype(VT::x))hp[i].imag()};
+    if (cudaMemcpyAsync(d.red_out, hv.data(), hv.size() * sizeof(VT), cudaMemcpyHostToDevice, d.st) != cudaSuccess)
       return HB_ECUDA;
-    k_sub_combo<VT><<<gsz(d.n * d.R), 256, 0, d.st>>>(V, vstride, nvec, d.red_out, w, d.n, d.R, 1.0); count_launch(d.f, 1);
+    k_sub_combo<VT><<<gsz(d.n * d.R), 256, 0, d.st>>>(V, vstride, nvec, (const VT*)d.red_out, w, d.n, d.R);
+    count_launch(d.f, 1);
   }
   std::vector<zc> nn;
   if ((rc = dots(d, w, 0, 1, w, nn))) return rc;
@@ -537,7 +546,14 @@ extern "C" int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int6
       gv[c].solve(k, cf.data());
       for (int i = 0; i < k; ++i) coef[(size_t)i * R + c] = cf[i];
     }
-    cudaMemcpyAsync(d.red_out, coef.data(), (size_t)kcyc * R * sizeof(double2), cudaMemcpyHostToDevice, st);
+    std::vector<float2> coef32;
+    if (mixed) {
+      coef32.resize((size_t)kcyc * R);
+      for (size_t i = 0; i < coef32.size(); ++i) coef32[i] = float2{(float)coef[i].real(), (float)coef[i].imag()};
+      cudaMemcpyAsync(d.red_out, coef32.data(), coef32.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
+    } else {
+      cudaMemcpyAsync(d.red_out, coef.data(), (size_t)kcyc * R * sizeof(double2), cudaMemcpyHostToDevice, st);
+    }
     if (!mixed) {
       // y += V c;  x = U'^{-1} y is formed for the residual check
       k_add_combo<double2><<<gsz(n * R), 256, 0, st>>>(V, (int64_t)n * R, kcyc, d.red_out, xv, n, R); count_launch(f, 1);
@@ -565,11 +581,11 @@ extern "C" int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int6
       double worst_prev = 0.0;
       for (int64_t c = 0; c < R; ++c) worst_prev = std::max(worst_prev, res_r[c]);
       if (worst_prev > 1e-3) {
-        k_add_combo<float2><<<gsz(n * R), 256, 0, st>>>(zf, (int64_t)n * R, kcyc, d.red_out, xv, n, R); count_launch(f, 1);
+        k_add_combo<float2><<<gsz(n * R), 256, 0, st>>>(zf, (int64_t)n * R, kcyc, (const float2*)d.red_out, xv, n, R); count_launch(f, 1);
         if ((rc = true_residual(xv, r))) return rc;
       } else {
         cudaMemsetAsync(tmp2, 0, vbytes, st);   // dz in FP64, then rounded once to FP32
-        k_add_combo<float2><<<gsz(n * R), 256, 0, st>>>(zf, (int64_t)n * R, kcyc, d.red_out, tmp2, n, R); count_launch(f, 1);
+        k_add_combo<float2><<<gsz(n * R), 256, 0, st>>>(zf, (int64_t)n * R, kcyc, (const float2*)d.red_out, tmp2, n, R); count_launch(f, 1);
         k_axpy1<double2><<<gsz(n * R), 256, 0, st>>>(tmp2, xv, n * R); count_launch(f, 1);
         k_to_f32<<<gsz(n * R), 256, 0, st>>>(tmp2, f32s, n * R); count_launch(f, 1);
         float2* adz = (float2*)tmp2;   // A dz (FP32) reuses the scratch
