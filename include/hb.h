@@ -115,9 +115,13 @@ void hb_geometry_destroy(hb_geometry_t g);
  * [1 - i (2/pi) ln(gamma k w_i / (4e))], k = 2 pi / wavelength) with leaf
  * size `leaf` (n0) and compression tolerance eps (Alg. 1, IDBF of the
  * Appendix with sampled IDs seeded by `seed`), then upload the level-packed
- * factors, dense leaves and leaf triangle inverses to the current device in
- * the storage `form`.  Construction runs on the host and is timed apart
- * from the hot path.  Requires N = leaf * 2^D with D >= 1, 8 <= leaf <= 256.
+ * factors, dense leaves and the sweeps' packed triangles (the exact inverse
+ * of L~ / U~ on every subtree of up to 128 rows, formed on the host by
+ * running Algs. 3/4 on unit vectors) to the current device in the storage
+ * `form`.  HB_SPLIT_BF16 is accepted and currently stores and computes like
+ * HB_C64 (complex FP32 on CUDA cores).  Construction runs on the host and is
+ * timed apart from the hot path.  Requires N = leaf * 2^D with D >= 1,
+ * 8 <= leaf <= 256.
  * Errors: HB_EINVAL, HB_EUNSUPPORTED (N not leaf*2^D), HB_ENOMEM, HB_ECUDA. */
 int hb_factor(hb_geometry_t g, double wavelength, double eta0, double gamma, int64_t leaf, double eps,
               int form, uint64_t seed, void* stream, hb_factor_t* out);
@@ -171,10 +175,13 @@ int hb_residual(hb_factor_t f, int op, const void* b, const void* x, void* r, in
 /* hb_gmres -- solve A x = b_phys for nrhs right-hand sides (complex128, the
  * PHYSICAL excitation; the rescaling a is applied internally, x is invariant).
  * HB_C128: GMRES(restart) on the split-preconditioned system (Eqs. (Axb2),
- * (Axb3)).  HB_C64 / HB_SPLIT_BF16: FP64 flexible GMRES right-preconditioned
- * by U~^{-1} L~^{-1} applied in the low-precision form, inside FP64 iterative
- * refinement.  Stops when the true relative residual ||b^ - A^_F x||/||b^||
- * <= rtol (FP64) for every column or after maxit inner iterations.  The
+ * (Axb3)).  HB_C64 / HB_SPLIT_BF16: flexible GMRES right-preconditioned by
+ * U~^{-1} L~^{-1}, with the preconditioner, A and the Krylov basis in complex
+ * FP32, inside FP64 iterative refinement (residual with FP64 arithmetic on
+ * the stored factors; once every column is within 1e-3, updated as
+ * r -= A dz with the FP32 apply on the correction, accumulated in FP64).
+ * Stops when that FP64 relative residual ||b^ - A^_F x||/||b^|| <= rtol for
+ * every column or after maxit inner iterations.  The
  * initial guess is zero; x is overwritten with the solution.  Synchronises
  * `stream` before returning; info may be NULL.
  * Errors: HB_EINVAL, HB_ENAN (non-finite b), HB_ENOCONV (info still filled). */
