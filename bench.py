@@ -151,7 +151,7 @@ class ClockSampler:
 # GPU arm
 # ----------------------------------------------------------------------------
 # dram__bytes_read.sum + dram__bytes_write.sum per launch, 256 columns, semicircle N = 262,144
-MEASURED_TRAFFIC = {"k_sweep": 2343898368 + 3137184000}
+MEASURED_TRAFFIC = {"k_sweep": 2247096576 + 2686350592}
 
 
 def shard_angles(rank, world):
