@@ -170,10 +170,6 @@ __global__ void k_to_f32(const double2* __restrict__ a, float2* __restrict__ b, 
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (; e < total; e += (int64_t)gridDim.x * blockDim.x) b[e] = {(float)a[e].x, (float)a[e].y};
 }
-__global__ void k_to_f64(const float2* __restrict__ a, double2* __restrict__ b, int64_t total) {
-  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (; e < total; e += (int64_t)gridDim.x * blockDim.x) b[e] = {(double)a[e].x, (double)a[e].y};
-}
 
 __global__ void k_nonfinite(const double2* __restrict__ a, int64_t ld, int64_t n, int64_t R, int* flag) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -2,21 +2,23 @@
 // adjoints (Algs. 3, 4), in place on the vector.
 //
 // The recursion of Alg. 3 / Alg. 4 is flattened on the host into a program
-// of phases (leaf solves, butterfly entry ops, butterfly stages, butterfly
-// exit ops); consecutive phases depend on each other, ops inside a phase do
-// not.  The program is cut into segments:
+// of phases (sweep-leaf solves -- packed triangles of the exact inverse on
+// subtrees of up to 128 rows --, butterfly entry ops, butterfly stages,
+// butterfly exit ops); consecutive phases depend on each other, ops inside a
+// phase do not.  The program is cut into segments:
 //   * a grid segment is one large phase (a stage of a big butterfly); its
-//     ops (or, with many right-hand sides, (op, column range) units) are
-//     spread over all CTAs, one unit per CTA at a time;
+//     ops (or, with many right-hand sides, (op, column range) units, taken by
+//     two-warp groups) are spread over all CTAs;
 //   * a local segment is a run of small phases (a subtree near the leaves);
 //     each CTA executes it for its own share of the right-hand sides, one op
-//     per warp, __syncthreads between phases.
+//     per warp, a barrier between phases.  Runs that fit are resident in
+//     shared memory and fed by a producer warp (see local_run_ring).
 // A grid barrier (bounded spin; HB_ETIMEOUT instead of a hang) separates a
 // grid segment from its neighbours; consecutive local segments need none.
-// Every op first stages its factor blocks into shared memory with
-// 16-byte cp.async copies (one memory round trip for the whole op), then
-// computes from shared memory.  Vector and butterfly-state reads bypass L1
-// (ld.global.cg) because other CTAs write them inside the same launch.
+// Ops outside resident runs stage their factor blocks and vector operands
+// into shared memory with 16-byte cp.async copies, then compute from shared
+// memory.  Vector and butterfly-state reads bypass L1 (ld.global.cg) because
+// other CTAs write them inside the same launch.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -473,14 +475,16 @@ __device__ void do_leaf(const SweepArgs& a, const FlatOp& f, char* buf, int64_t 
 }
 
 // ---------------------------------------------------------------------------
-// Resident single-CTA runs with a staging ring (complex FP32 factors,
-// n0 <= 64).  The run's vector rows and butterfly state live in shared memory
-// for the whole run.  The factor data of the coming phases (each phase's ops
-// packed into one contiguous area, offsets precomputed on the host) is copied
-// into a ring buffer with cp.async, up to kLook phases ahead of the phase being
-// computed and as far as the ring has room, one commit group per phase; so
-// only shared-memory work and barriers remain on the dependency chain.
-// Shared-memory map: [ring | leaf partial sums | resident rows + state].
+// Resident single-CTA runs with a staging ring (complex FP32 factors, sweep
+// leaves of <= 256 rows).  The run's vector rows and butterfly state live in
+// shared memory for the whole run, and its op records and phase table are
+// copied in once.  A producer warp copies the factor data of the coming phases
+// (each phase's ops packed into one contiguous area, offsets precomputed on
+// the host) into a ring buffer with cp.async.bulk, one mbarrier per phase slot,
+// up to kLook phases ahead of the compute warps and as far as the ring has
+// room; so only shared-memory work and barriers remain on the dependency chain.
+// Shared-memory map: [ring | op records | phase table | sweep-leaf partial
+// sums | resident rows + state].
 // ---------------------------------------------------------------------------
 constexpr int kSmemBytes = 224 * 1024;
 constexpr int kAuxBytes = 16 * 1024;                                    // sweep-leaf partial sums
@@ -488,19 +492,6 @@ constexpr int kRecBytes = kRunMaxOps * 64;                              // the r
 constexpr int kPhBytes = (kRunMaxPhases + 1) * 8;                       // the run's phase table (4 KB)
 constexpr int kRingBytes = kSmemBytes - kAuxBytes - kResidentBytes - kRecBytes - kPhBytes;   // 100 KB
 constexpr int kLook = 7;                                                // phases in flight beyond the current one
-
-__device__ __forceinline__ void cp_wait_n(int n) {
-  switch (n) {
-    case 0: asm volatile("cp.async.wait_group 0;\n" ::: "memory"); break;
-    case 1: asm volatile("cp.async.wait_group 1;\n" ::: "memory"); break;
-    case 2: asm volatile("cp.async.wait_group 2;\n" ::: "memory"); break;
-    case 3: asm volatile("cp.async.wait_group 3;\n" ::: "memory"); break;
-    case 4: asm volatile("cp.async.wait_group 4;\n" ::: "memory"); break;
-    case 5: asm volatile("cp.async.wait_group 5;\n" ::: "memory"); break;
-    case 6: asm volatile("cp.async.wait_group 6;\n" ::: "memory"); break;
-    default: asm volatile("cp.async.wait_group 7;\n" ::: "memory"); break;
-  }
-}
 
 // ---- mbarrier + bulk-copy helpers (one thread issues a phase's copies)
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
