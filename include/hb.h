@@ -46,7 +46,7 @@ extern "C" {
 #define HB_EUNSUPPORTED -7  /* valid request this build does not implement */
 
 /* ---- enums ------------------------------------------------------------- */
-enum { HB_STRIP = 0, HB_SPIRAL = 1, HB_ARC = 2, HB_PARALLEL_STRIPS = 3 };
+enum { HB_STRIP = 0, HB_SPIRAL = 1, HB_ARC = 2, HB_PARALLEL_STRIPS = 3, HB_POLYLINE = 4 };
 enum { HB_C128 = 0, HB_C64 = 1, HB_SPLIT_BF16 = 2 };
 enum { HB_OP_N = 0, HB_OP_H = 1 };
 
@@ -103,6 +103,18 @@ typedef struct {
  * after strip.  Lengths in wavelengths.  *out is owned by the library.
  * Errors: HB_EINVAL (bad kind, nparams, n_segments < 1), HB_ENOMEM. */
 int hb_geometry(int kind, const double* params, int nparams, int64_t n_segments, hb_geometry_t* out);
+
+/* hb_geometry_polyline -- an explicitly given scatterer (kind HB_POLYLINE):
+ * nnodes nodes xy_nodes[2*i], xy_nodes[2*i+1] (host, wavelengths) on ncurves
+ * open curves; curve c uses nodes curve_starts[c] .. curve_starts[c+1]-1 (the
+ * last up to nnodes-1) and contributes one pulse segment per pair of
+ * consecutive nodes (the chord: centre = midpoint, w = length, Sec. 3.1), so
+ * N = nnodes - ncurves, in the order given (the geometric order of Sec.
+ * 3.3.1 is the caller's).  Errors: HB_EINVAL (null pointers, curve_starts[0]
+ * != 0 or not increasing, a curve with fewer than 2 nodes, a non-finite
+ * coordinate, a zero-length segment), HB_ENOMEM. */
+int hb_geometry_polyline(const double* xy_nodes, const int64_t* curve_starts, int ncurves, int64_t nnodes,
+                         hb_geometry_t* out);
 
 /* Host copies of the segment centres (2N doubles, x/y interleaved) and
  * lengths (N doubles) into caller-owned buffers.  Either may be NULL. */

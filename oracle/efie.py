@@ -24,7 +24,7 @@ class Problem:
 
     def __init__(self, kind, params, n, wavelength=1.0, eta0=376.73, gamma=1.781072):
         self.kind = int(kind)
-        self.params = tuple(float(p) for p in params)
+        self.params = tuple(params) if self.kind == geometry.POLYLINE else tuple(float(p) for p in params)
         self.n = int(n)
         self.centres, self.lengths = geometry.segments(kind, params, n)
         self.kappa = 2.0 * math.pi / wavelength

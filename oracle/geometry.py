@@ -15,7 +15,7 @@ import math
 
 import numpy as np
 
-STRIP, SPIRAL, ARC, PARALLEL_STRIPS = 0, 1, 2, 3
+STRIP, SPIRAL, ARC, PARALLEL_STRIPS, POLYLINE = 0, 1, 2, 3, 4
 
 
 def _chords(nodes_x, nodes_y):
@@ -48,9 +48,31 @@ def spiral_nodes(a, theta0, theta1, n):
     return th
 
 
+def polyline_segments(nodes, curve_starts=(0,)):
+    """Explicit scatterer: curves given by their nodes (rows of `nodes`, x and y); curve c
+    uses nodes curve_starts[c] .. curve_starts[c+1] - 1 (the last one up to the end) and
+    contributes one segment per pair of consecutive nodes."""
+    nodes = np.asarray(nodes, dtype=np.float64)
+    starts = [int(c) for c in curve_starts] + [len(nodes)]
+    cs, ws = [], []
+    for c in range(len(starts) - 1):
+        sub = nodes[starts[c]:starts[c + 1]]
+        cc, w = _chords(sub[:, 0], sub[:, 1])
+        cs.append(cc)
+        ws.append(w)
+    return np.concatenate(cs), np.concatenate(ws)
+
+
 def segments(kind, params, n):
-    """Return (centres [n,2], lengths [n]) for the curve `kind` with `params`."""
+    """Return (centres [n,2], lengths [n]) for the curve `kind` with `params`
+    (POLYLINE: params = (nodes, curve_starts), see polyline_segments)."""
     kind = int(kind)
+    if kind == POLYLINE:
+        nodes, starts = params
+        c, w = polyline_segments(nodes, starts)
+        if len(w) != n:
+            raise ValueError("polyline: n does not match the node list")
+        return c, w
     if kind == STRIP:
         x0, y0, x1, y1 = params
         t = np.arange(n + 1, dtype=np.float64) / n

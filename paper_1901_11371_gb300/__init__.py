@@ -15,11 +15,12 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (HB_ARC, HB_C64, HB_C128, HB_OP_H, HB_OP_N, HB_PARALLEL_STRIPS, HB_SPIRAL, HB_SPLIT_BF16,
-                   HB_STRIP, HBError)
+from ._lib import (HB_ARC, HB_C64, HB_C128, HB_OP_H, HB_OP_N, HB_PARALLEL_STRIPS, HB_POLYLINE, HB_SPIRAL,
+                   HB_SPLIT_BF16, HB_STRIP, HBError)
 
-__all__ = ["HB_STRIP", "HB_SPIRAL", "HB_ARC", "HB_PARALLEL_STRIPS", "HB_C128", "HB_C64", "HB_SPLIT_BF16",
-           "HB_OP_N", "HB_OP_H", "HBError", "Geometry", "Factor", "hb_geometry", "hb_factor", "hb_factor_host",
+__all__ = ["HB_STRIP", "HB_SPIRAL", "HB_ARC", "HB_PARALLEL_STRIPS", "HB_POLYLINE", "HB_C128", "HB_C64",
+           "HB_SPLIT_BF16", "HB_OP_N", "HB_OP_H", "HBError", "Geometry", "Factor", "hb_geometry",
+           "hb_geometry_polyline", "hb_factor", "hb_factor_host",
            "hb_factor_info", "hb_tree", "hb_apply", "hb_apply_adjoint", "hb_precond_solve", "hb_lower_solve",
            "hb_upper_solve", "hb_residual", "hb_gmres", "hb_rhs_plane_wave", "hb_far_field", "hb_monostatic",
            "hb_host_apply", "hb_host_sweep", "hb_far_field_adjoint", "hb_profile", "hb_profile_read", "hb_autotune", "hb_autotune_times", "lib"]
@@ -81,6 +82,18 @@ def hb_geometry(kind, params, n_segments):
     out = C.c_void_p()
     _lib.check(lib().hb_geometry(int(kind), p, len(params), int(n_segments), C.byref(out)))
     return Geometry(out.value, n_segments)
+
+
+def hb_geometry_polyline(nodes, curve_starts=(0,)):
+    """Scatterer from explicit nodes (array (nnodes, 2), wavelengths); curve c uses nodes
+    curve_starts[c] .. curve_starts[c+1]-1, one segment per pair of consecutive nodes."""
+    xy = np.ascontiguousarray(np.asarray(nodes, dtype=np.float64).reshape(-1, 2))
+    st = np.ascontiguousarray(np.asarray(curve_starts, dtype=np.int64))
+    out = C.c_void_p()
+    _lib.check(lib().hb_geometry_polyline(xy.ctypes.data_as(C.POINTER(C.c_double)),
+                                          st.ctypes.data_as(C.POINTER(C.c_int64)), int(len(st)), int(len(xy)),
+                                          C.byref(out)))
+    return Geometry(out.value, len(xy) - len(st))
 
 
 def hb_factor(geom, leaf, eps, form=HB_C128, wavelength=1.0, eta0=376.73, gamma=1.781072, seed=0, stream=None):

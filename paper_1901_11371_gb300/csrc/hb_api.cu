@@ -249,6 +249,18 @@ int hb_geometry(int kind, const double* params, int nparams, int64_t n_segments,
   return HB_OK;
 }
 
+int hb_geometry_polyline(const double* xy_nodes, const int64_t* curve_starts, int ncurves, int64_t nnodes,
+                         hb_geometry_t* out) {
+  if (!out) { set_error("hb_geometry_polyline: out is null"); return HB_EINVAL; }
+  *out = nullptr;
+  hb_geometry_s* g = new (std::nothrow) hb_geometry_s();
+  if (!g) { set_error("hb_geometry_polyline: out of host memory"); return HB_ENOMEM; }
+  int rc = build_geometry_polyline(xy_nodes, curve_starts, ncurves, nnodes, g->geo);
+  if (rc) { delete g; return rc; }
+  *out = g;
+  return HB_OK;
+}
+
 int hb_geometry_segments(hb_geometry_t g, double* centers_xy, double* lengths) {
   if (!g) { set_error("hb_geometry_segments: null geometry"); return HB_EINVAL; }
   for (int64_t i = 0; i < g->geo.n; ++i) {

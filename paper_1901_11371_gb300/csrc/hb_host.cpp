@@ -114,6 +114,41 @@ int build_geometry(int kind, const double* params, int nparams, int64_t n, Geome
   return HB_OK;
 }
 
+int build_geometry_polyline(const double* xy, const int64_t* starts, int ncurves, int64_t nnodes, Geometry& g) {
+  if (!xy || !starts || ncurves < 1 || nnodes < 2) {
+    set_error("hb_geometry_polyline: null pointer, ncurves < 1 or nnodes < 2");
+    return HB_EINVAL;
+  }
+  if (starts[0] != 0) { set_error("hb_geometry_polyline: curve_starts[0] must be 0"); return HB_EINVAL; }
+  for (int c = 0; c < ncurves; ++c) {
+    const int64_t e = c + 1 < ncurves ? starts[c + 1] : nnodes;
+    if (e - starts[c] < 2 || e > nnodes) {
+      set_error("hb_geometry_polyline: curve %d needs at least 2 nodes inside the node list", c);
+      return HB_EINVAL;
+    }
+  }
+  for (int64_t i = 0; i < 2 * nnodes; ++i)
+    if (!std::isfinite(xy[i])) { set_error("hb_geometry_polyline: non-finite coordinate"); return HB_EINVAL; }
+  const int64_t n = nnodes - ncurves;
+  g.kind = HB_POLYLINE;
+  g.n = n;
+  g.params.clear();
+  g.cx.assign(n, 0.0);
+  g.cy.assign(n, 0.0);
+  g.w.assign(n, 0.0);
+  int64_t off = 0;
+  for (int c = 0; c < ncurves; ++c) {
+    const int64_t b = starts[c], e = c + 1 < ncurves ? starts[c + 1] : nnodes;
+    std::vector<double> nx((size_t)(e - b)), ny((size_t)(e - b));
+    for (int64_t i = b; i < e; ++i) { nx[(size_t)(i - b)] = xy[2 * i]; ny[(size_t)(i - b)] = xy[2 * i + 1]; }
+    chords(nx, ny, g, off);
+    off += e - b - 1;
+  }
+  for (int64_t i = 0; i < n; ++i)
+    if (!(g.w[i] > 0.0)) { set_error("hb_geometry_polyline: segment %lld has zero length", (long long)i); return HB_EINVAL; }
+  return HB_OK;
+}
+
 // ---------------------------------------------------------------------------
 // EFIE entries (Sec. 3.1), rescaled by a.  H0^(2) = J0 - i Y0 from the C
 // library's j0 / y0.

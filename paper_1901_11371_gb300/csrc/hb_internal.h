@@ -75,6 +75,8 @@ struct HostFactor {
 inline int64_t bf_id(int v, int64_t p, int kind) { return 2 * (((int64_t)1 << v) - 1 + p) + kind; }
 
 int build_geometry(int kind, const double* params, int nparams, int64_t n, Geometry& g);
+// Explicit node list (HB_POLYLINE): see hb_geometry_polyline.
+int build_geometry_polyline(const double* xy, const int64_t* starts, int ncurves, int64_t nnodes, Geometry& g);
 int build_factor(const Geometry& g, double wavelength, double eta0, double gamma, int64_t leaf, double eps,
                  uint64_t seed, HostFactor& hf);
 

@@ -1,0 +1,103 @@
+"""Explicitly given scatterers (HB_POLYLINE): the library's node-list geometry, its
+oracle counterpart, and a host-built H-IDBF of such a curve against the dense oracle.
+
+Pins: nodes on a line / on a circle / on eight strips reproduce the STRIP / ARC /
+PARALLEL_STRIPS discretisations (closed forms already pinned in test_oracle_efie);
+the compressed apply of a wavy curve stays within 10 eps of the dense EFIE matrix.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import efie, geometry
+
+
+@pytest.fixture(scope="module")
+def hb():
+    from paper_1901_11371_gb300 import build
+    build.build()
+    import paper_1901_11371_gb300 as hb
+    hb.lib()
+    return hb
+
+
+def _line_nodes(n, x1=51.2):
+    t = np.arange(n + 1) / n
+    return np.stack([x1 * t, np.zeros(n + 1)], axis=1)
+
+
+def test_oracle_polyline_matches_closed_forms():
+    n = 1024
+    c0, w0 = geometry.segments(W.STRIP, (0.0, 0.0, 51.2, 0.0), n)
+    c1, w1 = geometry.polyline_segments(_line_nodes(n))
+    np.testing.assert_allclose(c1, c0, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(w1, w0, rtol=1e-13)
+    R = 30.0
+    ph = math.pi * np.arange(n + 1) / n
+    c2, w2 = geometry.polyline_segments(np.stack([R * np.cos(ph), R * np.sin(ph)], axis=1))
+    c3, w3 = geometry.segments(W.ARC, (R, 0.0, math.pi), n)
+    np.testing.assert_allclose(c2, c3, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(w2, w3, rtol=1e-12)
+
+
+def test_library_polyline_matches_built_in_kinds(hb):
+    n = 1024
+    g0 = hb.hb_geometry(hb.HB_STRIP, (0.0, 0.0, 51.2, 0.0), n)
+    g1 = hb.hb_geometry_polyline(_line_nodes(n))
+    assert g1.n == n
+    c0, w0 = g0.segments()
+    c1, w1 = g1.segments()
+    np.testing.assert_array_equal(c1, c0)
+    np.testing.assert_array_equal(w1, w0)
+    # eight strips: eight curves of 257 nodes
+    per = 256
+    nodes = []
+    for s in range(8):
+        t = np.arange(per + 1) / per
+        nodes.append(np.stack([12.8 * t, np.full(per + 1, 2.0 * s)], axis=1))
+    g2 = hb.hb_geometry_polyline(np.concatenate(nodes), [s * (per + 1) for s in range(8)])
+    g3 = hb.hb_geometry(hb.HB_PARALLEL_STRIPS, (8.0, 12.8, 2.0), 8 * per)
+    assert g2.n == 8 * per
+    c2, w2 = g2.segments()
+    c3, w3 = g3.segments()
+    np.testing.assert_allclose(c2, c3, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(w2, w3, rtol=1e-13)
+
+
+def test_polyline_errors(hb):
+    nodes = _line_nodes(8)
+    with pytest.raises(hb.HBError):
+        hb.hb_geometry_polyline(nodes, [1])                 # first curve must start at node 0
+    with pytest.raises(hb.HBError):
+        hb.hb_geometry_polyline(nodes, [0, 8])             # second curve has a single node
+    with pytest.raises(hb.HBError):
+        hb.hb_geometry_polyline(nodes, [0, 5, 4])          # not increasing
+    bad = nodes.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(hb.HBError):
+        hb.hb_geometry_polyline(bad)
+    dup = np.concatenate([nodes[:4], nodes[3:]])           # repeated node: zero-length segment
+    with pytest.raises(hb.HBError):
+        hb.hb_geometry_polyline(dup)
+
+
+def test_host_factor_of_a_wavy_curve_within_10eps(hb):
+    # a sine-modulated open curve, 1024 segments, two curves of 513 nodes each
+    n_per = 512
+    t = np.arange(n_per + 1) / n_per
+    a = np.stack([25.6 * t, 1.5 * np.sin(2 * math.pi * 3 * t)], axis=1)
+    b = np.stack([25.6 * t, 6.0 + 0.8 * np.cos(2 * math.pi * 2 * t)], axis=1)
+    nodes = np.concatenate([a, b])
+    starts = [0, n_per + 1]
+    g = hb.hb_geometry_polyline(nodes, starts)
+    eps = 1e-6
+    f = hb.hb_factor_host(g, 32, eps)
+    p = efie.Problem(W.POLYLINE, (nodes, starts), 2 * n_per)
+    dense_a = p.dense()
+    for seed in (5, 6):
+        x = W.complex_gaussian(2 * n_per, seed)
+        y = hb.hb_host_apply(f, x)
+        ref = dense_a @ x
+        assert np.linalg.norm(y - ref) / np.linalg.norm(ref) <= 10 * eps

@@ -21,6 +21,7 @@ STRIP = 0            # params (x0, y0, x1, y1)
 SPIRAL = 1           # params (a, theta0, theta1): r = a*theta
 ARC = 2              # params (R, phi0, phi1): circle arc centred at the origin
 PARALLEL_STRIPS = 3  # params (n_strips, length, spacing): y = s*spacing, x in [0, length]
+POLYLINE = 4         # explicit nodes (hb_geometry_polyline): params (nodes [n+c, 2], curve_starts [c])
 
 # Physical constants fixed by the problem statement (wavelength lambda = 1).
 WAVELENGTH = 1.0
