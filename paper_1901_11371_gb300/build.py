@@ -17,7 +17,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["hb_kernels.cu", "hb_sweep.cu", "hb_api.cu", "hb_solver.cu", "hb_noalloc.cu"]
+CU_SOURCES = ["hb_kernels.cu", "hb_sweep.cu", "hb_sweep_f64.cu", "hb_sweep_f32n.cu", "hb_sweep_f32w.cu",
+              "hb_sweep_mix.cu", "hb_api.cu", "hb_solver.cu", "hb_noalloc.cu"]
 CPP_SOURCES = ["hb_host.cpp"]
 
 
