@@ -137,6 +137,20 @@ void hb_geometry_destroy(hb_geometry_t g);
  * Errors: HB_EINVAL, HB_EUNSUPPORTED (N not leaf*2^D), HB_ENOMEM, HB_ECUDA. */
 int hb_factor(hb_geometry_t g, double wavelength, double eta0, double gamma, int64_t leaf, double eps,
               int form, uint64_t seed, void* stream, hb_factor_t* out);
+
+/* Factor options (bit mask for hb_factor_ex / hb_factor_host_ex).
+ * HB_OPT_LEAF_LU: the leaf blocks of L~ and U~ are the LU factors of the dense
+ *   leaf block (A_leaf = L U, L unit lower, U upper, no pivoting) instead of
+ *   the entry-wise triangles of Eqs. (Lt), (Ut); the off-diagonal blocks and
+ *   Algs. 3/4 are unchanged.  A variant the paper implies (its leaf solves are
+ *   LAPACK triangular solves); HB_EUNSUPPORTED on a zero pivot. */
+#define HB_OPT_LEAF_LU 1
+
+/* hb_factor_ex / hb_factor_host_ex -- hb_factor / hb_factor_host with an
+ * options mask (0 = the defaults of hb_factor).  Errors as hb_factor, plus
+ * HB_EINVAL for unknown option bits. */
+int hb_factor_ex(hb_geometry_t g, double wavelength, double eta0, double gamma, int64_t leaf, double eps,
+                 int form, uint64_t seed, int options, void* stream, hb_factor_t* out);
 int hb_factor_info(hb_factor_t f, hb_factor_stats* s);
 void hb_factor_destroy(hb_factor_t f);
 
@@ -276,6 +290,8 @@ int hb_profile_read(hb_factor_t f, int kind, int64_t* count, double* total_ms);
  * Vectors are host arrays of N complex128 (interleaved doubles). */
 int hb_factor_host(hb_geometry_t g, double wavelength, double eta0, double gamma, int64_t leaf, double eps,
                    uint64_t seed, hb_factor_t* out);
+int hb_factor_host_ex(hb_geometry_t g, double wavelength, double eta0, double gamma, int64_t leaf, double eps,
+                      uint64_t seed, int options, hb_factor_t* out);
 int hb_host_apply(hb_factor_t f, int op, const double* x, double* y);
 int hb_host_sweep(hb_factor_t f, int which, double* vec);
 

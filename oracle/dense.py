@@ -75,6 +75,34 @@ def u_tilde(a):
     return np.triu(a)
 
 
+def leaf_lu(block):
+    """LU without pivoting (Doolittle): block = L U, L unit lower, U upper (the exact
+    leaf LU variant of the leaf solves of Algs. 3/4)."""
+    n = block.shape[0]
+    lo = np.eye(n, dtype=np.complex128)
+    up = np.zeros((n, n), dtype=np.complex128)
+    for k in range(n):
+        up[k, k:] = block[k, k:] - lo[k, :k] @ up[:k, k:]
+        lo[k + 1:, k] = (block[k + 1:, k] - lo[k + 1:, :k] @ up[:k, k]) / up[k, k]
+    return lo, up
+
+
+def l_tilde_leaf_lu(a, n0):
+    """L~ with each n0 x n0 diagonal block replaced by the L factor of that block of A."""
+    out = l_tilde(a)
+    for s in range(0, a.shape[0], n0):
+        out[s:s + n0, s:s + n0] = leaf_lu(a[s:s + n0, s:s + n0])[0]
+    return out
+
+
+def u_tilde_leaf_lu(a, n0):
+    """U~ with each n0 x n0 diagonal block replaced by the U factor of that block of A."""
+    out = u_tilde(a)
+    for s in range(0, a.shape[0], n0):
+        out[s:s + n0, s:s + n0] = leaf_lu(a[s:s + n0, s:s + n0])[1]
+    return out
+
+
 def precond_solve(a, b):
     """x = U~^{-1} L~^{-1} b with the exact entry-wise triangles of A."""
     y = forward_subst(l_tilde(a), b, unit=True)

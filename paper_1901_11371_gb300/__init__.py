@@ -15,11 +15,11 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (HB_ARC, HB_C64, HB_C128, HB_OP_H, HB_OP_N, HB_PARALLEL_STRIPS, HB_POLYLINE, HB_SPIRAL,
-                   HB_SPLIT_BF16, HB_STRIP, HBError)
+from ._lib import (HB_ARC, HB_C64, HB_C128, HB_OP_H, HB_OP_N, HB_OPT_LEAF_LU, HB_PARALLEL_STRIPS, HB_POLYLINE,
+                   HB_SPIRAL, HB_SPLIT_BF16, HB_STRIP, HBError)
 
 __all__ = ["HB_STRIP", "HB_SPIRAL", "HB_ARC", "HB_PARALLEL_STRIPS", "HB_POLYLINE", "HB_C128", "HB_C64",
-           "HB_SPLIT_BF16", "HB_OP_N", "HB_OP_H", "HBError", "Geometry", "Factor", "hb_geometry",
+           "HB_SPLIT_BF16", "HB_OP_N", "HB_OP_H", "HB_OPT_LEAF_LU", "HBError", "Geometry", "Factor", "hb_geometry",
            "hb_geometry_polyline", "hb_factor", "hb_factor_host",
            "hb_factor_info", "hb_tree", "hb_apply", "hb_apply_adjoint", "hb_precond_solve", "hb_lower_solve",
            "hb_upper_solve", "hb_residual", "hb_gmres", "hb_rhs_plane_wave", "hb_far_field", "hb_monostatic",
@@ -96,17 +96,19 @@ def hb_geometry_polyline(nodes, curve_starts=(0,)):
     return Geometry(out.value, len(xy) - len(st))
 
 
-def hb_factor(geom, leaf, eps, form=HB_C128, wavelength=1.0, eta0=376.73, gamma=1.781072, seed=0, stream=None):
+def hb_factor(geom, leaf, eps, form=HB_C128, wavelength=1.0, eta0=376.73, gamma=1.781072, seed=0, stream=None,
+              options=0):
+    """Build and upload the H-IDBF factor; options: HB_OPT_* bits (HB_OPT_LEAF_LU: exact leaf LU)."""
     out = C.c_void_p()
-    _lib.check(lib().hb_factor(geom._h, wavelength, eta0, gamma, int(leaf), float(eps), int(form), int(seed),
-                               _stream(stream), C.byref(out)))
+    _lib.check(lib().hb_factor_ex(geom._h, wavelength, eta0, gamma, int(leaf), float(eps), int(form), int(seed),
+                                  int(options), _stream(stream), C.byref(out)))
     return Factor(out.value, form)
 
 
-def hb_factor_host(geom, leaf, eps, wavelength=1.0, eta0=376.73, gamma=1.781072, seed=0):
+def hb_factor_host(geom, leaf, eps, wavelength=1.0, eta0=376.73, gamma=1.781072, seed=0, options=0):
     out = C.c_void_p()
-    _lib.check(lib().hb_factor_host(geom._h, wavelength, eta0, gamma, int(leaf), float(eps), int(seed),
-                                    C.byref(out)))
+    _lib.check(lib().hb_factor_host_ex(geom._h, wavelength, eta0, gamma, int(leaf), float(eps), int(seed),
+                                       int(options), C.byref(out)))
     return Factor(out.value, HB_C128, host_only=True)
 
 

@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(HERE, "libhb.so")
 
 HB_OK, HB_EINVAL, HB_ENOMEM, HB_ECUDA, HB_ENOCONV, HB_ETIMEOUT, HB_ENAN, HB_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
 HB_STRIP, HB_SPIRAL, HB_ARC, HB_PARALLEL_STRIPS, HB_POLYLINE = 0, 1, 2, 3, 4
+HB_OPT_LEAF_LU = 1
 HB_C128, HB_C64, HB_SPLIT_BF16 = 0, 1, 2
 HB_OP_N, HB_OP_H = 0, 1
 ERR_NAMES = {0: "HB_OK", -1: "HB_EINVAL", -2: "HB_ENOMEM", -3: "HB_ECUDA", -4: "HB_ENOCONV", -5: "HB_ETIMEOUT",
@@ -52,6 +53,8 @@ SIGNATURES = {
     "hb_geometry_destroy": (None, [_VP]),
     "hb_factor": (_INT, [_VP, _DBL, _DBL, _DBL, _I64, _DBL, _INT, C.c_uint64, _VP, C.POINTER(_VP)]),
     "hb_factor_host": (_INT, [_VP, _DBL, _DBL, _DBL, _I64, _DBL, C.c_uint64, C.POINTER(_VP)]),
+    "hb_factor_ex": (_INT, [_VP, _DBL, _DBL, _DBL, _I64, _DBL, _INT, C.c_uint64, _INT, _VP, C.POINTER(_VP)]),
+    "hb_factor_host_ex": (_INT, [_VP, _DBL, _DBL, _DBL, _I64, _DBL, C.c_uint64, _INT, C.POINTER(_VP)]),
     "hb_factor_info": (_INT, [_VP, C.POINTER(FactorStats)]),
     "hb_factor_destroy": (None, [_VP]),
     "hb_tree": (_INT, [_VP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),

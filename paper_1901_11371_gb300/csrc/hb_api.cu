@@ -276,13 +276,19 @@ void hb_geometry_destroy(hb_geometry_t g) { delete g; }
 
 int hb_factor(hb_geometry_t g, double wavelength, double eta0, double gamma, int64_t leaf, double eps, int form,
               uint64_t seed, void* stream, hb_factor_t* out) {
+  return hb_factor_ex(g, wavelength, eta0, gamma, leaf, eps, form, seed, 0, stream, out);
+}
+
+int hb_factor_ex(hb_geometry_t g, double wavelength, double eta0, double gamma, int64_t leaf, double eps, int form,
+                 uint64_t seed, int options, void* stream, hb_factor_t* out) {
   if (!out || !g) { set_error("hb_factor: null argument"); return HB_EINVAL; }
+  if (options & ~HB_OPT_LEAF_LU) { set_error("hb_factor: unknown option bits 0x%x", options); return HB_EINVAL; }
   *out = nullptr;
   if (form != HB_C128 && form != HB_C64 && form != HB_SPLIT_BF16) { set_error("hb_factor: bad form %d", form); return HB_EINVAL; }
   auto t0 = std::chrono::steady_clock::now();
   hb_factor_s* f = new (std::nothrow) hb_factor_s();
   if (!f) { set_error("hb_factor: out of host memory"); return HB_ENOMEM; }
-  int rc = build_factor(g->geo, wavelength, eta0, gamma, leaf, eps, seed, f->hf);
+  int rc = build_factor(g->geo, wavelength, eta0, gamma, leaf, eps, seed, f->hf, options);
   if (!rc) {
     pack_factor(f->hf, f->ph);
     for (const auto& b : f->hf.bf) {
@@ -311,11 +317,17 @@ int hb_factor(hb_geometry_t g, double wavelength, double eta0, double gamma, int
 
 int hb_factor_host(hb_geometry_t g, double wavelength, double eta0, double gamma, int64_t leaf, double eps,
                    uint64_t seed, hb_factor_t* out) {
+  return hb_factor_host_ex(g, wavelength, eta0, gamma, leaf, eps, seed, 0, out);
+}
+
+int hb_factor_host_ex(hb_geometry_t g, double wavelength, double eta0, double gamma, int64_t leaf, double eps,
+                      uint64_t seed, int options, hb_factor_t* out) {
   if (!out || !g) { set_error("hb_factor_host: null argument"); return HB_EINVAL; }
   *out = nullptr;
+  if (options & ~HB_OPT_LEAF_LU) { set_error("hb_factor_host: unknown option bits 0x%x", options); return HB_EINVAL; }
   hb_factor_s* f = new (std::nothrow) hb_factor_s();
   if (!f) { set_error("hb_factor_host: out of host memory"); return HB_ENOMEM; }
-  int rc = build_factor(g->geo, wavelength, eta0, gamma, leaf, eps, seed, f->hf);
+  int rc = build_factor(g->geo, wavelength, eta0, gamma, leaf, eps, seed, f->hf, options);
   if (rc) { delete f; return rc; }
   pack_factor(f->hf, f->ph);
   f->host_only = true;

@@ -507,8 +507,24 @@ static void triangle_inverse(const cplx* A, int n0, bool lower, cplx* X) {
 // L + 3 factors of a butterfly and over the H-IDBF levels.
 static constexpr double kIdTolFactor = 0.1;
 
+// In-place LU without pivoting (Doolittle) of the n0 x n0 row-major block A:
+// on return the strict lower part holds L (unit diagonal implied), the upper
+// part U.  Returns false on a zero pivot.
+static bool leaf_lu_inplace(cplx* A, int n0) {
+  for (int k = 0; k < n0; ++k) {
+    const cplx piv = A[k * n0 + k];
+    if (piv == cplx(0.0)) return false;
+    for (int i = k + 1; i < n0; ++i) {
+      const cplx l = A[i * n0 + k] / piv;
+      A[i * n0 + k] = l;
+      for (int j = k + 1; j < n0; ++j) A[i * n0 + j] -= l * A[k * n0 + j];
+    }
+  }
+  return true;
+}
+
 int build_factor(const Geometry& g, double wavelength, double eta0, double gamma, int64_t leaf, double eps,
-                 uint64_t seed, HostFactor& hf) {
+                 uint64_t seed, HostFactor& hf, int options) {
   auto t0 = std::chrono::steady_clock::now();
   if (leaf < 8 || leaf > 256 || eps <= 0 || eps >= 1 || wavelength <= 0) {
     set_error("hb_factor: need 8 <= leaf <= 256, 0 < eps < 1, wavelength > 0");
@@ -532,13 +548,33 @@ int build_factor(const Geometry& g, double wavelength, double eta0, double gamma
   hf.leaf.assign((size_t)m * leaf * leaf, cplx(0.0));
   hf.linv.assign(hf.leaf.size(), cplx(0.0));
   hf.uinv.assign(hf.leaf.size(), cplx(0.0));
+  // leaf triangles: the entry-wise triangles of A_leaf (Eqs. (Lt), (Ut)), or with
+  // HB_OPT_LEAF_LU the LU factors of A_leaf (unit lower L, upper U, no pivoting)
+  const bool leaf_lu = (options & HB_OPT_LEAF_LU) != 0;
+  hf.leaf_lu = leaf_lu;
+  int bad_pivot = 0;
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t j = 0; j < m; ++j) {
     cplx* A = &hf.leaf[(size_t)j * leaf * leaf];
     for (int64_t r = 0; r < leaf; ++r)
       for (int64_t c = 0; c < leaf; ++c) A[r * leaf + c] = K(j * leaf + r, j * leaf + c);
-    triangle_inverse(A, (int)leaf, true, &hf.linv[(size_t)j * leaf * leaf]);
-    triangle_inverse(A, (int)leaf, false, &hf.uinv[(size_t)j * leaf * leaf]);
+    if (leaf_lu) {
+      std::vector<cplx> lu(A, A + leaf * leaf);
+      if (!leaf_lu_inplace(lu.data(), (int)leaf)) {
+#pragma omp atomic write
+        bad_pivot = 1;
+        continue;
+      }
+      triangle_inverse(lu.data(), (int)leaf, true, &hf.linv[(size_t)j * leaf * leaf]);
+      triangle_inverse(lu.data(), (int)leaf, false, &hf.uinv[(size_t)j * leaf * leaf]);
+    } else {
+      triangle_inverse(A, (int)leaf, true, &hf.linv[(size_t)j * leaf * leaf]);
+      triangle_inverse(A, (int)leaf, false, &hf.uinv[(size_t)j * leaf * leaf]);
+    }
+  }
+  if (bad_pivot) {
+    set_error("hb_factor: LU of a leaf block without pivoting met a zero pivot");
+    return HB_EUNSUPPORTED;
   }
   // butterflies: F12 and F21 of every internal node (Alg. 1)
   int64_t nbf = 2 * (m - 1);

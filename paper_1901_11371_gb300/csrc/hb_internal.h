@@ -68,6 +68,7 @@ struct HostFactor {
   std::vector<Butterfly> bf;            // index = butterfly id (see bf_id)
   std::vector<cplx> leaf;               // m blocks, n0 x n0 row-major (scaled A)
   std::vector<cplx> linv, uinv;         // leaf triangle inverses, row-major
+  bool leaf_lu = false;                 // leaf triangles are LU factors of A_leaf (HB_OPT_LEAF_LU)
   double build_seconds = 0.0;
 };
 
@@ -77,8 +78,9 @@ inline int64_t bf_id(int v, int64_t p, int kind) { return 2 * (((int64_t)1 << v)
 int build_geometry(int kind, const double* params, int nparams, int64_t n, Geometry& g);
 // Explicit node list (HB_POLYLINE): see hb_geometry_polyline.
 int build_geometry_polyline(const double* xy, const int64_t* starts, int ncurves, int64_t nnodes, Geometry& g);
+// options: HB_OPT_* bits of include/hb.h
 int build_factor(const Geometry& g, double wavelength, double eta0, double gamma, int64_t leaf, double eps,
-                 uint64_t seed, HostFactor& hf);
+                 uint64_t seed, HostFactor& hf, int options = 0);
 
 // ---------------------------------------------------------------------------
 // Level-packed device image (built on the host, uploaded as flat arrays).
