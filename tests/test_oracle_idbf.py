@@ -175,3 +175,32 @@ def test_gmres_paper_protocol_b_equals_a_xt():
     b = a @ xt
     x, info = krylov.gmres_split(h.apply, h.solve_lower, h.solve_upper, b, rtol=1e-8)
     assert np.linalg.norm(x - xt) / np.linalg.norm(xt) < 1e-3
+
+
+def test_tfqmr_dense_system_matches_solve():
+    # Unpreconditioned TFQMR on a small well-conditioned nonsymmetric complex system reaches
+    # the direct solution; a wrong coefficient in the half-step recurrences stalls it.
+    n = 60
+    a = np.eye(n) * 4.0 + W.complex_gaussian(n * n, 21).reshape(n, n) * 0.4
+    b = W.complex_gaussian(n, 22)
+    ident = lambda v: v
+    x, info = krylov.tfqmr_split(lambda z: a @ z, ident, ident, b,
+                                 rstar=W.complex_gaussian(n, W.SEED_SHADOW), rtol=1e-10, maxit=400)
+    x_ref = np.linalg.solve(a, b)
+    assert info["true_rel_res"] <= 1e-10
+    assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) <= 1e-9
+    # one product per half step (plus the start, less one when it stops after an even step)
+    assert info["iters"] <= info["matvecs"] <= info["iters"] + 1
+
+
+def test_tfqmr_split_preconditioned_strip(strip1024):
+    # Sec. 4's solver on the split system: same solution as the dense LU, in about as many
+    # products with L~^{-1} A U~^{-1} as GMRES takes iterations.
+    p, a, h = strip1024
+    b = p.plane_wave(30.0)[:, 0] * p.scale
+    x_lu = dense.solve(a, b)
+    x, info = krylov.tfqmr_split(h.apply, h.solve_lower, h.solve_upper, b,
+                                 rstar=W.complex_gaussian(a.shape[0], W.SEED_SHADOW), rtol=1e-6)
+    assert info["true_rel_res"] <= 1e-6
+    assert np.linalg.norm(x - x_lu) / np.linalg.norm(x_lu) <= 1e-5
+    assert info["matvecs"] < 80

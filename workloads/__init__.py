@@ -135,3 +135,4 @@ SEED_XTRUE = 3      # x^t ~ CN(0, I) for the b = A x^t protocol (Sec. 4)
 SEED_TARGET = 1     # far-field target t ~ CN(0,1)
 SEED_FD = 2         # finite-difference directions d ~ CN(0, I)
 SEED_ROWS = 7       # sampled rows for exact residual checks
+SEED_SHADOW = 11    # TFQMR shadow vector r* ~ CN(0, I)
