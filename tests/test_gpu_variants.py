@@ -1,0 +1,84 @@
+"""GPU parity for the construction variants, through the C ABI: the exact-leaf-LU
+preconditioner (HB_OPT_LEAF_LU) and explicitly given curves (HB_POLYLINE).
+
+Tolerances (stated per test):
+* device sweeps vs the host interpreter of the same packed factor, FP64 on both
+  sides: 1e-12 (summation order only);
+* FP64 compressed apply vs the oracle's dense Z: 10 eps relative (eps = 1e-6);
+* GMRES solutions vs the oracle's dense LU solve: 1e-5 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import dense, efie
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hb():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_11371_gb300 import build
+    build.build()
+    import paper_1901_11371_gb300 as hb
+    return hb
+
+
+def _t(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _sweeps_match_host(hb, f, fh, n, seed):
+    b = W.complex_gaussian(n, seed)
+    for which, fn, op in ((0, hb.hb_lower_solve, hb.HB_OP_N), (1, hb.hb_upper_solve, hb.HB_OP_N),
+                          (2, hb.hb_lower_solve, hb.HB_OP_H), (3, hb.hb_upper_solve, hb.HB_OP_H)):
+        x = fn(f, _t(b), op).cpu().numpy()
+        assert _rel(x, hb.hb_host_sweep(fh, b, which)) <= 1e-12, which
+
+
+def test_leaf_lu_factor_on_the_device(hb):
+    wl = W.CONFIG1
+    g = hb.hb_geometry(wl.kind, wl.params, wl.n)
+    f = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C128, options=hb.HB_OPT_LEAF_LU)
+    fh = hb.hb_factor_host(g, wl.leaf, wl.eps, options=hb.HB_OPT_LEAF_LU)
+    _sweeps_match_host(hb, f, fh, wl.n, 41)
+    p = efie.Problem.from_workload(wl)
+    b = hb.hb_rhs_plane_wave(f, [30.0])
+    x, info = hb.hb_gmres(f, b, rtol=1e-6, restart=30, maxit=500)
+    x_lu = dense.solve(p.dense(), p.plane_wave(30.0)[:, 0] * p.scale)
+    assert info["true_rel_res"] <= 1e-6
+    assert _rel(x.cpu().numpy()[0], x_lu) <= 1e-5
+
+
+def test_polyline_factor_on_the_device(hb):
+    # two sine-modulated open curves of 512 segments each
+    n_per = 512
+    t = np.arange(n_per + 1) / n_per
+    c0 = np.stack([25.6 * t, 1.5 * np.sin(2 * math.pi * 3 * t)], axis=1)
+    c1 = np.stack([25.6 * t, 6.0 + 0.8 * np.cos(2 * math.pi * 2 * t)], axis=1)
+    nodes, starts = np.concatenate([c0, c1]), [0, n_per + 1]
+    n, eps = 2 * n_per, 1e-6
+    g = hb.hb_geometry_polyline(nodes, starts)
+    f = hb.hb_factor(g, 32, eps, form=hb.HB_C128)
+    fh = hb.hb_factor_host(g, 32, eps)
+    p = efie.Problem(W.POLYLINE, (nodes, starts), n)
+    a = p.dense()
+    x = W.complex_gaussian(n, 42)
+    assert _rel(hb.hb_apply(f, _t(x)).cpu().numpy(), a @ x) <= 10 * eps
+    _sweeps_match_host(hb, f, fh, n, 43)
+    b = hb.hb_rhs_plane_wave(f, [30.0])
+    np.testing.assert_allclose(b.cpu().numpy()[0], p.plane_wave(30.0)[:, 0], atol=1e-12)
+    xs, info = hb.hb_gmres(f, b, rtol=1e-6, restart=30, maxit=500)
+    x_lu = dense.solve(a, p.plane_wave(30.0)[:, 0] * p.scale)
+    assert info["true_rel_res"] <= 1e-6
+    assert _rel(xs.cpu().numpy()[0], x_lu) <= 1e-5
