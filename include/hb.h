@@ -214,6 +214,27 @@ int hb_residual(hb_factor_t f, int op, const void* b, const void* x, void* r, in
 int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int64_t nrhs, int64_t ld, int restart,
              double rtol, int maxit, hb_gmres_info* info, void* stream);
 
+/* hb_tfqmr -- solve A x = b_phys (complex128, physical excitation, as for
+ * hb_gmres) with transpose-free QMR, the Krylov solver of Sec. 4, on the
+ * split-preconditioned system (Eqs. (Axb2), (Axb3)): FP64 factors (HB_C128)
+ * only.  rstar: the shadow vectors r* of the Lanczos biorthogonalisation,
+ * complex128 device block laid out like b (nrhs columns, leading dimension
+ * ld), caller-owned and not modified; NULL takes r* = L~^{-1} b^ (the paper
+ * does not name one; on the split EFIE systems that choice can meet a
+ * near-breakdown and stall near 1e-5, while a random r* converges in about as
+ * many operator products as GMRES(30) takes iterations).  Columns run in
+ * lockstep with their own scalars; each half step costs at most one product
+ * with L~^{-1} A U~^{-1} (two per pair of half steps).  When the quasi-residual
+ * bound tau sqrt(m+1) reaches rtol ||L~^{-1} b^|| the FP64 true residual
+ * ||b^ - A^_F x||/||b^|| is formed; a column stops once it is <= rtol.  info:
+ * iters = half steps, restarts = true-residual checks, precond_rel_res = the
+ * largest final bound relative to ||L~^{-1} b^||.  x is overwritten;
+ * synchronises `stream` before returning; info may be NULL.
+ * Errors: HB_EINVAL, HB_EUNSUPPORTED (not HB_C128), HB_ENAN (non-finite b or
+ * rstar), HB_ENOCONV (maxit half steps or a breakdown; info still filled). */
+int hb_tfqmr(hb_factor_t f, int op, const void* b_phys, const void* rstar, void* x, int64_t nrhs, int64_t ld,
+             double rtol, int maxit, hb_gmres_info* info, void* stream);
+
 /* hb_rhs_plane_wave -- b_i = exp(-i k (x_i cos phi + y_i sin phi)) (the
  * incident field E^inc_z(rho_i) of Sec. 3.1, physical, unscaled) for nrhs
  * angles phi_deg (host array, degrees) into the complex128 device block b. */

@@ -22,7 +22,7 @@ __all__ = ["HB_STRIP", "HB_SPIRAL", "HB_ARC", "HB_PARALLEL_STRIPS", "HB_POLYLINE
            "HB_SPLIT_BF16", "HB_OP_N", "HB_OP_H", "HB_OPT_LEAF_LU", "HBError", "Geometry", "Factor", "hb_geometry",
            "hb_geometry_polyline", "hb_factor", "hb_factor_host",
            "hb_factor_info", "hb_tree", "hb_apply", "hb_apply_adjoint", "hb_precond_solve", "hb_lower_solve",
-           "hb_upper_solve", "hb_residual", "hb_gmres", "hb_rhs_plane_wave", "hb_far_field", "hb_monostatic",
+           "hb_upper_solve", "hb_residual", "hb_gmres", "hb_tfqmr", "hb_rhs_plane_wave", "hb_far_field", "hb_monostatic",
            "hb_host_apply", "hb_host_sweep", "hb_far_field_adjoint", "hb_profile", "hb_profile_read", "hb_autotune", "hb_autotune_times", "lib"]
 
 
@@ -203,6 +203,31 @@ def hb_gmres(f, b_phys, op=HB_OP_N, restart=30, rtol=1e-6, maxit=1000, out=None,
     d = dict(iters=info.iters, restarts=info.restarts, ir_steps=info.ir_steps, converged=info.converged,
              true_rel_res=info.true_rel_res, precond_rel_res=info.precond_rel_res, seconds=info.seconds,
              iters_per_rhs=list(it), res_per_rhs=list(rr), status=rc)
+    if check and rc not in (_lib.HB_OK,):
+        _lib.check(rc)
+    return x, d
+
+
+def hb_tfqmr(f, b_phys, rstar=None, op=HB_OP_N, rtol=1e-6, maxit=2000, out=None, stream=None, check=True):
+    """TFQMR (Sec. 4) on the split system; rstar: shadow vectors shaped like b (None: L~^{-1} b).
+    Returns (x, info dict); info["iters"] counts half steps."""
+    import torch
+    b, R = _block(b_phys, f.n, torch.complex128)
+    rs = None
+    if rstar is not None:
+        rs, R2 = _block(rstar, f.n, torch.complex128)
+        if R2 != R:
+            raise HBError(_lib.HB_EINVAL, "rstar must have the shape of b")
+    x = torch.empty_like(b) if out is None else out
+    info = _lib.GmresInfo()
+    it = (C.c_int32 * R)()
+    rr = (C.c_double * R)()
+    info.iters_per_rhs = C.cast(it, C.POINTER(C.c_int32))
+    info.res_per_rhs = C.cast(rr, C.POINTER(C.c_double))
+    rc = lib().hb_tfqmr(f._h, int(op), C.c_void_p(b.data_ptr()), C.c_void_p(rs.data_ptr() if rs is not None else None),
+                        C.c_void_p(x.data_ptr()), R, f.n, float(rtol), int(maxit), C.byref(info), _stream(stream))
+    d = dict(iters=info.iters, checks=info.restarts, converged=info.converged, true_rel_res=info.true_rel_res,
+             bound=info.precond_rel_res, seconds=info.seconds, iters_per_rhs=list(it), res_per_rhs=list(rr), status=rc)
     if check and rc not in (_lib.HB_OK,):
         _lib.check(rc)
     return x, d

@@ -66,6 +66,7 @@ SIGNATURES = {
     "hb_upper_solve": (_INT, [_VP, _INT, _VP, _VP, _I64, _I64, _VP]),
     "hb_residual": (_INT, [_VP, _INT, _VP, _VP, _VP, _I64, _I64, _VP]),
     "hb_gmres": (_INT, [_VP, _INT, _VP, _VP, _I64, _I64, _INT, _DBL, _INT, C.POINTER(GmresInfo), _VP]),
+    "hb_tfqmr": (_INT, [_VP, _INT, _VP, _VP, _VP, _I64, _I64, _DBL, _INT, C.POINTER(GmresInfo), _VP]),
     "hb_rhs_plane_wave": (_INT, [_VP, C.POINTER(C.c_double), _I64, _VP, _I64, _VP]),
     "hb_far_field": (_INT, [_VP, _VP, _I64, _I64, C.POINTER(C.c_double), _I64, _VP, _VP]),
     "hb_far_field_adjoint": (_INT, [_VP, _VP, _I64, C.POINTER(C.c_double), _I64, _VP, _I64, _VP]),

@@ -152,6 +152,16 @@ __global__ void k_add_combo(const S* __restrict__ Z, int64_t zstride, int nvec, 
   }
 }
 
+// y[row][r] = x[row][r] + s[r] y[row][r]  (complex per-column s; TFQMR direction updates)
+__global__ void k_xpay(const double2* __restrict__ x, const double2* __restrict__ s, double2* __restrict__ y,
+                       int64_t n, int64_t R) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e < n * R; e += (int64_t)gridDim.x * blockDim.x) {
+    const double2 c = s[e % R], yy = y[e], xx = x[e];
+    y[e] = {xx.x + c.x * yy.x - c.y * yy.y, xx.y + c.x * yy.y + c.y * yy.x};
+  }
+}
+
 // r[e] -= a[e]  (a complex FP32, r FP64)
 __global__ void k_sub_f32(const float2* __restrict__ a, double2* __restrict__ r, int64_t total) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -624,6 +634,203 @@ extern "C" int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int6
     if (rpr) for (int64_t c = 0; c < R; ++c) rpr[c] = res_r[c];
   }
   if (nconv < R) { set_error("hb_gmres: %d of %lld columns did not reach rtol in %d iterations", (int)(R - nconv), (long long)R, iters); return HB_ENOCONV; }
+  return HB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// TFQMR (the solver of Sec. 4): Freund's transpose-free QMR on the split system
+// L'^{-1} A U'^{-1} y = L'^{-1} b, x = U'^{-1} y, FP64 form, right-hand sides in
+// lockstep with per-column scalars.  Half step m (even: a new alpha = rho /
+// <r*, v> and the first direction u; odd: the second direction u - alpha v)
+// updates the squared residual w, the QMR direction d and the iterate (theta,
+// c, tau, eta); after an odd step rho' = <r*, w>, beta = rho' / rho,
+// u = w + beta u_2 and v = A u + beta (A u_2 + beta v).  tau sqrt(m + 1)
+// bounds the split residual; when it reaches rtol ||L'^{-1} b|| the true
+// residual is formed and the bound tightened if it misses.  Columns that have
+// converged (or broken down) get zero coefficients and stay frozen.
+// ---------------------------------------------------------------------------
+extern "C" int hb_tfqmr(hb_factor_t f, int op, const void* b_phys, const void* rstar, void* x, int64_t nrhs,
+                        int64_t ld, double rtol, int maxit, hb_gmres_info* info, void* stream) {
+  int rc = check_vec_args(f, b_phys, x, nrhs, ld, "hb_tfqmr");
+  if (rc) return rc;
+  if (op != HB_OP_N && op != HB_OP_H) { set_error("hb_tfqmr: bad op"); return HB_EINVAL; }
+  if (!(rtol > 0) || maxit < 1) { set_error("hb_tfqmr: bad rtol/maxit"); return HB_EINVAL; }
+  if (rstar == x) { set_error("hb_tfqmr: rstar and x must not alias"); return HB_EINVAL; }
+  if (f->df.form != HB_C128) { set_error("hb_tfqmr: needs an FP64 factor (HB_C128)"); return HB_EUNSUPPORTED; }
+  cudaStream_t st = (cudaStream_t)stream;
+  auto t0 = std::chrono::steady_clock::now();
+  if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("hb_tfqmr: stream error"); return HB_ECUDA; }
+  const DevFactor& df = f->df;
+  const int64_t n = df.n, R = nrhs, nR = n * R;
+  const bool adj = op == HB_OP_H;
+  const int lo = adj ? 3 : 0, up = adj ? 2 : 1;
+  const size_t vbytes = (size_t)nR * sizeof(double2);
+  Workspace& ws = f->ws;
+  double2* bh = (double2*)ws.get(WS_VEC2, vbytes);
+  double2* y = (double2*)ws.get(WS_VEC3, vbytes);
+  double2* t1 = (double2*)ws.get(WS_VEC0, vbytes);
+  double2* t2 = (double2*)ws.get(WS_VEC1, vbytes);
+  double2* blk = (double2*)ws.get(WS_BASIS, vbytes * 8);
+  double2* red = (double2*)ws.get(WS_RED, ((size_t)kRedBlocks * R + 6 * (size_t)R) * sizeof(double2));
+  int* flag = (int*)ws.get(WS_SMALL, 256);
+  if (!bh || !y || !t1 || !t2 || !blk || !red || !flag) { set_error("hb_tfqmr: workspace allocation failed"); return HB_ENOMEM; }
+  double2 *w = blk, *u = blk + nR, *v = blk + 2 * nR, *au = blk + 3 * nR, *dd = blk + 4 * nR, *rs = blk + 5 * nR,
+          *u2 = blk + 6 * nR, *rr = blk + 7 * nR;
+  Dev d{f, st, n, R, red, red + (size_t)kRedBlocks * R, (double*)(red + (size_t)kRedBlocks * R + R)};
+  double2* coef = red + (size_t)kRedBlocks * R + 2 * R;   // 4 x R per-column coefficients
+
+  // non-finite inputs
+  cudaMemsetAsync(flag, 0, sizeof(int), st);
+  k_nonfinite<<<gsz(nR), 256, 0, st>>>((const double2*)b_phys, ld, n, R, flag); count_launch(f, 1);
+  if (rstar) { k_nonfinite<<<gsz(nR), 256, 0, st>>>((const double2*)rstar, ld, n, R, flag); count_launch(f, 1); }
+  int hflag = 0;
+  cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("hb_tfqmr: CUDA error"); return HB_ECUDA; }
+  if (hflag) { set_error("hb_tfqmr: b or rstar contains NaN/Inf"); return HB_ENAN; }
+
+  // w = u = L'^{-1} b^,  r* (caller's, else w),  y = d = 0,  v = A u
+  auto opf = [&](const double2* z, double2* out) -> int {   // out = L'^{-1} A U'^{-1} z
+    int e;
+    cudaMemcpyAsync(t1, z, vbytes, cudaMemcpyDeviceToDevice, st);
+    if ((e = sweep_internal(f, PREC_F64, up, t1, R, st))) return e;
+    if ((e = apply_internal(f, PREC_F64, adj, t1, out, R, st))) return e;
+    return sweep_internal(f, PREC_F64, lo, out, R, st);
+  };
+  auto upload = [&](const std::vector<zc>& c, int slot) -> double2* {
+    double2* dst = coef + (size_t)slot * R;
+    cudaMemcpyAsync(dst, c.data(), R * sizeof(double2), cudaMemcpyHostToDevice, st);
+    return dst;
+  };
+  if ((rc = launch_gather_cols(b_phys, 0, ld, n, R, bh, 0, df.scale, st))) return rc;
+  std::vector<double> bnorm, tau;
+  if ((rc = norms(d, bh, bnorm))) return rc;
+  cudaMemcpyAsync(w, bh, vbytes, cudaMemcpyDeviceToDevice, st);
+  if ((rc = sweep_internal(f, PREC_F64, lo, w, R, st))) return rc;
+  cudaMemcpyAsync(u, w, vbytes, cudaMemcpyDeviceToDevice, st);
+  if (rstar) { if ((rc = launch_gather_cols(rstar, 0, ld, n, R, rs, 0, 1.0, st))) return rc; }
+  else cudaMemcpyAsync(rs, w, vbytes, cudaMemcpyDeviceToDevice, st);
+  cudaMemsetAsync(y, 0, vbytes, st);
+  cudaMemsetAsync(dd, 0, vbytes, st);
+  if ((rc = opf(u, v))) return rc;
+  cudaMemcpyAsync(au, v, vbytes, cudaMemcpyDeviceToDevice, st);
+  if ((rc = norms(d, w, tau))) return rc;
+  std::vector<zc> rho, alpha(R, zc(0.0)), eta(R, zc(0.0)), cz(R);
+  if ((rc = dots(d, rs, 0, 1, w, rho))) return rc;
+  std::vector<double> theta(R, 0.0), target(R), res_r(R, 1.0), bound(R, 1.0), tau0(tau), rn;
+  std::vector<char> active(R, 1), broken(R, 0);
+  std::vector<int32_t> it_r(R, 0);
+  for (int64_t c = 0; c < R; ++c) {
+    target[c] = rtol * tau[c];
+    if (!(bnorm[c] > 0)) { active[c] = 0; res_r[c] = 0.0; bound[c] = 0.0; }
+  }
+  auto true_residual = [&]() -> int {   // res_r = ||b^ - A U'^{-1} y|| / ||b^||
+    int e;
+    cudaMemcpyAsync(t2, y, vbytes, cudaMemcpyDeviceToDevice, st);
+    if ((e = sweep_internal(f, PREC_F64, up, t2, R, st))) return e;
+    if ((e = apply_internal(f, PREC_F64, adj, t2, t1, R, st))) return e;
+    k_sub_into<<<gsz(nR), 256, 0, st>>>(bh, t1, rr, nR); count_launch(f, 1);
+    if ((e = norms(d, rr, rn))) return e;
+    for (int64_t c = 0; c < R; ++c) res_r[c] = bnorm[c] > 0 ? rn[c] / bnorm[c] : 0.0;
+    return HB_OK;
+  };
+  auto n_active = [&]() { int k = 0; for (int64_t c = 0; c < R; ++c) k += active[c]; return k; };
+  int m = 0, checks = 0;
+  while (m < maxit && n_active() > 0) {
+    const bool even = (m % 2) == 0;
+    double2* cur = u;
+    if (even) {
+      std::vector<zc> sig;
+      if ((rc = dots(d, rs, 0, 1, v, sig))) return rc;
+      for (int64_t c = 0; c < R; ++c) {
+        if (!active[c]) { alpha[c] = 0.0; continue; }
+        if (!(std::abs(sig[c]) > 0) || !std::isfinite(std::abs(sig[c])) || !(std::abs(rho[c]) > 0)) {
+          active[c] = 0; broken[c] = 1; alpha[c] = 0.0; continue;   // Lanczos breakdown
+        }
+        alpha[c] = rho[c] / sig[c];
+      }
+      cudaMemcpyAsync(u2, u, vbytes, cudaMemcpyDeviceToDevice, st);      // u2 = u - alpha v
+      k_sub_combo<double2><<<gsz(nR), 256, 0, st>>>(v, 0, 1, upload(alpha, 0), u2, n, R); count_launch(f, 1);
+    } else {
+      cur = u2;
+      if ((rc = opf(u2, au))) return rc;                                  // au = A u2
+    }
+    for (int64_t c = 0; c < R; ++c) cz[c] = active[c] ? alpha[c] : zc(0.0);
+    k_sub_combo<double2><<<gsz(nR), 256, 0, st>>>(au, 0, 1, upload(cz, 1), w, n, R); count_launch(f, 1);   // w -= alpha A cur
+    for (int64_t c = 0; c < R; ++c) cz[c] = active[c] ? theta[c] * theta[c] * eta[c] / alpha[c] : zc(0.0);
+    k_xpay<<<gsz(nR), 256, 0, st>>>(cur, upload(cz, 2), dd, n, R); count_launch(f, 1);                      // d = cur + s d
+    std::vector<double> wn;
+    if ((rc = norms(d, w, wn))) return rc;
+    for (int64_t c = 0; c < R; ++c) {
+      if (!active[c]) { cz[c] = 0.0; continue; }
+      theta[c] = wn[c] / tau[c];
+      const double cc = 1.0 / std::sqrt(1.0 + theta[c] * theta[c]);
+      tau[c] *= theta[c] * cc;
+      eta[c] = cc * cc * alpha[c];
+      cz[c] = eta[c];
+    }
+    k_add_combo<double2><<<gsz(nR), 256, 0, st>>>(dd, 0, 1, upload(cz, 3), y, n, R); count_launch(f, 1);   // y += eta d
+    if (!even) {
+      std::vector<zc> rho_new, beta(R, zc(0.0));
+      if ((rc = dots(d, rs, 0, 1, w, rho_new))) return rc;
+      for (int64_t c = 0; c < R; ++c) {
+        if (!active[c]) continue;
+        beta[c] = rho_new[c] / rho[c];   // rho != 0: checked when alpha was formed
+        rho[c] = rho_new[c];
+      }
+      double2* bz = upload(beta, 0);
+      k_xpay<<<gsz(nR), 256, 0, st>>>(w, bz, u2, n, R); count_launch(f, 1);    // u2 = w + beta u2: the new u
+      std::swap(u, u2);
+      k_xpay<<<gsz(nR), 256, 0, st>>>(au, bz, v, n, R); count_launch(f, 1);    // v = A u2_old + beta v
+      if ((rc = opf(u, au))) return rc;                                         // au = A u
+      k_xpay<<<gsz(nR), 256, 0, st>>>(au, bz, v, n, R); count_launch(f, 1);    // v = A u + beta v
+    }
+    ++m;
+    bool check = false;
+    for (int64_t c = 0; c < R; ++c) {
+      if (!active[c]) continue;
+      it_r[c] = m;
+      bound[c] = tau[c] * std::sqrt(m + 1.0) / tau0[c];
+      if (tau[c] * std::sqrt(m + 1.0) <= target[c]) check = true;
+    }
+    if (check) {
+      if ((rc = true_residual())) return rc;
+      ++checks;
+      for (int64_t c = 0; c < R; ++c) {
+        if (!active[c]) continue;
+        if (res_r[c] <= rtol) active[c] = 0;
+        else if (!(tau[c] > 0)) { active[c] = 0; broken[c] = 1; }   // w = 0 but x misses rtol
+        else if (tau[c] * std::sqrt(m + 1.0) <= target[c]) target[c] *= std::min(0.5, rtol / res_r[c]);
+      }
+    }
+  }
+  // report the final true residual of every column, return x = U'^{-1} y
+  if ((rc = true_residual())) return rc;
+  if ((rc = launch_scatter_cols(t2, 0, n, R, x, 0, ld, 1.0, st))) return rc;
+  if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("hb_tfqmr: CUDA error"); return HB_ECUDA; }
+  int nconv = 0, nbroken = 0;
+  double worst = 0.0, worst_b = 0.0;
+  for (int64_t c = 0; c < R; ++c) {
+    nconv += res_r[c] <= rtol;
+    nbroken += broken[c];
+    worst = std::max(worst, res_r[c]);
+    worst_b = std::max(worst_b, bound[c]);
+  }
+  if (info) {
+    info->iters = m;
+    info->restarts = checks;
+    info->ir_steps = 0;
+    info->converged = nconv;
+    info->true_rel_res = worst;
+    info->precond_rel_res = worst_b;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info->iters_per_rhs) for (int64_t c = 0; c < R; ++c) info->iters_per_rhs[c] = it_r[c];
+    if (info->res_per_rhs) for (int64_t c = 0; c < R; ++c) info->res_per_rhs[c] = res_r[c];
+  }
+  if (nconv < R) {
+    set_error("hb_tfqmr: %d of %lld columns did not reach rtol in %d half steps (%d broke down)", (int)(R - nconv),
+              (long long)R, m, nbroken);
+    return HB_ENOCONV;
+  }
   return HB_OK;
 }
 

@@ -60,6 +60,8 @@ def test_error_paths_without_gpu(hb):
     # device entry points refuse a host-only factor (no silent CPU path)
     assert lib.hb_apply(f._h, 0, C.c_void_p(8), C.c_void_p(16), 1, 64, None) == hb._lib.HB_EINVAL
     assert b"no device image" in lib.hb_last_error()
+    assert lib.hb_tfqmr(f._h, 0, C.c_void_p(8), None, C.c_void_p(16), 1, 64, 1e-6, 10, None, None) == hb._lib.HB_EINVAL
+    assert b"no device image" in lib.hb_last_error()
 
 
 @pytest.mark.parametrize("cfg", [1, 2, 3, 4])

@@ -1,11 +1,11 @@
-"""GPU parity for the construction variants, through the C ABI: the exact-leaf-LU
-preconditioner (HB_OPT_LEAF_LU) and explicitly given curves (HB_POLYLINE).
+"""GPU parity for the variants, through the C ABI: the exact-leaf-LU preconditioner
+(HB_OPT_LEAF_LU), explicitly given curves (HB_POLYLINE) and the TFQMR solver of Sec. 4.
 
 Tolerances (stated per test):
 * device sweeps vs the host interpreter of the same packed factor, FP64 on both
   sides: 1e-12 (summation order only);
 * FP64 compressed apply vs the oracle's dense Z: 10 eps relative (eps = 1e-6);
-* GMRES solutions vs the oracle's dense LU solve: 1e-5 relative.
+* GMRES and TFQMR solutions vs the oracle's dense LU solve: 1e-5 relative.
 """
 import math
 
@@ -82,3 +82,43 @@ def test_polyline_factor_on_the_device(hb):
     x_lu = dense.solve(a, p.plane_wave(30.0)[:, 0] * p.scale)
     assert info["true_rel_res"] <= 1e-6
     assert _rel(xs.cpu().numpy()[0], x_lu) <= 1e-5
+
+
+@pytest.fixture(scope="module")
+def strip_tfqmr(hb):
+    wl = W.CONFIG1
+    g = hb.hb_geometry(wl.kind, wl.params, wl.n)
+    p = efie.Problem.from_workload(wl)
+    return dict(wl=wl, p=p, a=p.dense(), f=hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C128),
+                f32=hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C64))
+
+
+def test_tfqmr_matches_dense_lu(hb, strip_tfqmr):
+    # Sec. 4's solver on the device, three plane waves in lockstep, random shadow vectors
+    p, a, f = strip_tfqmr["p"], strip_tfqmr["a"], strip_tfqmr["f"]
+    angles = [0.0, 30.0, 75.0]
+    b = hb.hb_rhs_plane_wave(f, angles)
+    rs = _t(W.complex_gaussian(1024, W.SEED_SHADOW, 3).T)
+    x, info = hb.hb_tfqmr(f, b, rstar=rs, rtol=1e-6, maxit=400)
+    assert info["converged"] == 3 and info["true_rel_res"] <= 1e-6
+    xs = x.cpu().numpy()
+    for c, phi in enumerate(angles):
+        x_lu = dense.solve(a, p.plane_wave(phi)[:, 0] * p.scale)
+        assert _rel(xs[c], x_lu) <= 1e-5, phi
+        assert info["res_per_rhs"][c] <= 1e-6
+    assert max(info["iters_per_rhs"]) < 80          # half steps (one operator product each)
+
+
+def test_tfqmr_adjoint_and_errors(hb, strip_tfqmr):
+    p, a, f = strip_tfqmr["p"], strip_tfqmr["a"], strip_tfqmr["f"]
+    b = W.complex_gaussian(1024, 44)
+    rs = _t(W.complex_gaussian(1024, W.SEED_SHADOW)[None, :])
+    x, info = hb.hb_tfqmr(f, _t(b[None, :]), rstar=rs, op=hb.HB_OP_H, rtol=1e-8, maxit=600)
+    assert info["true_rel_res"] <= 1e-8
+    assert _rel(x.cpu().numpy()[0], dense.solve(a.conj().T, b * p.scale)) <= 1e-5
+    with pytest.raises(hb.HBError):
+        hb.hb_tfqmr(strip_tfqmr["f32"], _t(b[None, :]))             # FP64 factors only
+    bad = b.copy()
+    bad[7] = np.nan
+    with pytest.raises(hb.HBError):
+        hb.hb_tfqmr(f, _t(bad[None, :]), rstar=rs)
