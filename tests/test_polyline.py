@@ -128,3 +128,22 @@ def test_oracle_arc_array_preconditioned_gmres():
     ident = lambda v: v
     _, info0 = krylov.gmres_split(lambda z: a @ z, ident, ident, b, rtol=1e-6)
     assert info0["iters"] >= 3 * info["iters"]
+
+
+def test_host_factor_of_a_graded_strip_within_10eps(hb):
+    # Non-uniform segments: a strip with cosine-graded nodes (segments ~150x shorter at the
+    # edges than in the middle), a common refinement toward the edge singularity of the
+    # current.  The compressed operator stays within 10 eps of the dense EFIE matrix.
+    n = 1024
+    x = 25.6 * 0.5 * (1.0 - np.cos(math.pi * np.arange(n + 1) / n))
+    nodes = np.stack([x, np.zeros(n + 1)], axis=1)
+    c, w = geometry.polyline_segments(nodes)
+    assert w.max() / w.min() > 100
+    g = hb.hb_geometry_polyline(nodes)
+    eps = 1e-6
+    f = hb.hb_factor_host(g, 32, eps)
+    a = efie.Problem(W.POLYLINE, (nodes, [0]), n).dense()
+    for seed in (7, 8):
+        v = W.complex_gaussian(n, seed)
+        ref = a @ v
+        assert np.linalg.norm(hb.hb_host_apply(f, v) - ref) / np.linalg.norm(ref) <= 10 * eps
