@@ -131,7 +131,7 @@ def test_oracle_arc_array_preconditioned_gmres():
 
 
 def test_host_factor_of_a_graded_strip_within_10eps(hb):
-    # Non-uniform segments: a strip with cosine-graded nodes (segments ~150x shorter at the
+    # Non-uniform segments: a strip with cosine-graded nodes (segments ~650x shorter at the
     # edges than in the middle), a common refinement toward the edge singularity of the
     # current.  The compressed operator stays within 10 eps of the dense EFIE matrix.
     n = 1024
