@@ -17,11 +17,15 @@
  *  - Vectors are DEVICE pointers owned by the caller, column-major blocks of
  *    nrhs columns with leading dimension ld >= N (elements).  Element type:
  *    complex128 (interleaved double pairs) for form HB_C128 and for every
- *    FP64 outer vector (hb_gmres, hb_residual, hb_rhs_plane_wave); complex64
+ *    FP64 outer vector (hb_gmres, hb_tfqmr, hb_residual, hb_rhs_plane_wave); complex64
  *    (interleaved float pairs) for hb_apply / hb_precond_solve of the
  *    HB_C64 and HB_SPLIT_BF16 forms.
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
  *    asynchronous on that stream unless stated otherwise.
+ *  - A factor handle owns the device workspaces its calls use (grown on
+ *    demand, freed by hb_factor_destroy): calls on one handle must not
+ *    overlap on the GPU (issue them on one stream, or serialise them);
+ *    different handles are independent.
  *  - Unknowns follow the geometric order of the curve (Sec. 3.3.1); the
  *    operator acted on by hb_apply / hb_precond_solve is the RESCALED
  *    A^ = a A with a = 1 / max_i |A_ii| (Sec. 3.1 and Sec. 4).
