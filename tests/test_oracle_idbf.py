@@ -1,5 +1,6 @@
-"""Pins for the oracle's IDs, butterflies, H-IDBF apply/sweeps and GMRES (Secs. 2-3, Appendix)."""
+"""Pins for the oracle's IDs, butterflies, H-IDBF apply/sweeps, GMRES and TFQMR (Secs. 2-4, Appendix)."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -204,3 +205,38 @@ def test_tfqmr_split_preconditioned_strip(strip1024):
     assert info["true_rel_res"] <= 1e-6
     assert np.linalg.norm(x - x_lu) / np.linalg.norm(x_lu) <= 1e-5
     assert info["matvecs"] < 80
+
+
+def _paper_errors(golden_dir):
+    vals = {}
+    with open(os.path.join(golden_dir, "paper_solution_error_n5e3.txt")) as f:
+        for line in f:
+            parts = line.split("#")[0].split()
+            if parts:
+                vals[parts[0]] = float(parts[1])
+    return vals
+
+
+@pytest.mark.parametrize("shape", ["semicircle", "spiral"])
+def test_solution_error_has_the_papers_order(golden_dir, shape):
+    # Sec. 4's accuracy protocol on the oracle: random x^t, b = F x^t with the compressed F
+    # (eps = 1e-4), TFQMR to 1e-5 on the split system.  The solution error lands within a
+    # factor 5 of the paper's N = 5E3 value (here N = 2048, leaf 128; the spiral makes one
+    # turn from theta = 2 pi; the paper states neither size).  A wrong sign or term in the
+    # apply or the sweeps would leave it far larger.
+    n = 2048
+    if shape == "semicircle":
+        params, kind = (n / 20 / math.pi, 0.0, math.pi), W.ARC
+    else:
+        s = lambda t: 0.5 * (t * math.sqrt(1 + t * t) + math.asinh(t))
+        t0, t1 = 2 * math.pi, 4 * math.pi
+        params, kind = ((n / 20.0) / (s(t1) - s(t0)), t0, t1), W.SPIRAL
+    a = efie.Problem(kind, params, n).dense()
+    h = idbf.HIDBF(a, 128, 1e-4)
+    xt = W.complex_gaussian(n, W.SEED_XTRUE)
+    x, info = krylov.tfqmr_split(h.apply, h.solve_lower, h.solve_upper, h.apply(xt),
+                                 rstar=W.complex_gaussian(n, W.SEED_SHADOW), rtol=1e-5)
+    err = np.linalg.norm(x - xt) / np.linalg.norm(xt)
+    paper = _paper_errors(golden_dir)[shape]
+    assert paper / 5 <= err <= 5 * paper, (err, paper)
+    assert info["matvecs"] < 60
