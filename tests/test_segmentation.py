@@ -1,7 +1,9 @@
-"""Host logic of the sweep programs (no GPU): flattening, staging offsets and the
+"""Host logic of the sweep programs (no GPU): flattening, staging offsets, the
 segmentation into grid-wide phases and single-CTA runs (coverage, thresholds,
-residency budgets, butterfly state produced and consumed inside resident runs).
-The checks live in tests/segcheck.cpp, built here against the library's host code."""
+residency budgets, butterfly state produced and consumed inside resident runs), and
+the flattened records executed the way the sweep kernel reads them against the host
+interpreter (strip, arc, leaf-LU and polyline factors).  The checks live in
+tests/segcheck.cpp, built here against the library's host code."""
 import os
 import shutil
 import subprocess
