@@ -63,12 +63,12 @@ def oracle_sample(steps=1, warmup=0):
     """Time the oracle's split-preconditioned GMRES solve on the N=SAMPLE_N member of the
     curve family; scale the per-solve time to the full N by the N log^2 N cost of one iteration."""
     from oracle import efie, idbf, krylov
-    wl = W.CONFIG3
+    wl = W.SEMICIRCLE_N262144
     params = _arc_params(SAMPLE_N)
     p = efie.Problem(W.ARC, params, SAMPLE_N)
     a = p.dense()
     h = idbf.HIDBF(a, wl.leaf, wl.eps)
-    phi = W.incidence_angles_deg(3)[17:18]
+    phi = W.incidence_angles_deg(W.SEMICIRCLE_N262144)[17:18]
     b = p.plane_wave(phi)[:, 0] * p.scale
     times, iters = [], []
     for s in range(warmup + steps):
@@ -160,7 +160,7 @@ def shard_angles(rank, world):
     rank r's angles offset by r * 180 / (NRHS * world) so that the ranks' sets interleave
     without overlap (replicas of the factor, right-hand sides sharded; no collective on the
     data path)."""
-    base = W.incidence_angles_deg(3)
+    base = W.incidence_angles_deg(W.SEMICIRCLE_N262144)
     return base + (rank * 180.0 / NRHS / world if world > 1 else 0.0)
 
 
@@ -185,7 +185,7 @@ def run_gpu(args, rank, world):
         torch.distributed.barrier()
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    wl = W.CONFIG3
+    wl = W.SEMICIRCLE_N262144
     stream = torch.cuda.current_stream()
     g = hb.hb_geometry(wl.kind, wl.params, wl.n)
     t0 = time.perf_counter()
@@ -290,7 +290,7 @@ def run_kernels(args):
     import paper_1901_11371_gb300 as hb
     from paper_1901_11371_gb300 import build as hb_build
     hb_build.build()
-    wl = {"spiral": W.CONFIG2, "semicircle": W.CONFIG3, "strips": W.CONFIG4, "strip": W.CONFIG1}[args.workload]
+    wl = {"spiral": W.SPIRAL_N65536, "semicircle": W.SEMICIRCLE_N262144, "strips": W.STRIPS8_N131072, "strip": W.STRIP_N1024}[args.workload]
     R = args.nrhs
     g = hb.hb_geometry(wl.kind, wl.params, wl.n)
     f = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C64 if args.form == "c64" else hb.HB_C128)

@@ -64,9 +64,9 @@ def test_error_paths_without_gpu(hb):
     assert b"no device image" in lib.hb_last_error()
 
 
-@pytest.mark.parametrize("cfg", [1, 2, 3, 4])
-def test_geometry_matches_oracle(hb, cfg):
-    wl = W.CONFIGS[cfg]
+@pytest.mark.parametrize("name", ["strip_N1024", "spiral_N65536", "semicircle_N262144", "strips8_N131072"])
+def test_geometry_matches_oracle(hb, name):
+    wl = W.WORKLOADS[name]
     n = min(wl.n, 8192) if wl.kind != W.PARALLEL_STRIPS else 8192
     params = wl.params
     if wl.kind == W.SPIRAL or wl.kind == W.ARC:
@@ -80,7 +80,7 @@ def test_geometry_matches_oracle(hb, cfg):
 
 
 def test_tree_bit_exact(hb):
-    wl = W.CONFIG1
+    wl = W.STRIP_N1024
     g = hb.hb_geometry(wl.kind, wl.params, wl.n)
     f = hb.hb_factor_host(g, wl.leaf, wl.eps)
     b, e = hb.hb_tree(f)
@@ -96,7 +96,7 @@ def test_tree_bit_exact(hb):
 
 @pytest.fixture(scope="module")
 def strip_host(hb):
-    wl = W.CONFIG1
+    wl = W.STRIP_N1024
     g = hb.hb_geometry(wl.kind, wl.params, wl.n)
     f = hb.hb_factor_host(g, wl.leaf, wl.eps)
     p = efie.Problem.from_workload(wl)

@@ -28,7 +28,7 @@ def big():
     from paper_1901_11371_gb300 import build
     build.build()
     import paper_1901_11371_gb300 as hb
-    wl = W.CONFIG3
+    wl = W.SEMICIRCLE_N262144
     g = hb.hb_geometry(wl.kind, wl.params, wl.n)
     f = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C64)
     hb.hb_autotune(f, 256)
@@ -58,7 +58,7 @@ def test_fullsize_apply_sampled_rows(big):
 
 def test_fullsize_batched_solve_sampled_residual(big):
     torch, hb, wl, f, p = big
-    phis = W.incidence_angles_deg(3)
+    phis = W.incidence_angles_deg(W.SEMICIRCLE_N262144)
     b = hb.hb_rhs_plane_wave(f, phis)
     x, info = hb.hb_gmres(f, b, rtol=1e-6, restart=30, maxit=600)
     assert info["converged"] == 256 and info["true_rel_res"] <= 1e-6

@@ -44,7 +44,7 @@ def _rel(a, b):
 
 @pytest.fixture(scope="module")
 def strip(hb):
-    wl = W.CONFIG1
+    wl = W.STRIP_N1024
     g = hb.hb_geometry(wl.kind, wl.params, wl.n)
     p = efie.Problem.from_workload(wl)
     a = p.dense()

@@ -47,7 +47,7 @@ def _sweeps_match_host(hb, f, fh, n, seed):
 
 
 def test_leaf_lu_factor_on_the_device(hb):
-    wl = W.CONFIG1
+    wl = W.STRIP_N1024
     g = hb.hb_geometry(wl.kind, wl.params, wl.n)
     f = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C128, options=hb.HB_OPT_LEAF_LU)
     fh = hb.hb_factor_host(g, wl.leaf, wl.eps, options=hb.HB_OPT_LEAF_LU)
@@ -86,7 +86,7 @@ def test_polyline_factor_on_the_device(hb):
 
 @pytest.fixture(scope="module")
 def strip_tfqmr(hb):
-    wl = W.CONFIG1
+    wl = W.STRIP_N1024
     g = hb.hb_geometry(wl.kind, wl.params, wl.n)
     p = efie.Problem.from_workload(wl)
     return dict(wl=wl, p=p, a=p.dense(), f=hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C128),

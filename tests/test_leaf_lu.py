@@ -46,7 +46,7 @@ def test_oracle_variant_triangles_keep_the_off_diagonal_split():
 
 
 def test_host_sweeps_with_leaf_lu_are_variant_triangular_solves(hb):
-    wl = W.CONFIG1
+    wl = W.STRIP_N1024
     g = hb.hb_geometry(wl.kind, wl.params, wl.n)
     f = hb.hb_factor_host(g, wl.leaf, wl.eps, options=hb.HB_OPT_LEAF_LU)
     af = np.stack([hb.hb_host_apply(f, e) for e in np.eye(wl.n, dtype=np.complex128)], axis=1)

@@ -59,4 +59,4 @@ def test_two_ranks_shard_angles_and_take_max_time():
 def test_single_rank_angles_are_the_workload_angles():
     import bench
     import workloads as W
-    np.testing.assert_array_equal(bench.shard_angles(0, 1), W.incidence_angles_deg(3))
+    np.testing.assert_array_equal(bench.shard_angles(0, 1), W.incidence_angles_deg(W.SEMICIRCLE_N262144))

@@ -104,7 +104,7 @@ def test_ranks_flat_in_n():
 
 @pytest.fixture(scope="module")
 def strip1024():
-    p = efie.Problem.from_workload(W.CONFIG1)
+    p = efie.Problem.from_workload(W.STRIP_N1024)
     a = p.dense()
     h = idbf.HIDBF(a, 32, 1e-6)
     return p, a, h

@@ -26,7 +26,7 @@ def setup():
     from paper_1901_11371_gb300 import build
     build.build()
     import paper_1901_11371_gb300 as hb
-    wl = W.CONFIG1
+    wl = W.STRIP_N1024
     g = hb.hb_geometry(wl.kind, wl.params, wl.n)
     f = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C128)
     return torch, hb, f, wl

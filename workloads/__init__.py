@@ -79,37 +79,35 @@ def parallel_strips(n: int, leaf: int, eps: float, n_strips=8, length=None, spac
 
 
 # The five workloads of the measurement plan.
-CONFIG1 = Workload("strip_N1024", STRIP, (0.0, 0.0, 51.2, 0.0), 1024, 32, 1e-6, "c128",
+STRIP_N1024 = Workload("strip_N1024", STRIP, (0.0, 0.0, 51.2, 0.0), 1024, 32, 1e-6, "c128",
                    note="plain FP64 form; one plane wave at 30 deg")
-CONFIG2 = Workload("spiral_N65536", SPIRAL, (SPIRAL_A_3276_8, 2 * math.pi, 8 * math.pi), 65536, 64, 1e-6, "c64",
+SPIRAL_N65536 = Workload("spiral_N65536", SPIRAL, (SPIRAL_A_3276_8, 2 * math.pi, 8 * math.pi), 65536, 64, 1e-6, "c64",
                    note="complex FP32 apply/preconditioner, FP64 outer FGMRES + IR; phi ~ U[0,180) seed 0")
-CONFIG3 = Workload("semicircle_N262144", ARC, (SEMICIRCLE_R_6553_6, 0.0, math.pi), 262144, 64, 1e-6, "split_bf16",
+SEMICIRCLE_N262144 = Workload("semicircle_N262144", ARC, (SEMICIRCLE_R_6553_6, 0.0, math.pi), 262144, 64, 1e-6, "split_bf16",
                    nrhs=256, note="256 plane waves, multi-RHS block")
-CONFIG4 = Workload("strips8_N131072", PARALLEL_STRIPS, (8.0, 409.6, 2.0), 131072, 64, 1e-6, "c64",
+STRIPS8_N131072 = Workload("strips8_N131072", PARALLEL_STRIPS, (8.0, 409.6, 2.0), 131072, 64, 1e-6, "c64",
                    note="adjoint form; far-field loss")
-CONFIG5 = Workload("spiral_N4194304", SPIRAL, (SPIRAL_A_209715_2, 2 * math.pi, 8 * math.pi), 4194304, 128, 1e-5,
+SPIRAL_N4194304 = Workload("spiral_N4194304", SPIRAL, (SPIRAL_A_209715_2, 2 * math.pi, 8 * math.pi), 4194304, 128, 1e-5,
                    "c64", nrhs=16, note="scale form")
 
-CONFIGS = {1: CONFIG1, 2: CONFIG2, 3: CONFIG3, 4: CONFIG4, 5: CONFIG5}
+WORKLOADS = {wl.name: wl for wl in (STRIP_N1024, SPIRAL_N65536, SEMICIRCLE_N262144, STRIPS8_N131072, SPIRAL_N4194304)}
 
 
 # ----------------------------------------------------------------------------
 # Seeded draws
 # ----------------------------------------------------------------------------
 
-def incidence_angles_deg(cfg: int) -> np.ndarray:
-    """Incidence angles (degrees) of the plane waves for each workload."""
-    if cfg == 1:
+def incidence_angles_deg(wl: Workload) -> np.ndarray:
+    """Incidence angles (degrees) of the plane waves of a workload."""
+    if wl.name in ("strip_N1024", "strips8_N131072"):
         return np.array([30.0])
-    if cfg == 2:
+    if wl.name == "spiral_N65536":
         return np.random.default_rng(0).uniform(0.0, 180.0, size=1)
-    if cfg == 3:
+    if wl.name == "semicircle_N262144":
         return 180.0 * np.arange(256) / 256.0
-    if cfg == 4:
-        return np.array([30.0])
-    if cfg == 5:
+    if wl.name == "spiral_N4194304":
         return 180.0 * np.arange(16) / 16.0
-    raise ValueError(cfg)
+    raise ValueError(wl.name)
 
 
 def observation_angles_deg(n_obs: int = 64) -> np.ndarray:
