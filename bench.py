@@ -284,7 +284,8 @@ def run_gpu(args, rank, world):
 
 def run_kernels(args):
     """Kernel timings (no Krylov loop): hb_apply, one L~ sweep and one U~ sweep on one workload,
-    with algorithmic bytes per launch and the fraction of the measured HBM copy bandwidth."""
+    and the three adjoint counterparts, with algorithmic bytes per launch and the fraction of
+    the measured HBM copy bandwidth."""
     import torch
 
     import paper_1901_11371_gb300 as hb
@@ -320,11 +321,16 @@ def run_kernels(args):
     ms_a = timed(lambda: hb.hb_apply(f, x), args.steps)
     ms_l = timed(lambda: hb.hb_lower_solve(f, x), args.steps)
     ms_u = timed(lambda: hb.hb_upper_solve(f, x), args.steps)
+    # adjoint (Sec. 3 operators conjugate-transposed): A^H, L~^{-H} and U~^{-H}
+    ms_ah = timed(lambda: hb.hb_apply(f, x, op=hb.HB_OP_H), args.steps)
+    ms_lh = timed(lambda: hb.hb_lower_solve(f, x, hb.HB_OP_H), args.steps)
+    ms_uh = timed(lambda: hb.hb_upper_solve(f, x, hb.HB_OP_H), args.steps)
     eb = 8 if args.form == "c64" else 16
     vec_extra = 2 * wl.n * (R - 1) * eb
     out = {"mode": "kernels", "workload": wl.name, "nrhs": R, "form": args.form,
            "grid_min": args.grid_min or tuned, "autotune_ms": times,
            "apply_ms": ms_a, "lower_ms": ms_l, "upper_ms": ms_u,
+           "adjoint_apply_ms": ms_ah, "adjoint_lower_ms": ms_lh, "adjoint_upper_ms": ms_uh,
            "apply_GBps": (st["apply_bytes"] + vec_extra) / ms_a / 1e6,
            "lower_GBps": (st["lower_bytes"] + vec_extra) / ms_l / 1e6,
            "apply_frac": (st["apply_bytes"] + vec_extra) / ms_a / 1e6 / hbm, "peak_GBps": hbm, "peak_source": src,
