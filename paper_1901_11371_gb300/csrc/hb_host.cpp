@@ -248,7 +248,7 @@ static void column_id(std::vector<cplx>& M, int s, int c, double tol, IdBlock& o
 }
 
 // ---------------------------------------------------------------------------
-// Seeded sampling of s positions out of M (Mock-Chebyshev grid + uniform fill).
+// Seeded sampling for the IDs (Mock-Chebyshev grid + uniform fill + near field).
 // ---------------------------------------------------------------------------
 static inline uint64_t splitmix(uint64_t& x) {
   uint64_t z = (x += 0x9E3779B97F4A7C15ull);
@@ -257,35 +257,64 @@ static inline uint64_t splitmix(uint64_t& x) {
   return z ^ (z >> 31);
 }
 
-static void sample_positions(int64_t M, int s, uint64_t seed, std::vector<int64_t>& out) {
-  out.clear();
-  if (M <= s) {
-    out.resize(M);
-    std::iota(out.begin(), out.end(), 0);
-    return;
+static inline int sample_count(int c) { return 2 * c + 16; }
+
+// Reference points of a candidate list: up to 8 evenly spaced candidates.
+static int near_refs(const std::vector<int64_t>& cand, int64_t* refs) {
+  const int nc = (int)cand.size();
+  const int nref = std::min(nc, 8);
+  for (int r = 0; r < nref; ++r) refs[r] = cand[(int64_t)r * (nc - 1) / std::max(1, nref - 1)];
+  return nref;
+}
+
+// Squared distance of (px, py) to the nearest reference point.
+static inline double near_d2(const Geometry& g, double px, double py, const int64_t* refs, int nref) {
+  double dmin = 1e300;
+  for (int r = 0; r < nref; ++r) {
+    const double dx = px - g.cx[refs[r]], dy = py - g.cy[refs[r]];
+    dmin = std::min(dmin, dx * dx + dy * dy);
   }
-  std::vector<char> used(M, 0);
-  int nc = s / 2;
-  for (int i = 0; i < nc; ++i) {
-    double x = 0.5 * (1.0 - std::cos(M_PI * (2.0 * i + 1.0) / (2.0 * nc)));
+  return dmin;
+}
+
+// Chebyshev-spaced then uniform picks among M positions, skipping those in `used`,
+// until `out` holds s entries (the fill shared by both sampling paths).
+template <class Used>
+static void fill_picks(int64_t M, int s, int nn, uint64_t seed, Used& used, std::vector<int64_t>& out) {
+  const int nrest = s - nn;
+  const int ncheb = nrest / 2;
+  for (int i = 0; i < ncheb; ++i) {
+    double x = 0.5 * (1.0 - std::cos(M_PI * (2.0 * i + 1.0) / (2.0 * ncheb)));
     int64_t idx = std::min<int64_t>(M - 1, (int64_t)std::llround(x * (double)(M - 1)));
-    if (!used[idx]) { used[idx] = 1; out.push_back(idx); }
+    if (used.insert(idx)) out.push_back(idx);
   }
   uint64_t st = seed;
   while ((int)out.size() < s) {
     int64_t idx = (int64_t)(splitmix(st) % (uint64_t)M);
-    if (!used[idx]) { used[idx] = 1; out.push_back(idx); }
+    if (used.insert(idx)) out.push_back(idx);
   }
-  std::sort(out.begin(), out.end());
 }
 
-static inline int sample_count(int c) { return 2 * c + 16; }
+struct FlagSet {   // dense membership over [0, M)
+  std::vector<char> f;
+  explicit FlagSet(int64_t M) : f((size_t)M, 0) {}
+  bool insert(int64_t i) { if (f[(size_t)i]) return false; f[(size_t)i] = 1; return true; }
+};
+struct SmallSet {  // sparse membership (a few thousand entries at most)
+  std::vector<int64_t> v;
+  bool insert(int64_t i) {
+    auto it = std::lower_bound(v.begin(), v.end(), i);
+    if (it != v.end() && *it == i) return false;
+    v.insert(it, i);
+    return true;
+  }
+};
 
 // Sample positions of `pool` for an ID over the candidate points `cand`: half
 // of the sample is the pool entries geometrically nearest to the candidates
 // (the near field across block boundaries and between adjacent turns, which a
-// uniform or Chebyshev sample of a long pool can miss), the rest a Mock-
-// Chebyshev + uniform sample of the remaining entries.
+// uniform or Chebyshev sample of a long pool can miss; ties by position), the
+// rest a Mock-Chebyshev + uniform sample of the remaining entries.
 static void sample_near(const Geometry& g, const std::vector<int64_t>& pool, const std::vector<int64_t>& cand,
                         int s, uint64_t seed, std::vector<int64_t>& out) {
   const int64_t M = (int64_t)pool.size();
@@ -294,78 +323,226 @@ static void sample_near(const Geometry& g, const std::vector<int64_t>& pool, con
     std::iota(out.begin(), out.end(), 0);
     return;
   }
-  // distance of each pool point to (up to 8 evenly spaced) candidate points
-  const int nc = (int)cand.size();
-  const int nref = std::min(nc, 8);
+  int64_t refs[8];
+  const int nref = near_refs(cand, refs);
   std::vector<std::pair<double, int64_t>> dist(M);
-  for (int64_t e = 0; e < M; ++e) {
-    const double px = g.cx[pool[e]], py = g.cy[pool[e]];
-    double dmin = 1e300;
-    for (int r = 0; r < nref; ++r) {
-      const int64_t c = cand[(int64_t)r * (nc - 1) / std::max(1, nref - 1)];
-      const double dx = px - g.cx[c], dy = py - g.cy[c];
-      dmin = std::min(dmin, dx * dx + dy * dy);
-    }
-    dist[e] = {dmin, e};
-  }
+  for (int64_t e = 0; e < M; ++e) dist[e] = {near_d2(g, g.cx[pool[e]], g.cy[pool[e]], refs, nref), e};
   const int nn = s / 2;
   std::nth_element(dist.begin(), dist.begin() + nn, dist.end());
-  std::vector<char> used(M, 0);
+  FlagSet used(M);
   out.clear();
-  for (int i = 0; i < nn; ++i) { used[dist[i].second] = 1; out.push_back(dist[i].second); }
-  // Chebyshev-spaced and uniform picks among the rest
-  const int nrest = s - nn;
-  const int ncheb = nrest / 2;
-  for (int i = 0; i < ncheb; ++i) {
-    double x = 0.5 * (1.0 - std::cos(M_PI * (2.0 * i + 1.0) / (2.0 * ncheb)));
-    int64_t idx = std::min<int64_t>(M - 1, (int64_t)std::llround(x * (double)(M - 1)));
-    if (!used[idx]) { used[idx] = 1; out.push_back(idx); }
-  }
-  uint64_t st = seed;
-  while ((int)out.size() < s) {
-    int64_t idx = (int64_t)(splitmix(st) % (uint64_t)M);
-    if (!used[idx]) { used[idx] = 1; out.push_back(idx); }
-  }
+  for (int i = 0; i < nn; ++i) { used.insert(dist[i].second); out.push_back(dist[i].second); }
+  fill_picks(M, s, nn, seed, used, out);
   std::sort(out.begin(), out.end());
 }
 
+// k-d tree over the segment centres of a pool: a contiguous range [lo, lo + M)
+// (idx null) or an index list idx[0..M).  The pools of a butterfly stage are
+// shared by many of its IDs (the first row stage samples the whole column
+// range, the first column stage all row skeletons); nearest() returns the same
+// entries as the full scan of sample_near (the nn smallest (squared distance,
+// position) pairs) in O(nn log M) instead of O(M) per ID.
+struct PoolTree {
+  struct Node { double x0, y0, x1, y1; int32_t begin, end, left, right; };
+  const Geometry* g = nullptr;
+  const int64_t* idx = nullptr;
+  int64_t lo = 0, M = 0;
+  std::vector<int32_t> pts;   // pool positions in tree order
+  std::vector<Node> nodes;
+  int64_t global(int64_t p) const { return idx ? idx[p] : lo + p; }
+
+  int32_t build_node(int32_t b, int32_t e) {
+    Node nd{1e300, 1e300, -1e300, -1e300, b, e, -1, -1};
+    for (int32_t i = b; i < e; ++i) {
+      const double x = g->cx[global(pts[i])], y = g->cy[global(pts[i])];
+      nd.x0 = std::min(nd.x0, x); nd.x1 = std::max(nd.x1, x);
+      nd.y0 = std::min(nd.y0, y); nd.y1 = std::max(nd.y1, y);
+    }
+    const int32_t id = (int32_t)nodes.size();
+    nodes.push_back(nd);
+    if (e - b > 16) {
+      const bool xs = (nd.x1 - nd.x0) >= (nd.y1 - nd.y0);
+      const int32_t mid = b + (e - b) / 2;
+      std::nth_element(pts.begin() + b, pts.begin() + mid, pts.begin() + e, [&](int32_t u, int32_t v) {
+        const int64_t gu = global(u), gv = global(v);
+        const double a = xs ? g->cx[gu] : g->cy[gu], c = xs ? g->cx[gv] : g->cy[gv];
+        return a < c || (a == c && u < v);
+      });
+      const int32_t l = build_node(b, mid);
+      const int32_t r = build_node(mid, e);
+      nodes[id].left = l;
+      nodes[id].right = r;
+    }
+    return id;
+  }
+  void build(const Geometry& geo, const int64_t* idx_, int64_t lo_, int64_t M_) {
+    g = &geo; idx = idx_; lo = lo_; M = M_;
+    pts.resize((size_t)M);
+    std::iota(pts.begin(), pts.end(), 0);
+    nodes.clear();
+    nodes.reserve((size_t)(M / 8 + 2));
+    build_node(0, (int32_t)M);
+  }
+  // the nn pool positions not in `skip` (sorted) with the smallest (near_d2, position)
+  void nearest(const int64_t* refs, int nref, int nn, const std::vector<int64_t>& skip,
+               std::vector<int64_t>& out) const {
+    using Cand = std::pair<double, int64_t>;
+    std::vector<Cand> best;   // max-heap of the nn best so far
+    best.reserve((size_t)nn + 1);
+    auto box_d2 = [&](const Node& nd) {
+      double m = 1e300;
+      for (int r = 0; r < nref; ++r) {
+        const double px = g->cx[refs[r]], py = g->cy[refs[r]];
+        const double dx = std::max(0.0, std::max(nd.x0 - px, px - nd.x1));
+        const double dy = std::max(0.0, std::max(nd.y0 - py, py - nd.y1));
+        m = std::min(m, dx * dx + dy * dy);
+      }
+      return m * (1.0 - 1e-12);   // a lower bound also under rounding
+    };
+    using QE = std::pair<double, int32_t>;
+    std::vector<QE> queue;      // min-heap of nodes by lower bound
+    auto qcmp = [](const QE& a, const QE& b) { return a.first > b.first; };
+    queue.push_back({box_d2(nodes[0]), 0});
+    while (!queue.empty()) {
+      std::pop_heap(queue.begin(), queue.end(), qcmp);
+      const QE top = queue.back();
+      queue.pop_back();
+      if ((int)best.size() == nn && top.first > best.front().first) break;
+      const Node& nd = nodes[(size_t)top.second];
+      if (nd.left < 0) {
+        for (int32_t i = nd.begin; i < nd.end; ++i) {
+          const int64_t p = pts[(size_t)i];
+          if (!skip.empty() && std::binary_search(skip.begin(), skip.end(), p)) continue;
+          const int64_t gp = global(p);
+          const Cand cnd{near_d2(*g, g->cx[gp], g->cy[gp], refs, nref), p};
+          if ((int)best.size() < nn) {
+            best.push_back(cnd);
+            std::push_heap(best.begin(), best.end());
+          } else if (cnd < best.front()) {
+            std::pop_heap(best.begin(), best.end());
+            best.back() = cnd;
+            std::push_heap(best.begin(), best.end());
+          }
+        }
+      } else {
+        for (int32_t ch : {nd.left, nd.right}) {
+          queue.push_back({box_d2(nodes[(size_t)ch]), ch});
+          std::push_heap(queue.begin(), queue.end(), qcmp);
+        }
+      }
+    }
+    out.clear();
+    for (const Cand& c : best) out.push_back(c.second);
+  }
+};
+
+// Explicit pool of indices: the full-scan sampling above.
+struct ListPool {
+  const Geometry& g;
+  const std::vector<int64_t>& idx;
+  int64_t size() const { return (int64_t)idx.size(); }
+  int64_t at(int64_t p) const { return idx[(size_t)p]; }
+  void sample(const std::vector<int64_t>& cand, int s, uint64_t seed, std::vector<int64_t>& pos) const {
+    sample_near(g, idx, cand, s, seed, pos);
+  }
+  // probe rows: a sample of the unsampled entries (global indices, in pool order)
+  void probe(const std::vector<int64_t>& cand, const std::vector<int64_t>& pos, int s, uint64_t seed,
+             std::vector<int64_t>& rows) const {
+    const int64_t M = size();
+    std::vector<char> used((size_t)M, 0);
+    for (int64_t e : pos) used[(size_t)e] = 1;
+    std::vector<int64_t> rest;
+    rest.reserve((size_t)(M - (int64_t)pos.size()));
+    for (int64_t e = 0; e < M; ++e)
+      if (!used[(size_t)e]) rest.push_back(idx[(size_t)e]);
+    std::vector<int64_t> ppos;
+    sample_near(g, rest, cand, s, seed, ppos);
+    rows.clear();
+    for (int64_t r : ppos) rows.push_back(rest[(size_t)r]);
+  }
+};
+
+// Pool with its k-d tree: the same samples as ListPool over the same entries,
+// without touching all M of them per ID.
+struct TreePool {
+  const PoolTree& tree;
+  int64_t size() const { return tree.M; }
+  int64_t at(int64_t p) const { return tree.global(p); }
+  // sample_near over the pool with the (sorted) positions `skip` removed; the
+  // result counts positions over the remaining entries, as sample_near would
+  void sample_skip(const std::vector<int64_t>& cand, int s, uint64_t seed, const std::vector<int64_t>& skip,
+                   std::vector<int64_t>& out) const {
+    const int64_t M = tree.M - (int64_t)skip.size();
+    out.clear();
+    if (M <= s) {
+      out.resize(M);
+      std::iota(out.begin(), out.end(), 0);
+      return;
+    }
+    int64_t refs[8];
+    const int nref = near_refs(cand, refs);
+    const int nn = s / 2;
+    std::vector<int64_t> near;
+    tree.nearest(refs, nref, nn, skip, near);
+    SmallSet used;
+    for (int64_t p : near) {   // pool position -> position among the remaining entries
+      const int64_t r = p - (int64_t)(std::lower_bound(skip.begin(), skip.end(), p) - skip.begin());
+      used.insert(r);
+      out.push_back(r);
+    }
+    fill_picks(M, s, nn, seed, used, out);
+    std::sort(out.begin(), out.end());
+  }
+  void sample(const std::vector<int64_t>& cand, int s, uint64_t seed, std::vector<int64_t>& pos) const {
+    static const std::vector<int64_t> none;
+    sample_skip(cand, s, seed, none, pos);
+  }
+  void probe(const std::vector<int64_t>& cand, const std::vector<int64_t>& pos, int s, uint64_t seed,
+             std::vector<int64_t>& rows) const {
+    std::vector<int64_t> rpos;
+    sample_skip(cand, s, seed, pos, rpos);
+    // position r among the unsampled entries -> pool position (pos is sorted)
+    rows.clear();
+    size_t k = 0;
+    for (int64_t r : rpos) {   // rpos is sorted: walk pos once
+      int64_t q = r + (int64_t)k;
+      while (k < pos.size() && pos[k] <= q) { ++k; ++q; }
+      rows.push_back(tree.global(q));
+    }
+  }
+};
+
 // ---------------------------------------------------------------------------
-// Adaptive sampled ID.  cand: the c candidate indices; pool: indices of the
-// other dimension to sample; ent(pool_idx, cand_idx) gives the entry.  The ID
-// is computed on a sample (sample_near), then checked on a probe of unsampled
-// pool entries (nearest first, then uniform); while the probe residual
-// ||M_P(:,p) - M_P(:,q) T||_F exceeds 10 tol ||M_P||_F the sample is doubled.
+// Adaptive sampled ID.  cand: the c candidate indices; pool: the other
+// dimension's indices to sample (ListPool / TreePool); ent(pool index,
+// candidate index) gives the entry.  The ID is computed on a sample
+// (sample_near), then checked on a probe of unsampled pool entries (nearest
+// first, then uniform); while the probe residual ||M_P(:,p) - M_P(:,q) T||_F
+// exceeds 10 tol ||M_P||_F the sample is doubled.
 // ---------------------------------------------------------------------------
-template <class Ent>
-static void adaptive_id(const Geometry& geo, const std::vector<int64_t>& pool, const std::vector<int64_t>& cand,
-                        double tol, uint64_t seed, const Ent& ent, IdBlock& blk) {
+template <class Pool, class Ent>
+static void adaptive_id(const Pool& pool, const std::vector<int64_t>& cand, double tol, uint64_t seed,
+                        const Ent& ent, IdBlock& blk) {
   const int c = (int)cand.size();
-  const int64_t M = (int64_t)pool.size();
+  const int64_t M = pool.size();
   int s = sample_count(c);
-  std::vector<int64_t> pos;
+  std::vector<int64_t> pos, rows;
   for (int attempt = 0;; ++attempt) {
-    sample_near(geo, pool, cand, s, seed + 0x51ull * attempt, pos);
+    pool.sample(cand, s, seed + 0x51ull * attempt, pos);
     const int ns = (int)pos.size();
     std::vector<cplx> Mt((size_t)ns * c);
     for (int cc = 0; cc < c; ++cc)
-      for (int r = 0; r < ns; ++r) Mt[(size_t)cc * ns + r] = ent(pool[pos[r]], cand[cc]);
+      for (int r = 0; r < ns; ++r) Mt[(size_t)cc * ns + r] = ent(pool.at(pos[r]), cand[cc]);
     column_id(Mt, ns, c, tol, blk);
     if (ns >= M || blk.k >= c) return;          // whole pool used, or no compression: exact on the sample
     // probe: up to 16 + c/2 unsampled entries, the nearest half first
-    std::vector<char> used(M, 0);
-    for (int64_t e : pos) used[e] = 1;
-    std::vector<int64_t> rest;
-    rest.reserve(M - ns);
-    for (int64_t e = 0; e < M; ++e)
-      if (!used[e]) rest.push_back(pool[e]);
-    std::vector<int64_t> ppos;
-    sample_near(geo, rest, cand, std::min<int64_t>((int64_t)rest.size(), 16 + c / 2), seed ^ 0xFEEDull, ppos);
-    const int np = (int)ppos.size();
+    pool.probe(cand, pos, (int)std::min<int64_t>(M - ns, 16 + c / 2), seed ^ 0xFEEDull, rows);
+    const int np = (int)rows.size();
     double num = 0.0, den = 0.0;
     const int nr = c - blk.k;
     for (int r = 0; r < np; ++r) {
       std::vector<cplx> row(c);
-      for (int cc = 0; cc < c; ++cc) { row[cc] = ent(rest[ppos[r]], cand[cc]); den += std::norm(row[cc]); }
+      for (int cc = 0; cc < c; ++cc) { row[cc] = ent(rows[r], cand[cc]); den += std::norm(row[cc]); }
       for (int j = 0; j < nr; ++j) {
         cplx acc = row[blk.p[j]];
         for (int i = 0; i < blk.k; ++i) acc -= row[blk.q[i]] * blk.t[(size_t)i * nr + j];
@@ -389,10 +566,42 @@ static void build_butterfly(Butterfly& B, const Entries& K, int64_t n0, double t
   B.col.assign(B.hc, std::vector<IdBlock>(npairs));
   B.row.assign(B.hr, std::vector<IdBlock>(npairs));
   const int dmax = std::max(B.hc, B.hr);
+  // Sample pools are shared: the first row stage samples the whole column range,
+  // and a stage's other pools depend on one node pair only.  Each distinct pool
+  // is formed once per stage; pools of kTreeMin entries or more get a k-d tree.
+  constexpr int64_t kTreeMin = 1024;
+  std::vector<std::vector<int64_t>> lists;
+  std::vector<PoolTree> trees;
+  auto make_pools = [&](int64_t nkeys, const auto& fill) {
+    lists.assign((size_t)nkeys, {});
+    trees.assign((size_t)nkeys, PoolTree());
+#pragma omp parallel for schedule(dynamic, 1) if (par)
+    for (int64_t key = 0; key < nkeys; ++key) {
+      fill(key, lists[(size_t)key]);
+      const int64_t M = (int64_t)lists[(size_t)key].size();
+      if (M >= kTreeMin) trees[(size_t)key].build(geo, lists[(size_t)key].data(), 0, M);
+    }
+  };
+  PoolTree col_tree;   // row stage 0: the column range [col0, col0 + n)
+  col_tree.build(geo, nullptr, B.col0, B.n);
   for (int d = 0; d < dmax; ++d) {
     // ---- row stage d: pairs (a at row level L-d, b at column level d), g = b*2^(L-d) + a
     if (d < B.hr) {
       const int64_t na = (int64_t)1 << (L - d);
+      // d > 0: pool (ap, b) = column skeletons of column stage d-1 under column node b
+      // (level d): pairs (ap = ancestor of a at row level d-1, b'' at column level L-d+1)
+      const int sh = L - 2 * d + 1;
+      const int64_t nbd = (int64_t)1 << d;
+      if (d > 0) {
+        const int64_t nbpp = (int64_t)1 << (L - d + 1);
+        make_pools(((int64_t)1 << (d - 1)) * nbd, [&](int64_t key, std::vector<int64_t>& pool) {
+          const int64_t ap = key / nbd, b = key % nbd;
+          for (int64_t bb = b << sh; bb < ((b + 1) << sh); ++bb) {
+            const IdBlock& cb = B.col[d - 1][ap * nbpp + bb];
+            pool.insert(pool.end(), cb.skel.begin(), cb.skel.end());
+          }
+        });
+      }
 #pragma omp parallel for schedule(dynamic, 4) if (par)
       for (int64_t g = 0; g < npairs; ++g) {
         int64_t b = g / na, a = g % na;
@@ -407,25 +616,16 @@ static void build_butterfly(Butterfly& B, const Entries& K, int64_t n0, double t
           cand = c0.skel;
           cand.insert(cand.end(), c1.skel.begin(), c1.skel.end());
         }
-        // columns to sample
-        std::vector<int64_t> pool;
-        if (d == 0) {
-          pool.resize(B.n);
-          for (int64_t j = 0; j < B.n; ++j) pool[j] = B.col0 + j;
-        } else {
-          // column skeletons of column stage d-1 under column node b (level d):
-          // pairs (a' = ancestor of a at row level d-1, b'' at column level L-d+1)
-          int sh = L - 2 * d + 1;
-          int64_t ap = a >> sh;
-          const int64_t nbpp = (int64_t)1 << (L - d + 1);
-          for (int64_t bb = b << sh; bb < ((b + 1) << sh); ++bb) {
-            const IdBlock& cb = B.col[d - 1][ap * nbpp + bb];
-            pool.insert(pool.end(), cb.skel.begin(), cb.skel.end());
-          }
-        }
         uint64_t sd = seed ^ (0x1000003ull * (uint64_t)(d + 1)) ^ (0x9E37ull * (uint64_t)g) ^ 0xABCDull;
         // row ID: entries K(candidate row, sampled column)
-        adaptive_id(geo, pool, cand, tol, sd, [&](int64_t col, int64_t row) { return K(row, col); }, blk);
+        auto ent = [&](int64_t col, int64_t row) { return K(row, col); };
+        if (d == 0) {
+          adaptive_id(TreePool{col_tree}, cand, tol, sd, ent, blk);
+        } else {
+          const size_t key = (size_t)((a >> sh) * nbd + b);
+          if (trees[key].M > 0) adaptive_id(TreePool{trees[key]}, cand, tol, sd, ent, blk);
+          else adaptive_id(ListPool{geo, lists[key]}, cand, tol, sd, ent, blk);
+        }
         blk.skel.resize(blk.k);
         for (int i = 0; i < blk.k; ++i) blk.skel[i] = cand[blk.q[i]];
       }
@@ -433,6 +633,18 @@ static void build_butterfly(Butterfly& B, const Entries& K, int64_t n0, double t
     // ---- column stage d: pairs (a at row level d, b at column level L-d), g = a*2^(L-d) + b
     if (d < B.hc) {
       const int64_t nb = (int64_t)1 << (L - d);
+      // pool (a, bp) = row skeletons of row stage d under row node a (level d):
+      // pairs (a'' at row level L-d below a, bp = ancestor of b at column level d)
+      const int sh = L - 2 * d;
+      const int64_t nad = (int64_t)1 << d;
+      const int64_t na2 = (int64_t)1 << (L - d);
+      make_pools(nad * nad, [&](int64_t key, std::vector<int64_t>& pool) {
+        const int64_t a = key / nad, bp = key % nad;
+        for (int64_t aa = a << sh; aa < ((a + 1) << sh); ++aa) {
+          const IdBlock& rb = B.row[d][bp * na2 + aa];
+          pool.insert(pool.end(), rb.skel.begin(), rb.skel.end());
+        }
+      });
 #pragma omp parallel for schedule(dynamic, 4) if (par)
       for (int64_t g = 0; g < npairs; ++g) {
         int64_t a = g / nb, b = g % nb;
@@ -447,19 +659,12 @@ static void build_butterfly(Butterfly& B, const Entries& K, int64_t n0, double t
           cand = c0.skel;
           cand.insert(cand.end(), c1.skel.begin(), c1.skel.end());
         }
-        // rows to sample: row skeletons of row stage d under row node a (level d):
-        // pairs (a'' at row level L-d below a, b' = ancestor of b at column level d)
-        std::vector<int64_t> pool;
-        int sh = L - 2 * d;
-        int64_t bp = b >> sh;
-        const int64_t na2 = (int64_t)1 << (L - d);
-        for (int64_t aa = a << sh; aa < ((a + 1) << sh); ++aa) {
-          const IdBlock& rb = B.row[d][bp * na2 + aa];
-          pool.insert(pool.end(), rb.skel.begin(), rb.skel.end());
-        }
         uint64_t sd = seed ^ (0x2000011ull * (uint64_t)(d + 1)) ^ (0x7F4Aull * (uint64_t)g) ^ 0x1234ull;
         // column ID: entries K(sampled row, candidate column)
-        adaptive_id(geo, pool, cand, tol, sd, [&](int64_t row, int64_t col) { return K(row, col); }, blk);
+        auto ent = [&](int64_t row, int64_t col) { return K(row, col); };
+        const size_t key = (size_t)(a * nad + (b >> sh));
+        if (trees[key].M > 0) adaptive_id(TreePool{trees[key]}, cand, tol, sd, ent, blk);
+        else adaptive_id(ListPool{geo, lists[key]}, cand, tol, sd, ent, blk);
         blk.skel.resize(blk.k);
         for (int i = 0; i < blk.k; ++i) blk.skel[i] = cand[blk.q[i]];
       }

@@ -27,3 +27,17 @@ def test_sweep_program_segmentation_invariants():
         assert r.returncode == 0, r.stderr[-2000:]
         r = subprocess.run([exe], capture_output=True, text=True, timeout=600)
         assert r.returncode == 0 and r.stdout.strip().endswith("OK"), r.stdout[-3000:]
+
+
+def test_tree_sampling_equals_full_scan():
+    # the k-d tree path of the ID sampling picks exactly the full scan's samples
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "samplecheck")
+        cmd = [gxx, "-O2", "-std=c++17", "-fopenmp", "-I", CSRC, os.path.join(ROOT, "tests", "samplecheck.cpp"), "-o", exe]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr[-2000:]
+        r = subprocess.run([exe], capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0 and r.stdout.strip().endswith("OK"), r.stdout[-3000:]
