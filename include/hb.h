@@ -134,11 +134,10 @@ void hb_geometry_destroy(hb_geometry_t g);
  * factors, dense leaves and the sweeps' packed triangles (the exact inverse
  * of L~ / U~ on every subtree of up to 128 rows, formed on the host by
  * running Algs. 3/4 on unit vectors) to the current device in the storage
- * `form`.  HB_SPLIT_BF16 is accepted and currently stores and computes like
- * HB_C64 (complex FP32 on CUDA cores).  Construction runs on the host and is
+ * `form`.  HB_SPLIT_BF16 returns HB_EUNSUPPORTED (not built).  Construction runs on the host and is
  * timed apart from the hot path.  Requires N = leaf * 2^D with D >= 1,
  * 8 <= leaf <= 256.
- * Errors: HB_EINVAL, HB_EUNSUPPORTED (N not leaf*2^D), HB_ENOMEM, HB_ECUDA. */
+ * Errors: HB_EINVAL, HB_EUNSUPPORTED (N not leaf*2^D; HB_SPLIT_BF16), HB_ENOMEM, HB_ECUDA. */
 int hb_factor(hb_geometry_t g, double wavelength, double eta0, double gamma, int64_t leaf, double eps,
               int form, uint64_t seed, void* stream, hb_factor_t* out);
 
@@ -214,7 +213,11 @@ int hb_residual(hb_factor_t f, int op, const void* b, const void* x, void* r, in
  * every column or after maxit inner iterations.  The
  * initial guess is zero; x is overwritten with the solution.  Synchronises
  * `stream` before returning; info may be NULL.
- * Errors: HB_EINVAL, HB_ENAN (non-finite b), HB_ENOCONV (info still filled). */
+ * Errors: HB_EINVAL, HB_ENAN (non-finite b, or a residual that became
+ * non-finite: overflow of the preconditioned iteration; info filled, its
+ * residual NaN), HB_ENOCONV (info still filled),
+ * HB_ETIMEOUT (a bounded wait of a sweep kernel expired; x undefined; the
+ * flag is cleared, so the next call starts clean). */
 int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int64_t nrhs, int64_t ld, int restart,
              double rtol, int maxit, hb_gmres_info* info, void* stream);
 
@@ -235,7 +238,8 @@ int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int64_t nrhs, i
  * largest final bound relative to ||L~^{-1} b^||.  x is overwritten;
  * synchronises `stream` before returning; info may be NULL.
  * Errors: HB_EINVAL, HB_EUNSUPPORTED (not HB_C128), HB_ENAN (non-finite b or
- * rstar), HB_ENOCONV (maxit half steps or a breakdown; info still filled). */
+ * rstar), HB_ENOCONV (maxit half steps or a breakdown; info still filled),
+ * HB_ETIMEOUT (as hb_gmres). */
 int hb_tfqmr(hb_factor_t f, int op, const void* b_phys, const void* rstar, void* x, int64_t nrhs, int64_t ld,
              double rtol, int maxit, hb_gmres_info* info, void* stream);
 

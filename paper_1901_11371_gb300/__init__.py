@@ -158,24 +158,27 @@ def hb_apply_adjoint(f, x, out=None, stream=None):
     return hb_apply(f, x, HB_OP_H, out, stream)
 
 
-def _sweep_call(fn, f, b, op, out, stream):
+def _sweep_call(fn, f, b, op, out, stream, check_status):
     import torch
     b, R = _block(b, f.n, f.vec_dtype)
     x = torch.empty_like(b) if out is None else out
     _lib.check(fn(f._h, int(op), C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), R, f.n, _stream(stream)))
+    if check_status:
+        # synchronises the stream; raises HB_ETIMEOUT if a bounded wait of the sweep expired
+        _lib.check(lib().hb_status(f._h, _stream(stream)))
     return x
 
 
-def hb_precond_solve(f, b, op=HB_OP_N, out=None, stream=None):
-    return _sweep_call(lib().hb_precond_solve, f, b, op, out, stream)
+def hb_precond_solve(f, b, op=HB_OP_N, out=None, stream=None, check_status=True):
+    return _sweep_call(lib().hb_precond_solve, f, b, op, out, stream, check_status)
 
 
-def hb_lower_solve(f, b, op=HB_OP_N, out=None, stream=None):
-    return _sweep_call(lib().hb_lower_solve, f, b, op, out, stream)
+def hb_lower_solve(f, b, op=HB_OP_N, out=None, stream=None, check_status=True):
+    return _sweep_call(lib().hb_lower_solve, f, b, op, out, stream, check_status)
 
 
-def hb_upper_solve(f, b, op=HB_OP_N, out=None, stream=None):
-    return _sweep_call(lib().hb_upper_solve, f, b, op, out, stream)
+def hb_upper_solve(f, b, op=HB_OP_N, out=None, stream=None, check_status=True):
+    return _sweep_call(lib().hb_upper_solve, f, b, op, out, stream, check_status)
 
 
 def hb_residual(f, b, x, op=HB_OP_N, stream=None):

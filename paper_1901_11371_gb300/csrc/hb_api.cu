@@ -285,6 +285,7 @@ int hb_factor_ex(hb_geometry_t g, double wavelength, double eta0, double gamma, 
   if (options & ~HB_OPT_LEAF_LU) { set_error("hb_factor: unknown option bits 0x%x", options); return HB_EINVAL; }
   *out = nullptr;
   if (form != HB_C128 && form != HB_C64 && form != HB_SPLIT_BF16) { set_error("hb_factor: bad form %d", form); return HB_EINVAL; }
+  if (form == HB_SPLIT_BF16) { set_error("hb_factor: the split-BF16 tensor-core form is not built"); return HB_EUNSUPPORTED; }
   auto t0 = std::chrono::steady_clock::now();
   hb_factor_s* f = new (std::nothrow) hb_factor_s();
   if (!f) { set_error("hb_factor: out of host memory"); return HB_ENOMEM; }
@@ -298,7 +299,7 @@ int hb_factor_ex(hb_geometry_t g, double wavelength, double eta0, double gamma, 
       for (const auto& sm : b.mid) z += (int64_t)sm.size();
       (b.kind == 1 ? f->lower_nnz : f->upper_nnz) += z;
     }
-    rc = upload_factor(f->ph, f->hf, g->geo, form == HB_SPLIT_BF16 ? HB_C64 : form, (cudaStream_t)stream, f->df);
+    rc = upload_factor(f->ph, f->hf, g->geo, form, (cudaStream_t)stream, f->df);
     f->df.form = form;
   }
   if (rc) { free_factor(f->df); delete f; return rc; }

@@ -162,9 +162,11 @@ struct DSeg {
 // so the kernel needs a single record per op.  Element offsets/counts refer to
 // the factor pool (or, for leaf ops, the leaf-inverse array) in elements of the
 // storage type and to the index pool in int16 entries.
-enum FlatKind : int16_t { FK_GATHER = 0, FK_SCATTER = 1, FK_MIDDLE = 2, FK_LEAF = 3 };
+enum FlatKind : int16_t { FK_GATHER = 0, FK_SCATTER = 1, FK_MIDDLE = 2, FK_LEAF = 3,
+                          FK_DLEAF = 4 /* apply: columns [c1, c1 + k1) of a dense diagonal leaf block */ };
 enum FlatFlag : int16_t { FF_CONJ = 1, FF_SUB = 2, FF_ADJ = 4, FF_SRC_VEC = 8, FF_OUT_VEC = 16, FF_TWO = 32,
-                          FF_UPPER = 64 /* leaf op: packed upper triangle */ };
+                          FF_UPPER = 64 /* leaf op: packed upper triangle */,
+                          FF_ACC = 128 /* apply: add to the staged output rows instead of overwriting them */ };
 // Largest sweep leaf (rows) that pack_factor forms by merging subtrees.
 constexpr int kSweepLeafMax = 128;
 #ifdef __CUDACC__
@@ -206,6 +208,51 @@ inline int32_t flat_stage_bytes32(const FlatOp& f) {
   return (int32_t)(a16((int64_t)f.melems * 8) + (f.ioff >= 0 ? a16((int64_t)f.ielems * 2) : 0));
 }
 
+
+// ---------------------------------------------------------------------------
+// Single-column apply plan (persistent kernel k_apply1).  Alg. 2 as phases:
+// phase 0 = the V0 ops of every column leaf (one ENTER task per leaf) and the
+// first column chunk of every dense leaf product; phases 1..S = the inner
+// butterfly steps (one task per item), with further dense-leaf column chunks
+// (each adds to the rows the previous chunk wrote); the last phases = the U0
+// ops of every row leaf (EXIT tasks, added to the leaf product in the fixed
+// order of the depths, cut into chained chunks when one leaf's ops do not fit
+// a staging area).  Each CTA owns a contiguous range of every phase's tasks,
+// cut into batches: one batch = one staging area holding the batch's factor
+// and index blocks and its vector gather list (copied in by a producer warp
+// with bulk copies), followed by the vector entries the batch's ops read
+// (gathered by the compute warps after the phase barrier).
+// ---------------------------------------------------------------------------
+struct A1Task {
+  int32_t op0, nops;   // FlatOp range, executed in order by one warp
+  int32_t kind;        // 0 ENTER, 1 ITEM, 2 DLEAF, 3 EXIT
+  int32_t pad;
+};
+struct A1Batch {
+  int32_t phase;
+  int32_t task0, ntasks;
+  int32_t tma_bytes;   // bytes the producer copies (factor/index blocks + gather list)
+  int32_t area_bytes;  // staging area: tma_bytes + staged vector entries (16 bytes each)
+  int32_t gl_off;      // byte offset of the gather list inside the area
+  int32_t nvec;        // staged vector entries (= gather-list length)
+  int32_t vec_off;     // byte offset of the staged vector entries inside the area
+  int64_t gl_src;      // first gather-list entry in ApplyPlan::gl
+};
+// Gather-list entry: bit 31 set = row of the vector x (bits 0..30), else a
+// butterfly-state entry; bit 30 set (with bit 31) = a row of the output y.
+constexpr uint32_t kA1FromX = 0x80000000u;
+constexpr uint32_t kA1FromY = 0xC0000000u;
+struct ApplyPlan {
+  std::vector<FlatOp> ops;      // soff: byte offset of the op's blocks in its batch area;
+                                // pad: first staged vector entry of the op (inputs; EXIT/DLEAF: also the rows)
+  std::vector<A1Task> tasks;
+  std::vector<A1Batch> batches;
+  std::vector<int32_t> cta_batch;   // [G + 1]: batches of CTA g are [cta_batch[g], cta_batch[g+1])
+  std::vector<uint32_t> gl;         // gather lists of all batches
+  int nphase = 0;
+  int max_area = 0;
+  bool ok = true;
+};
 
 struct PackedHost {
   int64_t n = 0, n0 = 0, m = 0;
@@ -268,6 +315,14 @@ constexpr int kRunMaxPhases = 511;   // (phases + 1) x 8 bytes of phase table <=
 // result is annotated (annotate_segments).
 std::vector<DSeg> segment_program(const std::vector<DPhase>& prog, const FlatProgram& fp, int grid_min,
                                   int64_t res_entries);
+
+// Plan of the persistent single-column apply for G CTAs, factor entries of
+// fes bytes, staging areas of at most max_area bytes (adj: A^H).
+void build_apply_plan(const PackedHost& ph, bool adj, int G, int fes, int max_area, ApplyPlan& plan);
+// Execute a plan on the host in plan order (verification of the plan
+// without a GPU): y = A^_F x or A^_F^H x.
+void host_apply_plan(const PackedHost& ph, const HostFactor& hf, const ApplyPlan& plan, bool adj, const cplx* x,
+                     cplx* y);
 
 // FP64 host execution of the packed program (verification without a GPU).
 void host_apply(const PackedHost& ph, const HostFactor& hf, bool adj, const cplx* x, cplx* y);

@@ -71,7 +71,17 @@ extern "C" int hb_apply_noalloc(hb_factor_t f, int op, const void* x, void* y, i
   const Prec p = f64 ? PREC_F64 : PREC_F32;
   const int vt = f64 ? 0 : 1;
   const size_t es = f64 ? 16 : 8;
-  // scratch layout: [butterfly state][reordered x][reordered y] (the last two only for nrhs > 1)
+  // scratch layout: [butterfly state][reordered x][reordered y] (the last two only for nrhs > 1).
+  // The column count is bounded before any product is formed, so the sizes
+  // below cannot wrap around: one column of state plus two vector columns
+  // must fit the array nrhs times.
+  const size_t col_bytes = ((size_t)df.state_len + (nrhs > 1 ? 2 * (size_t)df.n : 0)) * es;
+  if (col_bytes == 0 || (uint64_t)nrhs > (uint64_t)(kNoAllocScratchBytes / col_bytes)) {
+    set_error("hb_apply_noalloc: %lld right-hand sides need more scratch than the fixed limit of %zu bytes "
+              "(%zu bytes per right-hand side; use hb_apply, or fewer right-hand sides)", (long long)nrhs,
+              kNoAllocScratchBytes, col_bytes);
+    return HB_EINVAL;
+  }
   const size_t state_bytes = round256((size_t)df.state_len * (size_t)nrhs * es);
   const size_t vec_bytes = nrhs > 1 ? round256((size_t)df.n * (size_t)nrhs * es) : 0;
   const size_t need = state_bytes + 2 * vec_bytes;

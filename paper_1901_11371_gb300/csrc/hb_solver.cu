@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "hb_api_internal.h"
+#include "hb_sweep_launch.h"
 
 namespace hb {
 
@@ -200,6 +201,9 @@ __global__ void k_residual_cols(const double2* __restrict__ b, int64_t ld, const
   }
 }
 
+// max that keeps a NaN once seen (reports of diverged columns)
+static inline double nan_max(double a, double b) { return (std::isnan(a) || std::isnan(b)) ? NAN : std::max(a, b); }
+
 static inline int gsz(int64_t total) {
   int64_t g = (total + 255) / 256;
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
@@ -306,7 +310,17 @@ static int dots(Dev& d, const VT* V, int64_t vstride, int nvec, const VT* w, std
   hh.resize(tot);
   if (cudaMemcpyAsync(hh.data(), d.red_out, tot * sizeof(double2), cudaMemcpyDeviceToHost, d.st) != cudaSuccess)
     return HB_ECUDA;
+  // the sweep kernels' bounded-wait flag travels with every reduction, so a
+  // timed-out preconditioner stops the solver at its next synchronisation
+  int herr = 0;
+  GridBar* gb = (GridBar*)d.f->df.bar;
+  if (cudaMemcpyAsync(&herr, &gb->err, sizeof(int), cudaMemcpyDeviceToHost, d.st) != cudaSuccess) return HB_ECUDA;
   if (cudaStreamSynchronize(d.st) != cudaSuccess) return HB_ECUDA;
+  if (herr) {
+    cudaMemsetAsync(&gb->err, 0, sizeof(int), d.st);   // reported here: later calls start clean
+    set_error("a bounded device-side wait expired in a sweep kernel during the solve");
+    return HB_ETIMEOUT;
+  }
   return HB_OK;
 }
 
@@ -480,8 +494,9 @@ extern "C" int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int6
   for (int64_t c = 0; c < R; ++c) res_r[c] = bnorm[c] > 0 ? 1.0 : 0.0;
   while (iters < maxit) {
     nconv = 0;
-    for (int64_t c = 0; c < R; ++c) { done[c] = res_r[c] <= rtol; nconv += done[c]; }
-    if (nconv == R) break;
+    bool bad = false;
+    for (int64_t c = 0; c < R; ++c) { done[c] = res_r[c] <= rtol; nconv += done[c]; bad |= !std::isfinite(res_r[c]); }
+    if (nconv == R || bad) break;   // a non-finite residual ends the solve (reported as HB_ENAN)
     // ---- start vector
     std::vector<double> beta;
     if (!mixed) {
@@ -613,12 +628,15 @@ extern "C" int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int6
     if ((rc = launch_scatter_cols(xv, 0, n, R, x, 0, ld, 1.0, st))) return rc;
   }
   if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("hb_gmres: CUDA error"); return HB_ECUDA; }
+  if ((rc = hb_status(f, stream))) return rc;   // the last sweep's bounded waits
   nconv = 0;
   double worst = 0.0, worst_p = 0.0;
+  bool nonfinite = false;
   for (int64_t c = 0; c < R; ++c) {
     nconv += res_r[c] <= rtol;
-    worst = std::max(worst, res_r[c]);
-    worst_p = std::max(worst_p, pres_r[c]);
+    nonfinite |= !std::isfinite(res_r[c]);
+    worst = nan_max(worst, res_r[c]);
+    worst_p = nan_max(worst_p, pres_r[c]);
   }
   if (info) {
     int32_t* ipr = info->iters_per_rhs;
@@ -632,6 +650,11 @@ extern "C" int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int6
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (ipr) for (int64_t c = 0; c < R; ++c) ipr[c] = it_r[c];
     if (rpr) for (int64_t c = 0; c < R; ++c) rpr[c] = res_r[c];
+  }
+  if (nonfinite) {
+    set_error("hb_gmres: the residual became non-finite after %d iterations (overflow in the preconditioned "
+              "iteration)", iters);
+    return HB_ENAN;
   }
   if (nconv < R) { set_error("hb_gmres: %d of %lld columns did not reach rtol in %d iterations", (int)(R - nconv), (long long)R, iters); return HB_ENOCONV; }
   return HB_OK;
@@ -807,13 +830,14 @@ extern "C" int hb_tfqmr(hb_factor_t f, int op, const void* b_phys, const void* r
   if ((rc = true_residual())) return rc;
   if ((rc = launch_scatter_cols(t2, 0, n, R, x, 0, ld, 1.0, st))) return rc;
   if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("hb_tfqmr: CUDA error"); return HB_ECUDA; }
+  if ((rc = hb_status(f, stream))) return rc;   // the last sweep's bounded waits
   int nconv = 0, nbroken = 0;
   double worst = 0.0, worst_b = 0.0;
   for (int64_t c = 0; c < R; ++c) {
     nconv += res_r[c] <= rtol;
     nbroken += broken[c];
-    worst = std::max(worst, res_r[c]);
-    worst_b = std::max(worst_b, bound[c]);
+    worst = nan_max(worst, res_r[c]);
+    worst_b = nan_max(worst_b, bound[c]);
   }
   if (info) {
     info->iters = m;
@@ -825,6 +849,10 @@ extern "C" int hb_tfqmr(hb_factor_t f, int op, const void* b_phys, const void* r
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (info->iters_per_rhs) for (int64_t c = 0; c < R; ++c) info->iters_per_rhs[c] = it_r[c];
     if (info->res_per_rhs) for (int64_t c = 0; c < R; ++c) info->res_per_rhs[c] = res_r[c];
+  }
+  if (std::isnan(worst)) {
+    set_error("hb_tfqmr: the residual became non-finite after %d half steps", m);
+    return HB_ENAN;
   }
   if (nconv < R) {
     set_error("hb_tfqmr: %d of %lld columns did not reach rtol in %d half steps (%d broke down)", (int)(R - nconv),

@@ -72,3 +72,33 @@ def test_fullsize_batched_solve_sampled_residual(big):
         r = bs[rows, j] - ax[:, j]
         est = math.sqrt(wl.n / len(rows) * np.sum(np.abs(r) ** 2)) / np.linalg.norm(bs[:, j])
         assert est <= 2 * (10 * wl.eps + 1e-6), (cols[j], est)
+
+
+@pytest.mark.parametrize("name", ["spiral_N65536", "strips8_N131072"])
+def test_fullsize_apply_sampled_rows_other_workloads(big, name):
+    # The precision form's spiral (theta in [2 pi, 8 pi], N = 65,536, ranks up to 79) and the
+    # adjoint form's eight parallel strips (N = 131,072, near-field strip-to-strip blocks with
+    # ranks up to 166): complex-FP32 factors, sampled rows of hb_apply against exact rows of
+    # A^ x from the oracle's Hankel function.  Measured estimates 5.7e-6 and 6.8e-6; bound
+    # 2 x 10 eps as above.
+    torch, hb = big[0], big[1]
+    wl = W.WORKLOADS[name]
+    g = hb.hb_geometry(wl.kind, wl.params, wl.n)
+    f = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C64)
+    p = efie.Problem.from_workload(wl)
+    x = W.complex_gaussian(wl.n, 70).astype(np.complex64)
+    y = hb.hb_apply(f, torch.from_numpy(x).cuda()).cpu().numpy().astype(np.complex128)
+    rows = W.sample_rows(wl.n, 16, W.SEED_ROWS)
+    exact = _exact_rows(p, rows, x.astype(np.complex128)[:, None])[:, 0]
+    est = math.sqrt(wl.n / len(rows) * np.sum(np.abs(y[rows] - exact) ** 2)) / np.linalg.norm(y)
+    assert est <= 2 * 10 * wl.eps, est
+    # the adjoint apply on the same rows: (A^H x)_i = sum_j conj(A_ji) x_j, and A^ is
+    # reciprocal up to the segment lengths (A_ji w_i = A_ij w_j), so exact rows of A^H
+    # follow from exact rows of A^ with the weights
+    yh = hb.hb_apply(f, torch.from_numpy(x).cuda(), hb.HB_OP_H).cpu().numpy().astype(np.complex128)
+    _, w = g.segments()
+    cols = np.arange(wl.n)
+    ex_h = np.array([np.conj(p.entries(np.array([i]), cols)[0] * p.scale * w[i] / w) @ x.astype(np.complex128)
+                     for i in rows])
+    est_h = math.sqrt(wl.n / len(rows) * np.sum(np.abs(yh[rows] - ex_h) ** 2)) / np.linalg.norm(yh)
+    assert est_h <= 2 * 10 * wl.eps, est_h
