@@ -322,6 +322,13 @@ int hb_factor_host(hb_geometry_t g, double wavelength, double eta0, double gamma
 int hb_factor_host_ex(hb_geometry_t g, double wavelength, double eta0, double gamma, int64_t leaf, double eps,
                       uint64_t seed, int options, hb_factor_t* out);
 int hb_host_apply(hb_factor_t f, int op, const double* x, double* y);
+/* hb_host_apply_plan -- build the schedule of the persistent single-column
+ * apply for `grid` CTAs and factor entries of factor_bytes (8: complex64,
+ * 16: complex128), check its structure, and execute it on the host in FP64
+ * exactly as the kernel stages it (y = A^_F x or A^_F^H x).  Verifies the
+ * schedule without a GPU.  Returns the number of staging batches (>= 0),
+ * HB_EUNSUPPORTED if the schedule failed its check, or HB_EINVAL. */
+int hb_host_apply_plan(hb_factor_t f, int op, int grid, int factor_bytes, const double* x, double* y);
 int hb_host_sweep(hb_factor_t f, int which, double* vec);
 
 const char* hb_last_error(void);

@@ -120,6 +120,29 @@ int upload_factor(const PackedHost& ph, const HostFactor& hf, const Geometry& g,
   }
   HB_CU(cudaMalloc(&df.bar, 64));
   HB_CU(cudaMemsetAsync(df.bar, 0, 64, st));
+  HB_CU(cudaMalloc(&df.abar, 64));
+  HB_CU(cudaMemsetAsync(df.abar, 0, 64, st));
+  {
+    // persistent single-column apply plans, cut for this device's SMs
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int fes = form == HB_C128 ? 16 : 8;
+    for (int adj = 0; adj < 2 && sms > 0; ++adj) {
+      ApplyPlan plan;
+      build_apply_plan(ph, hf, adj != 0, sms, fes, kA1RingBytes / 2, plan);
+      DevPlan& dp = df.plan[adj];
+      if (!plan.ok) continue;   // the per-step kernels serve this direction
+      if ((rc = up(plan.batches, &dp.batches, st, df.device_bytes))) return rc;
+      if ((rc = up(plan.cta_batch, &dp.cta_batch, st, df.device_bytes))) return rc;
+      if ((rc = up(plan.image, &dp.image, st, df.device_bytes))) return rc;
+      HB_CU(cudaStreamSynchronize(st));
+      dp.nphase = plan.nphase;
+      dp.grid = sms;
+      dp.nbatch = (int64_t)plan.batches.size();
+      dp.ok = true;
+    }
+  }
   if ((rc = set_grid_min(df, ph, 16, st))) return rc;
   if ((rc = build_candidates(df, ph, 0, 1, st))) return rc;
   if ((rc = build_candidates(df, ph, 1, 2, st))) return rc;
@@ -181,9 +204,14 @@ void free_factor(DevFactor& df) {
                   df.prog[2], df.prog[3], df.segs[0], df.segs[1], df.segs[2], df.segs[3], df.bar,
                   df.flat[0], df.flat[1], df.flat[2], df.flat[3], df.flat_base[0], df.flat_base[1],
                   df.flat_base[2], df.flat_base[3], df.flat_pbytes[0], df.flat_pbytes[1], df.flat_pbytes[2],
-                  df.flat_pbytes[3], df.cx, df.cy, df.w};
+                  df.flat_pbytes[3], df.cx, df.cy, df.w, df.abar};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (DevPlan& dp : df.plan) {
+    void* pp[] = {dp.batches, dp.cta_batch, dp.image};
+    for (void* p : pp)
+      if (p) cudaFree(p);
+  }
   for (auto& per_cls : df.cand_segs)
     for (auto& per_prog : per_cls)
       for (DSeg* p : per_prog)
@@ -343,6 +371,19 @@ int hb_host_apply(hb_factor_t f, int op, const double* x, double* y) {
   if (!f || !f->host_only || !x || !y || (op != HB_OP_N && op != HB_OP_H)) { set_error("hb_host_apply: bad argument"); return HB_EINVAL; }
   host_apply(f->ph, f->hf, op == HB_OP_H, reinterpret_cast<const cplx*>(x), reinterpret_cast<cplx*>(y));
   return HB_OK;
+}
+
+int hb_host_apply_plan(hb_factor_t f, int op, int grid, int factor_bytes, const double* x, double* y) {
+  if (!f || !f->host_only || !x || !y || (op != HB_OP_N && op != HB_OP_H) || grid < 1 ||
+      (factor_bytes != 8 && factor_bytes != 16)) {
+    set_error("hb_host_apply_plan: bad argument");
+    return HB_EINVAL;
+  }
+  ApplyPlan plan;
+  build_apply_plan(f->ph, f->hf, op == HB_OP_H, grid, factor_bytes, kA1RingBytes / 2, plan);
+  if (!plan.ok) { set_error("hb_host_apply_plan: the plan failed its structural check"); return HB_EUNSUPPORTED; }
+  host_apply_plan(f->ph, plan, factor_bytes, op == HB_OP_H, reinterpret_cast<const cplx*>(x), reinterpret_cast<cplx*>(y));
+  return (int)std::min<size_t>(plan.batches.size(), (size_t)INT32_MAX);
 }
 
 int hb_host_sweep(hb_factor_t f, int which, double* vec) {
@@ -541,7 +582,7 @@ int apply_internal(hb_factor_t f, Prec p, bool adj, const void* x, void* y, int6
   f->prof.begin(0, st, e);
   int rc = launch_apply(f->df, p, adj, x, y, R, state, st);
   f->prof.end(0, st, e);
-  count_launch(f, (int)f->df.step_ptr.size() + 1);
+  count_launch(f, (R == 1 && apply1_ready(f->df, adj)) ? 1 : (int)f->df.step_ptr.size() + 1);
   return rc;
 }
 

@@ -9,6 +9,19 @@
 
 namespace hb {
 
+// Device copy of an ApplyPlan (persistent single-column apply).
+struct DevPlan {
+  A1Batch* batches = nullptr;
+  int32_t* cta_batch = nullptr;
+  uint8_t* image = nullptr;    // batch images (ApplyPlan::image)
+  int nphase = 0;
+  int grid = 0;          // CTAs the plan was cut for (the device's SM count at upload)
+  bool ok = false;
+  int64_t nbatch = 0;
+};
+// Shared-memory staging ring of the persistent apply (bytes per CTA).
+constexpr int kA1RingBytes = 200 * 1024;
+
 struct DevFactor {
   int form = HB_C128;            // storage form of the factor pool
   int64_t n = 0, n0 = 0, m = 0;
@@ -53,6 +66,8 @@ struct DevFactor {
   float cand_ms[2][kNCand] = {};                            // last autotune timings
   int tuned[2] = {-1, -1};                                  // chosen candidate for 1 RHS / several RHS (-1: grid_min)
   void* bar = nullptr;                                      // grid barrier state + error flag
+  void* abar = nullptr;                                     // grid barrier of the persistent apply
+  DevPlan plan[2];                                          // persistent apply plans: forward, adjoint
   long long spin_limit = 1LL << 24;                         // bounded waits of the grid barrier
   // geometry on the device (far field, plane waves)
   double* cx = nullptr;
@@ -78,6 +93,10 @@ enum Prec { PREC_F64 = 0,        // double factors, double arithmetic (HB_C128)
 // `state` holds df.state_len * R complex entries of the same type.
 int launch_apply(const DevFactor& df, Prec p, bool adjoint, const void* x, void* y, int64_t R, void* state,
                  cudaStream_t st);
+// Persistent single-column apply (one cooperative launch); apply1_ready:
+// the plan of that direction exists for the current device.
+bool apply1_ready(const DevFactor& df, bool adjoint);
+int launch_apply1(const DevFactor& df, Prec p, bool adjoint, const void* x, void* y, void* state, cudaStream_t st);
 // Cooperative sweep, in place: vec holds b on entry and x on exit.  which:
 // 0 = L~^{-1}, 1 = U~^{-1}, 2 = L~^{-H}, 3 = U~^{-H}.  One launch per sweep,
 // grid barriers between segments.

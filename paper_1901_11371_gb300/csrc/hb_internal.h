@@ -4,6 +4,7 @@
 
 #include <complex>
 #include <cstdint>
+#include <cstring>
 #include <functional>
 #include <string>
 #include <vector>
@@ -224,31 +225,50 @@ inline int32_t flat_stage_bytes32(const FlatOp& f) {
 // (gathered by the compute warps after the phase barrier).
 // ---------------------------------------------------------------------------
 struct A1Task {
-  int32_t op0, nops;   // FlatOp range, executed in order by one warp
-  int32_t kind;        // 0 ENTER, 1 ITEM, 2 DLEAF, 3 EXIT
-  int32_t pad;
+  int32_t op0, nops;   // FlatOp range; DLEAF / EXIT: executed in order by one warp
+  int32_t kind;        // 0 ENTER, 1 ITEM (ops independent); 2 DLEAF, 3 EXIT (one warp)
+  int32_t pad;         // first staged vector entry of the task (batch-relative)
 };
+// Staging area of a batch: [task records][op records][factor / index
+// blocks][gather list][staged vector entries]; everything before the staged
+// entries is copied in by the producer warp.
 struct A1Batch {
   int32_t phase;
   int32_t task0, ntasks;
-  int32_t tma_bytes;   // bytes the producer copies (factor/index blocks + gather list)
+  int32_t op0, nops;   // op records of the batch (consecutive)
+  int32_t rec_off;     // byte offset of the op records (after ntasks 16-byte task records)
+  int32_t tma_bytes;   // bytes the producer copies
   int32_t area_bytes;  // staging area: tma_bytes + staged vector entries (16 bytes each)
   int32_t gl_off;      // byte offset of the gather list inside the area
   int32_t nvec;        // staged vector entries (= gather-list length)
   int32_t vec_off;     // byte offset of the staged vector entries inside the area
+  int32_t npar;        // the first npar ops (of ENTER / ITEM tasks) are independent: one warp each;
+                       // the tasks from task0 + nptask on (DLEAF / EXIT) take one warp per task
+  int32_t nptask;
+  int32_t pad;
   int64_t gl_src;      // first gather-list entry in ApplyPlan::gl
+  int64_t img;         // byte offset of the batch's image (its first tma_bytes bytes, ready to copy)
+  int64_t pad2;
 };
+static_assert(sizeof(A1Task) == 16, "task record");
+static_assert(sizeof(A1Batch) == 80, "batch record");
+// Largest number of tasks in one batch (the kernel's per-warp row table).
+constexpr int kA1MaxTasks = 128;
 // Gather-list entry: bit 31 set = row of the vector x (bits 0..30), else a
 // butterfly-state entry; bit 30 set (with bit 31) = a row of the output y.
 constexpr uint32_t kA1FromX = 0x80000000u;
 constexpr uint32_t kA1FromY = 0xC0000000u;
 struct ApplyPlan {
   std::vector<FlatOp> ops;      // soff: byte offset of the op's blocks in its batch area;
-                                // pad: first staged vector entry of the op (inputs; EXIT/DLEAF: also the rows)
+                                // pad: first staged vector entry of the op's inputs (batch-relative)
   std::vector<A1Task> tasks;
   std::vector<A1Batch> batches;
   std::vector<int32_t> cta_batch;   // [G + 1]: batches of CTA g are [cta_batch[g], cta_batch[g+1])
   std::vector<uint32_t> gl;         // gather lists of all batches
+  // Batch images: for every batch, in plan order, the bytes the producer copies into its
+  // staging area (task and op records, factor and index blocks in the factor's element
+  // type, gather list), so that one bulk copy fills a batch.
+  std::vector<uint8_t> image;
   int nphase = 0;
   int max_area = 0;
   bool ok = true;
@@ -316,13 +336,69 @@ constexpr int kRunMaxPhases = 511;   // (phases + 1) x 8 bytes of phase table <=
 std::vector<DSeg> segment_program(const std::vector<DPhase>& prog, const FlatProgram& fp, int grid_min,
                                   int64_t res_entries);
 
+// ---------------------------------------------------------------------------
+// Split-BF16 tensor-core operands of the forward many-column apply (form
+// HB_SPLIT_BF16).  The entry ops of a column leaf (its V0 blocks of every
+// depth, stacked) and the exit ops of a row leaf (its U0 blocks of every
+// depth side by side, then the dense diagonal block) are dense contractions
+// W (outputs x inputs) times the leaf's vector block (inputs x columns).
+// Each W is expanded to real form and cut into chunks of at most 64 complex
+// outputs and 64 complex inputs; a chunk's B operand holds
+//   rows n < nn:       [ Re W(n, :) | -Im W(n, :) ]
+//   rows nn + n:       [ Im W(n, :) |  Re W(n, :) ]
+// as bf16 hi and lo parts (W = hi + lo), each block in the canonical
+// K-major, no-swizzle tensor-core layout (8 x 8 core matrices of 128 bytes,
+// the K-adjacent ones contiguous, row groups (2 nk / 8) x 128 bytes apart).
+// ---------------------------------------------------------------------------
+struct TcChunk {
+  int64_t boff;      // bf16 offset of the chunk's B operand (hi block, then lo block; 2nn x 2nk each)
+  int32_t nn, nk;    // complex outputs / inputs (multiples of 8, at most 64)
+  int32_t in0, out0; // first entries of the chunk's input / output tables
+  int32_t tcol;      // tensor-memory column of the chunk's accumulator
+  int32_t flags;     // TC_ACC: add to the accumulator; TC_LAST: write the accumulator out after this chunk
+};
+static_assert(sizeof(TcChunk) == 32, "chunk record");
+enum { TC_ACC = 1, TC_LAST = 2 };
+struct TcJob { int32_t chunk0, nchunk; };
+// table entries: a butterfly-state entry, kTcVec | row of the vector (x for inputs, y for outputs), or kTcNone
+constexpr uint32_t kTcVec = 0x80000000u;
+constexpr uint32_t kTcNone = 0xFFFFFFFFu;
+struct TcOperands {
+  std::vector<uint16_t> bpool;      // bf16 bit patterns
+  std::vector<TcChunk> chunks;
+  std::vector<TcJob> enter, exit;   // per leaf
+  std::vector<uint32_t> tab;
+};
+void build_tc_operands(const PackedHost& ph, const HostFactor& hf, TcOperands& tc);
+// offset (elements) of entry (r, k) of a bf16 operand block with kk columns in the layout above
+inline int64_t tc_off(int64_t r, int64_t k, int64_t kk) {
+  return (r / 8) * (kk / 8) * 64 + (k / 8) * 64 + (r % 8) * 8 + (k % 8);
+}
+// bf16 bit pattern of a float, round to nearest even (finite inputs)
+inline uint16_t bf16_bits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+inline float bf16_value(uint16_t b) {
+  uint32_t u = (uint32_t)b << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
 // Plan of the persistent single-column apply for G CTAs, factor entries of
 // fes bytes, staging areas of at most max_area bytes (adj: A^H).
-void build_apply_plan(const PackedHost& ph, bool adj, int G, int fes, int max_area, ApplyPlan& plan);
-// Execute a plan on the host in plan order (verification of the plan
-// without a GPU): y = A^_F x or A^_F^H x.
-void host_apply_plan(const PackedHost& ph, const HostFactor& hf, const ApplyPlan& plan, bool adj, const cplx* x,
-                     cplx* y);
+void build_apply_plan(const PackedHost& ph, const HostFactor& hf, bool adj, int G, int fes, int max_area,
+                      ApplyPlan& plan);
+// Structural check of a plan against the layout the kernel assumes (areas,
+// offsets, alignment, gather-list ranges, op ranges); false on any violation.
+bool check_apply_plan(const ApplyPlan& plan, const PackedHost& ph, int fes, int max_area);
+// Execute a plan on the host in plan order, reading every record, block and
+// gather list from the batch images as the kernel does (verification of the
+// plan without a GPU): y = A^_F x or A^_F^H x.
+void host_apply_plan(const PackedHost& ph, const ApplyPlan& plan, int fes, bool adj, const cplx* x, cplx* y);
 
 // FP64 host execution of the packed program (verification without a GPU).
 void host_apply(const PackedHost& ph, const HostFactor& hf, bool adj, const cplx* x, cplx* y);

@@ -584,13 +584,14 @@ template <class T, class F>
 static int apply_dispatch(const DevFactor& df, bool adj, const void* x, void* y, int64_t R, void* st,
                           cudaStream_t s) {
   if (R >= kWideMin) return apply_wide<T, F>(df, adj, x, y, R, st, s);
-  if (R == 1) return apply_impl<T, F, 1>(df, adj, x, y, R, st, s);
+  if (R == 1) return apply_impl<T, F, 1>(df, adj, x, y, R, st, s);   // (the persistent kernel is tried first, in launch_apply)
   if (R <= 4) return apply_impl<T, F, 4>(df, adj, x, y, R, st, s);
   return apply_impl<T, F, 8>(df, adj, x, y, R, st, s);
 }
 
 int launch_apply(const DevFactor& df, Prec p, bool adjoint, const void* x, void* y, int64_t R, void* state,
                  cudaStream_t st) {
+  if (R == 1 && apply1_ready(df, adjoint)) return launch_apply1(df, p, adjoint, x, y, state, st);
   if (p == PREC_F64) return apply_dispatch<double, double2>(df, adjoint, x, y, R, state, st);
   if (p == PREC_F32) return apply_dispatch<float, float2>(df, adjoint, x, y, R, state, st);
   return apply_dispatch<double, float2>(df, adjoint, x, y, R, state, st);

@@ -11,6 +11,7 @@
 // one row leaf, which are placed in consecutive phases.
 #include <algorithm>
 #include <cstring>
+#include <functional>
 
 #include "hb_internal.h"
 
@@ -33,18 +34,25 @@ int64_t op_fbytes(const FlatOp& f, int fes) {
 }
 
 // area of a task: blocks + gather list (4 bytes per entry) + staged entries (16 bytes each)
-int64_t task_area(const TaskDraft& t) { return t.fbytes + 4 * (int64_t)t.gl.size() + 16 * (int64_t)t.gl.size(); }
+int64_t task_area(const TaskDraft& t) {
+  return 16 + 64 * (int64_t)t.ops.size() + t.fbytes + 4 * (int64_t)t.gl.size() + 16 * (int64_t)t.gl.size();
+}
 
 }  // namespace
 
-void build_apply_plan(const PackedHost& ph, bool adj, int G, int fes, int max_area, ApplyPlan& plan) {
+void build_apply_plan(const PackedHost& ph, const HostFactor& hf, bool adj, int G, int fes, int max_area,
+                      ApplyPlan& plan) {
   plan = ApplyPlan();
   const int D = ph.depth;
   const int64_t m = ph.m, n0 = ph.n0;
   const std::vector<int32_t>& ptr = adj ? ph.astep_ptr : ph.step_ptr;
   const std::vector<int32_t>& sidx = adj ? ph.astep_idx : ph.step_idx;
   const int S = (int)ptr.size() - 1;                    // inner steps
-  const int64_t task_max = std::max<int64_t>(max_area / 2, 4096);
+  // batches are consumed one per warp: a batch target of an eighth of the largest area lets
+  // the compute warps hold several batches each while the producer fills the rest of the ring;
+  // entry and exit tasks are cut to that size (a single larger op gets a batch of its own)
+  const int64_t batch_target = std::max<int64_t>(max_area / 8, 4096);
+  const int64_t task_max = batch_target;
   auto blkm = [](const DBlk& b) { return (int64_t)b.k * (b.c - b.k); };
 
   // ---- drafts per phase
@@ -83,9 +91,12 @@ void build_apply_plan(const PackedHost& ph, bool adj, int G, int fes, int max_ar
     flush();
   }
   // dense leaves: column chunks, chunk c in phase c (forward chunks accumulate)
-  int64_t nc = std::max<int64_t>(1, (int64_t)8192 / ((int64_t)fes * n0) * 2);   // <= 16 KB of matrix
-  nc = std::min<int64_t>(nc, n0);
+  // (at most half a batch of matrix per chunk; at least four chunks when there are phases for them, so
+  // that the independent leaf products spread over the first inner phases)
+  int64_t nc = std::max<int64_t>(1, batch_target / 2 / ((int64_t)fes * n0));
+  nc = std::min<int64_t>(nc, (n0 + 3) / 4);
   nc = std::max<int64_t>(nc, (n0 + S) / (S + 1));
+  nc = std::max<int64_t>(1, std::min<int64_t>(nc, n0));
   const int64_t nchunk = (n0 + nc - 1) / nc;
   if (nchunk > S + 1) plan.ok = false;
   for (int64_t l = 0; l < m; ++l)
@@ -210,36 +221,51 @@ void build_apply_plan(const PackedHost& ph, bool adj, int G, int fes, int max_ar
   for (auto& e : exits) phases.push_back(std::move(e));
   plan.nphase = (int)phases.size();
 
-  // ---- CTA ranges (balanced by area) and batches
-  std::vector<std::vector<A1Batch>> per_cta((size_t)G);
+  // ---- CTA assignment and batches.  Every task goes to the CTA with the least work so far
+  // (work = staging bytes plus a per-output-row charge), so that each CTA of a phase gets a
+  // mix of the phase's task kinds and about the same time; a CTA's tasks are then cut into
+  // batches of about batch_target bytes and at most kA1MaxTasks tasks.
   struct BatchDraft { int phase; std::vector<const TaskDraft*> tasks; };
   std::vector<std::vector<BatchDraft>> bd((size_t)G);
-  const int64_t batch_target = std::max<int64_t>(max_area / 4, 8192);
+  auto task_rows = [&](const TaskDraft& t) {
+    int64_t r = 0;
+    for (const FlatOp& f : t.ops) {
+      if (t.kind == 3) return (int64_t)n0;
+      if (f.kind == FK_GATHER) r += f.k0 + ((f.flags & FF_TWO) ? f.k1 : 0);
+      else if (f.kind == FK_SCATTER) r += f.c0;
+      else if (f.kind == FK_MIDDLE) r += (f.flags & FF_ADJ) ? f.c0 : f.k0;
+      else r += (f.flags & FF_ADJ) ? f.k1 : n0;
+    }
+    return r;
+  };
   for (int p = 0; p < plan.nphase; ++p) {
     const std::vector<TaskDraft>& tl = phases[(size_t)p];
-    int64_t total = 0;
+    std::vector<std::vector<const TaskDraft*>> mine((size_t)G);
+    // min-heap of (work, cta)
+    std::vector<std::pair<int64_t, int>> heap;
+    for (int g = 0; g < G; ++g) heap.push_back({0, g});
+    std::make_heap(heap.begin(), heap.end(), std::greater<std::pair<int64_t, int>>());
     for (const TaskDraft& t : tl) {
       const int64_t a = task_area(t);
       if (a + 16 > max_area) plan.ok = false;
-      total += a;
+      std::pop_heap(heap.begin(), heap.end(), std::greater<std::pair<int64_t, int>>());
+      auto& top = heap.back();
+      mine[(size_t)top.second].push_back(&t);
+      top.first += a + 96 * task_rows(t);
+      std::push_heap(heap.begin(), heap.end(), std::greater<std::pair<int64_t, int>>());
     }
-    size_t ti = 0;
-    int64_t acc = 0;
     for (int g = 0; g < G; ++g) {
-      const int64_t goal = (total * (int64_t)(g + 1)) / G;
       BatchDraft cur{p, {}};
       int64_t cur_area = 0;
-      while (ti < tl.size() && (acc < goal || g == G - 1)) {
-        const int64_t a = task_area(tl[ti]);
-        if (!cur.tasks.empty() && cur_area + a > batch_target) {
+      for (const TaskDraft* t : mine[(size_t)g]) {
+        const int64_t a = task_area(*t);
+        if (!cur.tasks.empty() && (cur_area + a > batch_target || (int)cur.tasks.size() >= kA1MaxTasks)) {
           bd[(size_t)g].push_back(cur);
           cur = BatchDraft{p, {}};
           cur_area = 0;
         }
-        cur.tasks.push_back(&tl[ti]);
-        cur_area += a + 64;
-        acc += a;
-        ++ti;
+        cur.tasks.push_back(t);
+        cur_area += a;
       }
       if (!cur.tasks.empty()) bd[(size_t)g].push_back(cur);
     }
@@ -253,9 +279,21 @@ void build_apply_plan(const PackedHost& ph, bool adj, int G, int fes, int max_ar
       B.phase = b.phase;
       B.task0 = (int32_t)plan.tasks.size();
       B.ntasks = (int32_t)b.tasks.size();
-      int64_t off = 0;
+      B.op0 = (int32_t)plan.ops.size();
+      int32_t nops = 0;
+      for (const TaskDraft* t : b.tasks) nops += (int32_t)t->ops.size();
+      B.nops = nops;
+      B.rec_off = (int32_t)(16 * (int64_t)B.ntasks);
+      int64_t off = B.rec_off + 64 * (int64_t)nops;
       int32_t nvec = 0;
-      for (const TaskDraft* t : b.tasks) {
+      // independent-op tasks first (their ops spread over the warps), then the one-warp tasks
+      std::vector<const TaskDraft*> order;
+      for (const TaskDraft* t : b.tasks) if (t->kind <= 1) order.push_back(t);
+      B.nptask = (int32_t)order.size();
+      B.npar = 0;
+      for (const TaskDraft* t : order) B.npar += (int32_t)t->ops.size();
+      for (const TaskDraft* t : b.tasks) if (t->kind > 1) order.push_back(t);
+      for (const TaskDraft* t : order) {
         A1Task T{};
         T.op0 = (int32_t)plan.ops.size();
         T.nops = (int32_t)t->ops.size();
@@ -264,7 +302,8 @@ void build_apply_plan(const PackedHost& ph, bool adj, int G, int fes, int max_ar
         for (FlatOp f : t->ops) {
           f.soff = (int32_t)off;
           off += op_fbytes(f, fes);
-          f.pad = (int16_t)(f.pad + 0);   // relative to the task's first staged entry
+          if (nvec + f.pad > INT16_MAX) plan.ok = false;
+          f.pad = (int16_t)(nvec + f.pad);   // batch-relative
           plan.ops.push_back(f);
         }
         plan.tasks.push_back(T);
@@ -287,6 +326,102 @@ void build_apply_plan(const PackedHost& ph, bool adj, int G, int fes, int max_ar
   }
   plan.cta_batch[(size_t)G] = (int32_t)plan.batches.size();
   for (int i = 0; i < 16; ++i) plan.gl.push_back(0);     // tail: 16-byte bulk copies stay inside
+  if (plan.ok) plan.ok = check_apply_plan(plan, ph, fes, max_area);
+  if (!plan.ok) return;
+  // ---- batch images
+  int64_t total = 0;
+  for (A1Batch& B : plan.batches) {
+    B.img = total;
+    total += B.tma_bytes;
+  }
+  plan.image.assign((size_t)total, 0);
+  auto put_elem = [&](uint8_t* dst, cplx v) {
+    if (fes == 16) {
+      const double d[2] = {v.real(), v.imag()};
+      std::memcpy(dst, d, 16);
+    } else {
+      const float f[2] = {(float)v.real(), (float)v.imag()};
+      std::memcpy(dst, f, 8);
+    }
+  };
+  for (const A1Batch& B : plan.batches) {
+    uint8_t* base = plan.image.data() + B.img;
+    std::memcpy(base, &plan.tasks[(size_t)B.task0], 16 * (size_t)B.ntasks);
+    std::memcpy(base + B.rec_off, &plan.ops[(size_t)B.op0], 64 * (size_t)B.nops);
+    for (int32_t o = B.op0; o < B.op0 + B.nops; ++o) {
+      const FlatOp& f = plan.ops[(size_t)o];
+      uint8_t* d = base + f.soff;
+      if (f.kind == FK_DLEAF) {
+        // device layout [leaf][c][r]: the chunk's columns one after the other
+        const int64_t l = f.moff / (ph.n0 * ph.n0), cb = f.c1;
+        for (int64_t cc = 0; cc < f.k1; ++cc)
+          for (int64_t r = 0; r < ph.n0; ++r)
+            put_elem(d + (cc * ph.n0 + r) * fes, hf.leaf[(size_t)((l * ph.n0 + r) * ph.n0 + cb + cc)]);
+      } else {
+        for (int64_t e = 0; e < f.melems; ++e) put_elem(d + e * fes, ph.fpool[(size_t)(f.moff + e)]);
+      }
+      if (f.ioff >= 0)
+        std::memcpy(d + a16((int64_t)f.melems * fes), &ph.ipool[(size_t)f.ioff], 2 * (size_t)f.ielems);
+    }
+    std::memcpy(base + B.gl_off, &plan.gl[(size_t)B.gl_src], 4 * (size_t)B.nvec);
+  }
+}
+
+bool check_apply_plan(const ApplyPlan& plan, const PackedHost& ph, int fes, int max_area) {
+  const int64_t nst = ph.state_len, n = ph.n, n0 = ph.n0;
+  const int G = (int)plan.cta_batch.size() - 1;
+  if (G < 1 || plan.cta_batch[0] != 0 || plan.cta_batch[(size_t)G] != (int32_t)plan.batches.size()) return false;
+  const int64_t fpool = (int64_t)ph.fpool.size(), ipool = (int64_t)ph.ipool.size(), leaf = ph.m * n0 * n0;
+  for (int g = 0; g < G; ++g) {
+    int last_phase = -1;
+    for (int32_t b = plan.cta_batch[(size_t)g]; b < plan.cta_batch[(size_t)g + 1]; ++b) {
+      const A1Batch& B = plan.batches[(size_t)b];
+      if (B.phase < last_phase || B.phase >= plan.nphase) return false;   // phase order per CTA
+      last_phase = B.phase;
+      if (B.area_bytes > max_area || B.area_bytes < B.tma_bytes || (B.area_bytes & 15)) return false;
+      if (B.rec_off != 16 * B.ntasks || (B.gl_off & 15) || (B.vec_off & 15)) return false;
+      if (B.ntasks < 1 || B.ntasks > kA1MaxTasks || B.nvec > INT16_MAX) return false;
+      if (B.vec_off + 16 * (int64_t)B.nvec > B.area_bytes || B.gl_off + 4 * (int64_t)B.nvec > B.tma_bytes) return false;
+      if (B.gl_src < 0 || (B.gl_src & 3) || B.gl_src + (B.nvec + 3) / 4 * 4 + 16 > (int64_t)plan.gl.size()) return false;
+      if (B.op0 < 0 || B.op0 + B.nops > (int32_t)plan.ops.size()) return false;
+      int64_t bytes = B.rec_off + 64 * (int64_t)B.nops;
+      int32_t op_next = B.op0;
+      for (int32_t t = B.task0; t < B.task0 + B.ntasks; ++t) {
+        const A1Task& T = plan.tasks[(size_t)t];
+        if (T.op0 != op_next || T.nops < 1) return false;
+        op_next += T.nops;
+        for (int32_t o = T.op0; o < T.op0 + T.nops; ++o) {
+          const FlatOp& f = plan.ops[(size_t)o];
+          const int64_t mb = a16((int64_t)f.melems * fes), ib = f.ioff >= 0 ? a16((int64_t)f.ielems * 2) : 0;
+          if (f.soff != bytes || (f.soff & 15)) return false;
+          bytes += mb + ib;
+          if (f.kind == FK_DLEAF) {
+            if (f.moff < 0 || f.moff + a16((int64_t)f.melems * fes) / fes > leaf || ((f.moff * fes) & 15)) return false;
+          } else if (f.moff < 0 || f.moff + mb / fes > fpool + 4 || ((f.moff * fes) & 15)) {
+            return false;
+          }
+          if (f.ioff >= 0 && ((f.ioff & 7) || f.ioff + ib / 2 > ipool)) return false;
+          const int64_t first = f.pad, cnt = f.n_s0 + f.n_s1 + ((f.flags & FF_ACC) && f.kind == FK_DLEAF ? n0 : 0);
+          if ((T.kind <= 1) != (t < B.task0 + B.nptask)) return false;
+          if (first < 0 || first + cnt > B.nvec) return false;
+          // gather-list entries in range
+          for (int64_t e = first; e < first + cnt; ++e) {
+            const uint32_t s = plan.gl[(size_t)(B.gl_src + e)];
+            if ((s & kA1FromY) == kA1FromY) { if ((int64_t)(s & 0x3FFFFFFFu) >= n) return false; }
+            else if (s & kA1FromX) { if ((int64_t)(s & 0x3FFFFFFFu) >= n) return false; }
+            else if ((int64_t)s >= nst) return false;
+          }
+          const bool outv = (f.flags & FF_OUT_VEC) != 0;
+          const int64_t lim = outv ? n : nst;
+          if (f.out0 < 0 || f.out0 >= lim || f.out1 < 0 || f.out1 >= std::max<int64_t>(nst, 1)) return false;
+        }
+      }
+      if (op_next != B.op0 + B.nops || bytes != B.gl_off) return false;
+      if (B.nptask < 0 || B.nptask > B.ntasks || B.npar < 0 || B.npar > B.nops) return false;
+      if (B.nptask < B.ntasks && plan.tasks[(size_t)(B.task0 + B.nptask)].op0 != B.op0 + B.npar) return false;
+    }
+  }
+  return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -294,49 +429,63 @@ void build_apply_plan(const PackedHost& ph, bool adj, int G, int fes, int max_ar
 // staging the vector entries through the gather lists exactly as the kernel
 // does, so a wrong offset, list or chain order shows up against host_apply.
 // ---------------------------------------------------------------------------
-void host_apply_plan(const PackedHost& ph, const HostFactor& hf, const ApplyPlan& plan, bool adj, const cplx* x,
-                     cplx* y) {
+void host_apply_plan(const PackedHost& ph, const ApplyPlan& plan, int fes, bool adj, const cplx* x, cplx* y) {
   const int64_t n0 = ph.n0;
   std::vector<cplx> st((size_t)ph.state_len, cplx(0.0));
   std::fill(y, y + ph.n, cplx(std::nan(""), 0.0));
   const int G = (int)plan.cta_batch.size() - 1;
-  auto M = [&](const FlatOp& f, int64_t e) { return ph.fpool[(size_t)(f.moff + e)]; };
-  auto I = [&](const FlatOp& f, int64_t e) { return ph.ipool[(size_t)(f.ioff + e)]; };
-  auto leafm = [&](const FlatOp& f, int64_t r, int64_t c) {   // device layout: [leaf][c][r]
-    const int64_t l = f.moff / (n0 * n0);
-    return hf.leaf[(size_t)((l * n0 + r) * n0 + c)];
+  auto elem = [&](const uint8_t* p) {
+    if (fes == 16) {
+      double d[2];
+      std::memcpy(d, p, 16);
+      return cplx(d[0], d[1]);
+    }
+    float f[2];
+    std::memcpy(f, p, 8);
+    return cplx(f[0], f[1]);
   };
   for (int p = 0; p < plan.nphase; ++p) {
     for (int g = 0; g < G; ++g) {
       for (int32_t b = plan.cta_batch[(size_t)g]; b < plan.cta_batch[(size_t)g + 1]; ++b) {
         const A1Batch& B = plan.batches[(size_t)b];
         if (B.phase != p) continue;
+        const uint8_t* area = plan.image.data() + B.img;     // what the producer copies in
+        std::vector<A1Task> tks((size_t)B.ntasks);
+        std::vector<FlatOp> recs((size_t)B.nops);
+        std::memcpy(tks.data(), area, 16 * (size_t)B.ntasks);
+        std::memcpy(recs.data(), area + B.rec_off, 64 * (size_t)B.nops);
+        std::vector<uint32_t> gl((size_t)B.nvec);
+        std::memcpy(gl.data(), area + B.gl_off, 4 * (size_t)B.nvec);
         std::vector<cplx> sv((size_t)B.nvec);
         for (int e = 0; e < B.nvec; ++e) {
-          const uint32_t s = plan.gl[(size_t)(B.gl_src + e)];
+          const uint32_t s = gl[(size_t)e];
           if ((s & kA1FromY) == kA1FromY) sv[(size_t)e] = y[s & 0x3FFFFFFFu];
           else if (s & kA1FromX) sv[(size_t)e] = x[s & 0x3FFFFFFFu];
           else sv[(size_t)e] = st[s];
         }
-        for (int32_t t = B.task0; t < B.task0 + B.ntasks; ++t) {
-          const A1Task& T = plan.tasks[(size_t)t];
+        for (int32_t t = 0; t < B.ntasks; ++t) {
+          const A1Task& T = tks[(size_t)t];
           const cplx* tv = sv.data() + T.pad;
           std::vector<cplx> acc;
           for (int32_t o = T.op0; o < T.op0 + T.nops; ++o) {
-            const FlatOp& f = plan.ops[(size_t)o];
-            const cplx* in = tv + f.pad;
+            const FlatOp& f = recs[(size_t)(o - B.op0)];
+            const cplx* in = sv.data() + f.pad;
+            const uint8_t* mb = area + f.soff;
+            const int16_t* ib = (const int16_t*)(area + f.soff + a16((int64_t)f.melems * fes));
+            auto M = [&](int64_t e) { return elem(mb + e * fes); };
+            auto I = [&](int64_t e) { return ib[e]; };
             if (f.kind == FK_DLEAF) {
-              const int64_t cb = f.c1, cn = f.k1;
+              const int64_t cn = f.k1;
               if (!adj) {
                 for (int64_t r = 0; r < n0; ++r) {
-                  cplx a = (f.flags & FF_ACC) ? tv[f.n_s0 + r] : cplx(0.0);
-                  for (int64_t c = 0; c < cn; ++c) a += leafm(f, r, cb + c) * in[c];
+                  cplx a = (f.flags & FF_ACC) ? in[f.n_s0 + r] : cplx(0.0);
+                  for (int64_t c = 0; c < cn; ++c) a += M(c * n0 + r) * in[c];
                   y[(size_t)(f.out0 + r)] = a;
                 }
               } else {
                 for (int64_t c = 0; c < cn; ++c) {
                   cplx a = 0.0;
-                  for (int64_t r = 0; r < n0; ++r) a += std::conj(leafm(f, r, cb + c)) * in[r];
+                  for (int64_t r = 0; r < n0; ++r) a += std::conj(M(c * n0 + r)) * in[r];
                   y[(size_t)(f.out0 + c)] = a;
                 }
               }
@@ -347,10 +496,10 @@ void host_apply_plan(const PackedHost& ph, const HostFactor& hf, const ApplyPlan
                 const int64_t mo = s2 ? f.m1 : 0, io = s2 ? f.i1 : 0;
                 const int32_t out = s2 ? f.out1 : f.out0;
                 for (int i = 0; i < k; ++i) {
-                  cplx a = in[I(f, io + i)];
+                  cplx a = in[I(io + i)];
                   for (int j = 0; j < nr; ++j) {
-                    cplx mm = cj ? std::conj(M(f, mo + (int64_t)i * nr + j)) : M(f, mo + (int64_t)j * k + i);
-                    a += mm * in[I(f, io + k + j)];
+                    cplx mm = cj ? std::conj(M(mo + (int64_t)i * nr + j)) : M(mo + (int64_t)j * k + i);
+                    a += mm * in[I(io + k + j)];
                   }
                   st[(size_t)(out + i)] = a;
                 }
@@ -358,21 +507,19 @@ void host_apply_plan(const PackedHost& ph, const HostFactor& hf, const ApplyPlan
             } else if (f.kind == FK_SCATTER) {
               const bool cj = (f.flags & FF_CONJ) != 0;
               const int nrow = f.c0;
-              if (f.flags & FF_ACC) {
-                if (acc.empty()) acc.assign(tv, tv + n0);
-              }
+              if ((f.flags & FF_ACC) && acc.empty()) acc.assign(tv, tv + n0);
               for (int r = 0; r < nrow; ++r) {
                 cplx a = 0.0;
                 for (int s2 = 0; s2 < ((f.flags & FF_TWO) ? 2 : 1); ++s2) {
                   const int k = s2 ? f.k1 : f.k0, c = s2 ? f.c1 : f.c0, nr = c - k;
                   const int64_t mo = s2 ? f.m1 : 0, io = s2 ? f.i1 : 0;
                   const cplx* yy = in + (s2 ? f.n_s0 : 0);
-                  const int code = I(f, io + c + r);
+                  const int code = I(io + c + r);
                   if (code >= 0) a += yy[code];
                   else {
                     const int j = -1 - code;
                     for (int i = 0; i < k; ++i) {
-                      cplx mm = cj ? std::conj(M(f, mo + (int64_t)j * k + i)) : M(f, mo + (int64_t)i * nr + j);
+                      cplx mm = cj ? std::conj(M(mo + (int64_t)j * k + i)) : M(mo + (int64_t)i * nr + j);
                       a += mm * yy[i];
                     }
                   }
@@ -388,13 +535,13 @@ void host_apply_plan(const PackedHost& ph, const HostFactor& hf, const ApplyPlan
               for (int o2 = 0; o2 < nout; ++o2) {
                 cplx a = 0.0;
                 for (int i = 0; i < nin; ++i)
-                  a += (a2 ? std::conj(M(f, (int64_t)o2 * kr + i)) : M(f, (int64_t)i * kr + o2)) * in[i];
+                  a += (a2 ? std::conj(M((int64_t)o2 * kr + i)) : M((int64_t)i * kr + o2)) * in[i];
                 st[(size_t)(f.out0 + o2)] = a;
               }
             }
           }
           if (!acc.empty()) {
-            const FlatOp& f0 = plan.ops[(size_t)T.op0];
+            const FlatOp& f0 = recs[(size_t)(T.op0 - B.op0)];
             for (int64_t r = 0; r < n0; ++r) y[(size_t)(f0.out0 + r)] = acc[(size_t)r];
           }
         }

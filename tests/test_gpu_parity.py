@@ -113,6 +113,28 @@ def test_apply_many_rhs_column_parallel(hb, strip, R):
     assert e32.max() <= 10 * 1e-6 + 2e-6, e32.max()
 
 
+def test_apply_single_column_kernel_matches_per_step_kernels(hb, strip):
+    # One right-hand side runs the persistent apply (one cooperative launch, Alg. 2 as
+    # phases with staged factor blocks); two or more run the per-step kernels.  Same
+    # operator, other summation order: equal to 1e-13 relative, forward and adjoint,
+    # for complex128, complex64 and the complex64-factor / FP64-arithmetic residual path.
+    import torch
+    x = W.complex_gaussian(1024, 38)
+    xx = np.stack([x, x])
+    for name, dt, tol in (("f64", torch.complex128, 1e-13), ("ftight", torch.complex128, 1e-13),
+                          ("f32", torch.complex64, 1e-5)):
+        f = strip[name]
+        for op in (hb.HB_OP_N, hb.HB_OP_H):
+            y1 = hb.hb_apply(f, _t(x, dt), op).cpu().numpy()
+            y2 = hb.hb_apply(f, _t(xx, dt), op).cpu().numpy()
+            assert _rel(y1, y2[0]) <= tol, (name, op)
+    # FP64 residual of the FP32 form (complex64 factors, FP64 arithmetic)
+    b = W.complex_gaussian(1024, 39)
+    r1 = hb.hb_residual(strip["f32"], _t(b[None, :]), _t(x[None, :])).cpu().numpy()
+    r2 = hb.hb_residual(strip["f32"], _t(np.stack([b, b])), _t(xx)).cpu().numpy()
+    assert _rel(r1[0], r2[0]) <= 1e-13
+
+
 def test_apply_leading_dimension(hb, strip):
     import torch
     a, f = strip["a"], strip["ftight"]
