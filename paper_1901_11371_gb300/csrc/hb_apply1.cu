@@ -13,8 +13,8 @@
 //     list contiguously (the plan's batch image), so a batch is one large
 //     transfer; the producer runs ahead of the compute warps across phase
 //     boundaries, since factor data never depends on the vectors;
-//   * fifteen compute warps take the batches in turn (batch q goes to warp
-//     q mod 15, so no CTA-wide barrier separates batches): a warp waits for
+//   * nineteen compute warps take the batches in turn (batch q goes to warp
+//     q mod 19, so no CTA-wide barrier separates batches): a warp waits for
 //     its batch, gathers the vector entries the batch's ops read (state
 //     written in earlier phases, x, or y) with L1-bypassing loads in one round
 //     trip, then its lanes take the batch's output rows in turn (an entry of
@@ -35,9 +35,9 @@ namespace hb {
 
 namespace {
 
-constexpr int kA1Threads = 512;
-constexpr int kA1Warps = kA1Threads / 32;
-constexpr int kA1Cw = kA1Warps - 1;     // compute warps; the last warp is the producer
+constexpr int kA1Threads = 640;
+static_assert(kA1Threads / 32 - 1 == kA1Warps, "compute warps");
+constexpr int kA1Cw = kA1Warps;         // compute warps; one more warp is the producer
 constexpr int kA1Slots = 32;            // batches in flight per CTA
 
 template <class T> struct CT1;
@@ -108,9 +108,11 @@ struct A1Args {
 
 // Grid barrier among the compute warps (the producer does not take part).
 __device__ bool a1_grid_sync(const A1Args& a, unsigned& gen, int* s_ok) {
-  __threadfence();
+  // the CTA barrier orders every compute thread's writes before thread 0's
+  // device-scope fence (fences are cumulative), which publishes them
   cw_sync();
   if (threadIdx.x == 0) {
+    __threadfence();
     int ok = 1;
     const unsigned g = gen;
     const unsigned old = atomicAdd(&a.gb->count, 1u);
@@ -163,12 +165,23 @@ __device__ __forceinline__ typename CT1<T>::t row_gather(const F* M, const int16
                                                          const typename CT1<T>::t* cand, int i) {
   using C = typename CT1<T>::t;
   const int nr = c - k;
-  C acc = cand[I[i]];
+  C acc = cand[I[i]], acc2 = {(T)0, (T)0};   // two chains: even and odd inputs, summed at the end
+  int j = 0;
   if (cj) {
-    for (int j = 0; j < nr; ++j) fma1(acc, cvc1<T>(M[i * nr + j]), cand[I[k + j]]);
+    for (; j + 1 < nr; j += 2) {
+      fma1(acc, cvc1<T>(M[i * nr + j]), cand[I[k + j]]);
+      fma1(acc2, cvc1<T>(M[i * nr + j + 1]), cand[I[k + j + 1]]);
+    }
+    if (j < nr) fma1(acc, cvc1<T>(M[i * nr + j]), cand[I[k + j]]);
   } else {
-    for (int j = 0; j < nr; ++j) fma1(acc, cv1<T>(M[j * k + i]), cand[I[k + j]]);
+    for (; j + 1 < nr; j += 2) {
+      fma1(acc, cv1<T>(M[j * k + i]), cand[I[k + j]]);
+      fma1(acc2, cv1<T>(M[(j + 1) * k + i]), cand[I[k + j + 1]]);
+    }
+    if (j < nr) fma1(acc, cv1<T>(M[j * k + i]), cand[I[k + j]]);
   }
+  acc.x += acc2.x;
+  acc.y += acc2.y;
   return acc;
 }
 
@@ -257,8 +270,15 @@ __device__ void run_row(const A1Args& a, const A1Task& tk, const FlatOp* recs, i
   } else {   // dense-leaf column chunk, column-major [cc][r]
     const int cn = f.k1;
     if (!(f.flags & FF_ADJ)) {
-      C acc = (f.flags & FF_ACC) ? in[f.n_s0 + lr] : C{(T)0, (T)0};
-      for (int cc = 0; cc < cn; ++cc) fma1(acc, cv1<T>(M[cc * n0 + lr]), in[cc]);
+      C acc = (f.flags & FF_ACC) ? in[f.n_s0 + lr] : C{(T)0, (T)0}, acc2 = {(T)0, (T)0};
+      int cc = 0;
+      for (; cc + 1 < cn; cc += 2) {
+        fma1(acc, cv1<T>(M[cc * n0 + lr]), in[cc]);
+        fma1(acc2, cv1<T>(M[(cc + 1) * n0 + lr]), in[cc + 1]);
+      }
+      if (cc < cn) fma1(acc, cv1<T>(M[cc * n0 + lr]), in[cc]);
+      acc.x += acc2.x;
+      acc.y += acc2.y;
       y[f.out0 + lr] = acc;
     } else {
       // output lr = a column of the chunk: the rows visited from a per-row offset so that

@@ -252,8 +252,10 @@ struct A1Batch {
 };
 static_assert(sizeof(A1Task) == 16, "task record");
 static_assert(sizeof(A1Batch) == 80, "batch record");
-// Largest number of tasks in one batch (the kernel's per-warp row table).
+// Largest number of tasks in one batch (the kernel's per-warp row table) and
+// the number of compute warps of the persistent apply.
 constexpr int kA1MaxTasks = 128;
+constexpr int kA1Warps = 19;
 // Gather-list entry: bit 31 set = row of the vector x (bits 0..30), else a
 // butterfly-state entry; bit 30 set (with bit 31) = a row of the output y.
 constexpr uint32_t kA1FromX = 0x80000000u;

@@ -208,7 +208,9 @@ void build_apply_plan(const PackedHost& ph, const HostFactor& hf, bool adj, int 
       f.out0 = (int32_t)(i * n0);
       f.split = o.blk.c;
       const int64_t fb = op_fbytes(f, fes);
-      if (!t.ops.empty() && t.fbytes + fb + 20 * (n0 + (int64_t)t.gl.size() + f.n_s0) > task_max) flush();
+      // (exit tasks may fill half an area: their rows run in parallel, and every extra chunk
+      // costs a phase)
+      if (!t.ops.empty() && t.fbytes + fb + 20 * (n0 + (int64_t)t.gl.size() + f.n_s0) > max_area / 2) flush();
       if (t.ops.empty())   // the rows the leaf product (or the previous chunk) wrote
         for (int64_t r = 0; r < n0; ++r) t.gl.push_back(kA1FromY | (uint32_t)(i * n0 + r));
       f.pad = (int16_t)t.gl.size();
@@ -255,11 +257,16 @@ void build_apply_plan(const PackedHost& ph, const HostFactor& hf, bool adj, int 
       std::push_heap(heap.begin(), heap.end(), std::greater<std::pair<int64_t, int>>());
     }
     for (int g = 0; g < G; ++g) {
+      // a phase with little work per CTA gets smaller batches, so that every compute warp
+      // takes part (about two batches per warp)
+      int64_t mine_area = 0;
+      for (const TaskDraft* t : mine[(size_t)g]) mine_area += task_area(*t);
+      const int64_t target = std::max<int64_t>(2048, std::min<int64_t>(batch_target, mine_area / (2 * kA1Warps)));
       BatchDraft cur{p, {}};
       int64_t cur_area = 0;
       for (const TaskDraft* t : mine[(size_t)g]) {
         const int64_t a = task_area(*t);
-        if (!cur.tasks.empty() && (cur_area + a > batch_target || (int)cur.tasks.size() >= kA1MaxTasks)) {
+        if (!cur.tasks.empty() && (cur_area + a > target || (int)cur.tasks.size() >= kA1MaxTasks)) {
           bd[(size_t)g].push_back(cur);
           cur = BatchDraft{p, {}};
           cur_area = 0;
