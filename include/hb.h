@@ -134,10 +134,16 @@ void hb_geometry_destroy(hb_geometry_t g);
  * factors, dense leaves and the sweeps' packed triangles (the exact inverse
  * of L~ / U~ on every subtree of up to 128 rows, formed on the host by
  * running Algs. 3/4 on unit vectors) to the current device in the storage
- * `form`.  HB_SPLIT_BF16 returns HB_EUNSUPPORTED (not built).  Construction runs on the host and is
+ * `form`.  HB_SPLIT_BF16 stores the factors like HB_C64 and adds, for every
+ * leaf, its entry contraction (the V0 blocks of all depths) and exit
+ * contraction (the U0 blocks of all depths and the dense diagonal block) as
+ * dense split-BF16 tensor-core operands: the forward hb_apply of 32 or more
+ * columns runs those on the tensor cores (tcgen05, bf16 hi/lo parts of both
+ * operands, three products accumulated in FP32) and the inner butterfly steps,
+ * the adjoint and the sweeps in complex FP32.  Construction runs on the host and is
  * timed apart from the hot path.  Requires N = leaf * 2^D with D >= 1,
  * 8 <= leaf <= 256.
- * Errors: HB_EINVAL, HB_EUNSUPPORTED (N not leaf*2^D; HB_SPLIT_BF16), HB_ENOMEM, HB_ECUDA. */
+ * Errors: HB_EINVAL, HB_EUNSUPPORTED (N not leaf*2^D), HB_ENOMEM, HB_ECUDA. */
 int hb_factor(hb_geometry_t g, double wavelength, double eta0, double gamma, int64_t leaf, double eps,
               int form, uint64_t seed, void* stream, hb_factor_t* out);
 
@@ -329,6 +335,13 @@ int hb_host_apply(hb_factor_t f, int op, const double* x, double* y);
  * schedule without a GPU.  Returns the number of staging batches (>= 0),
  * HB_EUNSUPPORTED if the schedule failed its check, or HB_EINVAL. */
 int hb_host_apply_plan(hb_factor_t f, int op, int grid, int factor_bytes, const double* x, double* y);
+/* hb_host_tc_apply -- build the split-BF16 tensor-core operands of the
+ * HB_SPLIT_BF16 form and emulate its forward apply of one column on the host:
+ * entry and exit contractions from those operands with the device's bf16
+ * hi/lo splitting of both operands and its three partial products, inner
+ * butterfly items in FP64.  Verifies the operands without a GPU.  Returns the
+ * number of operand chunks (>= 0) or HB_EINVAL. */
+int hb_host_tc_apply(hb_factor_t f, const double* x, double* y);
 int hb_host_sweep(hb_factor_t f, int which, double* vec);
 
 const char* hb_last_error(void);

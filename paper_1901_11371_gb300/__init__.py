@@ -23,7 +23,7 @@ __all__ = ["HB_STRIP", "HB_SPIRAL", "HB_ARC", "HB_PARALLEL_STRIPS", "HB_POLYLINE
            "hb_geometry_polyline", "hb_factor", "hb_factor_host",
            "hb_factor_info", "hb_tree", "hb_apply", "hb_apply_adjoint", "hb_precond_solve", "hb_lower_solve",
            "hb_upper_solve", "hb_residual", "hb_gmres", "hb_tfqmr", "hb_rhs_plane_wave", "hb_far_field", "hb_monostatic",
-           "hb_host_apply", "hb_host_apply_plan", "hb_host_sweep", "hb_far_field_adjoint", "hb_profile", "hb_profile_read", "hb_autotune", "hb_autotune_times", "lib"]
+           "hb_host_apply", "hb_host_apply_plan", "hb_host_tc_apply", "hb_host_sweep", "hb_far_field_adjoint", "hb_profile", "hb_profile_read", "hb_autotune", "hb_autotune_times", "lib"]
 
 
 def lib():
@@ -323,6 +323,17 @@ def hb_host_apply_plan(f, x, op=HB_OP_N, grid=152, factor_bytes=8):
     y = np.empty_like(x)
     rc = lib().hb_host_apply_plan(f._h, int(op), int(grid), int(factor_bytes),
                                   x.ctypes.data_as(C.POINTER(C.c_double)), y.ctypes.data_as(C.POINTER(C.c_double)))
+    if rc < 0:
+        _lib.check(rc)
+    return y, rc
+
+
+def hb_host_tc_apply(f, x):
+    """Host emulation of the split-BF16 tensor-core forward apply of one column (verification
+    without a GPU).  Returns (y, number of operand chunks)."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.complex128))
+    y = np.empty_like(x)
+    rc = lib().hb_host_tc_apply(f._h, x.ctypes.data_as(C.POINTER(C.c_double)), y.ctypes.data_as(C.POINTER(C.c_double)))
     if rc < 0:
         _lib.check(rc)
     return y, rc

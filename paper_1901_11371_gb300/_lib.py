@@ -81,6 +81,7 @@ SIGNATURES = {
     "hb_host_apply": (_INT, [_VP, _INT, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "hb_host_sweep": (_INT, [_VP, _INT, C.POINTER(C.c_double)]),
     "hb_host_apply_plan": (_INT, [_VP, _INT, _INT, _INT, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "hb_host_tc_apply": (_INT, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "hb_last_error": (C.c_char_p, []),
     "hb_version": (C.c_char_p, []),
 }

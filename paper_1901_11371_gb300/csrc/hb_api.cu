@@ -122,6 +122,18 @@ int upload_factor(const PackedHost& ph, const HostFactor& hf, const Geometry& g,
   HB_CU(cudaMemsetAsync(df.bar, 0, 64, st));
   HB_CU(cudaMalloc(&df.abar, 64));
   HB_CU(cudaMemsetAsync(df.abar, 0, 64, st));
+  if (form == HB_SPLIT_BF16) {
+    // the entry and exit contractions of every leaf as split-BF16 tensor-core operands
+    TcOperands tc;
+    build_tc_operands(ph, hf, tc);
+    if ((rc = up(tc.enter, &df.tc_enter, st, df.device_bytes))) return rc;
+    if ((rc = up(tc.exit, &df.tc_exit, st, df.device_bytes))) return rc;
+    if ((rc = up(tc.chunks, &df.tc_chunks, st, df.device_bytes))) return rc;
+    if ((rc = up(tc.bpool, &df.tc_bpool, st, df.device_bytes))) return rc;
+    if ((rc = up(tc.tab, &df.tc_tab, st, df.device_bytes))) return rc;
+    HB_CU(cudaStreamSynchronize(st));
+    df.tc_ok = true;
+  }
   {
     // persistent single-column apply plans, cut for this device's SMs
     int dev = 0, sms = 0;
@@ -204,7 +216,8 @@ void free_factor(DevFactor& df) {
                   df.prog[2], df.prog[3], df.segs[0], df.segs[1], df.segs[2], df.segs[3], df.bar,
                   df.flat[0], df.flat[1], df.flat[2], df.flat[3], df.flat_base[0], df.flat_base[1],
                   df.flat_base[2], df.flat_base[3], df.flat_pbytes[0], df.flat_pbytes[1], df.flat_pbytes[2],
-                  df.flat_pbytes[3], df.cx, df.cy, df.w, df.abar};
+                  df.flat_pbytes[3], df.cx, df.cy, df.w, df.abar, df.tc_enter, df.tc_exit, df.tc_chunks,
+                  df.tc_bpool, df.tc_tab};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (DevPlan& dp : df.plan) {
@@ -313,7 +326,6 @@ int hb_factor_ex(hb_geometry_t g, double wavelength, double eta0, double gamma, 
   if (options & ~HB_OPT_LEAF_LU) { set_error("hb_factor: unknown option bits 0x%x", options); return HB_EINVAL; }
   *out = nullptr;
   if (form != HB_C128 && form != HB_C64 && form != HB_SPLIT_BF16) { set_error("hb_factor: bad form %d", form); return HB_EINVAL; }
-  if (form == HB_SPLIT_BF16) { set_error("hb_factor: the split-BF16 tensor-core form is not built"); return HB_EUNSUPPORTED; }
   auto t0 = std::chrono::steady_clock::now();
   hb_factor_s* f = new (std::nothrow) hb_factor_s();
   if (!f) { set_error("hb_factor: out of host memory"); return HB_ENOMEM; }
@@ -384,6 +396,14 @@ int hb_host_apply_plan(hb_factor_t f, int op, int grid, int factor_bytes, const 
   if (!plan.ok) { set_error("hb_host_apply_plan: the plan failed its structural check"); return HB_EUNSUPPORTED; }
   host_apply_plan(f->ph, plan, factor_bytes, op == HB_OP_H, reinterpret_cast<const cplx*>(x), reinterpret_cast<cplx*>(y));
   return (int)std::min<size_t>(plan.batches.size(), (size_t)INT32_MAX);
+}
+
+int hb_host_tc_apply(hb_factor_t f, const double* x, double* y) {
+  if (!f || !f->host_only || !x || !y) { set_error("hb_host_tc_apply: bad argument"); return HB_EINVAL; }
+  TcOperands tc;
+  build_tc_operands(f->ph, f->hf, tc);
+  host_tc_apply(f->ph, f->hf, tc, reinterpret_cast<const cplx*>(x), reinterpret_cast<cplx*>(y));
+  return (int)std::min<size_t>(tc.chunks.size(), (size_t)INT32_MAX);
 }
 
 int hb_host_sweep(hb_factor_t f, int which, double* vec) {

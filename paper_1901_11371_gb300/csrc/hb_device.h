@@ -67,6 +67,13 @@ struct DevFactor {
   int tuned[2] = {-1, -1};                                  // chosen candidate for 1 RHS / several RHS (-1: grid_min)
   void* bar = nullptr;                                      // grid barrier state + error flag
   void* abar = nullptr;                                     // grid barrier of the persistent apply
+  // split-BF16 tensor-core operands (form HB_SPLIT_BF16; TcOperands)
+  bool tc_ok = false;
+  TcJob* tc_enter = nullptr;
+  TcJob* tc_exit = nullptr;
+  TcChunk* tc_chunks = nullptr;
+  uint16_t* tc_bpool = nullptr;
+  uint32_t* tc_tab = nullptr;
   DevPlan plan[2];                                          // persistent apply plans: forward, adjoint
   long long spin_limit = 1LL << 24;                         // bounded waits of the grid barrier
   // geometry on the device (far field, plane waves)
@@ -93,6 +100,11 @@ enum Prec { PREC_F64 = 0,        // double factors, double arithmetic (HB_C128)
 // `state` holds df.state_len * R complex entries of the same type.
 int launch_apply(const DevFactor& df, Prec p, bool adjoint, const void* x, void* y, int64_t R, void* state,
                  cudaStream_t st);
+// Split-BF16 tensor-core entry (exit_jobs = false: x -> butterfly state) or
+// exit (true: state and x -> y) contractions of every leaf for R columns
+// (complex64 vectors, layout [row][R]).  HB_EUNSUPPORTED without operands.
+int launch_tc_jobs(const DevFactor& df, bool exit_jobs, const void* x, void* st, void* y, int64_t R,
+                   cudaStream_t s);
 // Persistent single-column apply (one cooperative launch); apply1_ready:
 // the plan of that direction exists for the current device.
 bool apply1_ready(const DevFactor& df, bool adjoint);

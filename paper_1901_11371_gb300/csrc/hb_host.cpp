@@ -1593,6 +1593,16 @@ void host_apply(const PackedHost& ph, const HostFactor& hf, bool adj, const cplx
   HostExec ex(ph, hf);
   ex.apply(adj, x, y);
 }
+
+void host_apply_items(const PackedHost& ph, const HostFactor& hf, bool adj, std::vector<cplx>& st) {
+  HostExec ex(ph, hf);
+  ex.st = st;
+  const std::vector<int32_t>& ptr = adj ? ph.astep_ptr : ph.step_ptr;
+  const std::vector<int32_t>& ix = adj ? ph.astep_idx : ph.step_idx;
+  for (size_t s = 0; s + 1 < ptr.size(); ++s)
+    for (int32_t e = ptr[s]; e < ptr[s + 1]; ++e) ex.item(ph.items[ix[e]], adj);
+  st = ex.st;
+}
 void host_sweep(const PackedHost& ph, const HostFactor& hf, int which, cplx* vec) {
   HostExec ex(ph, hf);
   ex.sweep(which, vec);

@@ -372,6 +372,13 @@ struct TcOperands {
   std::vector<uint32_t> tab;
 };
 void build_tc_operands(const PackedHost& ph, const HostFactor& hf, TcOperands& tc);
+// Host emulation of the split-BF16 forward apply of one column: entry and exit
+// contractions from the tensor-core operands with the device's bf16 hi/lo
+// splitting of both operands and its three partial products (accumulated in
+// FP64 here), the inner butterfly items in FP64 (verification without a GPU).
+void host_tc_apply(const PackedHost& ph, const HostFactor& hf, const TcOperands& tc, const cplx* x, cplx* y);
+// The inner butterfly steps of the packed program on a host state vector (FP64).
+void host_apply_items(const PackedHost& ph, const HostFactor& hf, bool adj, std::vector<cplx>& st);
 // offset (elements) of entry (r, k) of a bf16 operand block with kk columns in the layout above
 inline int64_t tc_off(int64_t r, int64_t k, int64_t kk) {
   return (r / 8) * (kk / 8) * 64 + (k / 8) * 64 + (r % 8) * 8 + (k % 8);

@@ -589,9 +589,29 @@ static int apply_dispatch(const DevFactor& df, bool adj, const void* x, void* y,
   return apply_impl<T, F, 8>(df, adj, x, y, R, st, s);
 }
 
+// Forward many-column apply of the split-BF16 form: entry and exit contractions on the
+// tensor cores (hb_tc.cu), the inner butterfly items on CUDA cores in complex FP32.
+static int apply_wide_tc(const DevFactor& df, const void* xv, void* yv, int64_t R, void* stv, cudaStream_t s) {
+  int rc = launch_tc_jobs(df, false, xv, stv, nullptr, R, s);
+  if (rc) return rc;
+  const int thr = (int)(R < 256 ? (R + 31) / 32 * 32 : 256);
+  const unsigned cb = (unsigned)((R + thr - 1) / thr);
+  for (int stp = 0; stp + 1 < (int)df.step_ptr.size(); ++stp) {
+    int cnt = df.step_ptr[stp + 1] - df.step_ptr[stp];
+    if (cnt <= 0) continue;
+    const dim3 g((unsigned)cnt, cb);
+    k_wapply_items<float, float2, false><<<g, thr, 0, s>>>(df.items, df.step_idx + df.step_ptr[stp],
+                                                           (const float2*)df.fpool, df.ipool, (float2*)stv, R);
+  }
+  if (cudaGetLastError() != cudaSuccess) return HB_ECUDA;
+  return launch_tc_jobs(df, true, xv, stv, yv, R, s);
+}
+
 int launch_apply(const DevFactor& df, Prec p, bool adjoint, const void* x, void* y, int64_t R, void* state,
                  cudaStream_t st) {
   if (R == 1 && apply1_ready(df, adjoint)) return launch_apply1(df, p, adjoint, x, y, state, st);
+  if (p == PREC_F32 && !adjoint && R >= kWideMin && df.form == HB_SPLIT_BF16 && df.tc_ok)
+    return apply_wide_tc(df, x, y, R, state, st);
   if (p == PREC_F64) return apply_dispatch<double, double2>(df, adjoint, x, y, R, state, st);
   if (p == PREC_F32) return apply_dispatch<float, float2>(df, adjoint, x, y, R, state, st);
   return apply_dispatch<double, float2>(df, adjoint, x, y, R, state, st);

@@ -121,4 +121,67 @@ void build_tc_operands(const PackedHost& ph, const HostFactor& hf, TcOperands& t
   }
 }
 
+namespace {
+// one chunk: outputs from inputs with the device's split products
+void tc_chunk_host(const TcOperands& tc, const TcChunk& ch, const std::vector<cplx>& in, std::vector<cplx>& out) {
+  const int64_t K = 2 * ch.nk, N = 2 * ch.nn, blk = N * K;
+  const uint16_t* hi = &tc.bpool[(size_t)ch.boff];
+  const uint16_t* lo = hi + blk;
+  std::vector<double> ah((size_t)K), al((size_t)K);
+  for (int64_t k = 0; k < ch.nk; ++k) {
+    const float v[2] = {(float)in[(size_t)k].real(), (float)in[(size_t)k].imag()};
+    for (int part = 0; part < 2; ++part) {
+      const uint16_t h = bf16_bits(v[part]);
+      const uint16_t l = bf16_bits(v[part] - bf16_value(h));
+      ah[(size_t)(part * ch.nk + k)] = bf16_value(h);
+      al[(size_t)(part * ch.nk + k)] = bf16_value(l);
+    }
+  }
+  out.assign((size_t)ch.nn, cplx(0.0));
+  for (int64_t n = 0; n < ch.nn; ++n) {
+    double d[2] = {0.0, 0.0};
+    for (int part = 0; part < 2; ++part) {
+      const int64_t row = part * ch.nn + n;
+      for (int64_t k = 0; k < K; ++k) {
+        const int64_t o = tc_off(row, k, K);
+        const double bh = bf16_value(hi[o]), bl = bf16_value(lo[o]);
+        d[part] += ah[(size_t)k] * bh + ah[(size_t)k] * bl + al[(size_t)k] * bh;
+      }
+    }
+    out[(size_t)n] = cplx(d[0], d[1]);
+  }
+}
+
+void tc_jobs_host(const TcOperands& tc, const std::vector<TcJob>& jobs, const cplx* x, std::vector<cplx>& st, cplx* y) {
+  for (const TcJob& j : jobs) {
+    std::vector<cplx> acc;
+    for (int32_t c = j.chunk0; c < j.chunk0 + j.nchunk; ++c) {
+      const TcChunk& ch = tc.chunks[(size_t)c];
+      std::vector<cplx> in((size_t)ch.nk), part;
+      for (int64_t k = 0; k < ch.nk; ++k) {
+        const uint32_t e = tc.tab[(size_t)(ch.in0 + k)];
+        in[(size_t)k] = e == kTcNone ? cplx(0.0) : (e & kTcVec) ? x[e & ~kTcVec] : st[e];
+      }
+      tc_chunk_host(tc, ch, in, part);
+      if (!(ch.flags & TC_ACC)) acc.assign((size_t)ch.nn, cplx(0.0));
+      for (int64_t n = 0; n < ch.nn; ++n) acc[(size_t)n] += part[(size_t)n];
+      if (ch.flags & TC_LAST)
+        for (int64_t n = 0; n < ch.nn; ++n) {
+          const uint32_t e = tc.tab[(size_t)(ch.out0 + n)];
+          if (e == kTcNone) continue;
+          if (e & kTcVec) y[e & ~kTcVec] = acc[(size_t)n];
+          else st[e] = acc[(size_t)n];
+        }
+    }
+  }
+}
+}  // namespace
+
+void host_tc_apply(const PackedHost& ph, const HostFactor& hf, const TcOperands& tc, const cplx* x, cplx* y) {
+  std::vector<cplx> st((size_t)ph.state_len, cplx(0.0));
+  tc_jobs_host(tc, tc.enter, x, st, y);
+  host_apply_items(ph, hf, false, st);
+  tc_jobs_host(tc, tc.exit, x, st, y);
+}
+
 }  // namespace hb
