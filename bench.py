@@ -6,9 +6,11 @@ iteration -- to true relative residual 1e-6):
   PEC semicircular open arc, arc length 6553.6 lambda (R = 6553.6/pi),
   N = 262,144 pulse segments (40 per wavelength), leaf 64, eps = 1e-6,
   256 plane waves phi_i = 180 i / 256 deg solved as one block; chosen form =
-  complex FP32 factors, apply and preconditioner inside FP64 flexible GMRES with
-  iterative refinement.  The plain FP64 form (complex128 factors, FP64 GMRES on
-  the split system) runs on the same workload for the comparison.
+  split-BF16 (HB_SPLIT_BF16): the leaves' entry and exit contractions of the
+  apply on the tensor cores (bf16 hi/lo parts, FP32 accumulation), the inner
+  butterfly steps and the L~/U~ sweeps in complex FP32, inside FP64 flexible
+  GMRES with iterative refinement.  The plain FP64 form (complex128 factors,
+  FP64 GMRES on the split system) runs on the same columns for the comparison.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun each rank solves its own 256-angle block (angles offset by
@@ -236,7 +238,7 @@ def run_gpu(args, rank, world):
     stream = torch.cuda.current_stream()
     g = hb.hb_geometry(wl.kind, wl.params, wl.n)
     t0 = time.perf_counter()
-    f32 = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C64, seed=0)
+    f32 = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_SPLIT_BF16, seed=0)
     t_build = time.perf_counter() - t0
     st = hb.hb_factor_info(f32)
     tuned = hb.hb_autotune(f32, NRHS)
@@ -354,7 +356,8 @@ def run_kernels(args):
     wl = {"spiral": W.SPIRAL_N65536, "semicircle": W.SEMICIRCLE_N262144, "strips": W.STRIPS8_N131072, "strip": W.STRIP_N1024}[args.workload]
     R = args.nrhs
     g = hb.hb_geometry(wl.kind, wl.params, wl.n)
-    f = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C64 if args.form == "c64" else hb.HB_C128)
+    form = {"c64": hb.HB_C64, "c128": hb.HB_C128, "split": hb.HB_SPLIT_BF16}[args.form]
+    f = hb.hb_factor(g, wl.leaf, wl.eps, form=form)
     tuned, times = None, {}
     if args.grid_min:
         hb.lib().hb_set_sweep_grid_min(f._h, args.grid_min)
@@ -362,7 +365,7 @@ def run_kernels(args):
         tuned = hb.hb_autotune(f, R)
         times = hb.hb_autotune_times(f, R)
     st = hb.hb_factor_info(f)
-    dt = torch.complex64 if args.form == "c64" else torch.complex128
+    dt = torch.complex128 if args.form == "c128" else torch.complex64
     x = torch.randn((R, wl.n) if R > 1 else (wl.n,), dtype=dt, device="cuda")
 
     def timed(fn, reps):
@@ -385,7 +388,7 @@ def run_kernels(args):
     ms_ah = timed(lambda: hb.hb_apply(f, x, op=hb.HB_OP_H), args.steps)
     ms_lh = timed(lambda: hb.hb_lower_solve(f, x, hb.HB_OP_H), args.steps)
     ms_uh = timed(lambda: hb.hb_upper_solve(f, x, hb.HB_OP_H), args.steps)
-    eb = 8 if args.form == "c64" else 16
+    eb = 16 if args.form == "c128" else 8
     vec_extra = 2 * wl.n * (R - 1) * eb
     out = {"mode": "kernels", "workload": wl.name, "nrhs": R, "form": args.form,
            "grid_min": args.grid_min or tuned, "autotune_ms": times,
@@ -404,7 +407,7 @@ def main():
     ap.add_argument("--mode", default="solve", choices=["solve", "kernels"])
     ap.add_argument("--workload", default="spiral", choices=["spiral", "semicircle", "strips", "strip"])
     ap.add_argument("--nrhs", type=int, default=1)
-    ap.add_argument("--form", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--form", default="c64", choices=["c64", "c128", "split"])
     ap.add_argument("--grid-min", type=int, default=0)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -470,10 +473,13 @@ def main():
     line = {
         "metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": out["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c64 (factors, apply, sweeps) + f64 (Krylov, residuals)", "data": "synthetic",
+        "vs_baseline": None,
+        "dtype": "bf16x3->f32 (tensor-core leaf contractions) + c64 (butterfly steps, sweeps) + f64 (Krylov, residuals)",
+        "data": "synthetic",
         "config": {"workload": "semicircle_N262144: R = 6553.6/pi lambda, phi in [0, pi], N=262144, leaf 64, "
                                "eps 1e-6, 256 plane waves phi_i = 180 i/256 deg per step",
-                   "form": f"FP64 FGMRES({RESTART}) + IR around complex-FP32 U~^-1 L~^-1 and A_F (CUDA cores)",
+                   "form": f"split-BF16: FP64 FGMRES({RESTART}) + IR around U~^-1 L~^-1 (complex FP32) and A_F "
+                           "(leaf contractions on tcgen05 tensor cores, butterfly steps complex FP32)",
                    "rhs_per_step": NRHS, "sweep_grid_min": out["tuned"],
                    "sweep_autotune_ms": {str(k): round(v, 3) for k, v in out["tune_ms"].items()},
                    "l2": f"inputs larger than L2: factor {st['device_bytes'] / 1e6:.0f} MB",

@@ -348,12 +348,21 @@ std::vector<DSeg> segment_program(const std::vector<DPhase>& prog, const FlatPro
 // outputs and 64 complex inputs; a chunk's B operand holds
 //   rows n < nn:       [ Re W(n, :) | -Im W(n, :) ]
 //   rows nn + n:       [ Im W(n, :) |  Re W(n, :) ]
-// as bf16 hi and lo parts (W = hi + lo), each block in the canonical
-// K-major, no-swizzle tensor-core layout (8 x 8 core matrices of 128 bytes,
-// the K-adjacent ones contiguous, row groups (2 nk / 8) x 128 bytes apart).
+// as kTcParts bf16 parts (W = W1 + W2 + W3, each part the bf16 rounding of
+// what the earlier parts leave: 3 x 8 significant bits, the FP32 value's 24),
+// each part a block in the canonical K-major, no-swizzle tensor-core layout
+// (8 x 8 core matrices of 128 bytes, the K-adjacent ones contiguous, row
+// groups (2 nk / 8) x 128 bytes apart).  The vectors are split the same way
+// on the device and the kTcProducts products with part indices summing to at
+// most 2 (0-based: 11, 12, 21, 13, 22, 31 in 1-based terms) are accumulated;
+// the dropped ones are below 2^-24 relative.
 // ---------------------------------------------------------------------------
+constexpr int kTcParts = 3;
+constexpr int kTcProducts = 6;
+constexpr int kTcProdA[kTcProducts] = {0, 0, 1, 0, 1, 2};   // part of the vector operand
+constexpr int kTcProdB[kTcProducts] = {0, 1, 0, 2, 1, 0};   // part of the factor operand
 struct TcChunk {
-  int64_t boff;      // bf16 offset of the chunk's B operand (hi block, then lo block; 2nn x 2nk each)
+  int64_t boff;      // bf16 offset of the chunk's B operand (kTcParts blocks of 2nn x 2nk each)
   int32_t nn, nk;    // complex outputs / inputs (multiples of 8, at most 64)
   int32_t in0, out0; // first entries of the chunk's input / output tables
   int32_t tcol;      // tensor-memory column of the chunk's accumulator
@@ -361,7 +370,11 @@ struct TcChunk {
 };
 static_assert(sizeof(TcChunk) == 32, "chunk record");
 enum { TC_ACC = 1, TC_LAST = 2 };
-struct TcJob { int32_t chunk0, nchunk; };
+struct TcJob {
+  int32_t chunk0, nchunk;
+  int32_t nreg;      // accumulator regions (output chunks, 1 or 2) the job's chunks use
+  int32_t pad;
+};
 // table entries: a butterfly-state entry, kTcVec | row of the vector (x for inputs, y for outputs), or kTcNone
 constexpr uint32_t kTcVec = 0x80000000u;
 constexpr uint32_t kTcNone = 0xFFFFFFFFu;
@@ -395,6 +408,14 @@ inline float bf16_value(uint16_t b) {
   float f;
   std::memcpy(&f, &u, 4);
   return f;
+}
+// x = sum of kTcParts bf16 parts, each the rounding of the remainder (FP32 arithmetic)
+inline void bf16_split(float x, uint16_t* parts) {
+  float rem = x;
+  for (int q = 0; q < kTcParts; ++q) {
+    parts[q] = bf16_bits(rem);
+    rem = rem - bf16_value(parts[q]);
+  }
 }
 
 // Plan of the persistent single-column apply for G CTAs, factor entries of

@@ -8,10 +8,15 @@
 // outputs on N and the real-expanded inputs on K:
 //   D[m][n'] = sum_k' A[m][k'] B[n'][k'],  A = [Re V^T | Im V^T],
 //   B rows n < nn: [Re W(n,:) | -Im W(n,:)],  rows nn + n: [Im W(n,:) | Re W(n,:)]
-// so D[m][n] = Re OUT(n, m) and D[m][nn + n] = Im OUT(n, m).  Operands are
-// split into bf16 hi + lo parts and three MMAs (hi*hi + hi*lo + lo*hi)
-// accumulate in FP32 in tensor memory.  The host built every W chunk's B
-// operand (hi and lo) in the canonical K-major, no-swizzle layout; a CTA
+// so D[m][n] = Re OUT(n, m) and D[m][nn + n] = Im OUT(n, m).  Both operands
+// are split into three bf16 parts (x = x1 + x2 + x3, 24 significant bits in
+// all) and the six products x_a y_b with a + b <= 4 (1-based) accumulate in
+// FP32 in tensor memory -- the leading product x1 y1 in one accumulator, the
+// five smaller ones in another, added in the epilogue, so that their
+// accumulation rounds at their own (2^8 smaller) magnitude -- and the result
+// carries FP32 accuracy.  The host built
+// every W chunk's B operand (its three parts) in the canonical K-major,
+// no-swizzle layout; a CTA
 // copies it with one bulk copy, builds the A operand of each column tile from
 // the vectors (x / butterfly state) while converting and splitting, one
 // thread issues the MMAs (tcgen05.mma kind::f16, M = 128, N = 2 nn, K = 16
@@ -32,10 +37,9 @@ namespace {
 constexpr int kTcThreads = 128;
 constexpr int kTcMaxK = 128;                       // real-expanded inputs per chunk (2 x 64)
 constexpr int kTcMaxN = 128;                       // real-expanded outputs per chunk (2 x 64)
-constexpr int kTcTiles = 2;                        // column tiles per CTA pass (TMEM: 2 x 256 columns)
 constexpr int kTcABytes = 128 * kTcMaxK * 2;       // one bf16 A block (128 rows)
 constexpr int kTcBBytes = kTcMaxN * kTcMaxK * 2;   // one bf16 B block
-constexpr int kTcSmem = 2 * kTcABytes + 2 * kTcBBytes + 1024;
+constexpr int kTcSmem = kTcParts * kTcABytes + kTcParts * kTcBBytes + 1024;
 
 __device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -73,10 +77,31 @@ __device__ __forceinline__ bool mb_wait(uint64_t* b, unsigned parity, long long 
     if (++spins > limit) return false;
   return true;
 }
-__device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
-  // two bf16 values in one 32-bit word: element k in the low half, k + 1 in the high half
-  const __nv_bfloat162 v = __floats2bfloat162_rn(lo_elem, hi_elem);
-  return *reinterpret_cast<const uint32_t*>(&v);
+// three-part bf16 split of the pair (a, b) (elements k, k + 1): words[q] holds
+// part q of both (element k in the low half), and (a, b) is left with the remainder
+__device__ __forceinline__ void split3(float& a, float& b, uint32_t (&words)[kTcParts]) {
+#pragma unroll
+  for (int q = 0; q < kTcParts; ++q) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    words[q] = *reinterpret_cast<const uint32_t*>(&v);
+    const float2 f = __bfloat1622float2(v);
+    a -= f.x;
+    b -= f.y;
+  }
+}
+
+// parts of the vector / factor operand in product pq (the same pairs as
+// kTcProdA / kTcProdB, which the host emulation uses)
+__device__ __forceinline__ constexpr int prod_a(int pq) { return pq == 2 || pq == 4 ? 1 : pq == 5 ? 2 : 0; }
+__device__ __forceinline__ constexpr int prod_b(int pq) { return pq == 1 || pq == 4 ? 1 : pq == 3 ? 2 : 0; }
+static_assert(kTcProducts == 6 && kTcProdA[2] == 1 && kTcProdA[4] == 1 && kTcProdA[5] == 2 && kTcProdB[1] == 1 &&
+                  kTcProdB[4] == 1 && kTcProdB[3] == 2, "product table");
+
+// eight consecutive 32-bit accumulator columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(addr));
 }
 
 struct TcArgs {
@@ -94,9 +119,9 @@ struct TcArgs {
 
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_jobs(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char* sA = sm;                                   // A hi, then A lo
-  unsigned char* sB = sm + 2 * kTcABytes;                   // B hi, then B lo (as copied)
-  uint64_t* mbar = (uint64_t*)(sm + 2 * kTcABytes + 2 * kTcBBytes);   // [0] B copy, [1] MMA done
+  unsigned char* sA = sm;                                   // the vector operand's three parts
+  unsigned char* sB = sm + kTcParts * kTcABytes;            // the factor operand's three parts (as copied)
+  uint64_t* mbar = (uint64_t*)(sm + kTcParts * kTcABytes + kTcParts * kTcBBytes);   // [0] B copy, [1] MMA done
   uint32_t* s_tmem = (uint32_t*)(mbar + 2);
   int* s_bad = (int*)(s_tmem + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -120,13 +145,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_jobs(TcArgs a) {
   const int64_t R = a.R;
   const int ntile = (int)((R + 127) / 128);
   bool ok = true;
-  for (int g0 = 0; g0 < ntile && ok; g0 += kTcTiles) {
-    const int ng = (ntile - g0) < kTcTiles ? (ntile - g0) : kTcTiles;
+  // tensor memory (512 columns): per tile and output chunk a leading-product
+  // region and a correction region of 128 columns each
+  const int tiles_per_pass = job.nreg > 1 ? 1 : 2;
+  const uint32_t tile_cols = (uint32_t)(256 * job.nreg);
+  for (int g0 = 0; g0 < ntile && ok; g0 += tiles_per_pass) {
+    const int ng = (ntile - g0) < tiles_per_pass ? (ntile - g0) : tiles_per_pass;
     for (int ci = 0; ci < job.nchunk && ok; ++ci) {
       const TcChunk ch = a.chunks[job.chunk0 + ci];
       const int Kr = 2 * ch.nk, Nr = 2 * ch.nn;
-      const unsigned bbytes = (unsigned)(2 * Nr * Kr * 2);
-      // B operand (hi and lo) of the chunk: one bulk copy
+      const unsigned bbytes = (unsigned)(kTcParts * Nr * Kr * 2);
+      // B operand (its parts) of the chunk: one bulk copy
       if (tid == 0) {
         asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
                      ::"r"(su32(&mbar[0])), "r"(bbytes) : "memory");
@@ -138,8 +167,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_jobs(TcArgs a) {
         // ---- A operand of column tile g0 + t: thread = column m, 8 inputs per 16-byte store
         const int64_t col = (int64_t)(g0 + t) * 128 + tid;
         const bool live = col < R;
-        unsigned char* aHi = sA;
-        unsigned char* aLo = sA + kTcABytes;
         const int rb = (tid >> 3) * (Kr >> 3) * 128 + (tid & 7) * 16;   // byte offset of row m, K group 0
         for (int k0 = 0; k0 < ch.nk; k0 += 8) {
           float re[8], im[8];
@@ -151,23 +178,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_jobs(TcArgs a) {
             re[u] = v.x;
             im[u] = v.y;
           }
-          uint32_t h[2][4], l[2][4];
+          uint32_t wr[4][kTcParts], wi[4][kTcParts];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const __nv_bfloat162 hr = __floats2bfloat162_rn(re[2 * u], re[2 * u + 1]);
-            const __nv_bfloat162 hi_ = __floats2bfloat162_rn(im[2 * u], im[2 * u + 1]);
-            const float2 fr = __bfloat1622float2(hr), fi = __bfloat1622float2(hi_);
-            h[0][u] = *reinterpret_cast<const uint32_t*>(&hr);
-            h[1][u] = *reinterpret_cast<const uint32_t*>(&hi_);
-            l[0][u] = pack_bf16(re[2 * u] - fr.x, re[2 * u + 1] - fr.y);
-            l[1][u] = pack_bf16(im[2 * u] - fi.x, im[2 * u + 1] - fi.y);
+            split3(re[2 * u], re[2 * u + 1], wr[u]);
+            split3(im[2 * u], im[2 * u + 1], wi[u]);
           }
           const int offr = rb + (k0 >> 3) * 128;                 // real part: K columns k0 .. k0+7
           const int offi = rb + ((ch.nk + k0) >> 3) * 128;       // imaginary part: K columns nk + k0 ..
-          *reinterpret_cast<uint4*>(aHi + offr) = make_uint4(h[0][0], h[0][1], h[0][2], h[0][3]);
-          *reinterpret_cast<uint4*>(aLo + offr) = make_uint4(l[0][0], l[0][1], l[0][2], l[0][3]);
-          *reinterpret_cast<uint4*>(aHi + offi) = make_uint4(h[1][0], h[1][1], h[1][2], h[1][3]);
-          *reinterpret_cast<uint4*>(aLo + offi) = make_uint4(l[1][0], l[1][1], l[1][2], l[1][3]);
+#pragma unroll
+          for (int q = 0; q < kTcParts; ++q) {
+            unsigned char* aq = sA + q * kTcABytes;
+            *reinterpret_cast<uint4*>(aq + offr) = make_uint4(wr[0][q], wr[1][q], wr[2][q], wr[3][q]);
+            *reinterpret_cast<uint4*>(aq + offi) = make_uint4(wi[0][q], wi[1][q], wi[2][q], wi[3][q]);
+          }
         }
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
@@ -177,19 +201,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_jobs(TcArgs a) {
         }
         __syncthreads();
         if (*(volatile int*)s_bad) { ok = false; break; }
-        // ---- MMAs: K/16 steps x (hi*hi, hi*lo, lo*hi) into the tile's accumulator region
+        // ---- MMAs: K/16 steps x the six part products into the tile's accumulator region
         if (tid == 0) {
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
           const uint32_t idesc = idesc_bf16(128, Nr);
-          const unsigned sbo_a = (unsigned)(Kr >> 3) * 128, sbo_b = sbo_a;
-          const unsigned aH = su32(aHi), aL = su32(aLo), bH = su32(sB), bL = su32(sB) + (unsigned)(Nr * Kr * 2);
-          const uint32_t dt = tbase + (uint32_t)(t * 256 + ch.tcol);
+          const unsigned sbo = (unsigned)(Kr >> 3) * 128;
+          const unsigned a0 = su32(sA), b0 = su32(sB);
+          const unsigned bpart = (unsigned)(Nr * Kr * 2);
+          const uint32_t dmain = tbase + (uint32_t)t * tile_cols + (uint32_t)ch.tcol;
+          const uint32_t dcorr = dmain + 128u * (uint32_t)job.nreg;
           for (int s = 0; s < Kr / 16; ++s) {
             const unsigned ko = (unsigned)s * 256;   // two K core matrices per step
-            const uint32_t acc0 = ((ch.flags & TC_ACC) || s > 0) ? 1u : 0u;
-            mma_bf16(dt, sdesc(aH + ko, 128, sbo_a), sdesc(bH + ko, 128, sbo_b), idesc, acc0);
-            mma_bf16(dt, sdesc(aH + ko, 128, sbo_a), sdesc(bL + ko, 128, sbo_b), idesc, 1u);
-            mma_bf16(dt, sdesc(aL + ko, 128, sbo_a), sdesc(bH + ko, 128, sbo_b), idesc, 1u);
+#pragma unroll
+            for (int pq = 0; pq < kTcProducts; ++pq) {
+              const uint32_t acc = ((pq > 1) || s > 0 || (ch.flags & TC_ACC)) ? 1u : 0u;
+              mma_bf16(pq == 0 ? dmain : dcorr, sdesc(a0 + (unsigned)prod_a(pq) * kTcABytes + ko, 128, sbo),
+                       sdesc(b0 + (unsigned)prod_b(pq) * bpart + ko, 128, sbo), idesc, acc);
+            }
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
                        ::"r"(su32(&mbar[1])) : "memory");
@@ -199,17 +227,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_jobs(TcArgs a) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         // ---- epilogue of the tile's region after the chunk that completes it
         if (ch.flags & TC_LAST) {
-          const uint32_t rowaddr = tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(t * 256 + ch.tcol);
+          const uint32_t rowaddr = tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)t * tile_cols + (uint32_t)ch.tcol;
+          const uint32_t corr = 128u * (uint32_t)job.nreg;
           for (int n0 = 0; n0 < ch.nn; n0 += 8) {
-            uint32_t vr[8], vi[8];
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                         : "=r"(vr[0]), "=r"(vr[1]), "=r"(vr[2]), "=r"(vr[3]), "=r"(vr[4]), "=r"(vr[5]), "=r"(vr[6]),
-                           "=r"(vr[7])
-                         : "r"(rowaddr + (uint32_t)n0));
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                         : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]),
-                           "=r"(vi[7])
-                         : "r"(rowaddr + (uint32_t)(ch.nn + n0)));
+            uint32_t vr[8], vi[8], cr[8], ci[8];
+            tmem_ld8(rowaddr + (uint32_t)n0, vr);
+            tmem_ld8(rowaddr + (uint32_t)(ch.nn + n0), vi);
+            tmem_ld8(rowaddr + corr + (uint32_t)n0, cr);
+            tmem_ld8(rowaddr + corr + (uint32_t)(ch.nn + n0), ci);
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
             const int64_t c = (int64_t)(g0 + t) * 128 + 32 * warp + lane;
             if (c < R) {
@@ -218,7 +243,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_jobs(TcArgs a) {
                 const uint32_t e = a.tab[ch.out0 + n0 + u];
                 if (e == kTcNone) continue;
                 float2* d = (e & kTcVec) ? a.y + (int64_t)(e & ~kTcVec) * R + c : a.st + (int64_t)e * R + c;
-                *d = make_float2(__uint_as_float(vr[u]), __uint_as_float(vi[u]));
+                *d = make_float2(__uint_as_float(vr[u]) + __uint_as_float(cr[u]),
+                                 __uint_as_float(vi[u]) + __uint_as_float(ci[u]));
               }
             }
           }

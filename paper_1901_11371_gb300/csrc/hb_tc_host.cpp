@@ -22,8 +22,8 @@ int64_t up8(int64_t v) { return (v + 7) / 8 * 8; }
 // cut W into chunks of <= 64 outputs x <= 64 inputs; for every output chunk the input
 // chunks accumulate in order into one tensor-memory region
 void emit(const Dense& d, TcOperands& tc, std::vector<TcJob>& jobs) {
-  TcJob job{(int32_t)tc.chunks.size(), 0};
   const int64_t nN = (d.rows + 63) / 64, nK = (d.cols + 63) / 64;
+  TcJob job{(int32_t)tc.chunks.size(), 0, nN > 1 ? 2 : 1, 0};
   for (int64_t ni = 0; ni < nN; ++ni) {
     const int64_t r0 = ni * 64, rn = std::min<int64_t>(64, d.rows - r0), nn = up8(rn);
     for (int64_t ki = 0; ki < nK; ++ki) {
@@ -40,9 +40,9 @@ void emit(const Dense& d, TcOperands& tc, std::vector<TcJob>& jobs) {
       while (tc.bpool.size() % 64) tc.bpool.push_back(0);   // 128-byte aligned operand blocks
       ch.boff = (int64_t)tc.bpool.size();
       const int64_t R = 2 * nn, K = 2 * nk, blk = R * K;
-      tc.bpool.resize(tc.bpool.size() + (size_t)(2 * blk), 0);
-      uint16_t* hi = &tc.bpool[(size_t)ch.boff];
-      uint16_t* lo = hi + blk;
+      tc.bpool.resize(tc.bpool.size() + (size_t)(kTcParts * blk), 0);
+      uint16_t* part[kTcParts];
+      for (int q = 0; q < kTcParts; ++q) part[q] = &tc.bpool[(size_t)(ch.boff + q * blk)];
       for (int64_t n = 0; n < rn; ++n)
         for (int64_t k = 0; k < cn; ++k) {
           const cplx v = d.w[(size_t)((r0 + n) * d.cols + c0 + k)];
@@ -51,12 +51,10 @@ void emit(const Dense& d, TcOperands& tc, std::vector<TcJob>& jobs) {
                                      {(double)(nn + n), (double)k, v.imag()},
                                      {(double)(nn + n), (double)(nk + k), v.real()}};
           for (const auto& e : vals) {
-            const float f = (float)e[2];
-            const uint16_t h = bf16_bits(f);
-            const uint16_t l = bf16_bits((float)((double)f - (double)bf16_value(h)));
+            uint16_t b[kTcParts];
+            bf16_split((float)e[2], b);
             const int64_t o = tc_off((int64_t)e[0], (int64_t)e[1], K);
-            hi[o] = h;
-            lo[o] = l;
+            for (int q = 0; q < kTcParts; ++q) part[q][o] = b[q];
           }
         }
       tc.chunks.push_back(ch);
@@ -125,27 +123,27 @@ namespace {
 // one chunk: outputs from inputs with the device's split products
 void tc_chunk_host(const TcOperands& tc, const TcChunk& ch, const std::vector<cplx>& in, std::vector<cplx>& out) {
   const int64_t K = 2 * ch.nk, N = 2 * ch.nn, blk = N * K;
-  const uint16_t* hi = &tc.bpool[(size_t)ch.boff];
-  const uint16_t* lo = hi + blk;
-  std::vector<double> ah((size_t)K), al((size_t)K);
+  const uint16_t* bp = &tc.bpool[(size_t)ch.boff];
+  std::vector<double> av((size_t)(kTcParts * K));   // av[q * K + k]: part q of input k
   for (int64_t k = 0; k < ch.nk; ++k) {
     const float v[2] = {(float)in[(size_t)k].real(), (float)in[(size_t)k].imag()};
-    for (int part = 0; part < 2; ++part) {
-      const uint16_t h = bf16_bits(v[part]);
-      const uint16_t l = bf16_bits(v[part] - bf16_value(h));
-      ah[(size_t)(part * ch.nk + k)] = bf16_value(h);
-      al[(size_t)(part * ch.nk + k)] = bf16_value(l);
+    for (int half = 0; half < 2; ++half) {
+      uint16_t b[kTcParts];
+      bf16_split(v[half], b);
+      for (int q = 0; q < kTcParts; ++q) av[(size_t)(q * K + half * ch.nk + k)] = bf16_value(b[q]);
     }
   }
   out.assign((size_t)ch.nn, cplx(0.0));
   for (int64_t n = 0; n < ch.nn; ++n) {
     double d[2] = {0.0, 0.0};
-    for (int part = 0; part < 2; ++part) {
-      const int64_t row = part * ch.nn + n;
+    for (int half = 0; half < 2; ++half) {
+      const int64_t row = half * ch.nn + n;
       for (int64_t k = 0; k < K; ++k) {
         const int64_t o = tc_off(row, k, K);
-        const double bh = bf16_value(hi[o]), bl = bf16_value(lo[o]);
-        d[part] += ah[(size_t)k] * bh + ah[(size_t)k] * bl + al[(size_t)k] * bh;
+        for (int pq = 0; pq < kTcProducts; ++pq) {
+          const int qa = kTcProdA[pq], qb = kTcProdB[pq];
+          d[half] += av[(size_t)(qa * K + k)] * (double)bf16_value(bp[qb * blk + o]);
+        }
       }
     }
     out[(size_t)n] = cplx(d[0], d[1]);
