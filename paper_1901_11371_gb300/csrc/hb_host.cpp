@@ -1412,19 +1412,6 @@ FlatProgram flatten_program(const PackedHost& ph, const std::vector<DPhase>& pro
       off += flat_stage_bytes32(fp.ops[o]);
     }
     fp.pbytes.push_back(off);
-    // first output row of every op within the phase (row-parallel execution of resident
-    // runs); -1 throughout when the phase has more rows than the field holds
-    {
-      int64_t rows = 0;
-      for (int32_t o = fp.base.back(); o < (int32_t)fp.ops.size(); ++o) {
-        FlatOp& f = fp.ops[o];
-        f.pad = (int16_t)std::min<int64_t>(rows, INT16_MAX);
-        rows += f.kind == FK_GATHER ? f.k0 + ((f.flags & FF_TWO) ? f.k1 : 0)
-              : f.kind == FK_SCATTER ? f.c0 : f.kind == FK_MIDDLE ? ((f.flags & FF_ADJ) ? f.c0 : f.k0) : 0;
-      }
-      if (rows > INT16_MAX || P.kind == PH_LEAF)
-        for (int32_t o = fp.base.back(); o < (int32_t)fp.ops.size(); ++o) fp.ops[o].pad = -1;
-    }
   }
   fp.base.push_back((int32_t)fp.ops.size());
   return fp;

@@ -635,105 +635,6 @@ __device__ void do_op_res(const SweepArgs& a, const FlatOp& f, const char* half,
   g.sync();
 }
 
-// Output rows of one op of a resident run (the host stores each op's first row
-// within its phase in FlatOp::pad).
-__device__ __forceinline__ int op_rows(const FlatOp& f) {
-  if (f.kind == FK_GATHER) return f.k0 + ((f.flags & FF_TWO) ? f.k1 : 0);
-  if (f.kind == FK_SCATTER) return f.c0;
-  return (f.flags & FF_ADJ) ? f.c0 : f.k0;   // middle: k_c outputs in adjoint, k_r forward
-}
-
-// A whole phase of a resident run, row-parallel: the compute threads take the
-// (output row, column chunk) pairs of all the phase's ops in turn, so small ops
-// cost no per-op synchronisation; one barrier ends the phase.  stage: the
-// phase's staged factor data (SM) or null (factor data read from global memory).
-template <class T, class F, int RC, bool SM>
-__device__ void phase_rows(const SweepArgs& a, const FlatOp* ops, int nops, const char* stage,
-                           typename CT<T>::t* rvec, int row_lo, typename CT<T>::t* rst, int st_lo, int Wr, int ncol,
-                           const Grp& gc) {
-  using C = typename CT<T>::t;
-  __builtin_assume(__isShared(rvec));
-  __builtin_assume(__isShared(rst));
-  if (SM) __builtin_assume(__isShared(stage));
-  const int nrows = ops[nops - 1].pad + op_rows(ops[nops - 1]);
-  const int nch = (ncol + RC - 1) / RC;
-  for (int e = gc.t; e < nrows * nch; e += gc.nt) {
-    const int r = e % nrows, ch = e / nrows;
-    int lo = 0, hi = nops;   // ops[lo].pad <= r < ops[hi].pad
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (ops[mid].pad <= r) lo = mid;
-      else hi = mid;
-    }
-    const FlatOp& f = ops[lo];
-    const int lr = r - f.pad;
-    const int r0 = ch * RC;
-    const int rc = (ncol - r0) < RC ? (ncol - r0) : RC;
-    const C* src0 = ((f.flags & FF_SRC_VEC) ? rvec + (int64_t)(f.src0 - row_lo) * Wr : rst + (int64_t)(f.src0 - st_lo) * Wr) + r0;
-    const C* src1 = rst + (int64_t)(f.src1 - st_lo) * Wr + r0;
-    C* out0 = ((f.flags & FF_OUT_VEC) ? rvec + (int64_t)(f.out0 - row_lo) * Wr : rst + (int64_t)(f.out0 - st_lo) * Wr) + r0;
-    C* out1 = rst + (int64_t)(f.out1 - st_lo) * Wr + r0;
-    const int64_t mbytes = align16((int64_t)f.melems * (int64_t)sizeof(F));
-    const F* Ms = SM ? (const F*)(stage + f.soff) : (const F*)a.fp + f.moff;
-    const int16_t* Is = SM ? (const int16_t*)(stage + f.soff + mbytes) : (f.ioff >= 0 ? a.ip + f.ioff : nullptr);
-    const bool cj = (f.flags & FF_CONJ) != 0;
-    C acc[RC];
-    if (f.kind == FK_GATHER) {
-      const bool b1 = lr >= f.k0;
-      const F* M = b1 ? Ms + f.m1 : Ms;
-      const int16_t* I = b1 ? Is + f.i1 : Is;
-      const int k = b1 ? f.k1 : f.k0, c = b1 ? f.c1 : f.c0, i = b1 ? lr - f.k0 : lr, nr = c - k;
-      C* out = b1 ? out1 : out0;
-      const C* q = src0 + (int64_t)I[i] * Wr;
-#pragma unroll
-      for (int rr = 0; rr < RC; ++rr) acc[rr] = q[rr];
-#pragma unroll 4
-      for (int j = 0; j < nr; ++j) {
-        const C m = cj ? cvc<T>(M[(int64_t)i * nr + j]) : cv<T>(M[(int64_t)j * k + i]);
-        const C* sv = src0 + (int64_t)I[k + j] * Wr;
-#pragma unroll
-        for (int rr = 0; rr < RC; ++rr) fma2(acc[rr], m, sv[rr]);
-      }
-#pragma unroll
-      for (int rr = 0; rr < RC; ++rr)
-        if (rr < rc) out[(int64_t)i * Wr + rr] = acc[rr];
-    } else if (f.kind == FK_SCATTER) {
-#pragma unroll
-      for (int rr = 0; rr < RC; ++rr) acc[rr] = z2<T>();
-      if (cj) {
-        rowc<T, F, RC, true>(acc, Ms, Is, f.k0, f.c0, src0, Wr, lr);
-        if (f.flags & FF_TWO) rowc<T, F, RC, true>(acc, Ms + f.m1, Is + f.i1, f.k1, f.c1, src1, Wr, lr);
-      } else {
-        rowc<T, F, RC, false>(acc, Ms, Is, f.k0, f.c0, src0, Wr, lr);
-        if (f.flags & FF_TWO) rowc<T, F, RC, false>(acc, Ms + f.m1, Is + f.i1, f.k1, f.c1, src1, Wr, lr);
-      }
-      C* d = (!(f.flags & FF_TWO) || lr < f.split) ? out0 + (int64_t)lr * Wr : out1 + (int64_t)(lr - f.split) * Wr;
-#pragma unroll
-      for (int rr = 0; rr < RC; ++rr)
-        if (rr < rc) {
-          if (f.flags & FF_SUB) d[rr] = C{d[rr].x - acc[rr].x, d[rr].y - acc[rr].y};
-          else d[rr] = acc[rr];
-        }
-    } else {   // middle: y = S z (adjoint z = S^H y), S stored [c][r]
-      const int kr = f.k0, kc = f.c0;
-      const bool ad = (f.flags & FF_ADJ) != 0;
-      const int nin = ad ? kr : kc;
-#pragma unroll
-      for (int rr = 0; rr < RC; ++rr) acc[rr] = z2<T>();
-#pragma unroll 4
-      for (int i = 0; i < nin; ++i) {
-        const C sv = ad ? cvc<T>(Ms[(int64_t)lr * kr + i]) : cv<T>(Ms[(int64_t)i * kr + lr]);
-#pragma unroll
-        for (int rr = 0; rr < RC; ++rr) fma2(acc[rr], sv, src0[(int64_t)i * Wr + rr]);
-      }
-#pragma unroll
-      for (int rr = 0; rr < RC; ++rr)
-        if (rr < rc) out0[(int64_t)lr * Wr + rr] = acc[rr];
-    }
-  }
-  gc.sync();
-}
-
 // sweep-leaf solve of a resident run: rows in shared memory, triangle staged (or global)
 template <class T, class F, int RC, bool SM>
 __device__ void do_leaf_res(const SweepArgs& a, const FlatOp& f, const F* Tm, typename CT<T>::t* rvec, int row_lo,
@@ -890,12 +791,6 @@ __device__ bool local_run_ring(const SweepArgs& a, const DSeg& sg, char* smem, i
           do_leaf_res<T, F, RC, true>(a, ops[0], (const F*)(ring + myoff), rvec, sg.row_lo, Wr, ncol, part, gc);
         else
           do_leaf_res<T, F, RC, false>(a, ops[0], (const F*)a.tinv + ops[0].moff, rvec, sg.row_lo, Wr, ncol, part, gc);
-      } else if (ops[0].pad == 0) {
-        // row-parallel phase (ends with its own barrier)
-        if (myoff >= 0)
-          phase_rows<T, F, RC, true>(a, ops, nops, ring + myoff, rvec, sg.row_lo, rst, sg.st_lo, Wr, ncol, gc);
-        else
-          phase_rows<T, F, RC, false>(a, ops, nops, nullptr, rvec, sg.row_lo, rst, sg.st_lo, Wr, ncol, gc);
       } else {
         const Grp g{lane, 32, false};
         for (int o = warp; o < nops; o += cw) {
@@ -906,7 +801,7 @@ __device__ bool local_run_ring(const SweepArgs& a, const DSeg& sg, char* smem, i
             do_op_res<T, F, RC, false>(a, f, ring, false, rvec, sg.row_lo, rst, sg.st_lo, Wr, ncol, g);
         }
       }
-      if (ops[0].kind == FK_LEAF || ops[0].pad != 0) gc.sync();
+      gc.sync();
       if (threadIdx.x == 0) {
         __threadfence_block();
         *(volatile int*)&s_done = ph + 1;   // releases the phase's slot and ring area
