@@ -182,9 +182,13 @@ class ClockSampler:
 # dram__bytes_read.sum + dram__bytes_write.sum per launch (256 columns, semicircle N = 262,144)
 # from one ncu capture, keyed by the SHA-256 (first 16 hex digits) of the kernel's sources at
 # capture time; a kernel whose sources changed since has no traffic figure (None).
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    # profiles/k_sweep_coop_semicircle_N262144_traffic.md (autotuned 256-column launch)
+    "k_sweep": {"sha": "b4653ac2957de173", "bytes": 2247096576 + 2686350592},
+}
 KERNEL_SOURCES = {
     "k_sweep": ["hb_sweep_impl.cuh", "hb_sweep.cu", "hb_sweep_f32w.cu", "hb_sweep_launch.h"],
+    "k_apply1": ["hb_apply1.cu", "hb_plan.cpp"],
 }
 
 
@@ -303,10 +307,26 @@ def run_gpu(args, rank, world):
     e2e = {"value": args.steps * NRHS / e_s, "unit": UNIT, "h2d_bytes_per_step": int(b.numel() * 16),
            "d2h_bytes_per_step": int(x.numel() * 16 + NRHS * 16)}
 
+    # ---- single-column apply of the same factor (the persistent kernel), outside the timed
+    # region: CUDA events on the launching stream over 20 applies after 3 warm-up applies
+    x1 = b[0].to(torch.complex64).contiguous()
+    y1 = torch.empty_like(x1)
+    for _ in range(3):
+        hb.hb_apply(f32, x1, out=y1)
+    torch.cuda.synchronize()
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    for _ in range(20):
+        hb.hb_apply(f32, x1, out=y1)
+    eb.record(stream)
+    torch.cuda.synchronize()
+    apply1_ms = ea.elapsed_time(eb) / 20
+
     mono_np = mono.cpu().numpy()
     out = dict(value=value, ms=ms_max, iters=iters, ir_steps=ir_steps, res=res, st=st, t_build=t_build, clocks=clk, e2e=e2e, tuned=tuned, tune_ms=tune_ms,
                mono_db=[float(v) for v in 20 * np.log10(np.abs(mono_np[::32]) + 1e-300)],
                n_apply=n_apply, ms_apply=ms_apply, n_sweep=n_sweep, ms_sweep=ms_sweep, n_launch=n_launch,
+               apply1_ms=apply1_ms,
                x=x)
     # ---- like-for-like form comparison (rank 0 only, outside the contract's timed region):
     # the plain FP64 form and the chosen form on the same PLAIN_NRHS right-hand sides,
@@ -493,6 +513,12 @@ def main():
                      "apply_calls": out["n_apply"], "apply_ms_total": out["ms_apply"],
                      "apply_GBps": apply_bytes / (apply_ms / 1e3) / 1e9 if out["n_apply"] else None,
                      "us_per_leaf_step": sweep_ms * 1e3 / (st["n"] // st["leaf"])},
+        "roofline_single_column_apply": {
+            "bound": "hbm", "kernel": "k_apply1 (one column, complex64 factors, same factor)",
+            "achieved": st["apply_bytes"] / (out["apply1_ms"] / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": st["apply_bytes"] / (out["apply1_ms"] / 1e3) / 1e9 / hbm,
+            "algorithmic_bytes_per_launch": st["apply_bytes"], "avg_launch_ms": out["apply1_ms"],
+            "traffic": measured_traffic("k_apply1"), "peak_source": peak_kind},
         "gpu_launches": out["n_launch"],
         "clocks": out["clocks"],
         "e2e": out["e2e"],
