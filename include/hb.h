@@ -154,6 +154,11 @@ int hb_factor(hb_geometry_t g, double wavelength, double eta0, double gamma, int
  *   Algs. 3/4 are unchanged.  A variant the paper implies (its leaf solves are
  *   LAPACK triangular solves); HB_EUNSUPPORTED on a zero pivot. */
 #define HB_OPT_LEAF_LU 1
+/* HB_OPT_SWEEP_WINDOW_MIN: the column-partitioned sweep kernel (hb_set_sweep_kernel)
+ *   keeps only subtrees of at most 512 vector rows + butterfly-state entries
+ *   resident in shared memory, so that every larger butterfly runs as global
+ *   phases; a test and tuning aid for small problems (results are unchanged). */
+#define HB_OPT_SWEEP_WINDOW_MIN 2
 
 /* hb_factor_ex / hb_factor_host_ex -- hb_factor / hb_factor_host with an
  * options mask (0 = the defaults of hb_factor).  Errors as hb_factor, plus
@@ -229,8 +234,10 @@ int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int64_t nrhs, i
 
 /* hb_tfqmr -- solve A x = b_phys (complex128, physical excitation, as for
  * hb_gmres) with transpose-free QMR, the Krylov solver of Sec. 4, on the
- * split-preconditioned system (Eqs. (Axb2), (Axb3)): FP64 factors (HB_C128)
- * only.  rstar: the shadow vectors r* of the Lanczos biorthogonalisation,
+ * split-preconditioned system (Eqs. (Axb2), (Axb3)), every storage form: the
+ * vectors and scalars are FP64; the products with A^_F, L~^{-1} and U~^{-1} use
+ * FP64 arithmetic on the form's factors (complex128 for HB_C128, complex64 for
+ * HB_C64 and HB_SPLIT_BF16).  rstar: the shadow vectors r* of the Lanczos biorthogonalisation,
  * complex128 device block laid out like b (nrhs columns, leading dimension
  * ld), caller-owned and not modified; NULL takes r* = L~^{-1} b^ (the paper
  * does not name one; on the split EFIE systems that choice can meet a
@@ -243,7 +250,7 @@ int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int64_t nrhs, i
  * iters = half steps, restarts = true-residual checks, precond_rel_res = the
  * largest final bound relative to ||L~^{-1} b^||.  x is overwritten;
  * synchronises `stream` before returning; info may be NULL.
- * Errors: HB_EINVAL, HB_EUNSUPPORTED (not HB_C128), HB_ENAN (non-finite b or
+ * Errors: HB_EINVAL, HB_ENAN (non-finite b or
  * rstar), HB_ENOCONV (maxit half steps or a breakdown; info still filled),
  * HB_ETIMEOUT (as hb_gmres). */
 int hb_tfqmr(hb_factor_t f, int op, const void* b_phys, const void* rstar, void* x, int64_t nrhs, int64_t ld,
@@ -343,6 +350,15 @@ int hb_host_apply_plan(hb_factor_t f, int op, int grid, int factor_bytes, const 
  * number of operand chunks (>= 0) or HB_EINVAL. */
 int hb_host_tc_apply(hb_factor_t f, const double* x, double* y);
 int hb_host_sweep(hb_factor_t f, int which, double* vec);
+/* hb_host_sweep_sched -- build the schedule of the column-partitioned sweep
+ * kernel (sweep `which`; complex coefficients of coef_bytes: 8 = complex64 as
+ * on the device, 16 = complex128; runs cut for a resident window of win_slots
+ * entries, 0 = the kernel's full window) and execute it on the host in FP64 for
+ * the one column in vec (in place), reading every row, coefficient and slot from
+ * the batch images as the kernel does.  Verifies the schedule without a GPU.
+ * Returns the number of batches (>= 0), HB_EUNSUPPORTED if this factor has no
+ * such schedule, or HB_EINVAL. */
+int hb_host_sweep_sched(hb_factor_t f, int which, int coef_bytes, int win_slots, double* vec);
 
 const char* hb_last_error(void);
 const char* hb_version(void);

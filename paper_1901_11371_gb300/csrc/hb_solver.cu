@@ -662,7 +662,7 @@ extern "C" int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int6
 
 // ---------------------------------------------------------------------------
 // TFQMR (the solver of Sec. 4): Freund's transpose-free QMR on the split system
-// L'^{-1} A U'^{-1} y = L'^{-1} b, x = U'^{-1} y, FP64 form, right-hand sides in
+// L'^{-1} A U'^{-1} y = L'^{-1} b, x = U'^{-1} y, FP64 vectors, right-hand sides in
 // lockstep with per-column scalars.  Half step m (even: a new alpha = rho /
 // <r*, v> and the first direction u; odd: the second direction u - alpha v)
 // updates the squared residual w, the QMR direction d and the iterate (theta,
@@ -679,11 +679,13 @@ extern "C" int hb_tfqmr(hb_factor_t f, int op, const void* b_phys, const void* r
   if (op != HB_OP_N && op != HB_OP_H) { set_error("hb_tfqmr: bad op"); return HB_EINVAL; }
   if (!(rtol > 0) || maxit < 1) { set_error("hb_tfqmr: bad rtol/maxit"); return HB_EINVAL; }
   if (rstar == x) { set_error("hb_tfqmr: rstar and x must not alias"); return HB_EINVAL; }
-  if (f->df.form != HB_C128) { set_error("hb_tfqmr: needs an FP64 factor (HB_C128)"); return HB_EUNSUPPORTED; }
   cudaStream_t st = (cudaStream_t)stream;
   auto t0 = std::chrono::steady_clock::now();
   if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("hb_tfqmr: stream error"); return HB_ECUDA; }
   const DevFactor& df = f->df;
+  // operator arithmetic: FP64 for HB_C128; FP64 arithmetic on the complex-FP32
+  // factors otherwise (the vectors and the iteration stay FP64 in every form)
+  const Prec px = df.form == HB_C128 ? PREC_F64 : PREC_F32_ACC64;
   const int64_t n = df.n, R = nrhs, nR = n * R;
   const bool adj = op == HB_OP_H;
   const int lo = adj ? 3 : 0, up = adj ? 2 : 1;
@@ -715,9 +717,9 @@ extern "C" int hb_tfqmr(hb_factor_t f, int op, const void* b_phys, const void* r
   auto opf = [&](const double2* z, double2* out) -> int {   // out = L'^{-1} A U'^{-1} z
     int e;
     cudaMemcpyAsync(t1, z, vbytes, cudaMemcpyDeviceToDevice, st);
-    if ((e = sweep_internal(f, PREC_F64, up, t1, R, st))) return e;
-    if ((e = apply_internal(f, PREC_F64, adj, t1, out, R, st))) return e;
-    return sweep_internal(f, PREC_F64, lo, out, R, st);
+    if ((e = sweep_internal(f, px, up, t1, R, st))) return e;
+    if ((e = apply_internal(f, px, adj, t1, out, R, st))) return e;
+    return sweep_internal(f, px, lo, out, R, st);
   };
   auto upload = [&](const std::vector<zc>& c, int slot) -> double2* {
     double2* dst = coef + (size_t)slot * R;
@@ -728,7 +730,7 @@ extern "C" int hb_tfqmr(hb_factor_t f, int op, const void* b_phys, const void* r
   std::vector<double> bnorm, tau;
   if ((rc = norms(d, bh, bnorm))) return rc;
   cudaMemcpyAsync(w, bh, vbytes, cudaMemcpyDeviceToDevice, st);
-  if ((rc = sweep_internal(f, PREC_F64, lo, w, R, st))) return rc;
+  if ((rc = sweep_internal(f, px, lo, w, R, st))) return rc;
   cudaMemcpyAsync(u, w, vbytes, cudaMemcpyDeviceToDevice, st);
   if (rstar) { if ((rc = launch_gather_cols(rstar, 0, ld, n, R, rs, 0, 1.0, st))) return rc; }
   else cudaMemcpyAsync(rs, w, vbytes, cudaMemcpyDeviceToDevice, st);
@@ -749,8 +751,8 @@ extern "C" int hb_tfqmr(hb_factor_t f, int op, const void* b_phys, const void* r
   auto true_residual = [&]() -> int {   // res_r = ||b^ - A U'^{-1} y|| / ||b^||
     int e;
     cudaMemcpyAsync(t2, y, vbytes, cudaMemcpyDeviceToDevice, st);
-    if ((e = sweep_internal(f, PREC_F64, up, t2, R, st))) return e;
-    if ((e = apply_internal(f, PREC_F64, adj, t2, t1, R, st))) return e;
+    if ((e = sweep_internal(f, px, up, t2, R, st))) return e;
+    if ((e = apply_internal(f, px, adj, t2, t1, R, st))) return e;
     k_sub_into<<<gsz(nR), 256, 0, st>>>(bh, t1, rr, nR); count_launch(f, 1);
     if ((e = norms(d, rr, rn))) return e;
     for (int64_t c = 0; c < R; ++c) res_r[c] = bnorm[c] > 0 ? rn[c] / bnorm[c] : 0.0;
