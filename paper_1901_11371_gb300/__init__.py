@@ -15,15 +15,15 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (HB_ARC, HB_C64, HB_C128, HB_OP_H, HB_OP_N, HB_OPT_LEAF_LU, HB_PARALLEL_STRIPS, HB_POLYLINE,
+from ._lib import (HB_ARC, HB_C64, HB_C128, HB_OP_H, HB_OP_N, HB_OPT_LEAF_LU, HB_OPT_SWEEP_WINDOW_MIN, HB_PARALLEL_STRIPS, HB_POLYLINE,
                    HB_SPIRAL, HB_SPLIT_BF16, HB_STRIP, HBError)
 
 __all__ = ["HB_STRIP", "HB_SPIRAL", "HB_ARC", "HB_PARALLEL_STRIPS", "HB_POLYLINE", "HB_C128", "HB_C64",
-           "HB_SPLIT_BF16", "HB_OP_N", "HB_OP_H", "HB_OPT_LEAF_LU", "HBError", "Geometry", "Factor", "hb_geometry",
+           "HB_SPLIT_BF16", "HB_OP_N", "HB_OP_H", "HB_OPT_LEAF_LU", "HB_OPT_SWEEP_WINDOW_MIN", "HBError", "Geometry", "Factor", "hb_geometry",
            "hb_geometry_polyline", "hb_factor", "hb_factor_host",
            "hb_factor_info", "hb_tree", "hb_apply", "hb_apply_adjoint", "hb_precond_solve", "hb_lower_solve",
            "hb_upper_solve", "hb_residual", "hb_gmres", "hb_tfqmr", "hb_rhs_plane_wave", "hb_far_field", "hb_monostatic",
-           "hb_host_apply", "hb_host_apply_plan", "hb_host_tc_apply", "hb_host_sweep", "hb_far_field_adjoint", "hb_profile", "hb_profile_read", "hb_autotune", "hb_autotune_times", "lib"]
+           "hb_host_apply", "hb_host_apply_plan", "hb_host_tc_apply", "hb_host_sweep", "hb_host_sweep_sched", "hb_far_field_adjoint", "hb_profile", "hb_profile_read", "hb_autotune", "hb_autotune_times", "lib"]
 
 
 def lib():
@@ -343,3 +343,14 @@ def hb_host_sweep(f, b, which):
     v = np.array(b, dtype=np.complex128, copy=True)
     _lib.check(lib().hb_host_sweep(f._h, int(which), v.ctypes.data_as(C.POINTER(C.c_double))))
     return v
+
+
+def hb_host_sweep_sched(f, b, which, coef_bytes=16, win_slots=0):
+    """Host execution of the column-partitioned sweep kernel's schedule for one column
+    (verification without a GPU).  Returns (x, number of batches)."""
+    v = np.array(b, dtype=np.complex128, copy=True)
+    rc = lib().hb_host_sweep_sched(f._h, int(which), int(coef_bytes), int(win_slots),
+                                   v.ctypes.data_as(C.POINTER(C.c_double)))
+    if rc < 0:
+        _lib.check(rc)
+    return v, rc

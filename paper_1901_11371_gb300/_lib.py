@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "libhb.so")
 HB_OK, HB_EINVAL, HB_ENOMEM, HB_ECUDA, HB_ENOCONV, HB_ETIMEOUT, HB_ENAN, HB_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
 HB_STRIP, HB_SPIRAL, HB_ARC, HB_PARALLEL_STRIPS, HB_POLYLINE = 0, 1, 2, 3, 4
 HB_OPT_LEAF_LU = 1
+HB_OPT_SWEEP_WINDOW_MIN = 2
 HB_C128, HB_C64, HB_SPLIT_BF16 = 0, 1, 2
 HB_OP_N, HB_OP_H = 0, 1
 ERR_NAMES = {0: "HB_OK", -1: "HB_EINVAL", -2: "HB_ENOMEM", -3: "HB_ECUDA", -4: "HB_ENOCONV", -5: "HB_ETIMEOUT",
@@ -80,6 +81,7 @@ SIGNATURES = {
     "hb_profile_read": (_INT, [_VP, _INT, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "hb_host_apply": (_INT, [_VP, _INT, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "hb_host_sweep": (_INT, [_VP, _INT, C.POINTER(C.c_double)]),
+    "hb_host_sweep_sched": (_INT, [_VP, _INT, _INT, _INT, C.POINTER(C.c_double)]),
     "hb_host_apply_plan": (_INT, [_VP, _INT, _INT, _INT, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "hb_host_tc_apply": (_INT, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "hb_last_error": (C.c_char_p, []),

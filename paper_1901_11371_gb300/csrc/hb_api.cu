@@ -406,6 +406,19 @@ int hb_host_tc_apply(hb_factor_t f, const double* x, double* y) {
   return (int)std::min<size_t>(tc.chunks.size(), (size_t)INT32_MAX);
 }
 
+int hb_host_sweep_sched(hb_factor_t f, int which, int coef_bytes, int win_slots, double* vec) {
+  if (!f || !f->host_only || !vec || which < 0 || which > 3 || (coef_bytes != 8 && coef_bytes != 16) ||
+      win_slots < 0 || win_slots > kSwWinSlots) {
+    set_error("hb_host_sweep_sched: bad argument");
+    return HB_EINVAL;
+  }
+  SwSched S;
+  build_sweep_sched(f->ph, which, coef_bytes, win_slots > 0 ? win_slots : kSwWinSlots, S);
+  if (!S.ok) { set_error("hb_host_sweep_sched: no column-partitioned schedule for this factor (%s)", S.why); return HB_EUNSUPPORTED; }
+  host_sweep_sched(f->ph, S, reinterpret_cast<cplx*>(vec));
+  return (int)std::min<size_t>(S.batches.size(), (size_t)INT32_MAX);
+}
+
 int hb_host_sweep(hb_factor_t f, int which, double* vec) {
   if (!f || !f->host_only || !vec || which < 0 || which > 3) { set_error("hb_host_sweep: bad argument"); return HB_EINVAL; }
   host_sweep(f->ph, f->hf, which, reinterpret_cast<cplx*>(vec));

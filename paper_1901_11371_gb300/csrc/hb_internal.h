@@ -430,6 +430,80 @@ bool check_apply_plan(const ApplyPlan& plan, const PackedHost& ph, int fes, int 
 // plan without a GPU): y = A^_F x or A^_F^H x.
 void host_apply_plan(const PackedHost& ph, const ApplyPlan& plan, int fes, bool adj, const cplx* x, cplx* y);
 
+// ---------------------------------------------------------------------------
+// Column-partitioned sweep schedule (kernel k_sweep_cols).  Every CTA runs a
+// whole sweep (Alg. 3 / Alg. 4, flattened as for the cooperative kernel) for
+// its own one or two right-hand sides, so no CTA waits on another.  The
+// program is cut into
+//   * resident runs: subtrees whose vector rows and butterfly state fit the
+//     CTA's shared-memory window (BEGIN loads the rows, END writes them back);
+//   * global phases: the stages of the large butterflies, reading and
+//     writing the vector rows and a CTA-private butterfly state in global
+//     memory.
+// Every butterfly phase is a sparse product in row form (one output row =
+// an output slot and a list of (input slot, coefficient) entries: the ID's
+// identity entries, the T or S entries, conjugated and negated as the op
+// requires); sweep-leaf phases are the packed triangles of the exact subtree
+// inverse, applied in place.  Phases are cut into batches; a batch's image
+// (row table, coefficients in the factor's precision, input slots) is
+// contiguous, so one bulk copy stages it.  Compute warp w takes the batches
+// w, w + kSwWarps, ... of a phase (a triangle is taken by all of them).
+// ---------------------------------------------------------------------------
+constexpr int kSwWarps = 16;                 // compute warps (one more warp stages the batches)
+constexpr int kSwWinBytes = 96 * 1024;       // resident window: rows + state of a run
+constexpr int kSwRingBytes = 104 * 1024;     // staging ring of batch images
+constexpr int kSwPartBytes = 16 * 1024;      // partial sums of a triangle product
+constexpr int kSwMaxCols = 2;                // right-hand sides per CTA
+constexpr int kSwWinSlots = kSwWinBytes / (kSwMaxCols * 8);   // window slots (complex-FP32 entries per column)
+constexpr int kSwBatchBytes = 12 * 1024;     // target image bytes of one batch
+constexpr int32_t kSwAcc = (int32_t)0x80000000;  // output slot flag: add to the output instead of overwriting
+enum SwStepKind : int32_t { SW_BEGIN = 0, SW_END = 1, SW_PHASE = 2 };
+enum SwFlag : int32_t { SWF_RES = 1 /* slots are window positions (int16 inputs) */, SWF_TRI = 2,
+                        SWF_UPPER = 4 /* triangle: upper */ };
+struct SwStep {
+  int32_t kind;
+  int32_t a0, a1;    // BEGIN / END: rows [a0, a1); PHASE: batches [a0, a0 + a1)
+  int32_t flags;     // PHASE: SWF_*
+};
+// Batch image (16-byte aligned pieces), row form:
+//   out[nrows] (int32 slot | kSwAcc), e0[nrows + 1] (int32 entry offsets),
+//   coef[nent] (complex, the factor's precision), in[nent] (int16 window slot with
+//   SWF_RES, else int32 global slot: a vector row r < n, or n + a state entry);
+// triangle (SWF_TRI): the packed triangle of order nrows, column by column
+// (lower: rows c..s-1 of column c; upper: rows 0..c), applied in place to the
+// window rows a0 .. a0 + nrows - 1.
+struct SwBatch {
+  int64_t img;       // byte offset of the image
+  int32_t bytes;     // image bytes (multiple of 16)
+  int32_t nrows;
+  int32_t nent;
+  int16_t glog;      // log2 of the lanes that share one row (reduced by shuffles)
+  int16_t flags;     // SWF_*
+  int32_t a0;        // triangle: window slot of its first row
+  int32_t off_e0, off_coef, off_in;   // byte offsets of the pieces in the image
+};
+static_assert(sizeof(SwBatch) == 40, "batch record");
+struct SwSched {
+  std::vector<SwStep> steps;
+  std::vector<SwBatch> batches;
+  std::vector<uint8_t> image;
+  int coef_bytes = 8;          // bytes of one complex coefficient (8: complex FP32, 16: FP64)
+  int win_slots = kSwWinSlots; // resident window the runs were cut for
+  int max_bytes = 0;           // largest batch image
+  int64_t res_phases = 0, glob_phases = 0, runs = 0;
+  bool ok = true;
+  const char* why = "";        // reason when !ok
+};
+// Schedule of sweep `which` (0: L~^{-1}, 1: U~^{-1}, 2: L~^{-H}, 3: U~^{-H}) with
+// complex coefficients of coef_bytes (8 or 16) bytes, runs cut for a resident
+// window of win_slots (<= kSwWinSlots) entries; needs the factor pool and the
+// sweep-leaf triangles (before they are released after an upload).
+void build_sweep_sched(const PackedHost& ph, int which, int coef_bytes, int win_slots, SwSched& S);
+// Execute a schedule on the host for one right-hand side (FP64 arithmetic on the
+// image's coefficients), reading rows, entries and slots from the images as the
+// kernel does: vec = sweep(vec) (verification of the schedule without a GPU).
+void host_sweep_sched(const PackedHost& ph, const SwSched& S, cplx* vec);
+
 // FP64 host execution of the packed program (verification without a GPU).
 void host_apply(const PackedHost& ph, const HostFactor& hf, bool adj, const cplx* x, cplx* y);
 void host_sweep(const PackedHost& ph, const HostFactor& hf, int which, cplx* vec);
