@@ -189,6 +189,7 @@ MEASURED_TRAFFIC = {
 KERNEL_SOURCES = {
     "k_sweep": ["hb_sweep_impl.cuh", "hb_sweep.cu", "hb_sweep_f32w.cu", "hb_sweep_launch.h"],
     "k_apply1": ["hb_apply1.cu", "hb_plan.cpp"],
+    "k_sweep_cols": ["hb_sweep_cols.cu", "hb_swsched.cpp", "hb_sweep_launch.h"],
 }
 
 
@@ -381,7 +382,9 @@ def run_kernels(args):
     tuned, times = None, {}
     if args.grid_min:
         hb.lib().hb_set_sweep_grid_min(f._h, args.grid_min)
-    else:
+    if args.sweep_kernel >= 0:
+        hb.hb_set_sweep_kernel(f, args.sweep_kernel)
+    elif not args.grid_min:
         tuned = hb.hb_autotune(f, R)
         times = hb.hb_autotune_times(f, R)
     st = hb.hb_factor_info(f)
@@ -411,7 +414,7 @@ def run_kernels(args):
     eb = 16 if args.form == "c128" else 8
     vec_extra = 2 * wl.n * (R - 1) * eb
     out = {"mode": "kernels", "workload": wl.name, "nrhs": R, "form": args.form,
-           "grid_min": args.grid_min or tuned, "autotune_ms": times,
+           "grid_min": args.grid_min or tuned, "sweep_kernel": args.sweep_kernel, "autotune_ms": times,
            "apply_ms": ms_a, "lower_ms": ms_l, "upper_ms": ms_u,
            "adjoint_apply_ms": ms_ah, "adjoint_lower_ms": ms_lh, "adjoint_upper_ms": ms_uh,
            "apply_GBps": (st["apply_bytes"] + vec_extra) / ms_a / 1e6,
@@ -429,6 +432,8 @@ def main():
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--form", default="c64", choices=["c64", "c128", "split"])
     ap.add_argument("--grid-min", type=int, default=0)
+    ap.add_argument("--sweep-kernel", type=int, default=-1, choices=[-1, 0, 1],
+                    help="kernels mode: -1 autotune, 0 cooperative, 1 column-partitioned")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -477,8 +482,9 @@ def main():
     vec_extra = 2 * st["n"] * (NRHS - 1) * 8
     sweep_bytes = 0.5 * (st["lower_bytes"] + st["upper_bytes"]) + vec_extra
     apply_bytes = st["apply_bytes"] + vec_extra
-    dominant = "k_sweep" if out["ms_sweep"] >= out["ms_apply"] else "apply (k_apply_*)"
-    if dominant == "k_sweep":
+    sweep_kernel = "k_sweep_cols" if out["tuned"] == 0 else "k_sweep"
+    dominant = sweep_kernel if out["ms_sweep"] >= out["ms_apply"] else "apply (k_apply_*)"
+    if dominant == sweep_kernel:
         achieved = sweep_bytes / (sweep_ms / 1e3) / 1e9
         algo = sweep_bytes
         avg_ms = sweep_ms
@@ -501,6 +507,8 @@ def main():
                    "form": f"split-BF16: FP64 FGMRES({RESTART}) + IR around U~^-1 L~^-1 (complex FP32) and A_F "
                            "(leaf contractions on tcgen05 tensor cores, butterfly steps complex FP32)",
                    "rhs_per_step": NRHS, "sweep_grid_min": out["tuned"],
+                   "sweep_kernel": "column-partitioned (k_sweep_cols)" if out["tuned"] == 0
+                                   else f"cooperative (k_sweep_coop, grid_min {out['tuned']})",
                    "sweep_autotune_ms": {str(k): round(v, 3) for k, v in out["tune_ms"].items()},
                    "l2": f"inputs larger than L2: factor {st['device_bytes'] / 1e6:.0f} MB",
                    "kmax": st["kmax"], "kavg": round(st["kavg"], 2), "build_s": round(out["t_build"], 2)},

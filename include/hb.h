@@ -288,21 +288,35 @@ int hb_monostatic(hb_factor_t f, const void* x, int64_t nrhs, int64_t ld, const 
  * legacy default stream.  Returns the previous value (>= 1) or an error code. */
 int hb_set_sweep_grid_min(hb_factor_t f, int grid_min);
 
-/* hb_autotune -- time the sweep kernel for nrhs right-hand sides under each
- * candidate split between grid-wide and single-CTA phases (thresholds 4, 8,
- * 16, 32, 64 ops, and "all single-CTA"), keep the fastest for calls with one
- * right-hand side (nrhs == 1) or with several (nrhs > 1), and report the
- * chosen threshold in *chosen (may be NULL).  Synchronises `stream`; uses the
- * factor's workspace.  hb_set_sweep_grid_min clears the tuned choice.
+/* hb_autotune -- time the cooperative sweep kernel for nrhs right-hand sides
+ * under each candidate split between grid-wide and single-CTA phases
+ * (thresholds 4, 8, 16, 32, 64 ops, and "all single-CTA") and, for the
+ * complex-FP32 forms, the column-partitioned sweep kernel; keep the fastest
+ * for calls with one right-hand side (nrhs == 1) or with several (nrhs > 1),
+ * and report the choice in *chosen (may be NULL): the threshold, or 0 for the
+ * column-partitioned kernel.  Synchronises `stream`; uses the factor's
+ * workspace.  hb_set_sweep_grid_min clears the tuned choice.
  * Not in the paper: launch-configuration tuning. */
 int hb_autotune(hb_factor_t f, int64_t nrhs, void* stream, int* chosen);
 
 /* hb_autotune_times -- the per-candidate sweep times (ms per sweep) of the
  * last hb_autotune call of the class of nrhs (one / several right-hand
- * sides), with the candidates' thresholds (2^30 = all single-CTA).  Writes
- * min(max, 6) entries to ms_out / grid_min_out (host arrays) and returns the
- * number written, 0 if that class was never tuned, or HB_EINVAL. */
+ * sides), with the candidates' thresholds (2^30 = all single-CTA; 0 = the
+ * column-partitioned kernel, timed for the complex-FP32 forms only).  Writes
+ * at most max of the 6 or 7 entries to ms_out / grid_min_out (host arrays)
+ * and returns the number written, 0 if that class was never tuned, or HB_EINVAL. */
 int hb_autotune_times(hb_factor_t f, int64_t nrhs, float* ms_out, int* grid_min_out, int max);
+
+/* hb_set_sweep_kernel -- which kernel runs the sweeps (L~^{-1}, U~^{-1} and the
+ * adjoints; Algs. 3, 4): -1 = the last hb_autotune choice (default; the
+ * cooperative kernel until tuned), 0 = the cooperative kernel (grid-wide phases
+ * for large butterfly stages, single-CTA runs near the leaves), 1 = the
+ * column-partitioned kernel (every CTA runs the whole sweep for its own one or
+ * two right-hand sides from host-built schedules: no grid barriers;
+ * complex-FP32 forms only).  Results agree to the rounding of the forms'
+ * arithmetic.  Returns HB_OK, HB_EUNSUPPORTED (kind 1 for HB_C128, which has
+ * no schedules) or HB_EINVAL.  Not in the paper: an execution choice. */
+int hb_set_sweep_kernel(hb_factor_t f, int kind);
 
 /* hb_set_wait_limit -- iteration limit of every bounded device-side wait
  * (the sweep kernel's grid barrier; default 2^24 polls, about a second).

@@ -23,7 +23,7 @@ __all__ = ["HB_STRIP", "HB_SPIRAL", "HB_ARC", "HB_PARALLEL_STRIPS", "HB_POLYLINE
            "hb_geometry_polyline", "hb_factor", "hb_factor_host",
            "hb_factor_info", "hb_tree", "hb_apply", "hb_apply_adjoint", "hb_precond_solve", "hb_lower_solve",
            "hb_upper_solve", "hb_residual", "hb_gmres", "hb_tfqmr", "hb_rhs_plane_wave", "hb_far_field", "hb_monostatic",
-           "hb_host_apply", "hb_host_apply_plan", "hb_host_tc_apply", "hb_host_sweep", "hb_host_sweep_sched", "hb_far_field_adjoint", "hb_profile", "hb_profile_read", "hb_autotune", "hb_autotune_times", "lib"]
+           "hb_host_apply", "hb_host_apply_plan", "hb_host_tc_apply", "hb_host_sweep", "hb_host_sweep_sched", "hb_far_field_adjoint", "hb_profile", "hb_profile_read", "hb_autotune", "hb_autotune_times", "hb_set_sweep_kernel", "lib"]
 
 
 def lib():
@@ -281,20 +281,27 @@ def hb_monostatic(f, x, phi_deg, stream=None):
 
 
 def hb_autotune(f, nrhs, stream=None):
-    """Pick the fastest sweep segmentation for `nrhs` right-hand sides; returns the chosen threshold."""
+    """Pick the fastest sweep kernel / segmentation for `nrhs` right-hand sides; returns the chosen
+    threshold (0: the column-partitioned kernel)."""
     ch = C.c_int()
     _lib.check(lib().hb_autotune(f._h, int(nrhs), _stream(stream), C.byref(ch)))
     return ch.value
 
 
 def hb_autotune_times(f, nrhs):
-    """{threshold: ms per sweep} of the last hb_autotune for the class of `nrhs` ({} if untuned)."""
-    ms = (C.c_float * 6)()
-    gm = (C.c_int * 6)()
-    n = lib().hb_autotune_times(f._h, int(nrhs), ms, gm, 6)
+    """{threshold: ms per sweep} of the last hb_autotune for the class of `nrhs` ({} if untuned;
+    threshold 0: the column-partitioned kernel)."""
+    ms = (C.c_float * 7)()
+    gm = (C.c_int * 7)()
+    n = lib().hb_autotune_times(f._h, int(nrhs), ms, gm, 7)
     if n < 0:
         _lib.check(n)
     return {int(gm[i]): float(ms[i]) for i in range(n)}
+
+
+def hb_set_sweep_kernel(f, kind):
+    """Sweep kernel: -1 the autotuner's choice, 0 cooperative, 1 column-partitioned."""
+    _lib.check(lib().hb_set_sweep_kernel(f._h, int(kind)))
 
 
 def hb_profile(f, enable=True):

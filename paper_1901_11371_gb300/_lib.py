@@ -73,6 +73,7 @@ SIGNATURES = {
     "hb_far_field_adjoint": (_INT, [_VP, _VP, _I64, C.POINTER(C.c_double), _I64, _VP, _I64, _VP]),
     "hb_monostatic": (_INT, [_VP, _VP, _I64, _I64, C.POINTER(C.c_double), _VP, _VP]),
     "hb_set_sweep_grid_min": (_INT, [_VP, _INT]),
+    "hb_set_sweep_kernel": (_INT, [_VP, _INT]),
     "hb_set_wait_limit": (_INT, [_VP, C.c_longlong]),
     "hb_autotune": (_INT, [_VP, _I64, _VP, C.POINTER(C.c_int)]),
     "hb_autotune_times": (_INT, [_VP, _I64, C.POINTER(C.c_float), C.POINTER(C.c_int), C.c_int]),

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libhb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["hb_kernels.cu", "hb_sweep.cu", "hb_sweep_f64.cu", "hb_sweep_f32n.cu", "hb_sweep_f32w.cu",
-              "hb_sweep_mix.cu", "hb_api.cu", "hb_solver.cu", "hb_noalloc.cu", "hb_apply1.cu", "hb_tc.cu"]
+              "hb_sweep_mix.cu", "hb_api.cu", "hb_solver.cu", "hb_noalloc.cu", "hb_apply1.cu", "hb_tc.cu", "hb_sweep_cols.cu"]
 CPP_SOURCES = ["hb_host.cpp", "hb_plan.cpp", "hb_tc_host.cpp", "hb_swsched.cpp"]
 
 

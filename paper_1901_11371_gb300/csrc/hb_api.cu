@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <thread>
 
 #include "hb_api_internal.h"
 
@@ -155,6 +156,26 @@ int upload_factor(const PackedHost& ph, const HostFactor& hf, const Geometry& g,
       dp.ok = true;
     }
   }
+  if (form != HB_C128) {
+    // column-partitioned sweep schedules of the four sweeps (built in parallel;
+    // they need the factor pool and the sweep-leaf triangles, released after upload)
+    SwSched S[4];
+    std::thread th[4];
+    for (int w = 0; w < 4; ++w) th[w] = std::thread([&, w] { build_sweep_sched(ph, w, 8, df.sw_win, S[w]); });
+    for (auto& t : th) t.join();
+    for (int w = 0; w < 4; ++w) {
+      if (!S[w].ok) continue;   // the cooperative kernel serves this sweep
+      DevSched& d = df.sw[w];
+      if ((rc = up(S[w].steps, &d.steps, st, df.device_bytes))) return rc;
+      if ((rc = up(S[w].batches, &d.batches, st, df.device_bytes))) return rc;
+      if ((rc = up(S[w].image, &d.image, st, df.device_bytes))) return rc;
+      HB_CU(cudaStreamSynchronize(st));
+      d.nstep = (int)S[w].steps.size();
+      d.nbatch = (int64_t)S[w].batches.size();
+      d.ok = true;
+      std::vector<uint8_t>().swap(S[w].image);
+    }
+  }
   if ((rc = set_grid_min(df, ph, 16, st))) return rc;
   if ((rc = build_candidates(df, ph, 0, 1, st))) return rc;
   if ((rc = build_candidates(df, ph, 1, 2, st))) return rc;
@@ -229,6 +250,11 @@ void free_factor(DevFactor& df) {
     for (auto& per_prog : per_cls)
       for (DSeg* p : per_prog)
         if (p) cudaFree(p);
+  for (DevSched& s : df.sw) {
+    void* pp[] = {s.steps, s.batches, s.image};
+    for (void* p : pp)
+      if (p) cudaFree(p);
+  }
   df = DevFactor();
 }
 
@@ -323,7 +349,7 @@ int hb_factor(hb_geometry_t g, double wavelength, double eta0, double gamma, int
 int hb_factor_ex(hb_geometry_t g, double wavelength, double eta0, double gamma, int64_t leaf, double eps, int form,
                  uint64_t seed, int options, void* stream, hb_factor_t* out) {
   if (!out || !g) { set_error("hb_factor: null argument"); return HB_EINVAL; }
-  if (options & ~HB_OPT_LEAF_LU) { set_error("hb_factor: unknown option bits 0x%x", options); return HB_EINVAL; }
+  if (options & ~(HB_OPT_LEAF_LU | HB_OPT_SWEEP_WINDOW_MIN)) { set_error("hb_factor: unknown option bits 0x%x", options); return HB_EINVAL; }
   *out = nullptr;
   if (form != HB_C128 && form != HB_C64 && form != HB_SPLIT_BF16) { set_error("hb_factor: bad form %d", form); return HB_EINVAL; }
   auto t0 = std::chrono::steady_clock::now();
@@ -339,6 +365,7 @@ int hb_factor_ex(hb_geometry_t g, double wavelength, double eta0, double gamma, 
       for (const auto& sm : b.mid) z += (int64_t)sm.size();
       (b.kind == 1 ? f->lower_nnz : f->upper_nnz) += z;
     }
+    if (options & HB_OPT_SWEEP_WINDOW_MIN) f->df.sw_win = 512;
     rc = upload_factor(f->ph, f->hf, g->geo, form, (cudaStream_t)stream, f->df);
     f->df.form = form;
   }
@@ -365,7 +392,7 @@ int hb_factor_host_ex(hb_geometry_t g, double wavelength, double eta0, double ga
                       uint64_t seed, int options, hb_factor_t* out) {
   if (!out || !g) { set_error("hb_factor_host: null argument"); return HB_EINVAL; }
   *out = nullptr;
-  if (options & ~HB_OPT_LEAF_LU) { set_error("hb_factor_host: unknown option bits 0x%x", options); return HB_EINVAL; }
+  if (options & ~(HB_OPT_LEAF_LU | HB_OPT_SWEEP_WINDOW_MIN)) { set_error("hb_factor_host: unknown option bits 0x%x", options); return HB_EINVAL; }
   hb_factor_s* f = new (std::nothrow) hb_factor_s();
   if (!f) { set_error("hb_factor_host: out of host memory"); return HB_ENOMEM; }
   int rc = build_factor(g->geo, wavelength, eta0, gamma, leaf, eps, seed, f->hf, options);
@@ -509,6 +536,7 @@ int hb_tree(hb_factor_t f, int64_t* node_begin, int64_t* node_end) {
 int hb_set_sweep_grid_min(hb_factor_t f, int grid_min) {
   if (!f || f->host_only || grid_min < 1) { set_error("hb_set_sweep_grid_min: bad argument"); return HB_EINVAL; }
   f->df.tuned[0] = f->df.tuned[1] = -1;
+  f->df.cols_won[0] = f->df.cols_won[1] = false;
   int old = f->df.grid_min;
   int rc = set_grid_min(f->df, f->ph, grid_min, nullptr);
   return rc ? rc : old;
@@ -540,10 +568,10 @@ int hb_autotune(hb_factor_t f, int64_t nrhs, void* stream, int* chosen) {
   int bestc = -1;
   for (int c = 0; c < DevFactor::kNCand; ++c) {
     df.tuned[cls] = c;
-    int rc = sweep_internal(f, p, 0, v, nrhs, st);   // warm
+    int rc = sweep_run(f, p, 0, v, nrhs, st, 0);   // warm
     if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
     cudaEventRecord(e0, st);
-    for (int r = 0; r < 2; ++r) sweep_internal(f, p, 0, v, nrhs, st);
+    for (int r = 0; r < 2; ++r) sweep_run(f, p, 0, v, nrhs, st, 0);
     cudaEventRecord(e1, st);
     cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -551,10 +579,25 @@ int hb_autotune(hb_factor_t f, int64_t nrhs, void* stream, int* chosen) {
     df.cand_ms[cls][c] = ms / 2;
     if (ms < best) { best = ms; bestc = c; }
   }
+  df.tuned[cls] = bestc;
+  // the column-partitioned kernel (complex-FP32 factors with schedules)
+  df.cols_won[cls] = false;
+  df.cols_ms[cls] = 0.f;
+  if (p == PREC_F32 && df.sw[0].ok) {
+    int rc = sweep_run(f, p, 0, v, nrhs, st, 1);   // warm
+    if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 2; ++r) sweep_run(f, p, 0, v, nrhs, st, 1);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    df.cols_ms[cls] = ms / 2;
+    df.cols_won[cls] = ms < best;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  df.tuned[cls] = bestc;
-  if (chosen) *chosen = DevFactor::kCand[bestc];
+  if (chosen) *chosen = df.cols_won[cls] ? 0 : DevFactor::kCand[bestc];
   return hb_status(f, stream);
 }
 
@@ -570,7 +613,22 @@ int hb_autotune_times(hb_factor_t f, int64_t nrhs, float* ms_out, int* grid_min_
     ms_out[c] = f->df.cand_ms[cls][c];
     grid_min_out[c] = DevFactor::kCand[c];
   }
+  if (f->df.cols_ms[cls] > 0.f && max > n) {
+    ms_out[n] = f->df.cols_ms[cls];
+    grid_min_out[n] = 0;   // the column-partitioned kernel
+    return n + 1;
+  }
   return n;
+}
+
+int hb_set_sweep_kernel(hb_factor_t f, int kind) {
+  if (!f || f->host_only || kind < -1 || kind > 1) { set_error("hb_set_sweep_kernel: bad argument"); return HB_EINVAL; }
+  if (kind == 1 && !(f->df.sw[0].ok && f->df.sw[1].ok && f->df.sw[2].ok && f->df.sw[3].ok)) {
+    set_error("hb_set_sweep_kernel: this factor has no column-partitioned schedules (complex-FP32 forms only)");
+    return HB_EUNSUPPORTED;
+  }
+  f->df.sweep_kernel = kind;
+  return HB_OK;
 }
 
 int hb_set_wait_limit(hb_factor_t f, long long spins) {
@@ -619,16 +677,26 @@ int apply_internal(hb_factor_t f, Prec p, bool adj, const void* x, void* y, int6
   return rc;
 }
 
-int sweep_internal(hb_factor_t f, Prec p, int which, void* vec, int64_t R, cudaStream_t st) {
-  size_t es = (p == PREC_F32) ? 8 : 16;
-  void* state = f->ws.get(WS_STATE_SWEEP, (size_t)f->df.state_len * R * es);
+// kernel: 0 = cooperative, 1 = column-partitioned
+int sweep_run(hb_factor_t f, Prec p, int which, void* vec, int64_t R, cudaStream_t st, int kernel) {
+  const size_t es = (p == PREC_F32) ? 8 : 16;
+  const size_t need = kernel == 1 ? (size_t)sweep_cols_state_entries(f->df, R) * 8 : (size_t)f->df.state_len * R * es;
+  void* state = f->ws.get(WS_STATE_SWEEP, need);
   if (!state) { set_error("sweep: cannot allocate state workspace"); return HB_ENOMEM; }
   cudaEvent_t e;
   f->prof.begin(1, st, e);
-  int rc = launch_sweep_coop(f->df, p, which, vec, R, state, f->df.bar, st, f->df.spin_limit);
+  int rc = kernel == 1 ? launch_sweep_cols(f->df, which, vec, R, state, st)
+                       : launch_sweep_coop(f->df, p, which, vec, R, state, f->df.bar, st, f->df.spin_limit);
   f->prof.end(1, st, e);
-  count_launch(f, 1);
+  count_launch(f, kernel == 1 ? sweep_cols_launches(R) : 1);
   return rc;
+}
+
+int sweep_internal(hb_factor_t f, Prec p, int which, void* vec, int64_t R, cudaStream_t st) {
+  const DevFactor& df = f->df;
+  const bool cols = p == PREC_F32 && df.sw[which].ok &&
+                    (df.sweep_kernel == 1 || (df.sweep_kernel < 0 && df.cols_won[R > 1 ? 1 : 0]));
+  return sweep_run(f, p, which, vec, R, st, cols ? 1 : 0);
 }
 
 }  // namespace hb

@@ -53,6 +53,8 @@ namespace hb {
 int check_vec_args(hb_factor_t f, const void* a, const void* b, int64_t nrhs, int64_t ld, const char* who);
 int apply_internal(hb_factor_t f, Prec p, bool adj, const void* x, void* y, int64_t R, cudaStream_t st);
 int sweep_internal(hb_factor_t f, Prec p, int which, void* vec, int64_t R, cudaStream_t st);
+// one sweep with a given kernel (0: cooperative, 1: column-partitioned)
+int sweep_run(hb_factor_t f, Prec p, int which, void* vec, int64_t R, cudaStream_t st, int kernel);
 // count kernels launched by the library (profiling)
 inline void count_launch(hb_factor_t f, int n) { f->prof.count[2] += n; }
 // r(col-major, ld) = b(col-major, ld) - y(internal [row][R], double2)

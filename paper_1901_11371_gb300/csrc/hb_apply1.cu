@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(kA1Threads, 1) k_apply1(A1Args a) {
     for (int q = 0; q < iss; ++q) {
       if (s_bdone[q % kA1Slots] == q + 1 || q + kA1Slots < iss) continue;
       long long spins = 0;
-      while (!mb_try_wait(&s_mbar[q % kA1Slots], (unsigned)(q / kA1Slots) & 1u) && ++spins < a.spin_limit) {
+      while (!mb_try_wait(&s_mbar[q % kA1Slots], (unsigned)(q / kA1Slots) & 1u) && ++spins < drain_limit(a.spin_limit)) {
       }
     }
   }

@@ -22,6 +22,16 @@ struct DevPlan {
 // Shared-memory staging ring of the persistent apply (bytes per CTA).
 constexpr int kA1RingBytes = 200 * 1024;
 
+// Device copy of a column-partitioned sweep schedule (SwSched).
+struct DevSched {
+  SwStep* steps = nullptr;
+  SwBatch* batches = nullptr;
+  uint8_t* image = nullptr;
+  int nstep = 0;
+  int64_t nbatch = 0;
+  bool ok = false;
+};
+
 struct DevFactor {
   int form = HB_C128;            // storage form of the factor pool
   int64_t n = 0, n0 = 0, m = 0;
@@ -65,6 +75,14 @@ struct DevFactor {
   int64_t cand_budget[2] = {0, 0};                          // residency budget (entries) of each set
   float cand_ms[2][kNCand] = {};                            // last autotune timings
   int tuned[2] = {-1, -1};                                  // chosen candidate for 1 RHS / several RHS (-1: grid_min)
+  // column-partitioned sweep kernel (complex-FP32 factors): schedules of the four
+  // sweeps, the window their runs were cut for, the kernel choice (-1: the
+  // autotuner's, 0: cooperative, 1: column-partitioned) and the autotuner's verdict
+  DevSched sw[4];
+  int sw_win = kSwWinSlots;
+  int sweep_kernel = -1;
+  bool cols_won[2] = {false, false};
+  float cols_ms[2] = {0.f, 0.f};
   void* bar = nullptr;                                      // grid barrier state + error flag
   void* abar = nullptr;                                     // grid barrier of the persistent apply
   // split-BF16 tensor-core operands (form HB_SPLIT_BF16; TcOperands)
@@ -114,6 +132,13 @@ int launch_apply1(const DevFactor& df, Prec p, bool adjoint, const void* x, void
 // grid barriers between segments.
 int launch_sweep_coop(const DevFactor& df, Prec p, int which, void* vec, int64_t R, void* state, void* bar,
                       cudaStream_t st, long long spin_limit);
+// Column-partitioned sweep, in place (complex-FP32 vectors [row][R]): every CTA
+// runs the whole sweep for its own columns (kernel k_sweep_cols).  `state`: at
+// least sweep_cols_state_entries(df, R) complex-FP32 entries.  HB_EUNSUPPORTED
+// without a schedule for `which`.
+int launch_sweep_cols(const DevFactor& df, int which, void* vec, int64_t R, void* state, cudaStream_t st);
+int64_t sweep_cols_state_entries(const DevFactor& df, int64_t R);
+int sweep_cols_launches(int64_t R);
 // Read the barrier error flag (synchronises st).  *err != 0: a bounded wait expired.
 int read_grid_error(void* bar, cudaStream_t st, int* err);
 // Shared memory that a single-CTA run may use to keep its vector rows and

@@ -817,7 +817,7 @@ __device__ bool local_run_ring(const SweepArgs& a, const DSeg& sg, char* smem, i
     const int done = s_done, iss = s_issued;
     for (int q = done; q < iss; ++q) {
       long long spins = 0;
-      while (!mbar_try_wait(&s_mbar[q % (kLook + 1)], (unsigned)(q / (kLook + 1)) & 1u) && ++spins < a.spin_limit) {
+      while (!mbar_try_wait(&s_mbar[q % (kLook + 1)], (unsigned)(q / (kLook + 1)) & 1u) && ++spins < drain_limit(a.spin_limit)) {
       }
     }
   }

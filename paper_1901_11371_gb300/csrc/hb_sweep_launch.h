@@ -19,6 +19,13 @@ struct GridBar {
   int pad;
 };
 
+// Limit of the wait for a CTA's own bulk copies still in flight after another
+// bounded wait gave up: at least 2^22 polls whatever the configured limit, so
+// that no copy lands in shared memory after the CTA has left.
+__host__ __device__ inline long long drain_limit(long long spin_limit) {
+  return spin_limit > (1LL << 22) ? spin_limit : (1LL << 22);
+}
+
 // q = columns per CTA of the single-CTA runs (ceil(R / #SMs)); each function
 // picks the column-chunk width RC for q and launches the kernel.
 int sweep_coop_f64(const DevFactor& df, int which, void* vec, int64_t R, void* st, void* bar, cudaStream_t s,

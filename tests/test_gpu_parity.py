@@ -277,7 +277,8 @@ def test_sweeps_256_columns_vs_oracle_triangles(hb, semi4096):
              (hb.hb_lower_solve, hb.HB_OP_H), (hb.hb_upper_solve, hb.HB_OP_H)]
     for name, dt, bound in (("f32", torch.complex64, 1e-6), ("f64", torch.complex128, 2e-7)):
         f = semi4096[name]
-        assert hb.hb_autotune(f, R) >= 4
+        ch = hb.hb_autotune(f, R)
+        assert ch >= 4 or (ch == 0 and name == "f32")     # 0: the column-partitioned kernel
         bt = _t(b.T.copy(), dt)
         for w, (fn, op) in enumerate(calls):
             x = fn(f, bt, op).cpu().numpy().astype(np.complex128).T
@@ -395,8 +396,9 @@ def test_sweeps_many_rhs_fp32(hb, strip, R):
     lib = hb.lib()
     for gm in (1, 8, 1 << 20, None):
         if gm is None:
-            assert hb.hb_autotune(f, R) >= 4
-            assert len(hb.hb_autotune_times(f, R)) == 6
+            ch = hb.hb_autotune(f, R)
+            assert ch >= 4 or ch == 0                      # 0: the column-partitioned kernel
+            assert len(hb.hb_autotune_times(f, R)) == 7     # six segmentations + that kernel
         else:
             assert lib.hb_set_sweep_grid_min(f._h, gm) >= 1
         for w, (fn, op) in enumerate(calls):

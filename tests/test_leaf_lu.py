@@ -67,4 +67,4 @@ def test_host_sweeps_with_leaf_lu_are_variant_triangular_solves(hb):
 def test_unknown_option_bits_are_rejected(hb):
     g = hb.hb_geometry(hb.HB_STRIP, (0.0, 0.0, 3.2, 0.0), 64)
     with pytest.raises(hb.HBError):
-        hb.hb_factor_host(g, 32, 1e-6, options=2)
+        hb.hb_factor_host(g, 32, 1e-6, options=4)   # bits 1 and 2 are HB_OPT_LEAF_LU and HB_OPT_SWEEP_WINDOW_MIN
