@@ -166,12 +166,10 @@ int upload_factor(const PackedHost& ph, const HostFactor& hf, const Geometry& g,
     for (int w = 0; w < 4; ++w) {
       if (!S[w].ok) continue;   // the cooperative kernel serves this sweep
       DevSched& d = df.sw[w];
-      if ((rc = up(S[w].steps, &d.steps, st, df.device_bytes))) return rc;
-      if ((rc = up(S[w].batches, &d.batches, st, df.device_bytes))) return rc;
+      if ((rc = up(S[w].groups, &d.groups, st, df.device_bytes))) return rc;
       if ((rc = up(S[w].image, &d.image, st, df.device_bytes))) return rc;
       HB_CU(cudaStreamSynchronize(st));
-      d.nstep = (int)S[w].steps.size();
-      d.nbatch = (int64_t)S[w].batches.size();
+      d.ngroup = (int64_t)S[w].groups.size();
       d.ok = true;
       std::vector<uint8_t>().swap(S[w].image);
     }
@@ -251,7 +249,7 @@ void free_factor(DevFactor& df) {
       for (DSeg* p : per_prog)
         if (p) cudaFree(p);
   for (DevSched& s : df.sw) {
-    void* pp[] = {s.steps, s.batches, s.image};
+    void* pp[] = {s.groups, s.image};
     for (void* p : pp)
       if (p) cudaFree(p);
   }
@@ -443,7 +441,7 @@ int hb_host_sweep_sched(hb_factor_t f, int which, int coef_bytes, int win_slots,
   build_sweep_sched(f->ph, which, coef_bytes, win_slots > 0 ? win_slots : kSwWinSlots, S);
   if (!S.ok) { set_error("hb_host_sweep_sched: no column-partitioned schedule for this factor (%s)", S.why); return HB_EUNSUPPORTED; }
   host_sweep_sched(f->ph, S, reinterpret_cast<cplx*>(vec));
-  return (int)std::min<size_t>(S.batches.size(), (size_t)INT32_MAX);
+  return (int)std::min<int64_t>(S.batches, (int64_t)INT32_MAX);
 }
 
 int hb_host_sweep(hb_factor_t f, int which, double* vec) {

@@ -24,11 +24,9 @@ constexpr int kA1RingBytes = 200 * 1024;
 
 // Device copy of a column-partitioned sweep schedule (SwSched).
 struct DevSched {
-  SwStep* steps = nullptr;
-  SwBatch* batches = nullptr;
+  SwGroup* groups = nullptr;
   uint8_t* image = nullptr;
-  int nstep = 0;
-  int64_t nbatch = 0;
+  int64_t ngroup = 0;
   bool ok = false;
 };
 

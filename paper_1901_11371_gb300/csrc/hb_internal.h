@@ -436,61 +436,76 @@ void host_apply_plan(const PackedHost& ph, const ApplyPlan& plan, int fes, bool 
 // its own one or two right-hand sides, so no CTA waits on another.  The
 // program is cut into
 //   * resident runs: subtrees whose vector rows and butterfly state fit the
-//     CTA's shared-memory window (BEGIN loads the rows, END writes them back);
+//     CTA's shared-memory window (their first group loads the rows, their
+//     last writes them back);
 //   * global phases: the stages of the large butterflies, reading and
 //     writing the vector rows and a CTA-private butterfly state in global
-//     memory.
+//     memory (each batch first gathers its distinct inputs into its warp's
+//     slice of the window, which is free between runs).
 // Every butterfly phase is a sparse product in row form (one output row =
-// an output slot and a list of (input slot, coefficient) entries: the ID's
+// an output slot and a list of (input, coefficient) entries: the ID's
 // identity entries, the T or S entries, conjugated and negated as the op
 // requires); sweep-leaf phases are the packed triangles of the exact subtree
-// inverse, applied in place.  Phases are cut into batches; a batch's image
-// (row table, coefficients in the factor's precision, input slots) is
-// contiguous, so one bulk copy stages it.  Compute warp w takes the batches
-// w, w + kSwWarps, ... of a phase (a triangle is taken by all of them).
+// inverse, applied in place.  The schedule is a sequence of staging groups,
+// one bulk copy each: a header, the batch descriptors, the batches' data.
+// A resident phase is one group (compute warp w takes its batches w, w + 16,
+// ...); a global phase is cut into groups of at most 16 batches; a triangle
+// is one group taken by all compute warps.
 // ---------------------------------------------------------------------------
-constexpr int kSwWarps = 16;                 // compute warps (one more warp stages the batches)
+constexpr int kSwWarps = 16;                 // compute warps (one more warp stages the groups)
 constexpr int kSwWinBytes = 96 * 1024;       // resident window: rows + state of a run
-constexpr int kSwRingBytes = 104 * 1024;     // staging ring of batch images
+constexpr int kSwRingBytes = 104 * 1024;     // staging ring of group images
 constexpr int kSwPartBytes = 16 * 1024;      // partial sums of a triangle product
 constexpr int kSwMaxCols = 2;                // right-hand sides per CTA
 constexpr int kSwWinSlots = kSwWinBytes / (kSwMaxCols * 8);   // window slots (complex-FP32 entries per column)
-constexpr int kSwBatchBytes = 12 * 1024;     // target image bytes of one batch
+constexpr int kSwGather = kSwWinSlots / kSwWarps;             // gathered inputs of a global batch (a warp's slice)
+constexpr int kSwBatchBytes = 12 * 1024;     // target data bytes of one resident batch
+constexpr int kSwGlobBytes = 3 * 1024;       // target data bytes of one global batch
+constexpr int kSwGroupBytes = 48 * 1024;     // target bytes of a global phase's group
 constexpr int32_t kSwAcc = (int32_t)0x80000000;  // output slot flag: add to the output instead of overwriting
-enum SwStepKind : int32_t { SW_BEGIN = 0, SW_END = 1, SW_PHASE = 2 };
-enum SwFlag : int32_t { SWF_RES = 1 /* slots are window positions (int16 inputs) */, SWF_TRI = 2,
-                        SWF_UPPER = 4 /* triangle: upper */ };
-struct SwStep {
-  int32_t kind;
-  int32_t a0, a1;    // BEGIN / END: rows [a0, a1); PHASE: batches [a0, a0 + a1)
-  int32_t flags;     // PHASE: SWF_*
+enum SwGroupFlag : int32_t {
+  SWG_END = 1,      // the phase ends with this group: barrier among the compute warps
+  SWG_TRI = 2,      // one triangle batch, taken by all compute warps
+  SWG_RES = 4,      // batches on the window (int16 window slots)
+  SWG_BEGIN = 8,    // load window rows [beg_lo, beg_hi) before the batches
+  SWG_ENDRUN = 16,  // write window rows [end_lo, end_hi) back after the barrier
+  SWG_UPPER = 32    // triangle: upper
 };
-// Batch image (16-byte aligned pieces), row form:
-//   out[nrows] (int32 slot | kSwAcc), e0[nrows + 1] (int32 entry offsets),
-//   coef[nent] (complex, the factor's precision), in[nent] (int16 window slot with
-//   SWF_RES, else int32 global slot: a vector row r < n, or n + a state entry);
-// triangle (SWF_TRI): the packed triangle of order nrows, column by column
-// (lower: rows c..s-1 of column c; upper: rows 0..c), applied in place to the
-// window rows a0 .. a0 + nrows - 1.
-struct SwBatch {
-  int64_t img;       // byte offset of the image
-  int32_t bytes;     // image bytes (multiple of 16)
-  int32_t nrows;
-  int32_t nent;
+struct SwGroup {     // one bulk copy
+  int64_t img;       // byte offset of the group image
+  int32_t bytes;     // multiple of 16
+  int32_t pad;
+};
+struct SwGroupHdr {  // first 32 bytes of a group image
+  int32_t nb, flags;
+  int32_t beg_lo, beg_hi, end_lo, end_hi;
+  int32_t pad0, pad1;
+};
+// Batch descriptor (after the header, nb of them); offsets relative to the batch
+// start.  Row form: out[nrows] (int32 slot | kSwAcc; window slot for resident
+// batches, else a global slot: a vector row r < n or n + a state entry),
+// e0[nrows + 1], coef[nent] (complex, the factor's precision), in[nent] (int16:
+// window slot, or position in the gather list), gl[ngl] (int32 global slots of
+// the distinct inputs, global batches only).  Triangle: the packed triangle of
+// order nrows, column by column (lower: rows c..s-1 of column c; upper: rows
+// 0..c), applied in place to window rows a0 .. a0 + nrows - 1.
+struct SwDesc {
+  int32_t off;       // byte offset of the batch inside the group image
+  int32_t nrows, nent, ngl;
+  int32_t a0;
+  int32_t off_e0, off_coef, off_in, off_gl;
   int16_t glog;      // log2 of the lanes that share one row (reduced by shuffles)
-  int16_t flags;     // SWF_*
-  int32_t a0;        // triangle: window slot of its first row
-  int32_t off_e0, off_coef, off_in;   // byte offsets of the pieces in the image
+  int16_t pad;
 };
-static_assert(sizeof(SwBatch) == 40, "batch record");
+static_assert(sizeof(SwGroupHdr) == 32, "group header");
+static_assert(sizeof(SwDesc) == 40, "batch descriptor");
 struct SwSched {
-  std::vector<SwStep> steps;
-  std::vector<SwBatch> batches;
+  std::vector<SwGroup> groups;
   std::vector<uint8_t> image;
   int coef_bytes = 8;          // bytes of one complex coefficient (8: complex FP32, 16: FP64)
   int win_slots = kSwWinSlots; // resident window the runs were cut for
-  int max_bytes = 0;           // largest batch image
-  int64_t res_phases = 0, glob_phases = 0, runs = 0;
+  int max_bytes = 0;           // largest group image
+  int64_t res_phases = 0, glob_phases = 0, runs = 0, batches = 0;
   bool ok = true;
   const char* why = "";        // reason when !ok
 };
@@ -500,8 +515,9 @@ struct SwSched {
 // sweep-leaf triangles (before they are released after an upload).
 void build_sweep_sched(const PackedHost& ph, int which, int coef_bytes, int win_slots, SwSched& S);
 // Execute a schedule on the host for one right-hand side (FP64 arithmetic on the
-// image's coefficients), reading rows, entries and slots from the images as the
-// kernel does: vec = sweep(vec) (verification of the schedule without a GPU).
+// image's coefficients), reading headers, descriptors, rows, entries and slots
+// from the group images as the kernel does: vec = sweep(vec) (verification of
+// the schedule without a GPU).
 void host_sweep_sched(const PackedHost& ph, const SwSched& S, cplx* vec);
 
 // FP64 host execution of the packed program (verification without a GPU).

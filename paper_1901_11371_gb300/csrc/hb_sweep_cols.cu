@@ -6,26 +6,31 @@
 // grid-wide, every link costs a grid barrier; run by one CTA, every link is a
 // shared-memory round trip.  So here each CTA runs the whole sweep for its own
 // one or two right-hand sides and never waits on another CTA:
-//   * a producer warp streams the schedule's batch images (host-built, see
-//     hb_swsched.cpp) into a shared-memory ring with one cp.async.bulk each,
-//     as far ahead as the ring allows -- the factor data never depends on the
-//     vectors;
+//   * a producer warp streams the schedule's group images (host-built, see
+//     hb_swsched.cpp: a header, batch descriptors, the batches' data) into a
+//     shared-memory ring with one cp.async.bulk each, as far ahead as the
+//     ring allows -- the factor data never depends on the vectors, and the
+//     compute warps find every record they need in the ring;
 //   * resident runs (subtrees whose rows and butterfly state fit the 96 KB
 //     window) start by loading their rows into shared memory and end by
 //     writing them back; inside them every phase reads and writes the window;
 //   * global phases (stages of the large butterflies) read and write the
-//     vector rows and a CTA-private butterfly state in global memory;
+//     vector rows and a CTA-private butterfly state in global memory: a batch
+//     first gathers its distinct inputs into its warp's slice of the window
+//     (free between runs) in one round trip;
 //   * a butterfly phase is a sparse product in row form: compute warp w takes
-//     the batches w, w + 16, ...; in a batch, groups of 2^glog lanes share a
-//     row (entries strided over the lanes, then a shuffle reduction), so that
-//     short dot products do not serialise on one lane;
+//     the batches w, w + 16, ... of a group; in a batch, groups of 2^glog lanes
+//     share a row (entries strided over the lanes, then a shuffle reduction),
+//     so that short dot products do not serialise on one lane;
 //   * a sweep-leaf phase (packed triangle, in place on the window rows) is
 //     taken by all compute warps: pairs of rows (j, s-1-j) times column
 //     groups, partial sums, a barrier, the reduction written back.
 // Consecutive phases are separated by one named barrier among the compute
-// warps.  Every wait is bounded; a wait that gives up raises the factor's
-// error flag (reported by hb_status / the solvers) and the CTA returns after a
-// second bounded wait for its copies still in flight.
+// warps; the groups of one phase are not.  Every wait is bounded; a warp whose
+// wait gives up stops computing but still meets the barriers up to the end of
+// the phase, where all compute warps learn of it and stop; the factor's error
+// flag is raised (reported by hb_status / the solvers) and the CTA returns
+// after a second bounded wait for its copies still in flight.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -39,7 +44,7 @@ namespace hb {
 namespace {
 
 constexpr int kSwThreads = (kSwWarps + 1) * 32;
-constexpr int kSwSlots = 64;   // batches in flight per CTA
+constexpr int kSwSlots = 64;   // groups in flight per CTA
 constexpr int kSwSmem = kSwRingBytes + kSwWinBytes + kSwPartBytes;
 static_assert(kSwSmem <= 224 * 1024, "dynamic shared memory of the column-partitioned sweep");
 
@@ -83,10 +88,8 @@ __device__ __forceinline__ bool cw_red_or(bool v) {
 }
 
 struct SwArgs {
-  const SwStep* steps;
-  int nstep;
-  const SwBatch* batches;
-  int64_t nbatch;
+  const SwGroup* groups;
+  int64_t ngroup;
   const uint8_t* image;
   float2* x;           // vectors, layout [row][R]
   int64_t R, n;
@@ -109,9 +112,9 @@ __device__ __forceinline__ void cmac(float2& acc, const float2 a, const float2 b
   acc.y = fmaf(a.y, b.x, acc.y);
 }
 
-// NC window entries (16-byte vector load for two columns)
+// NC consecutive shared-memory entries (16-byte vector load for two columns)
 template <int NC>
-__device__ __forceinline__ Cv<NC> win_load(const float2* p) {
+__device__ __forceinline__ Cv<NC> sm_load(const float2* p) {
   Cv<NC> r;
   if constexpr (NC == 2) {
     const float4 v = *reinterpret_cast<const float4*>(p);
@@ -124,52 +127,37 @@ __device__ __forceinline__ Cv<NC> win_load(const float2* p) {
   return r;
 }
 
-// input slot of a global phase: a vector row (this CTA's columns of x) or a
+// address of a global slot: a vector row (this CTA's columns of x) or a
 // CTA-private state entry
-template <int NC>
-__device__ __forceinline__ Cv<NC> glob_load(const SwArgs& a, int32_t s, const float2* xb, const float2* stp, int ncol) {
-  Cv<NC> r;
-  if (s < a.n) {
-    const float2* p = xb + (int64_t)s * a.R;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) r.v[c] = c < ncol ? p[c] : make_float2(0.f, 0.f);
-  } else {
-    r = win_load<NC>(stp + (int64_t)(s - a.n) * NC);
-  }
-  return r;
+__device__ __forceinline__ float2* gaddr(const SwArgs& a, int32_t s, float2* xb, float2* stp, int nc) {
+  return s < a.n ? xb + (int64_t)s * a.R : stp + (int64_t)(s - a.n) * nc;
 }
 
-// One batch of a butterfly phase in row form, one warp.  RES: slots are window
-// positions (int16), else global slots (int32).
+// One batch in row form, one warp.  Inputs: `in` (the window for resident
+// batches, the warp's gathered slice for global ones); outputs: window slots
+// (RES) or global slots.
 template <int NC, bool RES>
-__device__ void run_rows(const SwArgs& a, const SwBatch& B, const char* area, float2* win, float2* xb, float2* stp,
-                         int ncol, int lane) {
-  const int32_t* out = reinterpret_cast<const int32_t*>(area);
-  const int32_t* e0 = reinterpret_cast<const int32_t*>(area + B.off_e0);
-  const float2* cf = reinterpret_cast<const float2*>(area + B.off_coef);
-  const int16_t* in16 = reinterpret_cast<const int16_t*>(area + B.off_in);
-  const int32_t* in32 = reinterpret_cast<const int32_t*>(area + B.off_in);
-  const int glog = B.glog, G = 1 << glog, ng = 32 >> glog;
+__device__ void run_rows(const SwArgs& a, const SwDesc& D, const char* bb, const float2* in, float2* win,
+                         float2* xb, float2* stp, int ncol, int lane) {
+  const int32_t* out = reinterpret_cast<const int32_t*>(bb);
+  const int32_t* e0 = reinterpret_cast<const int32_t*>(bb + D.off_e0);
+  const float2* cf = reinterpret_cast<const float2*>(bb + D.off_coef);
+  const int16_t* ix = reinterpret_cast<const int16_t*>(bb + D.off_in);
+  const int glog = D.glog, G = 1 << glog, ng = 32 >> glog;
   const int q = lane >> glog, l = lane & (G - 1);
-  for (int base = 0; base < B.nrows; base += ng) {
+  for (int base = 0; base < D.nrows; base += ng) {
     const int r = base + q;
     float2 acc[NC], acc2[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] = acc2[c] = make_float2(0.f, 0.f);
-    if (r < B.nrows) {
+    if (r < D.nrows) {
       const int ea = e0[r], eb = e0[r + 1];
       int e = ea + l;
       // two independent accumulator chains
       for (; e + G < eb; e += 2 * G) {
         const float2 m0 = cf[e], m1 = cf[e + G];
-        Cv<NC> v0, v1;
-        if constexpr (RES) {
-          v0 = win_load<NC>(win + (int)in16[e] * NC);
-          v1 = win_load<NC>(win + (int)in16[e + G] * NC);
-        } else {
-          v0 = glob_load<NC>(a, in32[e], xb, stp, ncol);
-          v1 = glob_load<NC>(a, in32[e + G], xb, stp, ncol);
-        }
+        const Cv<NC> v0 = sm_load<NC>(in + (int)ix[e] * NC);
+        const Cv<NC> v1 = sm_load<NC>(in + (int)ix[e + G] * NC);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           cmac(acc[c], m0, v0.v[c]);
@@ -178,9 +166,7 @@ __device__ void run_rows(const SwArgs& a, const SwBatch& B, const char* area, fl
       }
       if (e < eb) {
         const float2 m0 = cf[e];
-        Cv<NC> v0;
-        if constexpr (RES) v0 = win_load<NC>(win + (int)in16[e] * NC);
-        else v0 = glob_load<NC>(a, in32[e], xb, stp, ncol);
+        const Cv<NC> v0 = sm_load<NC>(in + (int)ix[e] * NC);
 #pragma unroll
         for (int c = 0; c < NC; ++c) cmac(acc[c], m0, v0.v[c]);
       }
@@ -198,7 +184,7 @@ __device__ void run_rows(const SwArgs& a, const SwBatch& B, const char* area, fl
         acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, d);
       }
     }
-    if (l == 0 && r < B.nrows) {
+    if (l == 0 && r < D.nrows) {
       const int32_t o = out[r];
       const bool add = (o & kSwAcc) != 0;
       const int32_t s = o & ~kSwAcc;
@@ -206,15 +192,19 @@ __device__ void run_rows(const SwArgs& a, const SwBatch& B, const char* area, fl
         float2* d = win + (int64_t)s * NC;
 #pragma unroll
         for (int c = 0; c < NC; ++c) d[c] = add ? make_float2(d[c].x + acc[c].x, d[c].y + acc[c].y) : acc[c];
-      } else if (s < a.n) {
-        float2* d = xb + (int64_t)s * a.R;
+      } else {
+        float2* d = gaddr(a, s, xb, stp, NC);
+        const int nc = s < a.n ? ncol : NC;
 #pragma unroll
         for (int c = 0; c < NC; ++c)
-          if (c < ncol) d[c] = add ? make_float2(d[c].x + acc[c].x, d[c].y + acc[c].y) : acc[c];
-      } else {
-        float2* d = stp + (int64_t)(s - a.n) * NC;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) d[c] = add ? make_float2(d[c].x + acc[c].x, d[c].y + acc[c].y) : acc[c];
+          if (c < nc) {
+            if (add) {
+              const float2 cur = __ldcg(d + c);
+              d[c] = make_float2(cur.x + acc[c].x, cur.y + acc[c].y);
+            } else {
+              d[c] = acc[c];
+            }
+          }
       }
     }
   }
@@ -223,12 +213,11 @@ __device__ void run_rows(const SwArgs& a, const SwBatch& B, const char* area, fl
 // Sweep-leaf phase: window rows a0 .. a0 + s - 1 replaced by T times them (T the
 // packed triangle), all compute threads (t < nct).  Thread (pair j, column
 // group g) owns rows j and s-1-j (s + 1 entries together) and the columns
-// c = g (mod ncg) of them.  The triangle is not read after the first barrier.
+// c = g (mod ncg) of them.  The triangle is not read after the barrier inside.
 template <int NC>
-__device__ void run_tri(const SwBatch& B, const float2* T, float2* win, float2* part, int t, int nct) {
-  const int s = B.nrows;
-  const bool up = (B.flags & SWF_UPPER) != 0;
-  float2* b = win + (int64_t)B.a0 * NC;
+__device__ void run_tri(const SwDesc& D, bool up, const float2* T, float2* win, float2* part, int t, int nct) {
+  const int s = D.nrows;
+  float2* b = win + (int64_t)D.a0 * NC;
   const int npair = s >> 1;
   int ncg = nct / npair;
   const int cap = kSwPartBytes / (s * NC * 8);
@@ -248,7 +237,7 @@ __device__ void run_tri(const SwBatch& B, const float2* T, float2* win, float2* 
         for (int c = g; c < s; c += ncg) {
           if (c >= r) {
             const float2 m = T[((c * (c + 1)) >> 1) + r];
-            const Cv<NC> v = win_load<NC>(b + (int64_t)c * NC);
+            const Cv<NC> v = sm_load<NC>(b + (int64_t)c * NC);
 #pragma unroll
             for (int cc = 0; cc < NC; ++cc) cmac(acc[cc], m, v.v[cc]);
           }
@@ -257,7 +246,7 @@ __device__ void run_tri(const SwBatch& B, const float2* T, float2* win, float2* 
         // row r: columns 0 .. r; entry (r, c) at c s - c (c - 1) / 2 + r - c
         for (int c = g; c <= r; c += ncg) {
           const float2 m = T[c * s - ((c * (c - 1)) >> 1) + r - c];
-          const Cv<NC> v = win_load<NC>(b + (int64_t)c * NC);
+          const Cv<NC> v = sm_load<NC>(b + (int64_t)c * NC);
 #pragma unroll
           for (int cc = 0; cc < NC; ++cc) cmac(acc[cc], m, v.v[cc]);
         }
@@ -285,10 +274,10 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep_cols(SwArgs a) {
   char* ring = smem;
   float2* win = reinterpret_cast<float2*>(smem + kSwRingBytes);
   float2* part = reinterpret_cast<float2*>(smem + kSwRingBytes + kSwWinBytes);
-  __shared__ int s_off[kSwSlots];                 // ring offset of each batch in flight
-  __shared__ int s_bdone[kSwSlots];               // q + 1 once batch q (slot q % kSwSlots) is consumed
+  __shared__ int s_off[kSwSlots];                 // ring offset of each group in flight
+  __shared__ int s_cnt[kSwSlots];                 // compute warps done with the slot's group
   __shared__ __align__(8) uint64_t s_mbar[kSwSlots];
-  __shared__ __align__(16) SwBatch s_brec[32];    // the producer's window of batch records
+  __shared__ __align__(16) SwGroup s_grec[32];    // the producer's window of group records
   __shared__ int s_abort, s_issued;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t lb = a.col0 + (int64_t)blockIdx.x * NC;
@@ -298,7 +287,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep_cols(SwArgs a) {
   if (threadIdx.x == 0) {
     for (int k = 0; k < kSwSlots; ++k) {
       mb_init(&s_mbar[k], 1);
-      s_bdone[k] = 0;
+      s_cnt[k] = 0;
     }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     s_abort = 0;
@@ -306,29 +295,30 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep_cols(SwArgs a) {
   }
   __syncthreads();
   if (warp == kSwWarps) {
-    // ---- producer: every batch of the schedule, in order, into the ring; batches
-    // [oldest, q) are in flight; the ring space is recycled from the oldest batch
-    // not yet consumed (completions come out of order).  Lane 0 keeps the ring
-    // state and issues the copies; the warp loads the batch records 32 at a time.
-    int head = 0, oldest = 0;
-    int64_t q = 0;
-    for (; q < a.nbatch; ++q) {
-      if ((q & 31) == 0) {
+    // ---- producer: every group of the schedule, in order, into the ring; groups
+    // [oldest, g) are in flight; a group's ring area is free once every compute
+    // warp is done with it, and space is recycled from the oldest group.  Lane 0
+    // keeps the ring state and issues the copies; the warp loads the group
+    // records 32 at a time.
+    int head = 0;
+    int64_t oldest = 0, g = 0;
+    for (; g < a.ngroup; ++g) {
+      if ((g & 31) == 0) {
         __syncwarp();
-        if (q + lane < a.nbatch) s_brec[lane] = a.batches[q + lane];
+        if (g + lane < a.ngroup) s_grec[lane] = a.groups[g + lane];
         __syncwarp();
       }
       int off = -1;
       if (lane == 0) {
-        const SwBatch& B = s_brec[q & 31];
-        const int bytes = B.bytes;
+        const SwGroup& G = s_grec[g & 31];
+        const int bytes = G.bytes;
         long long spins = 0;
         for (;;) {
-          while (oldest < q && *(volatile int*)&s_bdone[oldest % kSwSlots] == oldest + 1) ++oldest;
+          while (oldest < g && *(volatile int*)&s_cnt[oldest % kSwSlots] == kSwWarps) ++oldest;
           __threadfence_block();
           if (*(volatile int*)&s_abort) break;
-          if (q - oldest < kSwSlots) {
-            if (oldest == q) {
+          if (g - oldest < kSwSlots) {
+            if (oldest == g) {
               off = 0;
             } else {
               const int tail = s_off[oldest % kSwSlots];
@@ -348,72 +338,101 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep_cols(SwArgs a) {
           __nanosleep(20);
         }
         if (off >= 0) {
-          uint64_t* mb = &s_mbar[q % kSwSlots];
-          s_off[q % kSwSlots] = off;
+          const int slot = (int)(g % kSwSlots);
+          uint64_t* mb = &s_mbar[slot];
+          s_off[slot] = off;
+          s_cnt[slot] = 0;   // published with the arrive (release) below
           asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
           mb_arrive_tx(mb, (unsigned)bytes);
-          bulk_copy(ring + off, a.image + B.img, (unsigned)bytes, mb);
+          bulk_copy(ring + off, a.image + G.img, (unsigned)bytes, mb);
           head = off + bytes;
         }
       }
       off = __shfl_sync(0xffffffffu, off, 0);
       if (off < 0) break;
     }
-    if (lane == 0) s_issued = (int)q;
+    if (lane == 0) s_issued = (int)g;
     __syncwarp();
   } else {
     const int t = threadIdx.x, nct = kSwWarps * 32;
-    bool bad = false;   // uniform among the compute warps after each step
-    for (int si = 0; si < a.nstep && !bad; ++si) {
-      const SwStep S = a.steps[si];
-      if (S.kind == SW_BEGIN) {
-        const int nrow = S.a1 - S.a0;
-        for (int e = t; e < nrow * NC; e += nct) {
-          const int r = e / NC, c = e % NC;
-          win[e] = c < ncol ? __ldcg(xb + (int64_t)(S.a0 + r) * a.R + c) : make_float2(0.f, 0.f);
-        }
-      } else if (S.kind == SW_END) {
-        const int nrow = S.a1 - S.a0;
-        for (int e = t; e < nrow * NC; e += nct) {
-          const int r = e / NC, c = e % NC;
-          if (c < ncol) xb[(int64_t)(S.a0 + r) * a.R + c] = win[e];
-        }
-      } else if (S.flags & SWF_TRI) {
-        const int64_t q = S.a0;
+    float2* slice = win + (int64_t)warp * kSwGather * NC;   // gather area of global batches
+    bool bad = false;   // warp-uniform; after a failed wait the warp only follows the barriers
+    for (int64_t g = 0; g < a.ngroup; ++g) {
+      const int slot = (int)(g % kSwSlots);
+      if (!bad) {
         long long spins = 0;
         bool ok = true;
-        while (!mb_test_wait(&s_mbar[q % kSwSlots], (unsigned)(q / kSwSlots) & 1u)) {
+        while (!mb_test_wait(&s_mbar[slot], (unsigned)(g / kSwSlots) & 1u)) {
           if (++spins > a.spin_limit || *(volatile int*)&s_abort) { ok = false; break; }
         }
-        if (cw_red_or(!ok)) { bad = true; break; }
-        const SwBatch B = a.batches[q];
-        run_tri<NC>(B, reinterpret_cast<const float2*>(ring + s_off[q % kSwSlots]), win, part, t, nct);
-        if (t == 0) {
-          __threadfence_block();
-          *(volatile int*)&s_bdone[q % kSwSlots] = (int)q + 1;   // the triangle was read before run_tri's barrier
+        if (__any_sync(0xffffffffu, !ok)) {
+          bad = true;
+          if (lane == 0) atomicExch(&s_abort, 1);
         }
-      } else {
-        const bool res = (S.flags & SWF_RES) != 0;
-        for (int64_t q = S.a0 + warp; q < (int64_t)S.a0 + S.a1; q += kSwWarps) {
-          const SwBatch B = a.batches[q];
-          long long spins = 0;
-          bool ok = true;
-          while (!mb_test_wait(&s_mbar[q % kSwSlots], (unsigned)(q / kSwSlots) & 1u)) {
-            if (++spins > a.spin_limit || *(volatile int*)&s_abort) { ok = false; break; }
+      }
+      // the header: from the ring, or (after a failed wait) from the image in global memory
+      const char* gimg = bad ? reinterpret_cast<const char*>(a.image + a.groups[g].img) : ring + s_off[slot];
+      const SwGroupHdr H = *reinterpret_cast<const SwGroupHdr*>(gimg);
+      const SwDesc* desc = reinterpret_cast<const SwDesc*>(gimg + 32);
+      if (H.flags & SWG_BEGIN) {
+        if (!bad) {
+          const int nrow = H.beg_hi - H.beg_lo;
+          for (int e = t; e < nrow * NC; e += nct) {
+            const int r = e / NC, c = e % NC;
+            win[e] = c < ncol ? __ldcg(xb + (int64_t)(H.beg_lo + r) * a.R + c) : make_float2(0.f, 0.f);
           }
-          if (__any_sync(0xffffffffu, !ok)) { bad = true; break; }
-          const char* area = ring + s_off[q % kSwSlots];
-          if (res) run_rows<NC, true>(a, B, area, win, xb, stp, ncol, lane);
-          else run_rows<NC, false>(a, B, area, win, xb, stp, ncol, lane);
-          __syncwarp();
-          if (lane == 0) {
-            __threadfence_block();
-            *(volatile int*)&s_bdone[q % kSwSlots] = (int)q + 1;   // releases the batch's ring area
+        }
+        cw_sync();
+      }
+      if (H.flags & SWG_TRI) {
+        if (!bad) {
+          const SwDesc D = desc[0];
+          run_tri<NC>(D, (H.flags & SWG_UPPER) != 0, reinterpret_cast<const float2*>(gimg + D.off), win, part, t, nct);
+        } else {
+          cw_sync();   // the barrier inside run_tri
+        }
+      } else if (!bad) {
+        const bool res = (H.flags & SWG_RES) != 0;
+        for (int b = warp; b < H.nb; b += kSwWarps) {
+          const SwDesc D = desc[b];
+          const char* bb = gimg + D.off;
+          if (res) {
+            run_rows<NC, true>(a, D, bb, win, win, xb, stp, ncol, lane);
+          } else {
+            // gather the batch's distinct inputs into the warp's slice, one round trip
+            const int32_t* gl = reinterpret_cast<const int32_t*>(bb + D.off_gl);
+            for (int k = lane; k < D.ngl; k += 32) {
+              const int32_t s = gl[k];
+              const float2* src = gaddr(a, s, xb, stp, NC);
+              const int nc = s < a.n ? ncol : NC;
+#pragma unroll
+              for (int c = 0; c < NC; ++c) slice[k * NC + c] = c < nc ? __ldcg(src + c) : make_float2(0.f, 0.f);
+            }
+            __syncwarp();
+            run_rows<NC, false>(a, D, bb, slice, win, xb, stp, ncol, lane);
+            __syncwarp();
           }
         }
       }
-      // end of the step: every compute warp's writes are visible to the next step
-      if (cw_red_or(bad)) bad = true;
+      if (!bad) {
+        __syncwarp();
+        if (lane == 0) {
+          __threadfence_block();
+          atomicAdd(&s_cnt[slot], 1);   // this warp no longer reads the group's ring area
+        }
+      }
+      if (H.flags & SWG_END) {
+        // end of the phase: every compute warp's writes are visible to the next phase
+        if (cw_red_or(bad)) { bad = true; break; }
+      }
+      if (H.flags & SWG_ENDRUN) {
+        const int nrow = H.end_hi - H.end_lo;
+        for (int e = t; e < nrow * NC; e += nct) {
+          const int r = e / NC, c = e % NC;
+          if (c < ncol) xb[(int64_t)(H.end_lo + r) * a.R + c] = win[e];
+        }
+        cw_sync();
+      }
     }
     if (bad && t == 0) {
       atomicExch(&s_abort, 1);
@@ -425,7 +444,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep_cols(SwArgs a) {
     // give the copies still in flight a second bounded wait before leaving
     const int iss = s_issued;
     for (int q = 0; q < iss; ++q) {
-      if (s_bdone[q % kSwSlots] == q + 1 || q + kSwSlots < iss) continue;
+      if (q + kSwSlots < iss) continue;
       long long spins = 0;
       while (!mb_try_wait(&s_mbar[q % kSwSlots], (unsigned)(q / kSwSlots) & 1u) &&
              ++spins < drain_limit(a.spin_limit)) {
@@ -450,10 +469,8 @@ int launch_nc(const DevFactor& df, const DevSched& sc, float2* vec, int64_t R, i
     attr_done = true;
   }
   SwArgs a;
-  a.steps = sc.steps;
-  a.nstep = sc.nstep;
-  a.batches = sc.batches;
-  a.nbatch = sc.nbatch;
+  a.groups = sc.groups;
+  a.ngroup = sc.ngroup;
   a.image = sc.image;
   a.x = vec;
   a.R = R;

@@ -137,57 +137,108 @@ void put_coef(uint8_t* dst, cplx v) {
   std::memcpy(dst, p, sizeof(p));
 }
 
+// A batch before layout: rows of one phase (indices into PhaseRows), or a triangle.
+struct PBatch {
+  std::vector<int32_t> rows;
+  std::vector<int32_t> gl;   // global batches: distinct input slots
+  int glog = 0;
+  bool tri = false;
+  int64_t tri_off = 0, tri_n = 0;   // triangle: offset in the sweep-leaf array, order
+  int32_t a0 = 0;
+};
+
 struct Builder {
   const PackedHost& ph;
   SwSched& S;
-  int cb;
-  Builder(const PackedHost& p, SwSched& s, int coef_bytes) : ph(p), S(s), cb(coef_bytes) {}
+  int cb, which;
+  Builder(const PackedHost& p, SwSched& s, int coef_bytes, int w) : ph(p), S(s), cb(coef_bytes), which(w) {}
 
-  int64_t alloc(int64_t bytes) {
-    const int64_t at = (int64_t)S.image.size();
-    S.image.resize((size_t)(at + al16(bytes)), 0);
-    return at;
-  }
   void coef_at(uint8_t* dst, cplx v) {
     if (cb == 8) put_coef<float>(dst, v);
     else put_coef<double>(dst, v);
   }
-
-  // one batch: rows rows[r0 .. r1) of P, in that order
-  void emit_batch(const PhaseRows& P, const std::vector<int32_t>& rows, size_t r0, size_t r1, int glog, bool res) {
-    SwBatch B{};
-    B.nrows = (int32_t)(r1 - r0);
+  int64_t batch_bytes(const PhaseRows& P, const PBatch& B, bool res) const {
+    if (B.tri) return al16(packed_tri(B.tri_n) * cb);
     int64_t ne = 0;
-    for (size_t q = r0; q < r1; ++q) ne += P.len(rows[q]);
-    if (ne > INT32_MAX / 16) { S.ok = false; S.why = "batch too large"; return; }
-    B.nent = (int32_t)ne;
-    B.glog = (int16_t)glog;
-    B.flags = (int16_t)(res ? SWF_RES : 0);
-    B.off_e0 = (int32_t)al16(4 * (int64_t)B.nrows);
-    B.off_coef = B.off_e0 + (int32_t)al16(4 * ((int64_t)B.nrows + 1));
-    B.off_in = B.off_coef + (int32_t)al16((int64_t)cb * ne);
-    const int64_t bytes = B.off_in + al16((res ? 2 : 4) * ne);
-    B.bytes = (int32_t)bytes;
-    B.img = alloc(bytes);
-    uint8_t* base = S.image.data() + B.img;
-    int32_t* out = (int32_t*)base;
-    int32_t* e0 = (int32_t*)(base + B.off_e0);
-    uint8_t* coef = base + B.off_coef;
-    int32_t e = 0;
-    for (size_t q = r0; q < r1; ++q) {
-      const int32_t r = rows[q];
-      out[q - r0] = P.out[r];
-      e0[q - r0] = e;
-      const int32_t s0 = P.start[r], n = P.len(r);
-      for (int32_t t = 0; t < n; ++t, ++e) {
-        coef_at(coef + (int64_t)e * cb, P.coef[s0 + t]);
-        if (res) ((int16_t*)(base + B.off_in))[e] = (int16_t)P.slot[s0 + t];
-        else ((int32_t*)(base + B.off_in))[e] = P.slot[s0 + t];
+    for (int32_t r : B.rows) ne += P.len(r);
+    const int64_t nr = (int64_t)B.rows.size();
+    return al16(4 * nr) + al16(4 * (nr + 1)) + al16(cb * ne) + al16(2 * ne) + (res ? 0 : al16(4 * (int64_t)B.gl.size()));
+  }
+
+  // lay out one group: header, descriptors, the batches' data
+  void emit_group(const PhaseRows& P, const std::vector<PBatch>& bs, size_t b0, size_t b1, int32_t flags,
+                  int32_t beg_lo, int32_t beg_hi, int32_t end_lo, int32_t end_hi) {
+    const bool res = (flags & SWG_RES) != 0;
+    const int64_t nb = (int64_t)(b1 - b0);
+    int64_t off = al16(32 + 40 * nb), bytes = off;
+    for (size_t q = b0; q < b1; ++q) bytes += batch_bytes(P, bs[q], res);
+    if (bytes > INT32_MAX / 2) { S.ok = false; S.why = "group too large"; return; }
+    SwGroup G{(int64_t)S.image.size(), (int32_t)bytes, 0};
+    S.image.resize((size_t)(G.img + bytes), 0);
+    uint8_t* base = S.image.data() + G.img;
+    SwGroupHdr H{(int32_t)nb, flags, beg_lo, beg_hi, end_lo, end_hi, 0, 0};
+    std::memcpy(base, &H, sizeof(H));
+    for (size_t q = b0; q < b1; ++q) {
+      const PBatch& B = bs[q];
+      SwDesc D{};
+      D.off = (int32_t)off;
+      D.glog = (int16_t)B.glog;
+      uint8_t* d = base + off;
+      if (B.tri) {
+        D.nrows = (int32_t)B.tri_n;
+        D.nent = (int32_t)packed_tri(B.tri_n);
+        D.a0 = B.a0;
+        const cplx* T = ph.sl[which].data() + B.tri_off;
+        for (int64_t e = 0; e < D.nent; ++e) coef_at(d + e * cb, T[e]);
+      } else {
+        int64_t ne = 0;
+        for (int32_t r : B.rows) ne += P.len(r);
+        const int64_t nr = (int64_t)B.rows.size();
+        D.nrows = (int32_t)nr;
+        D.nent = (int32_t)ne;
+        D.ngl = (int32_t)B.gl.size();
+        D.off_e0 = (int32_t)al16(4 * nr);
+        D.off_coef = D.off_e0 + (int32_t)al16(4 * (nr + 1));
+        D.off_in = D.off_coef + (int32_t)al16(cb * ne);
+        D.off_gl = D.off_in + (int32_t)al16(2 * ne);
+        int32_t* out = (int32_t*)d;
+        int32_t* e0 = (int32_t*)(d + D.off_e0);
+        int16_t* in = (int16_t*)(d + D.off_in);
+        int32_t* gl = (int32_t*)(d + D.off_gl);
+        // global batches: input slot -> position in the gather list
+        std::vector<std::pair<int32_t, int32_t>> pos;
+        if (!res) {
+          for (size_t k = 0; k < B.gl.size(); ++k) {
+            gl[k] = B.gl[k];
+            pos.emplace_back(B.gl[k], (int32_t)k);
+          }
+          std::sort(pos.begin(), pos.end());
+        }
+        int32_t e = 0;
+        for (int64_t q2 = 0; q2 < nr; ++q2) {
+          const int32_t r = B.rows[q2];
+          out[q2] = P.out[r];
+          e0[q2] = e;
+          const int32_t s0 = P.start[r], n = P.len(r);
+          for (int32_t t = 0; t < n; ++t, ++e) {
+            coef_at(d + D.off_coef + (int64_t)e * cb, P.coef[s0 + t]);
+            const int32_t sl = P.slot[s0 + t];
+            if (res) {
+              in[e] = (int16_t)sl;
+            } else {
+              auto it = std::lower_bound(pos.begin(), pos.end(), std::make_pair(sl, INT32_MIN));
+              in[e] = (int16_t)it->second;
+            }
+          }
+        }
+        e0[nr] = e;
       }
+      std::memcpy(base + 32 + 40 * (q - b0), &D, sizeof(D));
+      off += batch_bytes(P, B, res);
+      S.batches++;
     }
-    e0[B.nrows] = e;
-    S.max_bytes = std::max(S.max_bytes, B.bytes);
-    S.batches.push_back(B);
+    S.max_bytes = std::max<int64_t>(S.max_bytes, bytes);
+    S.groups.push_back(G);
   }
 
   // lanes per row: about eight entries per lane
@@ -198,70 +249,95 @@ struct Builder {
     return g;
   }
 
-  void emit_phase(const PhaseRows& P, bool res) {
+  // batches -> groups of at most kSwGroupBytes (a group holds at least one batch)
+  void emit_groups(const PhaseRows& P, const std::vector<PBatch>& bs, int32_t flags, bool begin, int32_t beg_lo,
+                   int32_t beg_hi, bool endrun, int32_t end_lo, int32_t end_hi) {
+    const bool res = (flags & SWG_RES) != 0;
+    size_t g0 = 0;
+    int64_t acc = 0;
+    for (size_t q = 0; q <= bs.size(); ++q) {
+      const int64_t add = q < bs.size() ? 40 + batch_bytes(P, bs[q], res) : 0;
+      const bool last = q == bs.size();
+      if (last || (acc + add > kSwGroupBytes && q > g0)) {
+        int32_t fl = flags;
+        if (g0 == 0 && begin) fl |= SWG_BEGIN;
+        if (last) fl |= SWG_END | (endrun ? SWG_ENDRUN : 0);
+        emit_group(P, bs, g0, q, fl, begin ? beg_lo : 0, begin ? beg_hi : 0, endrun ? end_lo : 0,
+                   endrun ? end_hi : 0);
+        if (!S.ok) return;
+        g0 = q;
+        acc = 0;
+      }
+      acc += add;
+    }
+  }
+
+  void phase_batches(const PhaseRows& P, bool res, std::vector<PBatch>& bs) {
+    bs.clear();
     const int32_t nrows = P.nrows();
     const int glog = pick_glog(P);
     const int per_round = 32 >> glog;
-    const int32_t b0 = (int32_t)S.batches.size();
-    const int64_t rowb = (int64_t)cb + (res ? 2 : 4);
-    int64_t tot = 16 * (int64_t)nrows;
-    for (int32_t r = 0; r < nrows; ++r) tot += rowb * P.len(r);
     std::vector<int32_t> order(nrows);
     for (int32_t r = 0; r < nrows; ++r) order[r] = r;
     if (res) {
-      // small dependent phase: at most one batch per compute warp (more if the
-      // images would be too large), rows by decreasing length dealt round-robin
+      // a dependent phase: about one batch per compute warp (more if the data would
+      // be too large), rows by decreasing length dealt round-robin
+      int64_t tot = 0;
+      for (int32_t r = 0; r < nrows; ++r) tot += 8 + (int64_t)(cb + 2) * P.len(r);
       int64_t nb = std::min<int64_t>(kSwWarps, (nrows + per_round - 1) / per_round);
       nb = std::max<int64_t>(nb, (tot + kSwBatchBytes - 1) / kSwBatchBytes);
       nb = std::max<int64_t>(1, std::min<int64_t>(nb, nrows));
       std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return P.len(a) > P.len(b); });
-      std::vector<int32_t> dealt;
-      dealt.reserve(nrows);
-      std::vector<size_t> cut(nb + 1, 0);
+      bs.resize(nb);
       for (int64_t q = 0; q < nb; ++q) {
-        cut[q] = dealt.size();
-        for (int64_t i = q; i < nrows; i += nb) dealt.push_back(order[i]);
+        bs[q].glog = glog;
+        for (int64_t i2 = q; i2 < nrows; i2 += nb) bs[q].rows.push_back(order[i2]);
       }
-      cut[nb] = dealt.size();
-      for (int64_t q = 0; q < nb; ++q) emit_batch(P, dealt, cut[q], cut[q + 1], glog, true);
-    } else {
-      // wide phase: consecutive rows (inputs shared by an op's rows stay together),
-      // batches of about kSwBatchBytes, the rows of a batch by decreasing length
-      size_t r0 = 0;
-      int64_t acc = 0;
-      for (size_t r = 0; r <= (size_t)nrows; ++r) {
-        const int64_t add = r < (size_t)nrows ? 16 + rowb * P.len((int32_t)r) : 0;
-        if (r == (size_t)nrows || (acc + add > kSwBatchBytes && r > r0)) {
-          if (r > r0) {
-            std::stable_sort(order.begin() + r0, order.begin() + r,
-                             [&](int32_t a, int32_t b) { return P.len(a) > P.len(b); });
-            emit_batch(P, order, r0, r, glog, false);
-          }
-          r0 = r;
-          acc = 0;
-        }
-        acc += add;
-      }
+      return;
     }
-    S.steps.push_back(SwStep{SW_PHASE, b0, (int32_t)S.batches.size() - b0, res ? SWF_RES : 0});
-  }
-
-  void emit_tri(const FlatOp& f, int which, int32_t a0) {
-    const int64_t s = f.c0;
-    SwBatch B{};
-    B.nrows = (int32_t)s;
-    B.flags = (int16_t)(SWF_TRI | SWF_RES | ((f.flags & FF_UPPER) ? SWF_UPPER : 0));
-    B.a0 = a0;
-    const int64_t ne = packed_tri(s);
-    B.nent = (int32_t)ne;
-    B.bytes = (int32_t)al16(ne * cb);
-    B.img = alloc(B.bytes);
-    uint8_t* base = S.image.data() + B.img;
-    const cplx* T = ph.sl[which].data() + f.moff;
-    for (int64_t e = 0; e < ne; ++e) coef_at(base + e * cb, T[e]);
-    S.max_bytes = std::max(S.max_bytes, B.bytes);
-    S.steps.push_back(SwStep{SW_PHASE, (int32_t)S.batches.size(), 1, SWF_TRI | SWF_RES});
-    S.batches.push_back(B);
+    // wide phase: consecutive rows (an op's rows share inputs), batches of about
+    // kSwGlobBytes of data with at most kSwGather distinct inputs
+    PBatch cur;
+    cur.glog = glog;
+    std::vector<int32_t> seen;   // sorted distinct inputs of cur
+    int64_t acc = 0;
+    std::vector<int32_t> fresh;
+    for (int32_t r = 0; r < nrows; ++r) {
+      fresh.clear();
+      const int32_t s0 = P.start[r], n = P.len(r);
+      for (int32_t t = 0; t < n; ++t) {
+        const int32_t sl = P.slot[s0 + t];
+        if (!std::binary_search(seen.begin(), seen.end(), sl) &&
+            std::find(fresh.begin(), fresh.end(), sl) == fresh.end())
+          fresh.push_back(sl);
+      }
+      const int64_t add = 8 + (int64_t)(cb + 2) * n + 4 * (int64_t)fresh.size();
+      if (!cur.rows.empty() &&
+          (acc + add > kSwGlobBytes || seen.size() + fresh.size() > (size_t)kSwGather)) {
+        cur.gl = seen;
+        bs.push_back(std::move(cur));
+        cur = PBatch();
+        cur.glog = glog;
+        seen.clear();
+        acc = 0;
+        fresh.clear();
+        for (int32_t t = 0; t < n; ++t) {
+          const int32_t sl = P.slot[s0 + t];
+          if (std::find(fresh.begin(), fresh.end(), sl) == fresh.end()) fresh.push_back(sl);
+        }
+      }
+      if (fresh.size() > (size_t)kSwGather) { S.ok = false; S.why = "a row has too many inputs"; return; }
+      cur.rows.push_back(r);
+      for (int32_t sl : fresh) seen.insert(std::lower_bound(seen.begin(), seen.end(), sl), sl);
+      acc += 8 + (int64_t)(cb + 2) * n + 4 * (int64_t)fresh.size();
+    }
+    if (!cur.rows.empty()) {
+      cur.gl = seen;
+      bs.push_back(std::move(cur));
+    }
+    // rows of a batch by decreasing length (the lanes' rounds stay balanced)
+    for (PBatch& B : bs)
+      std::stable_sort(B.rows.begin(), B.rows.end(), [&](int32_t a, int32_t b) { return P.len(a) > P.len(b); });
   }
 };
 
@@ -277,8 +353,9 @@ void build_sweep_sched(const PackedHost& ph, int which, int coef_bytes, int win_
   const FlatProgram fp = flatten_program(ph, prog, which);
   if (!fp.ok) { S.ok = false; S.why = "flattened program"; return; }
   const std::vector<DSeg> segs = segment_program(prog, fp, 1 << 30, S.win_slots);
-  Builder bd(ph, S, coef_bytes);
+  Builder bd(ph, S, coef_bytes, which);
   PhaseRows P;
+  std::vector<PBatch> bs;
   for (const DSeg& sg : segs) {
     const int64_t rows = sg.row_hi - sg.row_lo, nst = sg.st_hi - sg.st_lo;
     const bool res = !sg.grid && !sg.st_cross && rows + nst <= S.win_slots && rows > 0;
@@ -286,36 +363,46 @@ void build_sweep_sched(const PackedHost& ph, int which, int coef_bytes, int win_
     sm.n = ph.n;
     sm.res = res;
     sm.row_lo = sg.row_lo; sm.row_hi = sg.row_hi; sm.st_lo = sg.st_lo; sm.st_hi = sg.st_hi;
-    if (res) {
-      S.steps.push_back(SwStep{SW_BEGIN, sg.row_lo, sg.row_hi, 0});
-      S.runs++;
-    }
-    for (int p = sg.first; p < sg.first + sg.count; ++p) {
+    if (res) S.runs++;
+    // phases of the segment that hold ops
+    std::vector<int> phs;
+    for (int p = sg.first; p < sg.first + sg.count; ++p)
+      if (fp.base[p + 1] > fp.base[p]) phs.push_back(p);
+    for (size_t k = 0; k < phs.size(); ++k) {
+      const int p = phs[k];
       const int32_t o0 = fp.base[p], o1 = fp.base[p + 1];
-      if (o1 <= o0) continue;
+      const bool first = k == 0, last = k + 1 == phs.size();
+      P.clear();
+      int32_t flags = res ? SWG_RES : 0;
       if (fp.ops[o0].kind == FK_LEAF) {
         // a sweep leaf always lies inside a resident run (its rows alone fit the window)
-        if (!res) { S.ok = false; S.why = "sweep leaf outside a resident run"; return; }
-        for (int32_t o = o0; o < o1; ++o) bd.emit_tri(fp.ops[o], which, sm.vec(fp.ops[o].src0));
+        if (!res || o1 - o0 != 1) { S.ok = false; S.why = "sweep leaf outside a resident run"; return; }
+        const FlatOp& f = fp.ops[o0];
+        bs.assign(1, PBatch());
+        bs[0].tri = true;
+        bs[0].tri_off = f.moff;
+        bs[0].tri_n = f.c0;
+        bs[0].a0 = sm.vec(f.src0);
+        flags |= SWG_TRI | ((f.flags & FF_UPPER) ? SWG_UPPER : 0);
       } else {
-        P.clear();
         for (int32_t o = o0; o < o1; ++o) expand_op(ph, fp.ops[o], sm, P);
-        bd.emit_phase(P, res);
+        bd.phase_batches(P, res, bs);
       }
-      if (res) S.res_phases++;
-      else S.glob_phases++;
       if (sm.bad) { S.ok = false; S.why = "slot outside the run's window"; return; }
       if (!S.ok) return;
+      bd.emit_groups(P, bs, flags, res && first, sg.row_lo, sg.row_hi, res && last, sg.row_lo, sg.row_hi);
+      if (!S.ok) return;
+      if (res) S.res_phases++;
+      else S.glob_phases++;
     }
-    if (res) S.steps.push_back(SwStep{SW_END, sg.row_lo, sg.row_hi, 0});
   }
   // (the device stages complex-FP32 images; FP64 images serve host checks only)
-  if (coef_bytes == 8 && S.max_bytes > kSwRingBytes) { S.ok = false; S.why = "batch image larger than the staging ring"; }
+  if (coef_bytes == 8 && S.max_bytes > kSwRingBytes) { S.ok = false; S.why = "group image larger than the staging ring"; }
 }
 
 void host_sweep_sched(const PackedHost& ph, const SwSched& S, cplx* vec) {
   const int64_t n = ph.n;
-  std::vector<cplx> st((size_t)ph.state_len, cplx(0.0, 0.0)), win(kSwWinSlots), tmp;
+  std::vector<cplx> st((size_t)ph.state_len, cplx(0.0, 0.0)), win(kSwWinSlots), tmp, gv;
   auto coef = [&](const uint8_t* p, int64_t e) -> cplx {
     if (S.coef_bytes == 8) {
       float v[2];
@@ -326,55 +413,57 @@ void host_sweep_sched(const PackedHost& ph, const SwSched& S, cplx* vec) {
     std::memcpy(v, p + e * 16, 16);
     return cplx(v[0], v[1]);
   };
+  auto gslot = [&](int32_t sl) -> cplx& { return sl < n ? vec[sl] : st[sl - n]; };
+  // a phase's outputs are stored at its end (its groups never read them)
   struct Out { bool res; int32_t o; cplx v; };
   std::vector<Out> outs;
-  for (const SwStep& s : S.steps) {
-    if (s.kind == SW_BEGIN) {
-      for (int32_t r = s.a0; r < s.a1; ++r) win[r - s.a0] = vec[r];
-      continue;
-    }
-    if (s.kind == SW_END) {
-      for (int32_t r = s.a0; r < s.a1; ++r) vec[r] = win[r - s.a0];
-      continue;
-    }
-    // outputs of a phase never feed the same phase: compute every batch from the
-    // values before the phase, then store (as the kernel's phase barrier implies)
-    outs.clear();
-    for (int32_t b = s.a0; b < s.a0 + s.a1; ++b) {
-      const SwBatch& B = S.batches[b];
-      const uint8_t* base = S.image.data() + B.img;
-      if (B.flags & SWF_TRI) {
-        const int64_t sz = B.nrows;
+  for (const SwGroup& G : S.groups) {
+    const uint8_t* gb = S.image.data() + G.img;
+    SwGroupHdr H;
+    std::memcpy(&H, gb, sizeof(H));
+    if (H.flags & SWG_BEGIN)
+      for (int32_t r = H.beg_lo; r < H.beg_hi; ++r) win[r - H.beg_lo] = vec[r];
+    const bool res = (H.flags & SWG_RES) != 0;
+    for (int32_t b = 0; b < H.nb; ++b) {
+      SwDesc D;
+      std::memcpy(&D, gb + 32 + 40 * b, sizeof(D));
+      const uint8_t* base = gb + D.off;
+      if (H.flags & SWG_TRI) {
+        const int64_t sz = D.nrows;
         tmp.assign((size_t)sz, cplx(0.0, 0.0));
-        const bool up = (B.flags & SWF_UPPER) != 0;
+        const bool up = (H.flags & SWG_UPPER) != 0;
         for (int64_t c = 0; c < sz; ++c)
           for (int64_t r = up ? 0 : c; r < (up ? c + 1 : sz); ++r) {
             const int64_t off = up ? tri_off_upper(r, c) : tri_off_lower(sz, r, c);
-            tmp[r] += coef(base, off) * win[B.a0 + c];
+            tmp[r] += coef(base, off) * win[D.a0 + c];
           }
-        for (int64_t r = 0; r < sz; ++r) win[B.a0 + r] = tmp[r];
+        for (int64_t r = 0; r < sz; ++r) win[D.a0 + r] = tmp[r];
         continue;
       }
       const int32_t* out = (const int32_t*)base;
-      const int32_t* e0 = (const int32_t*)(base + B.off_e0);
-      const uint8_t* cf = base + B.off_coef;
-      const bool res = (B.flags & SWF_RES) != 0;
-      auto in_val = [&](int64_t e) -> cplx {
-        if (res) return win[((const int16_t*)(base + B.off_in))[e]];
-        const int32_t sl = ((const int32_t*)(base + B.off_in))[e];
-        return sl < n ? vec[sl] : st[sl - n];
-      };
-      for (int32_t r = 0; r < B.nrows; ++r) {
+      const int32_t* e0 = (const int32_t*)(base + D.off_e0);
+      const int16_t* in = (const int16_t*)(base + D.off_in);
+      const int32_t* gl = (const int32_t*)(base + D.off_gl);
+      if (!res) {   // gather the batch's distinct inputs
+        gv.resize((size_t)D.ngl);
+        for (int32_t k = 0; k < D.ngl; ++k) gv[k] = gslot(gl[k]);
+      }
+      for (int32_t r = 0; r < D.nrows; ++r) {
         cplx acc(0.0, 0.0);
-        for (int32_t e = e0[r]; e < e0[r + 1]; ++e) acc += coef(cf, e) * in_val(e);
+        for (int32_t e = e0[r]; e < e0[r + 1]; ++e) acc += coef(base + D.off_coef, e) * (res ? win[in[e]] : gv[in[e]]);
         outs.push_back(Out{res, out[r], acc});
       }
     }
-    for (const Out& ov : outs) {
-      const bool acc = (ov.o & kSwAcc) != 0;
-      const int32_t sl = ov.o & ~kSwAcc;
-      cplx* d = ov.res ? &win[sl] : (sl < n ? &vec[sl] : &st[sl - n]);
-      *d = acc ? *d + ov.v : ov.v;
+    if (H.flags & SWG_END) {
+      for (const Out& ov : outs) {
+        const bool add = (ov.o & kSwAcc) != 0;
+        const int32_t sl = ov.o & ~kSwAcc;
+        cplx* d = ov.res ? &win[sl] : &gslot(sl);
+        *d = add ? *d + ov.v : ov.v;
+      }
+      outs.clear();
+      if (H.flags & SWG_ENDRUN)
+        for (int32_t r = H.end_lo; r < H.end_hi; ++r) vec[r] = win[r - H.end_lo];
     }
   }
 }
