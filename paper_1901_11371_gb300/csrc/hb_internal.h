@@ -447,10 +447,12 @@ void host_apply_plan(const PackedHost& ph, const ApplyPlan& plan, int fes, bool 
 // identity entries, the T or S entries, conjugated and negated as the op
 // requires); sweep-leaf phases are the packed triangles of the exact subtree
 // inverse, applied in place.  The schedule is a sequence of staging groups,
-// one bulk copy each: a header, the batch descriptors, the batches' data.
-// A resident phase is one group (compute warp w takes its batches w, w + 16,
-// ...); a global phase is cut into groups of at most 16 batches; a triangle
-// is one group taken by all compute warps.
+// one bulk copy each: a header, a phase table, the batch descriptors, the
+// batches' data.  A group holds several consecutive small phases of a resident
+// run (a barrier among the compute warps after each), or one part of a large
+// phase (the phase's last part ends with the barrier); a triangle is a group of
+// its own, taken by all compute warps.  Compute warp w takes the batches w,
+// w + 16, ... of a phase part.
 // ---------------------------------------------------------------------------
 constexpr int kSwWarps = 16;                 // compute warps (one more warp stages the groups)
 constexpr int kSwWinBytes = 96 * 1024;       // resident window: rows + state of a run
@@ -459,36 +461,43 @@ constexpr int kSwPartBytes = 16 * 1024;      // partial sums of a triangle produ
 constexpr int kSwMaxCols = 2;                // right-hand sides per CTA
 constexpr int kSwWinSlots = kSwWinBytes / (kSwMaxCols * 8);   // window slots (complex-FP32 entries per column)
 constexpr int kSwGather = kSwWinSlots / kSwWarps;             // gathered inputs of a global batch (a warp's slice)
-constexpr int kSwBatchBytes = 12 * 1024;     // target data bytes of one resident batch
+constexpr int kSwBatchBytes = 6 * 1024;      // target data bytes of one resident batch
 constexpr int kSwGlobBytes = 3 * 1024;       // target data bytes of one global batch
-constexpr int kSwGroupBytes = 48 * 1024;     // target bytes of a global phase's group
+constexpr int kSwGroupBytes = 32 * 1024;     // target bytes of a group
+constexpr int kSwMaxPhases = 64;             // phases of one group
 constexpr int32_t kSwAcc = (int32_t)0x80000000;  // output slot flag: add to the output instead of overwriting
 enum SwGroupFlag : int32_t {
-  SWG_END = 1,      // the phase ends with this group: barrier among the compute warps
-  SWG_TRI = 2,      // one triangle batch, taken by all compute warps
-  SWG_RES = 4,      // batches on the window (int16 window slots)
-  SWG_BEGIN = 8,    // load window rows [beg_lo, beg_hi) before the batches
-  SWG_ENDRUN = 16,  // write window rows [end_lo, end_hi) back after the barrier
-  SWG_UPPER = 32    // triangle: upper
+  SWG_RES = 4,      // group: batches on the window (int16 window slots)
+  SWG_BEGIN = 8,    // group: load window rows [beg_lo, beg_hi) first
+  SWG_ENDRUN = 16,  // group: write window rows [end_lo, end_hi) back after its last phase
+};
+enum SwPhaseFlag : int32_t {
+  SWP_END = 1,      // the phase ends with this part: barrier among the compute warps
+  SWP_TRI = 2,      // one triangle batch, taken by all compute warps
+  SWP_UPPER = 4     // triangle: upper
 };
 struct SwGroup {     // one bulk copy
   int64_t img;       // byte offset of the group image
   int32_t bytes;     // multiple of 16
   int32_t pad;
 };
-struct SwGroupHdr {  // first 32 bytes of a group image
-  int32_t nb, flags;
+struct SwGroupHdr {  // first 32 bytes of a group image; then nph phase entries (8 bytes)
+  int32_t nph, flags;
   int32_t beg_lo, beg_hi, end_lo, end_hi;
-  int32_t pad0, pad1;
+  int32_t off_desc;  // byte offset of the descriptors (all phases' batches in order)
+  int32_t pad;
 };
-// Batch descriptor (after the header, nb of them); offsets relative to the batch
-// start.  Row form: out[nrows] (int32 slot | kSwAcc; window slot for resident
-// batches, else a global slot: a vector row r < n or n + a state entry),
-// e0[nrows + 1], coef[nent] (complex, the factor's precision), in[nent] (int16:
-// window slot, or position in the gather list), gl[ngl] (int32 global slots of
-// the distinct inputs, global batches only).  Triangle: the packed triangle of
-// order nrows, column by column (lower: rows c..s-1 of column c; upper: rows
-// 0..c), applied in place to window rows a0 .. a0 + nrows - 1.
+struct SwPhase {
+  int32_t nb, flags;
+};
+// Batch descriptor; offsets relative to the batch start.  Row form: out[nrows]
+// (int32 slot | kSwAcc; window slot for resident batches, else a global slot: a
+// vector row r < n or n + a state entry), e0[nrows + 1], coef[nent] (complex, the
+// factor's precision), in[nent] (int16: window slot, or position in the gather
+// list), gl[ngl] (int32 global slots of the distinct inputs, global batches
+// only).  Triangle: the packed triangle of order nrows, column by column (lower:
+// rows c..s-1 of column c; upper: rows 0..c), applied in place to window rows
+// a0 .. a0 + nrows - 1.
 struct SwDesc {
   int32_t off;       // byte offset of the batch inside the group image
   int32_t nrows, nent, ngl;
@@ -498,6 +507,7 @@ struct SwDesc {
   int16_t pad;
 };
 static_assert(sizeof(SwGroupHdr) == 32, "group header");
+static_assert(sizeof(SwPhase) == 8, "phase entry");
 static_assert(sizeof(SwDesc) == 40, "batch descriptor");
 struct SwSched {
   std::vector<SwGroup> groups;

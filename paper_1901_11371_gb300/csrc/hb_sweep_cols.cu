@@ -373,7 +373,9 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep_cols(SwArgs a) {
       // the header: from the ring, or (after a failed wait) from the image in global memory
       const char* gimg = bad ? reinterpret_cast<const char*>(a.image + a.groups[g].img) : ring + s_off[slot];
       const SwGroupHdr H = *reinterpret_cast<const SwGroupHdr*>(gimg);
-      const SwDesc* desc = reinterpret_cast<const SwDesc*>(gimg + 32);
+      const SwPhase* tab = reinterpret_cast<const SwPhase*>(gimg + 32);
+      const SwDesc* desc = reinterpret_cast<const SwDesc*>(gimg + H.off_desc);
+      const bool res = (H.flags & SWG_RES) != 0;
       if (H.flags & SWG_BEGIN) {
         if (!bad) {
           const int nrow = H.beg_hi - H.beg_lo;
@@ -384,46 +386,78 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep_cols(SwArgs a) {
         }
         cw_sync();
       }
-      if (H.flags & SWG_TRI) {
-        if (!bad) {
-          const SwDesc D = desc[0];
-          run_tri<NC>(D, (H.flags & SWG_UPPER) != 0, reinterpret_cast<const float2*>(gimg + D.off), win, part, t, nct);
-        } else {
-          cw_sync();   // the barrier inside run_tri
-        }
-      } else if (!bad) {
-        const bool res = (H.flags & SWG_RES) != 0;
-        for (int b = warp; b < H.nb; b += kSwWarps) {
-          const SwDesc D = desc[b];
-          const char* bb = gimg + D.off;
-          if (res) {
-            run_rows<NC, true>(a, D, bb, win, win, xb, stp, ncol, lane);
+      int di = 0;
+      bool stop = false, last_end = false;
+      for (int k = 0; k < H.nph; ++k) {
+        const SwPhase PH = tab[k];
+        if (PH.flags & SWP_TRI) {
+          if (!bad) {
+            const SwDesc D = desc[di];
+            run_tri<NC>(D, (PH.flags & SWP_UPPER) != 0, reinterpret_cast<const float2*>(gimg + D.off), win, part, t,
+                        nct);
           } else {
-            // gather the batch's distinct inputs into the warp's slice, one round trip
-            const int32_t* gl = reinterpret_cast<const int32_t*>(bb + D.off_gl);
-            for (int k = lane; k < D.ngl; k += 32) {
-              const int32_t s = gl[k];
-              const float2* src = gaddr(a, s, xb, stp, NC);
-              const int nc = s < a.n ? ncol : NC;
+            cw_sync();   // the barrier inside run_tri
+          }
+        } else if (!bad) {
+          for (int b = warp; b < PH.nb; b += kSwWarps) {
+            const SwDesc D = desc[di + b];
+            const char* bb = gimg + D.off;
+            if (res) {
+              run_rows<NC, true>(a, D, bb, win, win, xb, stp, ncol, lane);
+            } else {
+              // gather the batch's distinct inputs into the warp's slice: eight loads in
+              // flight per lane before their stores
+              const int32_t* gl = reinterpret_cast<const int32_t*>(bb + D.off_gl);
+              for (int k0 = 0; k0 < D.ngl; k0 += 8 * 32) {
+                float2 v[8][NC];
 #pragma unroll
-              for (int c = 0; c < NC; ++c) slice[k * NC + c] = c < nc ? __ldcg(src + c) : make_float2(0.f, 0.f);
+                for (int u = 0; u < 8; ++u) {
+                  const int kk = k0 + u * 32 + lane;
+                  if (kk < D.ngl) {
+                    const int32_t sl = gl[kk];
+                    const float2* src = gaddr(a, sl, xb, stp, NC);
+                    const int nc = sl < a.n ? ncol : NC;
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) v[u][c] = c < nc ? __ldcg(src + c) : make_float2(0.f, 0.f);
+                  }
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                  const int kk = k0 + u * 32 + lane;
+                  if (kk < D.ngl) {
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) slice[kk * NC + c] = v[u][c];
+                  }
+                }
+              }
+              __syncwarp();
+              run_rows<NC, false>(a, D, bb, slice, win, xb, stp, ncol, lane);
+              __syncwarp();
             }
-            __syncwarp();
-            run_rows<NC, false>(a, D, bb, slice, win, xb, stp, ncol, lane);
-            __syncwarp();
           }
         }
-      }
-      if (!bad) {
-        __syncwarp();
-        if (lane == 0) {
-          __threadfence_block();
-          atomicAdd(&s_cnt[slot], 1);   // this warp no longer reads the group's ring area
+        di += PH.nb;
+        if (PH.flags & SWP_END) {
+          // end of a phase: every compute warp's writes are visible to the next phase
+          if (cw_red_or(bad)) { bad = true; stop = true; break; }
+          last_end = k + 1 == H.nph;
         }
       }
-      if (H.flags & SWG_END) {
-        // end of the phase: every compute warp's writes are visible to the next phase
-        if (cw_red_or(bad)) { bad = true; break; }
+      if (stop) break;
+      if (!bad) {
+        if (last_end) {
+          // every compute warp has passed the barrier: the group is consumed
+          if (t == 0) {
+            __threadfence_block();
+            *(volatile int*)&s_cnt[slot] = kSwWarps;
+          }
+        } else {
+          __syncwarp();
+          if (lane == 0) {
+            __threadfence_block();
+            atomicAdd(&s_cnt[slot], 1);   // this warp no longer reads the group's ring area
+          }
+        }
       }
       if (H.flags & SWG_ENDRUN) {
         const int nrow = H.end_hi - H.end_lo;

@@ -147,15 +147,110 @@ struct PBatch {
   int32_t a0 = 0;
 };
 
+// One phase part laid out on its own: descriptors with offsets relative to the
+// part's data, and the data.
+struct Part {
+  int32_t flags = 0;   // SWP_*
+  std::vector<SwDesc> descs;
+  std::vector<uint8_t> data;
+};
+
+// log2 of the lanes per row of a batch: as many lanes per row as the warp's 32
+// allow for the batch's rows, but not more than half the average row length
+int batch_glog(const PhaseRows& P, const std::vector<int32_t>& rows) {
+  if (rows.empty()) return 0;
+  int64_t ne = 0;
+  for (int32_t r : rows) ne += P.len(r);
+  const double avg = (double)ne / (double)rows.size();
+  int g = 0;
+  while (g < 5 && ((int64_t)rows.size() << (g + 1)) <= 32 && (double)(2 << g) <= avg) ++g;
+  return g;
+}
+
 struct Builder {
   const PackedHost& ph;
   SwSched& S;
   int cb, which;
+  // the group being collected
+  std::vector<Part> pend;
+  int64_t pend_bytes = 0;
+  bool pend_res = false;
   Builder(const PackedHost& p, SwSched& s, int coef_bytes, int w) : ph(p), S(s), cb(coef_bytes), which(w) {}
 
   void coef_at(uint8_t* dst, cplx v) {
     if (cb == 8) put_coef<float>(dst, v);
     else put_coef<double>(dst, v);
+  }
+
+  // lay out batches bs[b0, b1) as one part
+  Part make_part(const PhaseRows& P, const std::vector<PBatch>& bs, size_t b0, size_t b1, bool res, int32_t pflags) {
+    Part pt;
+    pt.flags = pflags;
+    for (size_t q = b0; q < b1; ++q) {
+      const PBatch& B = bs[q];
+      SwDesc D{};
+      D.off = (int32_t)pt.data.size();
+      D.glog = (int16_t)B.glog;
+      if (B.tri) {
+        D.nrows = (int32_t)B.tri_n;
+        D.nent = (int32_t)packed_tri(B.tri_n);
+        D.a0 = B.a0;
+        pt.data.resize(pt.data.size() + al16((int64_t)D.nent * cb), 0);
+        uint8_t* d = pt.data.data() + D.off;
+        const cplx* T = ph.sl[which].data() + B.tri_off;
+        for (int64_t e = 0; e < D.nent; ++e) coef_at(d + e * cb, T[e]);
+        pt.descs.push_back(D);
+        S.batches++;
+        continue;
+      }
+      int64_t ne = 0;
+      for (int32_t r : B.rows) ne += P.len(r);
+      const int64_t nr = (int64_t)B.rows.size();
+      D.nrows = (int32_t)nr;
+      D.nent = (int32_t)ne;
+      D.ngl = (int32_t)B.gl.size();
+      D.off_e0 = (int32_t)al16(4 * nr);
+      D.off_coef = D.off_e0 + (int32_t)al16(4 * (nr + 1));
+      D.off_in = D.off_coef + (int32_t)al16(cb * ne);
+      D.off_gl = D.off_in + (int32_t)al16(2 * ne);
+      const int64_t bytes = D.off_gl + (res ? 0 : al16(4 * (int64_t)D.ngl));
+      pt.data.resize(pt.data.size() + bytes, 0);
+      uint8_t* d = pt.data.data() + D.off;
+      int32_t* out = (int32_t*)d;
+      int32_t* e0 = (int32_t*)(d + D.off_e0);
+      int16_t* in = (int16_t*)(d + D.off_in);
+      int32_t* gl = (int32_t*)(d + D.off_gl);
+      // global batches: input slot -> position in the gather list
+      std::vector<std::pair<int32_t, int32_t>> pos;
+      if (!res) {
+        for (size_t k = 0; k < B.gl.size(); ++k) {
+          gl[k] = B.gl[k];
+          pos.emplace_back(B.gl[k], (int32_t)k);
+        }
+        std::sort(pos.begin(), pos.end());
+      }
+      int32_t e = 0;
+      for (int64_t q2 = 0; q2 < nr; ++q2) {
+        const int32_t r = B.rows[q2];
+        out[q2] = P.out[r];
+        e0[q2] = e;
+        const int32_t s0 = P.start[r], n = P.len(r);
+        for (int32_t t = 0; t < n; ++t, ++e) {
+          coef_at(d + D.off_coef + (int64_t)e * cb, P.coef[s0 + t]);
+          const int32_t sl = P.slot[s0 + t];
+          if (res) {
+            in[e] = (int16_t)sl;
+          } else {
+            auto it = std::lower_bound(pos.begin(), pos.end(), std::make_pair(sl, INT32_MIN));
+            in[e] = (int16_t)it->second;
+          }
+        }
+      }
+      e0[nr] = e;
+      pt.descs.push_back(D);
+      S.batches++;
+    }
+    return pt;
   }
   int64_t batch_bytes(const PhaseRows& P, const PBatch& B, bool res) const {
     if (B.tri) return al16(packed_tri(B.tri_n) * cb);
@@ -164,141 +259,72 @@ struct Builder {
     const int64_t nr = (int64_t)B.rows.size();
     return al16(4 * nr) + al16(4 * (nr + 1)) + al16(cb * ne) + al16(2 * ne) + (res ? 0 : al16(4 * (int64_t)B.gl.size()));
   }
+  static int64_t part_bytes(const Part& pt) { return 8 + 40 * (int64_t)pt.descs.size() + (int64_t)pt.data.size(); }
 
-  // lay out one group: header, descriptors, the batches' data
-  void emit_group(const PhaseRows& P, const std::vector<PBatch>& bs, size_t b0, size_t b1, int32_t flags,
-                  int32_t beg_lo, int32_t beg_hi, int32_t end_lo, int32_t end_hi) {
-    const bool res = (flags & SWG_RES) != 0;
-    const int64_t nb = (int64_t)(b1 - b0);
-    int64_t off = al16(32 + 40 * nb), bytes = off;
-    for (size_t q = b0; q < b1; ++q) bytes += batch_bytes(P, bs[q], res);
-    if (bytes > INT32_MAX / 2) { S.ok = false; S.why = "group too large"; return; }
+  // write the collected parts as one group
+  void flush(bool begin, int32_t beg_lo, int32_t beg_hi) {
+    if (pend.empty()) return;
+    const int64_t nph = (int64_t)pend.size();
+    int64_t nd = 0;
+    for (const Part& pt : pend) nd += (int64_t)pt.descs.size();
+    const int64_t off_desc = al16(32 + 8 * nph);
+    const int64_t off_data = al16(off_desc + 40 * nd);
+    int64_t bytes = off_data;
+    for (const Part& pt : pend) bytes += al16((int64_t)pt.data.size());
+    if (bytes > INT32_MAX / 2) { S.ok = false; S.why = "group too large"; pend.clear(); return; }
     SwGroup G{(int64_t)S.image.size(), (int32_t)bytes, 0};
     S.image.resize((size_t)(G.img + bytes), 0);
     uint8_t* base = S.image.data() + G.img;
-    SwGroupHdr H{(int32_t)nb, flags, beg_lo, beg_hi, end_lo, end_hi, 0, 0};
+    SwGroupHdr H{(int32_t)nph, pend_res ? SWG_RES : 0, 0, 0, 0, 0, (int32_t)off_desc, 0};
+    if (begin) {
+      H.flags |= SWG_BEGIN;
+      H.beg_lo = beg_lo;
+      H.beg_hi = beg_hi;
+    }
     std::memcpy(base, &H, sizeof(H));
-    for (size_t q = b0; q < b1; ++q) {
-      const PBatch& B = bs[q];
-      SwDesc D{};
-      D.off = (int32_t)off;
-      D.glog = (int16_t)B.glog;
-      uint8_t* d = base + off;
-      if (B.tri) {
-        D.nrows = (int32_t)B.tri_n;
-        D.nent = (int32_t)packed_tri(B.tri_n);
-        D.a0 = B.a0;
-        const cplx* T = ph.sl[which].data() + B.tri_off;
-        for (int64_t e = 0; e < D.nent; ++e) coef_at(d + e * cb, T[e]);
-      } else {
-        int64_t ne = 0;
-        for (int32_t r : B.rows) ne += P.len(r);
-        const int64_t nr = (int64_t)B.rows.size();
-        D.nrows = (int32_t)nr;
-        D.nent = (int32_t)ne;
-        D.ngl = (int32_t)B.gl.size();
-        D.off_e0 = (int32_t)al16(4 * nr);
-        D.off_coef = D.off_e0 + (int32_t)al16(4 * (nr + 1));
-        D.off_in = D.off_coef + (int32_t)al16(cb * ne);
-        D.off_gl = D.off_in + (int32_t)al16(2 * ne);
-        int32_t* out = (int32_t*)d;
-        int32_t* e0 = (int32_t*)(d + D.off_e0);
-        int16_t* in = (int16_t*)(d + D.off_in);
-        int32_t* gl = (int32_t*)(d + D.off_gl);
-        // global batches: input slot -> position in the gather list
-        std::vector<std::pair<int32_t, int32_t>> pos;
-        if (!res) {
-          for (size_t k = 0; k < B.gl.size(); ++k) {
-            gl[k] = B.gl[k];
-            pos.emplace_back(B.gl[k], (int32_t)k);
-          }
-          std::sort(pos.begin(), pos.end());
-        }
-        int32_t e = 0;
-        for (int64_t q2 = 0; q2 < nr; ++q2) {
-          const int32_t r = B.rows[q2];
-          out[q2] = P.out[r];
-          e0[q2] = e;
-          const int32_t s0 = P.start[r], n = P.len(r);
-          for (int32_t t = 0; t < n; ++t, ++e) {
-            coef_at(d + D.off_coef + (int64_t)e * cb, P.coef[s0 + t]);
-            const int32_t sl = P.slot[s0 + t];
-            if (res) {
-              in[e] = (int16_t)sl;
-            } else {
-              auto it = std::lower_bound(pos.begin(), pos.end(), std::make_pair(sl, INT32_MIN));
-              in[e] = (int16_t)it->second;
-            }
-          }
-        }
-        e0[nr] = e;
+    int64_t di = 0, dat = off_data;
+    for (int64_t k = 0; k < nph; ++k) {
+      const Part& pt = pend[k];
+      const SwPhase ph_ent{(int32_t)pt.descs.size(), pt.flags};
+      std::memcpy(base + 32 + 8 * k, &ph_ent, sizeof(ph_ent));
+      for (SwDesc D : pt.descs) {
+        D.off += (int32_t)dat;
+        std::memcpy(base + off_desc + 40 * di, &D, sizeof(D));
+        ++di;
       }
-      std::memcpy(base + 32 + 40 * (q - b0), &D, sizeof(D));
-      off += batch_bytes(P, B, res);
-      S.batches++;
+      if (!pt.data.empty()) std::memcpy(base + dat, pt.data.data(), pt.data.size());
+      dat += al16((int64_t)pt.data.size());
     }
     S.max_bytes = std::max<int64_t>(S.max_bytes, bytes);
     S.groups.push_back(G);
+    pend.clear();
+    pend_bytes = 0;
   }
 
-  // lanes per row: about eight entries per lane
-  static int pick_glog(const PhaseRows& P) {
-    const double avg = P.nrows() > 0 ? (double)P.slot.size() / P.nrows() : 1.0;
-    int g = 0;
-    while (g < 5 && (double)(8 << g) < avg) ++g;
-    return g;
-  }
-
-  // batches -> groups of at most kSwGroupBytes (a group holds at least one batch)
-  void emit_groups(const PhaseRows& P, const std::vector<PBatch>& bs, int32_t flags, bool begin, int32_t beg_lo,
-                   int32_t beg_hi, bool endrun, int32_t end_lo, int32_t end_hi) {
-    const bool res = (flags & SWG_RES) != 0;
-    size_t g0 = 0;
-    int64_t acc = 0;
-    for (size_t q = 0; q <= bs.size(); ++q) {
-      const int64_t add = q < bs.size() ? 40 + batch_bytes(P, bs[q], res) : 0;
-      const bool last = q == bs.size();
-      if (last || (acc + add > kSwGroupBytes && q > g0)) {
-        int32_t fl = flags;
-        if (g0 == 0 && begin) fl |= SWG_BEGIN;
-        if (last) fl |= SWG_END | (endrun ? SWG_ENDRUN : 0);
-        emit_group(P, bs, g0, q, fl, begin ? beg_lo : 0, begin ? beg_hi : 0, endrun ? end_lo : 0,
-                   endrun ? end_hi : 0);
-        if (!S.ok) return;
-        g0 = q;
-        acc = 0;
-      }
-      acc += add;
-    }
-  }
-
-  void phase_batches(const PhaseRows& P, bool res, std::vector<PBatch>& bs) {
+  void batches_of_phase(const PhaseRows& P, bool res, std::vector<PBatch>& bs) {
     bs.clear();
     const int32_t nrows = P.nrows();
-    const int glog = pick_glog(P);
-    const int per_round = 32 >> glog;
     std::vector<int32_t> order(nrows);
     for (int32_t r = 0; r < nrows; ++r) order[r] = r;
     if (res) {
-      // a dependent phase: about one batch per compute warp (more if the data would
-      // be too large), rows by decreasing length dealt round-robin
+      // a dependent phase: one batch per compute warp (more if the data would be
+      // too large), rows by decreasing length dealt round-robin
       int64_t tot = 0;
       for (int32_t r = 0; r < nrows; ++r) tot += 8 + (int64_t)(cb + 2) * P.len(r);
-      int64_t nb = std::min<int64_t>(kSwWarps, (nrows + per_round - 1) / per_round);
+      int64_t nb = std::min<int64_t>(kSwWarps, nrows);
       nb = std::max<int64_t>(nb, (tot + kSwBatchBytes - 1) / kSwBatchBytes);
       nb = std::max<int64_t>(1, std::min<int64_t>(nb, nrows));
       std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return P.len(a) > P.len(b); });
       bs.resize(nb);
       for (int64_t q = 0; q < nb; ++q) {
-        bs[q].glog = glog;
         for (int64_t i2 = q; i2 < nrows; i2 += nb) bs[q].rows.push_back(order[i2]);
+        bs[q].glog = batch_glog(P, bs[q].rows);
       }
       return;
     }
     // wide phase: consecutive rows (an op's rows share inputs), batches of about
     // kSwGlobBytes of data with at most kSwGather distinct inputs
     PBatch cur;
-    cur.glog = glog;
     std::vector<int32_t> seen;   // sorted distinct inputs of cur
     int64_t acc = 0;
     std::vector<int32_t> fresh;
@@ -317,7 +343,6 @@ struct Builder {
         cur.gl = seen;
         bs.push_back(std::move(cur));
         cur = PBatch();
-        cur.glog = glog;
         seen.clear();
         acc = 0;
         fresh.clear();
@@ -336,8 +361,48 @@ struct Builder {
       bs.push_back(std::move(cur));
     }
     // rows of a batch by decreasing length (the lanes' rounds stay balanced)
-    for (PBatch& B : bs)
+    for (PBatch& B : bs) {
       std::stable_sort(B.rows.begin(), B.rows.end(), [&](int32_t a, int32_t b) { return P.len(a) > P.len(b); });
+      int64_t ne = 0;
+      for (int32_t r : B.rows) ne += P.len(r);
+      const double avg = (double)ne / (double)B.rows.size();
+      int g = 0;
+      while (g < 5 && (double)(8 << g) < avg) ++g;   // about eight entries per lane
+      B.glog = g;
+    }
+  }
+
+  // add a phase's batches to the groups: parts of at most kSwGroupBytes, the last
+  // one ending the phase; resident parts share groups, global ones do not
+  void add_phase(const PhaseRows& P, const std::vector<PBatch>& bs, bool res, int32_t pflags, bool& begin,
+                 int32_t beg_lo, int32_t beg_hi) {
+    size_t b0 = 0;
+    while (b0 < bs.size()) {
+      size_t b1 = b0;
+      int64_t acc = 0;
+      while (b1 < bs.size()) {
+        const int64_t add = 40 + batch_bytes(P, bs[b1], res);
+        if (b1 > b0 && acc + add > kSwGroupBytes) break;
+        acc += add;
+        ++b1;
+      }
+      const bool last = b1 == bs.size();
+      Part pt = make_part(P, bs, b0, b1, res, pflags & ~(last ? 0 : SWP_END));
+      const int64_t pb = part_bytes(pt);
+      if (!pend.empty() && (!res || !pend_res || (pflags & SWP_TRI) || pend_bytes + pb > kSwGroupBytes ||
+                            (int)pend.size() >= kSwMaxPhases)) {
+        flush(begin, beg_lo, beg_hi);
+        begin = false;
+      }
+      pend_res = res;
+      pend.push_back(std::move(pt));
+      pend_bytes += pb;
+      if (!res || (pflags & SWP_TRI)) {   // global parts and triangles form groups of their own
+        flush(begin, beg_lo, beg_hi);
+        begin = false;
+      }
+      b0 = b1;
+    }
   }
 };
 
@@ -363,17 +428,13 @@ void build_sweep_sched(const PackedHost& ph, int which, int coef_bytes, int win_
     sm.n = ph.n;
     sm.res = res;
     sm.row_lo = sg.row_lo; sm.row_hi = sg.row_hi; sm.st_lo = sg.st_lo; sm.st_hi = sg.st_hi;
+    bool begin = res;   // the run's first group loads its rows
     if (res) S.runs++;
-    // phases of the segment that hold ops
-    std::vector<int> phs;
-    for (int p = sg.first; p < sg.first + sg.count; ++p)
-      if (fp.base[p + 1] > fp.base[p]) phs.push_back(p);
-    for (size_t k = 0; k < phs.size(); ++k) {
-      const int p = phs[k];
+    for (int p = sg.first; p < sg.first + sg.count; ++p) {
       const int32_t o0 = fp.base[p], o1 = fp.base[p + 1];
-      const bool first = k == 0, last = k + 1 == phs.size();
+      if (o1 <= o0) continue;
       P.clear();
-      int32_t flags = res ? SWG_RES : 0;
+      int32_t pflags = SWP_END;
       if (fp.ops[o0].kind == FK_LEAF) {
         // a sweep leaf always lies inside a resident run (its rows alone fit the window)
         if (!res || o1 - o0 != 1) { S.ok = false; S.why = "sweep leaf outside a resident run"; return; }
@@ -383,17 +444,29 @@ void build_sweep_sched(const PackedHost& ph, int which, int coef_bytes, int win_
         bs[0].tri_off = f.moff;
         bs[0].tri_n = f.c0;
         bs[0].a0 = sm.vec(f.src0);
-        flags |= SWG_TRI | ((f.flags & FF_UPPER) ? SWG_UPPER : 0);
+        pflags |= SWP_TRI | ((f.flags & FF_UPPER) ? SWP_UPPER : 0);
       } else {
         for (int32_t o = o0; o < o1; ++o) expand_op(ph, fp.ops[o], sm, P);
-        bd.phase_batches(P, res, bs);
+        bd.batches_of_phase(P, res, bs);
       }
       if (sm.bad) { S.ok = false; S.why = "slot outside the run's window"; return; }
       if (!S.ok) return;
-      bd.emit_groups(P, bs, flags, res && first, sg.row_lo, sg.row_hi, res && last, sg.row_lo, sg.row_hi);
+      bd.add_phase(P, bs, res, pflags, begin, sg.row_lo, sg.row_hi);
       if (!S.ok) return;
       if (res) S.res_phases++;
       else S.glob_phases++;
+    }
+    bd.flush(begin, sg.row_lo, sg.row_hi);
+    begin = false;
+    if (res && !S.groups.empty()) {
+      // the run's last group writes the rows back after its last phase
+      SwGroupHdr H;
+      uint8_t* hb = S.image.data() + S.groups.back().img;
+      std::memcpy(&H, hb, sizeof(H));
+      H.flags |= SWG_ENDRUN;
+      H.end_lo = sg.row_lo;
+      H.end_hi = sg.row_hi;
+      std::memcpy(hb, &H, sizeof(H));
     }
   }
   // (the device stages complex-FP32 images; FP64 images serve host checks only)
@@ -414,7 +487,7 @@ void host_sweep_sched(const PackedHost& ph, const SwSched& S, cplx* vec) {
     return cplx(v[0], v[1]);
   };
   auto gslot = [&](int32_t sl) -> cplx& { return sl < n ? vec[sl] : st[sl - n]; };
-  // a phase's outputs are stored at its end (its groups never read them)
+  // a phase's outputs are stored when it ends (its parts never read them)
   struct Out { bool res; int32_t o; cplx v; };
   std::vector<Out> outs;
   for (const SwGroup& G : S.groups) {
@@ -424,47 +497,53 @@ void host_sweep_sched(const PackedHost& ph, const SwSched& S, cplx* vec) {
     if (H.flags & SWG_BEGIN)
       for (int32_t r = H.beg_lo; r < H.beg_hi; ++r) win[r - H.beg_lo] = vec[r];
     const bool res = (H.flags & SWG_RES) != 0;
-    for (int32_t b = 0; b < H.nb; ++b) {
-      SwDesc D;
-      std::memcpy(&D, gb + 32 + 40 * b, sizeof(D));
-      const uint8_t* base = gb + D.off;
-      if (H.flags & SWG_TRI) {
-        const int64_t sz = D.nrows;
-        tmp.assign((size_t)sz, cplx(0.0, 0.0));
-        const bool up = (H.flags & SWG_UPPER) != 0;
-        for (int64_t c = 0; c < sz; ++c)
-          for (int64_t r = up ? 0 : c; r < (up ? c + 1 : sz); ++r) {
-            const int64_t off = up ? tri_off_upper(r, c) : tri_off_lower(sz, r, c);
-            tmp[r] += coef(base, off) * win[D.a0 + c];
-          }
-        for (int64_t r = 0; r < sz; ++r) win[D.a0 + r] = tmp[r];
-        continue;
+    int64_t di = 0;
+    for (int32_t k = 0; k < H.nph; ++k) {
+      SwPhase PH;
+      std::memcpy(&PH, gb + 32 + 8 * k, sizeof(PH));
+      for (int32_t b = 0; b < PH.nb; ++b, ++di) {
+        SwDesc D;
+        std::memcpy(&D, gb + H.off_desc + 40 * di, sizeof(D));
+        const uint8_t* base = gb + D.off;
+        if (PH.flags & SWP_TRI) {
+          const int64_t sz = D.nrows;
+          tmp.assign((size_t)sz, cplx(0.0, 0.0));
+          const bool up = (PH.flags & SWP_UPPER) != 0;
+          for (int64_t c = 0; c < sz; ++c)
+            for (int64_t r = up ? 0 : c; r < (up ? c + 1 : sz); ++r) {
+              const int64_t off = up ? tri_off_upper(r, c) : tri_off_lower(sz, r, c);
+              tmp[r] += coef(base, off) * win[D.a0 + c];
+            }
+          for (int64_t r = 0; r < sz; ++r) win[D.a0 + r] = tmp[r];
+          continue;
+        }
+        const int32_t* out = (const int32_t*)base;
+        const int32_t* e0 = (const int32_t*)(base + D.off_e0);
+        const int16_t* in = (const int16_t*)(base + D.off_in);
+        const int32_t* gl = (const int32_t*)(base + D.off_gl);
+        if (!res) {   // gather the batch's distinct inputs
+          gv.resize((size_t)D.ngl);
+          for (int32_t q = 0; q < D.ngl; ++q) gv[q] = gslot(gl[q]);
+        }
+        for (int32_t r = 0; r < D.nrows; ++r) {
+          cplx acc(0.0, 0.0);
+          for (int32_t e = e0[r]; e < e0[r + 1]; ++e)
+            acc += coef(base + D.off_coef, e) * (res ? win[in[e]] : gv[in[e]]);
+          outs.push_back(Out{res, out[r], acc});
+        }
       }
-      const int32_t* out = (const int32_t*)base;
-      const int32_t* e0 = (const int32_t*)(base + D.off_e0);
-      const int16_t* in = (const int16_t*)(base + D.off_in);
-      const int32_t* gl = (const int32_t*)(base + D.off_gl);
-      if (!res) {   // gather the batch's distinct inputs
-        gv.resize((size_t)D.ngl);
-        for (int32_t k = 0; k < D.ngl; ++k) gv[k] = gslot(gl[k]);
-      }
-      for (int32_t r = 0; r < D.nrows; ++r) {
-        cplx acc(0.0, 0.0);
-        for (int32_t e = e0[r]; e < e0[r + 1]; ++e) acc += coef(base + D.off_coef, e) * (res ? win[in[e]] : gv[in[e]]);
-        outs.push_back(Out{res, out[r], acc});
+      if (PH.flags & SWP_END) {
+        for (const Out& ov : outs) {
+          const bool add = (ov.o & kSwAcc) != 0;
+          const int32_t sl = ov.o & ~kSwAcc;
+          cplx* d = ov.res ? &win[sl] : &gslot(sl);
+          *d = add ? *d + ov.v : ov.v;
+        }
+        outs.clear();
       }
     }
-    if (H.flags & SWG_END) {
-      for (const Out& ov : outs) {
-        const bool add = (ov.o & kSwAcc) != 0;
-        const int32_t sl = ov.o & ~kSwAcc;
-        cplx* d = ov.res ? &win[sl] : &gslot(sl);
-        *d = add ? *d + ov.v : ov.v;
-      }
-      outs.clear();
-      if (H.flags & SWG_ENDRUN)
-        for (int32_t r = H.end_lo; r < H.end_hi; ++r) vec[r] = win[r - H.end_lo];
-    }
+    if (H.flags & SWG_ENDRUN)
+      for (int32_t r = H.end_lo; r < H.end_hi; ++r) vec[r] = win[r - H.end_lo];
   }
 }
 
