@@ -451,18 +451,21 @@ void host_apply_plan(const PackedHost& ph, const ApplyPlan& plan, int fes, bool 
 // batches' data.  A group holds several consecutive small phases of a resident
 // run (a barrier among the compute warps after each), or one part of a large
 // phase (the phase's last part ends with the barrier); a triangle is a group of
-// its own, taken by all compute warps.  Compute warp w takes the batches w,
-// w + 16, ... of a phase part.
+// its own.  A resident run is executed by the first kSwChain compute warps
+// alone (their own barrier between phases; the other warps wait for the run's
+// end), which keeps the per-phase instruction overhead of this dependent chain
+// small; a global phase part's batches go round-robin to all compute warps.
 // ---------------------------------------------------------------------------
 constexpr int kSwWarps = 16;                 // compute warps (one more warp stages the groups)
+constexpr int kSwChain = 4;                  // compute warps that execute the resident runs
 constexpr int kSwWinBytes = 96 * 1024;       // resident window: rows + state of a run
 constexpr int kSwRingBytes = 104 * 1024;     // staging ring of group images
 constexpr int kSwPartBytes = 16 * 1024;      // partial sums of a triangle product
 constexpr int kSwMaxCols = 2;                // right-hand sides per CTA
 constexpr int kSwWinSlots = kSwWinBytes / (kSwMaxCols * 8);   // window slots (complex-FP32 entries per column)
 constexpr int kSwGather = kSwWinSlots / kSwWarps;             // gathered inputs of a global batch (a warp's slice)
-constexpr int kSwBatchBytes = 6 * 1024;      // target data bytes of one resident batch
-constexpr int kSwGlobBytes = 3 * 1024;       // target data bytes of one global batch
+constexpr int kSwBatchBytes = 8 * 1024;      // target data bytes of one resident batch
+constexpr int kSwGlobBytes = 6 * 1024;       // target data bytes of one global batch
 constexpr int kSwGroupBytes = 32 * 1024;     // target bytes of a group
 constexpr int kSwMaxPhases = 64;             // phases of one group
 constexpr int32_t kSwAcc = (int32_t)0x80000000;  // output slot flag: add to the output instead of overwriting
@@ -485,7 +488,8 @@ struct SwGroupHdr {  // first 32 bytes of a group image; then nph phase entries 
   int32_t nph, flags;
   int32_t beg_lo, beg_hi, end_lo, end_hi;
   int32_t off_desc;  // byte offset of the descriptors (all phases' batches in order)
-  int32_t pad;
+  int32_t aux;       // first group of a run (SWG_BEGIN): the run's group count; global
+                     // group: the compute warp that takes its first batch
 };
 struct SwPhase {
   int32_t nb, flags;

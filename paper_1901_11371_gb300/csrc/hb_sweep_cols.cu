@@ -80,6 +80,15 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned b
 __device__ __forceinline__ void cw_sync() {   // named barrier 1 among the compute warps
   asm volatile("bar.sync 1, %0;\n" ::"n"(kSwWarps * 32) : "memory");
 }
+__device__ __forceinline__ void ch_sync() {   // named barrier 2 among the chain warps
+  asm volatile("bar.sync 2, %0;\n" ::"n"(kSwChain * 32) : "memory");
+}
+__device__ __forceinline__ bool ch_red_or(bool v) {
+  unsigned r;
+  asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 2, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+               : "=r"(r) : "r"((unsigned)v), "n"(kSwChain * 32) : "memory");
+  return r != 0;
+}
 __device__ __forceinline__ bool cw_red_or(bool v) {
   unsigned r;
   asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
@@ -216,6 +225,7 @@ __device__ void run_rows(const SwArgs& a, const SwDesc& D, const char* bb, const
 // c = g (mod ncg) of them.  The triangle is not read after the barrier inside.
 template <int NC>
 __device__ void run_tri(const SwDesc& D, bool up, const float2* T, float2* win, float2* part, int t, int nct) {
+  // (t < nct = the chain warps' threads; their barrier separates the two steps)
   const int s = D.nrows;
   float2* b = win + (int64_t)D.a0 * NC;
   const int npair = s >> 1;
@@ -255,7 +265,7 @@ __device__ void run_tri(const SwDesc& D, bool up, const float2* T, float2* win, 
       for (int cc = 0; cc < NC; ++cc) part[((int64_t)g * s + r) * NC + cc] = acc[cc];
     }
   }
-  cw_sync();
+  ch_sync();
   for (int e = t; e < s * NC; e += nct) {
     const int r = e / NC, cc = e % NC;
     float2 sum = make_float2(0.f, 0.f);
@@ -354,10 +364,12 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep_cols(SwArgs a) {
     if (lane == 0) s_issued = (int)g;
     __syncwarp();
   } else {
-    const int t = threadIdx.x, nct = kSwWarps * 32;
+    const int t = threadIdx.x;
+    const bool chain = warp < kSwChain;
     float2* slice = win + (int64_t)warp * kSwGather * NC;   // gather area of global batches
     bool bad = false;   // warp-uniform; after a failed wait the warp only follows the barriers
-    for (int64_t g = 0; g < a.ngroup; ++g) {
+    // wait for group g (bounded); returns its image (ring, or global memory after a failure)
+    auto group = [&](int64_t g) -> const char* {
       const int slot = (int)(g % kSwSlots);
       if (!bad) {
         long long spins = 0;
@@ -370,102 +382,145 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep_cols(SwArgs a) {
           if (lane == 0) atomicExch(&s_abort, 1);
         }
       }
-      // the header: from the ring, or (after a failed wait) from the image in global memory
-      const char* gimg = bad ? reinterpret_cast<const char*>(a.image + a.groups[g].img) : ring + s_off[slot];
-      const SwGroupHdr H = *reinterpret_cast<const SwGroupHdr*>(gimg);
-      const SwPhase* tab = reinterpret_cast<const SwPhase*>(gimg + 32);
-      const SwDesc* desc = reinterpret_cast<const SwDesc*>(gimg + H.off_desc);
-      const bool res = (H.flags & SWG_RES) != 0;
-      if (H.flags & SWG_BEGIN) {
-        if (!bad) {
-          const int nrow = H.beg_hi - H.beg_lo;
-          for (int e = t; e < nrow * NC; e += nct) {
-            const int r = e / NC, c = e % NC;
-            win[e] = c < ncol ? __ldcg(xb + (int64_t)(H.beg_lo + r) * a.R + c) : make_float2(0.f, 0.f);
-          }
-        }
-        cw_sync();
-      }
-      int di = 0;
-      bool stop = false, last_end = false;
-      for (int k = 0; k < H.nph; ++k) {
-        const SwPhase PH = tab[k];
-        if (PH.flags & SWP_TRI) {
+      return bad ? reinterpret_cast<const char*>(a.image + a.groups[g].img) : ring + s_off[slot];
+    };
+    int64_t g = 0;
+    while (g < a.ngroup) {
+      const char* gimg = group(g);
+      SwGroupHdr H = *reinterpret_cast<const SwGroupHdr*>(gimg);
+      if (H.flags & SWG_RES) {
+        // ---- a resident run: groups g .. g + H.aux - 1, executed by the chain warps
+        const int64_t g0 = g, gend = g + H.aux;
+        if (!chain) {
+          // the other warps only read the run's length; they release their hold on the
+          // first group's ring area, then wait for the run's end
           if (!bad) {
-            const SwDesc D = desc[di];
-            run_tri<NC>(D, (PH.flags & SWP_UPPER) != 0, reinterpret_cast<const float2*>(gimg + D.off), win, part, t,
-                        nct);
-          } else {
-            cw_sync();   // the barrier inside run_tri
+            __syncwarp();
+            if (lane == 0) {
+              __threadfence_block();
+              atomicAdd(&s_cnt[(int)(g % kSwSlots)], 1);
+            }
           }
-        } else if (!bad) {
-          for (int b = warp; b < PH.nb; b += kSwWarps) {
-            const SwDesc D = desc[di + b];
-            const char* bb = gimg + D.off;
-            if (res) {
-              run_rows<NC, true>(a, D, bb, win, win, xb, stp, ncol, lane);
-            } else {
-              // gather the batch's distinct inputs into the warp's slice: eight loads in
-              // flight per lane before their stores
-              const int32_t* gl = reinterpret_cast<const int32_t*>(bb + D.off_gl);
-              for (int k0 = 0; k0 < D.ngl; k0 += 8 * 32) {
-                float2 v[8][NC];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                  const int kk = k0 + u * 32 + lane;
-                  if (kk < D.ngl) {
-                    const int32_t sl = gl[kk];
-                    const float2* src = gaddr(a, sl, xb, stp, NC);
-                    const int nc = sl < a.n ? ncol : NC;
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) v[u][c] = c < nc ? __ldcg(src + c) : make_float2(0.f, 0.f);
-                  }
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                  const int kk = k0 + u * 32 + lane;
-                  if (kk < D.ngl) {
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) slice[kk * NC + c] = v[u][c];
-                  }
-                }
+          g = gend;
+          if (cw_red_or(bad)) { bad = true; break; }   // the run is done, its rows written back
+          continue;
+        }
+        const int ct = t, nct = kSwChain * 32;
+        bool stop = false;
+        for (; g < gend && !stop; ++g) {
+          if (g > g0) {
+            gimg = group(g);
+            H = *reinterpret_cast<const SwGroupHdr*>(gimg);
+          }
+          const int slot = (int)(g % kSwSlots);
+          const SwPhase* tab = reinterpret_cast<const SwPhase*>(gimg + 32);
+          const SwDesc* desc = reinterpret_cast<const SwDesc*>(gimg + H.off_desc);
+          if (H.flags & SWG_BEGIN) {
+            if (!bad) {
+              const int nrow = H.beg_hi - H.beg_lo;
+              for (int e = ct; e < nrow * NC; e += nct) {
+                const int r = e / NC, c = e % NC;
+                win[e] = c < ncol ? __ldcg(xb + (int64_t)(H.beg_lo + r) * a.R + c) : make_float2(0.f, 0.f);
               }
-              __syncwarp();
-              run_rows<NC, false>(a, D, bb, slice, win, xb, stp, ncol, lane);
-              __syncwarp();
+            }
+            ch_sync();
+          }
+          int di = 0;
+          for (int k = 0; k < H.nph; ++k) {
+            const SwPhase PH = tab[k];
+            if (PH.flags & SWP_TRI) {
+              if (!bad) {
+                const SwDesc D = desc[di];
+                run_tri<NC>(D, (PH.flags & SWP_UPPER) != 0, reinterpret_cast<const float2*>(gimg + D.off), win, part,
+                            ct, nct);
+              } else {
+                ch_sync();   // the barrier inside run_tri
+              }
+            } else if (!bad) {
+              for (int b = warp; b < PH.nb; b += kSwChain) {
+                const SwDesc D = desc[di + b];
+                run_rows<NC, true>(a, D, gimg + D.off, win, win, xb, stp, ncol, lane);
+              }
+            }
+            di += PH.nb;
+            if (PH.flags & SWP_END) {
+              if (ch_red_or(bad)) { bad = true; stop = true; break; }
+            }
+          }
+          if (stop) break;
+          // every chain warp has passed the group's last barrier: the group is consumed
+          // (the run's first group: together with the other warps' holds)
+          if (!bad && ct == 0) {
+            __threadfence_block();
+            if (g == g0) atomicAdd(&s_cnt[slot], kSwChain);
+            else *(volatile int*)&s_cnt[slot] = kSwWarps;
+          }
+          if (H.flags & SWG_ENDRUN) {
+            const int nrow = H.end_hi - H.end_lo;
+            for (int e = ct; e < nrow * NC; e += nct) {
+              const int r = e / NC, c = e % NC;
+              if (c < ncol) xb[(int64_t)(H.end_lo + r) * a.R + c] = win[e];
             }
           }
         }
-        di += PH.nb;
-        if (PH.flags & SWP_END) {
-          // end of a phase: every compute warp's writes are visible to the next phase
-          if (cw_red_or(bad)) { bad = true; stop = true; break; }
-          last_end = k + 1 == H.nph;
-        }
+        g = gend;
+        if (cw_red_or(bad)) { bad = true; break; }   // the run is done, its rows written back
+        continue;
       }
-      if (stop) break;
-      if (!bad) {
-        if (last_end) {
-          // every compute warp has passed the barrier: the group is consumed
+      // ---- a part of a global phase: batches round-robin over all compute warps
+      {
+        const int slot = (int)(g % kSwSlots);
+        const SwPhase PH = *reinterpret_cast<const SwPhase*>(gimg + 32);
+        const SwDesc* desc = reinterpret_cast<const SwDesc*>(gimg + H.off_desc);
+        if (!bad) {
+          for (int b = (warp - H.aux + kSwWarps) % kSwWarps; b < PH.nb; b += kSwWarps) {
+            const SwDesc D = desc[b];
+            const char* bb = gimg + D.off;
+            // gather the batch's distinct inputs into the warp's slice: eight loads in
+            // flight per lane before their stores
+            const int32_t* gl = reinterpret_cast<const int32_t*>(bb + D.off_gl);
+            for (int k0 = 0; k0 < D.ngl; k0 += 8 * 32) {
+              float2 v[8][NC];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int kk = k0 + u * 32 + lane;
+                if (kk < D.ngl) {
+                  const int32_t sl = gl[kk];
+                  const float2* src = gaddr(a, sl, xb, stp, NC);
+                  const int nc = sl < a.n ? ncol : NC;
+#pragma unroll
+                  for (int c = 0; c < NC; ++c) v[u][c] = c < nc ? __ldcg(src + c) : make_float2(0.f, 0.f);
+                }
+              }
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int kk = k0 + u * 32 + lane;
+                if (kk < D.ngl) {
+#pragma unroll
+                  for (int c = 0; c < NC; ++c) slice[kk * NC + c] = v[u][c];
+                }
+              }
+            }
+            __syncwarp();
+            run_rows<NC, false>(a, D, bb, slice, win, xb, stp, ncol, lane);
+            __syncwarp();
+          }
+        }
+        if (PH.flags & SWP_END) {
+          // end of the phase: every compute warp's writes are visible to the next phase
+          if (cw_red_or(bad)) { bad = true; break; }
           if (t == 0) {
             __threadfence_block();
             *(volatile int*)&s_cnt[slot] = kSwWarps;
           }
-        } else {
+        } else if (!bad) {
           __syncwarp();
           if (lane == 0) {
             __threadfence_block();
             atomicAdd(&s_cnt[slot], 1);   // this warp no longer reads the group's ring area
           }
         }
-      }
-      if (H.flags & SWG_ENDRUN) {
-        const int nrow = H.end_hi - H.end_lo;
-        for (int e = t; e < nrow * NC; e += nct) {
-          const int r = e / NC, c = e % NC;
-          if (c < ncol) xb[(int64_t)(H.end_lo + r) * a.R + c] = win[e];
-        }
-        cw_sync();
+        ++g;
       }
     }
     if (bad && t == 0) {

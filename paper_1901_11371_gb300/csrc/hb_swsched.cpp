@@ -163,7 +163,7 @@ int batch_glog(const PhaseRows& P, const std::vector<int32_t>& rows) {
   for (int32_t r : rows) ne += P.len(r);
   const double avg = (double)ne / (double)rows.size();
   int g = 0;
-  while (g < 5 && ((int64_t)rows.size() << (g + 1)) <= 32 && (double)(2 << g) <= avg) ++g;
+  while (g < 5 && ((int64_t)rows.size() << (g + 1)) <= 32 && (double)(4 << g) <= avg) ++g;
   return g;
 }
 
@@ -175,6 +175,7 @@ struct Builder {
   std::vector<Part> pend;
   int64_t pend_bytes = 0;
   bool pend_res = false;
+  int64_t glob_batches = 0;   // batches of the current global phase so far (warp rotation)
   Builder(const PackedHost& p, SwSched& s, int coef_bytes, int w) : ph(p), S(s), cb(coef_bytes), which(w) {}
 
   void coef_at(uint8_t* dst, cplx v) {
@@ -275,7 +276,9 @@ struct Builder {
     SwGroup G{(int64_t)S.image.size(), (int32_t)bytes, 0};
     S.image.resize((size_t)(G.img + bytes), 0);
     uint8_t* base = S.image.data() + G.img;
-    SwGroupHdr H{(int32_t)nph, pend_res ? SWG_RES : 0, 0, 0, 0, 0, (int32_t)off_desc, 0};
+    SwGroupHdr H{(int32_t)nph, pend_res ? SWG_RES : 0, 0, 0, 0, 0, (int32_t)off_desc,
+                 pend_res ? 0 : (int32_t)(glob_batches % kSwWarps)};
+    if (!pend_res) glob_batches += nd;
     if (begin) {
       H.flags |= SWG_BEGIN;
       H.beg_lo = beg_lo;
@@ -311,7 +314,7 @@ struct Builder {
       // too large), rows by decreasing length dealt round-robin
       int64_t tot = 0;
       for (int32_t r = 0; r < nrows; ++r) tot += 8 + (int64_t)(cb + 2) * P.len(r);
-      int64_t nb = std::min<int64_t>(kSwWarps, nrows);
+      int64_t nb = std::min<int64_t>(kSwChain, nrows);
       nb = std::max<int64_t>(nb, (tot + kSwBatchBytes - 1) / kSwBatchBytes);
       nb = std::max<int64_t>(1, std::min<int64_t>(nb, nrows));
       std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return P.len(a) > P.len(b); });
@@ -409,6 +412,7 @@ struct Builder {
 }  // namespace
 
 void build_sweep_sched(const PackedHost& ph, int which, int coef_bytes, int win_slots, SwSched& S) {
+  // (resident runs: their groups are counted into the first one's header below)
   S = SwSched{};
   S.coef_bytes = coef_bytes;
   S.win_slots = std::max(1, std::min(win_slots, kSwWinSlots));
@@ -430,6 +434,8 @@ void build_sweep_sched(const PackedHost& ph, int which, int coef_bytes, int win_
     sm.row_lo = sg.row_lo; sm.row_hi = sg.row_hi; sm.st_lo = sg.st_lo; sm.st_hi = sg.st_hi;
     bool begin = res;   // the run's first group loads its rows
     if (res) S.runs++;
+    const size_t run_g0 = S.groups.size();
+    bd.glob_batches = 0;
     for (int p = sg.first; p < sg.first + sg.count; ++p) {
       const int32_t o0 = fp.base[p], o1 = fp.base[p + 1];
       if (o1 <= o0) continue;
@@ -455,17 +461,24 @@ void build_sweep_sched(const PackedHost& ph, int which, int coef_bytes, int win_
       if (!S.ok) return;
       if (res) S.res_phases++;
       else S.glob_phases++;
+      bd.glob_batches = 0;
     }
     bd.flush(begin, sg.row_lo, sg.row_hi);
     begin = false;
-    if (res && !S.groups.empty()) {
-      // the run's last group writes the rows back after its last phase
+    if (res && S.groups.size() > run_g0) {
+      // the run's last group writes the rows back after its last phase; its first
+      // group tells how many groups the run has
       SwGroupHdr H;
       uint8_t* hb = S.image.data() + S.groups.back().img;
       std::memcpy(&H, hb, sizeof(H));
       H.flags |= SWG_ENDRUN;
       H.end_lo = sg.row_lo;
       H.end_hi = sg.row_hi;
+      std::memcpy(hb, &H, sizeof(H));
+      hb = S.image.data() + S.groups[run_g0].img;
+      std::memcpy(&H, hb, sizeof(H));
+      if (!(H.flags & SWG_BEGIN)) { S.ok = false; S.why = "resident run without its first group"; return; }
+      H.aux = (int32_t)(S.groups.size() - run_g0);
       std::memcpy(hb, &H, sizeof(H));
     }
   }
