@@ -440,6 +440,10 @@ int hb_host_sweep_sched(hb_factor_t f, int which, int coef_bytes, int win_slots,
   SwSched S;
   build_sweep_sched(f->ph, which, coef_bytes, win_slots > 0 ? win_slots : kSwWinSlots, S);
   if (!S.ok) { set_error("hb_host_sweep_sched: no column-partitioned schedule for this factor (%s)", S.why); return HB_EUNSUPPORTED; }
+  if (const char* bad = check_sweep_sched(f->ph, S); *bad) {
+    set_error("hb_host_sweep_sched: the schedule failed its structural check (%s)", bad);
+    return HB_EUNSUPPORTED;
+  }
   host_sweep_sched(f->ph, S, reinterpret_cast<cplx*>(vec));
   return (int)std::min<int64_t>(S.batches, (int64_t)INT32_MAX);
 }

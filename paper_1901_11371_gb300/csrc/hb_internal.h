@@ -533,6 +533,11 @@ void build_sweep_sched(const PackedHost& ph, int which, int coef_bytes, int win_
 // from the group images as the kernel does: vec = sweep(vec) (verification of
 // the schedule without a GPU).
 void host_sweep_sched(const PackedHost& ph, const SwSched& S, cplx* vec);
+// Structural check of a schedule against what the kernel assumes (group sizes
+// within the ring, pieces inside their group, slots inside the window or the
+// vector / state, gather lists within a warp's slice, run headers, triangle
+// rows inside the window); returns "" or the first violation found.
+const char* check_sweep_sched(const PackedHost& ph, const SwSched& S);
 
 // FP64 host execution of the packed program (verification without a GPU).
 void host_apply(const PackedHost& ph, const HostFactor& hf, bool adj, const cplx* x, cplx* y);

@@ -426,8 +426,10 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep_cols(SwArgs a) {
             ch_sync();
           }
           int di = 0;
+          bool last_end = false;
           for (int k = 0; k < H.nph; ++k) {
             const SwPhase PH = tab[k];
+            last_end = (PH.flags & SWP_END) != 0;
             if (PH.flags & SWP_TRI) {
               if (!bad) {
                 const SwDesc D = desc[di];
@@ -448,6 +450,9 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep_cols(SwArgs a) {
             }
           }
           if (stop) break;
+          // a group that ends inside a phase (a large phase spread over several groups):
+          // every chain warp must be done with it before it is released
+          if (!last_end) ch_sync();
           // every chain warp has passed the group's last barrier: the group is consumed
           // (the run's first group: together with the other warps' holds)
           if (!bad && ct == 0) {

@@ -560,4 +560,84 @@ void host_sweep_sched(const PackedHost& ph, const SwSched& S, cplx* vec) {
   }
 }
 
+const char* check_sweep_sched(const PackedHost& ph, const SwSched& S) {
+  const int64_t n = ph.n;
+  const int cb = S.coef_bytes;
+  int64_t run_left = 0;   // groups of the current resident run still to come
+  int32_t win_rows = 0;
+  for (size_t gi = 0; gi < S.groups.size(); ++gi) {
+    const SwGroup& G = S.groups[gi];
+    if (G.img % 16 || G.bytes % 16 || G.bytes <= 0) return "group not 16-byte aligned";
+    if (cb == 8 && G.bytes > kSwRingBytes) return "group larger than the ring";
+    if (G.img + G.bytes > (int64_t)S.image.size()) return "group outside the image";
+    const uint8_t* gb = S.image.data() + G.img;
+    SwGroupHdr H;
+    std::memcpy(&H, gb, sizeof(H));
+    const bool res = (H.flags & SWG_RES) != 0;
+    if (H.nph < 1 || 32 + 8 * (int64_t)H.nph > H.off_desc) return "phase table";
+    if (res) {
+      if (run_left == 0) {
+        if (!(H.flags & SWG_BEGIN) || H.aux < 1) return "run start without BEGIN or length";
+        run_left = H.aux;
+        win_rows = H.beg_hi - H.beg_lo;
+        if (win_rows < 1 || win_rows > S.win_slots) return "run rows";
+      } else if (H.flags & SWG_BEGIN) {
+        return "BEGIN inside a run";
+      }
+      --run_left;
+      if ((run_left == 0) != ((H.flags & SWG_ENDRUN) != 0)) return "ENDRUN not on the run's last group";
+    } else {
+      if (run_left != 0) return "global group inside a run";
+      if (H.nph != 1) return "global group with several phases";
+      if (H.aux < 0 || H.aux >= kSwWarps) return "warp rotation";
+    }
+    int64_t di = 0;
+    for (int32_t k = 0; k < H.nph; ++k) {
+      SwPhase PH;
+      std::memcpy(&PH, gb + 32 + 8 * k, sizeof(PH));
+      if (PH.nb < 1) return "empty phase part";
+      if ((PH.flags & SWP_TRI) && (PH.nb != 1 || !res)) return "triangle part";
+      if (res && !(PH.flags & SWP_END)) {
+        // a resident phase split over groups: only its last part ends it
+        if (k + 1 != H.nph) return "unfinished resident phase inside a group";
+      }
+      for (int32_t b = 0; b < PH.nb; ++b, ++di) {
+        SwDesc D;
+        if (H.off_desc + 40 * (di + 1) > G.bytes) return "descriptor outside the group";
+        std::memcpy(&D, gb + H.off_desc + 40 * di, sizeof(D));
+        if (D.off % 16 || D.off < H.off_desc) return "batch offset";
+        if (PH.flags & SWP_TRI) {
+          const int64_t s = D.nrows;
+          if (s < 2 || (s & 1) || 2 * (s / 2) * 1 == 0) return "triangle order";
+          if (D.off + al16(packed_tri(s) * cb) > G.bytes) return "triangle outside the group";
+          if (D.a0 < 0 || D.a0 + s > win_rows) return "triangle rows outside the window rows";
+          if (s * kSwMaxCols * 8 > kSwPartBytes) return "triangle partial sums";
+          continue;
+        }
+        const int64_t end = D.off + D.off_gl + (res ? 0 : al16(4 * (int64_t)D.ngl));
+        if (end > G.bytes) return "batch outside the group";
+        if (D.glog < 0 || D.glog > 5) return "lanes per row";
+        if (!res && (D.ngl < 0 || D.ngl > kSwGather)) return "gather list longer than a warp slice";
+        const uint8_t* bb = gb + D.off;
+        const int32_t* out = (const int32_t*)bb;
+        const int32_t* e0 = (const int32_t*)(bb + D.off_e0);
+        const int16_t* in = (const int16_t*)(bb + D.off_in);
+        const int32_t* gl = (const int32_t*)(bb + D.off_gl);
+        if (e0[0] != 0 || e0[D.nrows] != D.nent) return "row offsets";
+        for (int32_t r = 0; r < D.nrows; ++r) {
+          if (e0[r + 1] < e0[r]) return "row offsets";
+          const int32_t o = out[r] & ~kSwAcc;
+          if (res ? (o < 0 || o >= S.win_slots) : (o < 0 || o >= n + ph.state_len)) return "output slot";
+        }
+        for (int32_t e = 0; e < D.nent; ++e)
+          if (res ? (in[e] < 0 || in[e] >= S.win_slots) : (in[e] < 0 || in[e] >= D.ngl)) return "input slot";
+        for (int32_t q = 0; q < D.ngl && !res; ++q)
+          if (gl[q] < 0 || gl[q] >= n + ph.state_len) return "gathered slot";
+      }
+    }
+  }
+  if (run_left != 0) return "run not closed";
+  return "";
+}
+
 }  // namespace hb
