@@ -499,9 +499,10 @@ struct SwPhase {
 // vector row r < n or n + a state entry), e0[nrows + 1], coef[nent] (complex, the
 // factor's precision), in[nent] (int16: window slot, or position in the gather
 // list), gl[ngl] (int32 global slots of the distinct inputs, global batches
-// only).  Triangle: the packed triangle of order nrows, column by column (lower:
-// rows c..s-1 of column c; upper: rows 0..c), applied in place to window rows
-// a0 .. a0 + nrows - 1.
+// only).  Triangle: a packed lower triangle of order nrows, column by column
+// (rows c..s-1 of column c), applied in place to window rows a0 .. a0 + nrows - 1;
+// an upper triangle U is stored reversed (stored (r, c) = U(s-1-r, s-1-c), with
+// SWP_UPPER: stored row / column i stands for window row a0 + s-1-i).
 struct SwDesc {
   int32_t off;       // byte offset of the batch inside the group image
   int32_t nrows, nent, ngl;

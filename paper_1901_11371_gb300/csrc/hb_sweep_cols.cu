@@ -77,9 +77,6 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned b
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
                ::"r"(su32(dst)), "l"(src), "r"(bytes), "r"(su32(b)) : "memory");
 }
-__device__ __forceinline__ void cw_sync() {   // named barrier 1 among the compute warps
-  asm volatile("bar.sync 1, %0;\n" ::"n"(kSwWarps * 32) : "memory");
-}
 __device__ __forceinline__ void ch_sync() {   // named barrier 2 among the chain warps
   asm volatile("bar.sync 2, %0;\n" ::"n"(kSwChain * 32) : "memory");
 }
@@ -220,12 +217,15 @@ __device__ void run_rows(const SwArgs& a, const SwDesc& D, const char* bb, const
 }
 
 // Sweep-leaf phase: window rows a0 .. a0 + s - 1 replaced by T times them (T the
-// packed triangle), all compute threads (t < nct).  Thread (pair j, column
-// group g) owns rows j and s-1-j (s + 1 entries together) and the columns
-// c = g (mod ncg) of them.  The triangle is not read after the barrier inside.
+// packed triangle), all chain threads (t < nct).  T is stored as a lower
+// triangle, column by column; an upper triangle U is stored reversed (entry
+// (r, c) of the stored triangle is U(s-1-r, s-1-c)), so rev maps the stored
+// rows and columns to window rows s-1-i.  Thread (pair j, column group g) owns
+// stored rows j and s-1-j (s + 1 entries together) and their columns
+// c = g (mod ncg); the lanes of a warp share g and read consecutive entries of
+// one column.  The triangle is not read after the barrier inside.
 template <int NC>
-__device__ void run_tri(const SwDesc& D, bool up, const float2* T, float2* win, float2* part, int t, int nct) {
-  // (t < nct = the chain warps' threads; their barrier separates the two steps)
+__device__ void run_tri(const SwDesc& D, bool rev, const float2* T, float2* win, float2* part, int t, int nct) {
   const int s = D.nrows;
   float2* b = win + (int64_t)D.a0 * NC;
   const int npair = s >> 1;
@@ -238,31 +238,48 @@ __device__ void run_tri(const SwDesc& D, bool up, const float2* T, float2* win, 
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int r = h == 0 ? j : s - 1 - j;
-      float2 acc[NC];
+      constexpr int U = 4;   // independent accumulator chains
+      float2 acc[4][NC];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) acc[c] = make_float2(0.f, 0.f);
-      if (up) {
-        // row r: columns r .. s-1; entry (r, c) at c (c + 1) / 2 + r.  The lanes of a warp
-        // share g and step through the same columns (a predicate skips c < r).
-        for (int c = g; c < s; c += ncg) {
-          if (c >= r) {
-            const float2 m = T[((c * (c + 1)) >> 1) + r];
-            const Cv<NC> v = sm_load<NC>(b + (int64_t)c * NC);
+      for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int cc = 0; cc < NC; ++cc) cmac(acc[cc], m, v.v[cc]);
-          }
+        for (int c = 0; c < NC; ++c) acc[u][c] = make_float2(0.f, 0.f);
+      // entry (r, c) at c s - c (c - 1) / 2 + r - c; from c to c + ncg the offset grows by
+      // d = ncg (s - c) - ncg (ncg + 1) / 2, and d shrinks by ncg^2 per step
+      int c = g;
+      int off = c * s - ((c * (c - 1)) >> 1) + r - c;
+      int d = ncg * (s - c) - ((ncg * (ncg + 1)) >> 1);
+      const int dd = ncg * ncg;
+      for (; c + (U - 1) * ncg <= r; c += U * ncg) {
+        float2 m[U];
+        Cv<NC> v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          m[u] = T[off];
+          const int cc = c + u * ncg;
+          v[u] = sm_load<NC>(b + (int64_t)(rev ? s - 1 - cc : cc) * NC);
+          off += d;
+          d -= dd;
         }
-      } else {
-        // row r: columns 0 .. r; entry (r, c) at c s - c (c - 1) / 2 + r - c
-        for (int c = g; c <= r; c += ncg) {
-          const float2 m = T[c * s - ((c * (c - 1)) >> 1) + r - c];
-          const Cv<NC> v = sm_load<NC>(b + (int64_t)c * NC);
 #pragma unroll
-          for (int cc = 0; cc < NC; ++cc) cmac(acc[cc], m, v.v[cc]);
-        }
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int k = 0; k < NC; ++k) cmac(acc[u][k], m[u], v[u].v[k]);
       }
+      for (; c <= r; c += ncg) {
+        const float2 m = T[off];
+        const Cv<NC> v = sm_load<NC>(b + (int64_t)(rev ? s - 1 - c : c) * NC);
 #pragma unroll
-      for (int cc = 0; cc < NC; ++cc) part[((int64_t)g * s + r) * NC + cc] = acc[cc];
+        for (int k = 0; k < NC; ++k) cmac(acc[0][k], m, v.v[k]);
+        off += d;
+        d -= dd;
+      }
+      const int ro = rev ? s - 1 - r : r;
+#pragma unroll
+      for (int k = 0; k < NC; ++k)
+        part[((int64_t)g * s + ro) * NC + k] =
+            make_float2(acc[0][k].x + acc[1][k].x + acc[2][k].x + acc[3][k].x,
+                        acc[0][k].y + acc[1][k].y + acc[2][k].y + acc[3][k].y);
     }
   }
   ch_sync();
@@ -279,7 +296,7 @@ __device__ void run_tri(const SwDesc& D, bool up, const float2* T, float2* win, 
 }
 
 template <int NC>
-__global__ void __launch_bounds__(kSwThreads, 1) k_sweep_cols(SwArgs a) {
+__global__ void __maxnreg__(112) k_sweep_cols(SwArgs a) {   // 544 threads, one CTA per SM
   extern __shared__ __align__(128) char smem[];
   char* ring = smem;
   float2* win = reinterpret_cast<float2*>(smem + kSwRingBytes);
@@ -376,6 +393,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep_cols(SwArgs a) {
         bool ok = true;
         while (!mb_test_wait(&s_mbar[slot], (unsigned)(g / kSwSlots) & 1u)) {
           if (++spins > a.spin_limit || *(volatile int*)&s_abort) { ok = false; break; }
+          if (spins > 4) __nanosleep(32);   // leave the issue slots to the producer warp
         }
         if (__any_sync(0xffffffffu, !ok)) {
           bad = true;

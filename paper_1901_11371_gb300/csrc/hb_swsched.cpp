@@ -198,8 +198,16 @@ struct Builder {
         D.a0 = B.a0;
         pt.data.resize(pt.data.size() + al16((int64_t)D.nent * cb), 0);
         uint8_t* d = pt.data.data() + D.off;
+        // stored as a lower triangle, column by column; an upper triangle U reversed:
+        // stored (r, c) = U(s-1-r, s-1-c)
         const cplx* T = ph.sl[which].data() + B.tri_off;
-        for (int64_t e = 0; e < D.nent; ++e) coef_at(d + e * cb, T[e]);
+        const int64_t sz = B.tri_n;
+        const bool up = which == 1 || which == 2;
+        for (int64_t c = 0; c < sz; ++c)
+          for (int64_t r = c; r < sz; ++r) {
+            const cplx v = up ? T[tri_off_upper(sz - 1 - r, sz - 1 - c)] : T[tri_off_lower(sz, r, c)];
+            coef_at(d + tri_off_lower(sz, r, c) * cb, v);
+          }
         pt.descs.push_back(D);
         S.batches++;
         continue;
@@ -519,13 +527,14 @@ void host_sweep_sched(const PackedHost& ph, const SwSched& S, cplx* vec) {
         std::memcpy(&D, gb + H.off_desc + 40 * di, sizeof(D));
         const uint8_t* base = gb + D.off;
         if (PH.flags & SWP_TRI) {
+          // lower layout; reversed rows and columns for an upper triangle
           const int64_t sz = D.nrows;
           tmp.assign((size_t)sz, cplx(0.0, 0.0));
-          const bool up = (PH.flags & SWP_UPPER) != 0;
+          const bool rev = (PH.flags & SWP_UPPER) != 0;
           for (int64_t c = 0; c < sz; ++c)
-            for (int64_t r = up ? 0 : c; r < (up ? c + 1 : sz); ++r) {
-              const int64_t off = up ? tri_off_upper(r, c) : tri_off_lower(sz, r, c);
-              tmp[r] += coef(base, off) * win[D.a0 + c];
+            for (int64_t r = c; r < sz; ++r) {
+              const int64_t ro = rev ? sz - 1 - r : r, co = rev ? sz - 1 - c : c;
+              tmp[ro] += coef(base, tri_off_lower(sz, r, c)) * win[D.a0 + co];
             }
           for (int64_t r = 0; r < sz; ++r) win[D.a0 + r] = tmp[r];
           continue;
