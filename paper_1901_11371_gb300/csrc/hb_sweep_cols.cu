@@ -18,13 +18,18 @@
 //     vector rows and a CTA-private butterfly state in global memory: a batch
 //     first gathers its distinct inputs into its warp's slice of the window
 //     (free between runs) in one round trip;
-//   * a butterfly phase is a sparse product in row form: compute warp w takes
-//     the batches w, w + 16, ... of a group; in a batch, groups of 2^glog lanes
-//     share a row (entries strided over the lanes, then a shuffle reduction),
-//     so that short dot products do not serialise on one lane;
+//   * the resident runs -- the long dependent chain -- are executed by four
+//     chain warps (one per scheduler) with their own barrier, so that the
+//     per-phase overhead is paid four times, not twelve; the other compute
+//     warps wait for the run's end; a global phase's batches go round-robin
+//     to all twelve compute warps;
+//   * a butterfly phase is a sparse product in row form; in a batch, groups of
+//     2^glog lanes share a row (entries strided over the lanes, then a shuffle
+//     reduction), so that short dot products do not serialise on one lane;
 //   * a sweep-leaf phase (packed triangle, in place on the window rows) is
-//     taken by all compute warps: pairs of rows (j, s-1-j) times column
-//     groups, partial sums, a barrier, the reduction written back.
+//     taken by all chain warps: pairs of rows (j, s-1-j) times column groups,
+//     four independent accumulation chains, partial sums, a barrier, the
+//     reduction written back.
 // Consecutive phases are separated by one named barrier among the compute
 // warps; the groups of one phase are not.  Every wait is bounded; a warp whose
 // wait gives up stops computing but still meets the barriers up to the end of
@@ -44,6 +49,8 @@ namespace hb {
 namespace {
 
 constexpr int kSwThreads = (kSwWarps + 1) * 32;
+// at most four warps per scheduler: every thread may hold 128 registers
+static_assert((kSwWarps + 1 + 3) / 4 * 128 * 32 <= 16384, "registers per scheduler");
 constexpr int kSwSlots = 64;   // groups in flight per CTA
 constexpr int kSwSmem = kSwRingBytes + kSwWinBytes + kSwPartBytes;
 static_assert(kSwSmem <= 224 * 1024, "dynamic shared memory of the column-partitioned sweep");
@@ -296,7 +303,7 @@ __device__ void run_tri(const SwDesc& D, bool rev, const float2* T, float2* win,
 }
 
 template <int NC>
-__global__ void __maxnreg__(112) k_sweep_cols(SwArgs a) {   // 544 threads, one CTA per SM
+__global__ void __launch_bounds__(kSwThreads, 1) k_sweep_cols(SwArgs a) {
   extern __shared__ __align__(128) char smem[];
   char* ring = smem;
   float2* win = reinterpret_cast<float2*>(smem + kSwRingBytes);
