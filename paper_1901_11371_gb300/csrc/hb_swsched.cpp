@@ -98,7 +98,15 @@ void expand_op(const PackedHost& ph, const FlatOp& f, SlotMap& sm, PhaseRows& P)
       int32_t o;
       if (!two || r < f.split) o = out0(r);
       else o = sm.st(f.out1 + (r - f.split));
-      P.begin_row(sub ? (o | kSwAcc) : o);
+      // subtracting from an output: in the window, add to it in place; in global
+      // memory, read its old value as one more input (coefficient 1), so that the
+      // kernel's store needs no dependent load
+      if (sub && !sm.res) {
+        P.begin_row(o);
+        P.add(o, cplx(1.0, 0.0));
+      } else {
+        P.begin_row(sub ? (o | kSwAcc) : o);
+      }
       for (int b = 0; b < (two ? 2 : 1); ++b) {
         const cplx* Mb = M + (b ? f.m1 : 0);
         const int16_t* Ib = I + (b ? f.i1 : 0);
