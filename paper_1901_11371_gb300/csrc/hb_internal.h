@@ -463,7 +463,8 @@ constexpr int kSwRingBytes = 104 * 1024;     // staging ring of group images
 constexpr int kSwPartBytes = 16 * 1024;      // partial sums of a triangle product
 constexpr int kSwMaxCols = 2;                // right-hand sides per CTA
 constexpr int kSwWinSlots = kSwWinBytes / (kSwMaxCols * 8);   // window slots (complex-FP32 entries per column)
-constexpr int kSwGather = kSwWinSlots / kSwWarps;             // gathered inputs of a global batch (a warp's slice)
+constexpr int kSwGather = kSwWinSlots / (2 * kSwWarps);       // gathered inputs of a global batch (half a warp's
+                                                              // slice: the next batch's gather fills the other half)
 constexpr int kSwBatchBytes = 8 * 1024;      // target data bytes of one resident batch
 constexpr int kSwGlobBytes = 6 * 1024;       // target data bytes of one global batch
 constexpr int kSwGroupBytes = 32 * 1024;     // target bytes of a group

@@ -80,6 +80,18 @@ __device__ __forceinline__ bool mb_test_wait(uint64_t* b, unsigned parity) {
                : "=r"(ok) : "r"(su32(b)), "r"(parity) : "memory");
   return ok != 0;
 }
+// asynchronous global -> shared copy of `bytes` (8 or 16), the first `src_bytes` of
+// them from src and the rest zero
+__device__ __forceinline__ void cp_async(void* dst, const void* src, int bytes, int src_bytes) {
+  if (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(su32(dst)), "l"(src), "r"(src_bytes) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(su32(dst)), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, uint64_t* b) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
                ::"r"(su32(dst)), "l"(src), "r"(bytes), "r"(su32(b)) : "memory");
@@ -144,6 +156,26 @@ __device__ __forceinline__ Cv<NC> sm_load(const float2* p) {
 // CTA-private state entry
 __device__ __forceinline__ float2* gaddr(const SwArgs& a, int32_t s, float2* xb, float2* stp, int nc) {
   return s < a.n ? xb + (int64_t)s * a.R : stp + (int64_t)(s - a.n) * nc;
+}
+
+// NC columns of global slot s into dst (shared, 8 * NC bytes) asynchronously; the
+// columns beyond this CTA's ncol read as zero.  x rows are 16-byte aligned when the
+// row stride and the CTA's first column are even (vec16).
+template <int NC>
+__device__ __forceinline__ void slot_async(const SwArgs& a, int32_t s, float2* dst, float2* xb, float2* stp, int ncol,
+                                           bool vec16) {
+  if (s < a.n) {
+    const float2* src = xb + (int64_t)s * a.R;
+    if (NC == 2 && vec16) {
+      cp_async(dst, src, 16, 8 * ncol);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) cp_async(dst + c, c < ncol ? src + c : src, 8, c < ncol ? 8 : 0);
+    }
+  } else {
+    const float2* src = stp + (int64_t)(s - a.n) * NC;
+    cp_async(dst, src, 8 * NC, 8 * NC);
+  }
 }
 
 // One batch in row form, one warp.  Inputs: `in` (the window for resident
@@ -390,7 +422,8 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep_cols(SwArgs a) {
   } else {
     const int t = threadIdx.x;
     const bool chain = warp < kSwChain;
-    float2* slice = win + (int64_t)warp * kSwGather * NC;   // gather area of global batches
+    float2* slice = win + (int64_t)warp * 2 * kSwGather * NC;   // gather area of global batches (two halves)
+    const bool vec16 = NC == 2 && (a.R % 2) == 0 && (lb % 2) == 0;
     bool bad = false;   // warp-uniform; after a failed wait the warp only follows the barriers
     // wait for group g (bounded); returns its image (ring, or global memory after a failure)
     auto group = [&](int64_t g) -> const char* {
@@ -442,11 +475,10 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep_cols(SwArgs a) {
           const SwDesc* desc = reinterpret_cast<const SwDesc*>(gimg + H.off_desc);
           if (H.flags & SWG_BEGIN) {
             if (!bad) {
-              const int nrow = H.beg_hi - H.beg_lo;
-              for (int e = ct; e < nrow * NC; e += nct) {
-                const int r = e / NC, c = e % NC;
-                win[e] = c < ncol ? __ldcg(xb + (int64_t)(H.beg_lo + r) * a.R + c) : make_float2(0.f, 0.f);
-              }
+              // the run's rows, all in flight at once
+              for (int r = ct; r < H.beg_hi - H.beg_lo; r += nct) slot_async<NC>(a, H.beg_lo + r, win + r * NC, xb, stp, ncol, vec16);
+              cp_commit();
+              cp_wait<0>();
             }
             ch_sync();
           }
@@ -503,37 +535,30 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep_cols(SwArgs a) {
         const SwPhase PH = *reinterpret_cast<const SwPhase*>(gimg + 32);
         const SwDesc* desc = reinterpret_cast<const SwDesc*>(gimg + H.off_desc);
         if (!bad) {
-          for (int b = (warp - H.aux + kSwWarps) % kSwWarps; b < PH.nb; b += kSwWarps) {
-            const SwDesc D = desc[b];
-            const char* bb = gimg + D.off;
-            // gather the batch's distinct inputs into the warp's slice: eight loads in
-            // flight per lane before their stores
-            const int32_t* gl = reinterpret_cast<const int32_t*>(bb + D.off_gl);
-            for (int k0 = 0; k0 < D.ngl; k0 += 8 * 32) {
-              float2 v[8][NC];
-#pragma unroll
-              for (int u = 0; u < 8; ++u) {
-                const int kk = k0 + u * 32 + lane;
-                if (kk < D.ngl) {
-                  const int32_t sl = gl[kk];
-                  const float2* src = gaddr(a, sl, xb, stp, NC);
-                  const int nc = sl < a.n ? ncol : NC;
-#pragma unroll
-                  for (int c = 0; c < NC; ++c) v[u][c] = c < nc ? __ldcg(src + c) : make_float2(0.f, 0.f);
-                }
-              }
-#pragma unroll
-              for (int u = 0; u < 8; ++u) {
-                const int kk = k0 + u * 32 + lane;
-                if (kk < D.ngl) {
-#pragma unroll
-                  for (int c = 0; c < NC; ++c) slice[kk * NC + c] = v[u][c];
-                }
-              }
+          // this warp's batches b0, b0 + 12, ...: the gather of the next one (cp.async into
+          // the other half of the warp's slice) is in flight while this one is computed
+          const int b0 = (warp - H.aux + kSwWarps) % kSwWarps;
+          auto gather = [&](int b, float2* dst) {
+            const SwDesc& D = desc[b];
+            const int32_t* gl = reinterpret_cast<const int32_t*>(gimg + D.off + D.off_gl);
+            for (int k = lane; k < D.ngl; k += 32) slot_async<NC>(a, gl[k], dst + k * NC, xb, stp, ncol, vec16);
+            cp_commit();
+          };
+          int buf = 0;
+          if (b0 < PH.nb) gather(b0, slice);
+          for (int b = b0; b < PH.nb; b += kSwWarps) {
+            const int bn = b + kSwWarps;
+            if (bn < PH.nb) {
+              gather(bn, slice + (buf ^ 1) * kSwGather * NC);
+              cp_wait<1>();
+            } else {
+              cp_wait<0>();
             }
             __syncwarp();
-            run_rows<NC, false>(a, D, bb, slice, win, xb, stp, ncol, lane);
+            const SwDesc D = desc[b];
+            run_rows<NC, false>(a, D, gimg + D.off, slice + buf * kSwGather * NC, win, xb, stp, ncol, lane);
             __syncwarp();
+            buf ^= 1;
           }
         }
         if (PH.flags & SWP_END) {
