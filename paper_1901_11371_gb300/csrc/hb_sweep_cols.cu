@@ -192,68 +192,64 @@ __device__ void run_rows(const SwArgs& a, const SwDesc& D, const char* bb, const
   const int q = lane >> glog, l = lane & (G - 1);
   for (int base = 0; base < D.nrows; base += ng) {
     const int r = base + q;
-    const bool live = r < D.nrows;
-    // the row's bounds and output slot: independent loads, issued together
-    int ea = 0, eb = 0, o = 0;
-    if (live) {
-      ea = e0[r];
-      eb = e0[r + 1];
-      o = out[r];
-    }
-    float2 acc[4][NC];
+    float2 acc[NC], acc2[NC];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int c = 0; c < NC; ++c) acc[c] = acc2[c] = make_float2(0.f, 0.f);
+    if (r < D.nrows) {
+      const int ea = e0[r], eb = e0[r + 1];
+      int e = ea + l;
+      // two independent accumulator chains
+      for (; e + G < eb; e += 2 * G) {
+        const float2 m0 = cf[e], m1 = cf[e + G];
+        const Cv<NC> v0 = sm_load<NC>(in + (int)ix[e] * NC);
+        const Cv<NC> v1 = sm_load<NC>(in + (int)ix[e + G] * NC);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) acc[u][c] = make_float2(0.f, 0.f);
-    // four entries per step: their coefficients and input slots first, then the
-    // four inputs, then four independent accumulation chains
-    for (int e = ea + l; e < eb; e += 4 * G) {
-      float2 m[4];
-      int id[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const bool ok = e + u * G < eb;
-        m[u] = ok ? cf[e + u * G] : make_float2(0.f, 0.f);
-        id[u] = ok ? (int)ix[e + u * G] : 0;
-      }
-      Cv<NC> v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = sm_load<NC>(in + id[u] * NC);
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (e + u * G < eb) {
-#pragma unroll
-          for (int c = 0; c < NC; ++c) cmac(acc[u][c], m[u], v[u].v[c]);
+        for (int c = 0; c < NC; ++c) {
+          cmac(acc[c], m0, v0.v[c]);
+          cmac(acc2[c], m1, v1.v[c]);
         }
+      }
+      if (e < eb) {
+        const float2 m0 = cf[e];
+        const Cv<NC> v0 = sm_load<NC>(in + (int)ix[e] * NC);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) cmac(acc[c], m0, v0.v[c]);
+      }
     }
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      acc[0][c].x += acc[1][c].x + acc[2][c].x + acc[3][c].x;
-      acc[0][c].y += acc[1][c].y + acc[2][c].y + acc[3][c].y;
+      acc[c].x += acc2[c].x;
+      acc[c].y += acc2[c].y;
     }
     // sum over the group's lanes (groups are aligned runs of G lanes)
     for (int d = G >> 1; d > 0; d >>= 1) {
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        acc[0][c].x += __shfl_xor_sync(0xffffffffu, acc[0][c].x, d);
-        acc[0][c].y += __shfl_xor_sync(0xffffffffu, acc[0][c].y, d);
+        acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, d);
+        acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, d);
       }
     }
-    if (l == 0 && live) {
+    if (l == 0 && r < D.nrows) {
+      const int32_t o = out[r];
       const bool add = (o & kSwAcc) != 0;
       const int32_t s = o & ~kSwAcc;
       if (RES) {
         float2* d = win + (int64_t)s * NC;
 #pragma unroll
-        for (int c = 0; c < NC; ++c)
-          d[c] = add ? make_float2(d[c].x + acc[0][c].x, d[c].y + acc[0][c].y) : acc[0][c];
+        for (int c = 0; c < NC; ++c) d[c] = add ? make_float2(d[c].x + acc[c].x, d[c].y + acc[c].y) : acc[c];
       } else {
-        // global rows never add (the old value is one of their gathered inputs)
         float2* d = gaddr(a, s, xb, stp, NC);
         const int nc = s < a.n ? ncol : NC;
 #pragma unroll
         for (int c = 0; c < NC; ++c)
-          if (c < nc) d[c] = acc[0][c];
+          if (c < nc) {
+            if (add) {
+              const float2 cur = __ldcg(d + c);
+              d[c] = make_float2(cur.x + acc[c].x, cur.y + acc[c].y);
+            } else {
+              d[c] = acc[c];
+            }
+          }
       }
     }
   }
