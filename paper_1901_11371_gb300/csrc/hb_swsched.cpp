@@ -643,6 +643,7 @@ const char* check_sweep_sched(const PackedHost& ph, const SwSched& S) {
         if (e0[0] != 0 || e0[D.nrows] != D.nent) return "row offsets";
         for (int32_t r = 0; r < D.nrows; ++r) {
           if (e0[r + 1] < e0[r]) return "row offsets";
+          if (!res && (out[r] & kSwAcc)) return "global row that adds in place";
           const int32_t o = out[r] & ~kSwAcc;
           if (res ? (o < 0 || o >= S.win_slots) : (o < 0 || o >= n + ph.state_len)) return "output slot";
         }
