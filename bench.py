@@ -185,6 +185,8 @@ class ClockSampler:
 MEASURED_TRAFFIC = {
     # profiles/k_sweep_coop_semicircle_N262144_traffic.md (autotuned 256-column launch)
     "k_sweep": {"sha": "b4653ac2957de173", "bytes": 2247096576 + 2686350592},
+    # profiles/k_sweep_cols_semicircle_N262144.md (256-column launch, 128 CTAs x 2 columns)
+    "k_sweep_cols": {"sha": "f870a86e523f19df", "bytes": 2338996736 + 2601327104},
 }
 KERNEL_SOURCES = {
     "k_sweep": ["hb_sweep_impl.cuh", "hb_sweep.cu", "hb_sweep_f32w.cu", "hb_sweep_launch.h"],
