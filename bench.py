@@ -427,77 +427,9 @@ def run_kernels(args):
     print(json.dumps(out))
 
 
-def run_scale(args):
-    """The scale form: the spiral of 209,715.2 wavelengths at N = 4,194,304 (leaf 128, eps 1e-5,
-    complex-FP32 factors), 16 plane waves as one block.  Construction is timed apart; then the
-    single-column apply and the 16-column apply and sweeps (CUDA events, against the measured
-    HBM bandwidth), and one FP64-refined FGMRES(30) solve of the 16 columns (iterations,
-    residual reached, solves/s).  One JSON line."""
-    import torch
-
-    import paper_1901_11371_gb300 as hb
-    from paper_1901_11371_gb300 import build as hb_build
-    hb_build.build()
-    wl = W.SPIRAL_N4194304
-    R = 16
-    g = hb.hb_geometry(wl.kind, wl.params, wl.n)
-    t0 = time.perf_counter()
-    f = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_C64)
-    t_build = time.perf_counter() - t0
-    st = hb.hb_factor_info(f)
-    hbm, src = _peaks()
-    stream = torch.cuda.current_stream()
-
-    def timed(fn, reps, warm=2):
-        for _ in range(warm):
-            fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
-
-    x1 = torch.randn(wl.n, dtype=torch.complex64, device="cuda")
-    ms_a1 = timed(lambda: hb.hb_apply(f, x1), 10)
-    ms_l1 = timed(lambda: hb.hb_lower_solve(f, x1), 2, 1)
-    tuned = hb.hb_autotune(f, R)
-    xr = torch.randn((R, wl.n), dtype=torch.complex64, device="cuda")
-    ms_a = timed(lambda: hb.hb_apply(f, xr), 3, 1)
-    ms_l = timed(lambda: hb.hb_lower_solve(f, xr), 2, 1)
-    ms_u = timed(lambda: hb.hb_upper_solve(f, xr), 2, 1)
-    phis = W.incidence_angles_deg(wl)
-    b = hb.hb_rhs_plane_wave(f, phis)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    x, info = hb.hb_gmres(f, b, rtol=1e-6, restart=30, maxit=args.scale_maxit, check=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_solve = e0.elapsed_time(e1)
-    vec = 2 * wl.n * (R - 1) * 8
-    nlog = wl.n * math.log2(wl.n) ** 2
-    out = {"mode": "scale", "workload": wl.name, "n": wl.n, "leaf": wl.leaf, "eps": wl.eps, "nrhs": R,
-           "form": "complex64 factors, FP64 FGMRES(30) + IR",
-           "build_s": round(t_build, 1), "device_bytes": st["device_bytes"],
-           "device_bytes_per_N_log2N_sq": st["device_bytes"] / nlog, "kmax": st["kmax"], "kavg": round(st["kavg"], 2),
-           "apply1_ms": ms_a1, "apply1_GBps": st["apply_bytes"] / ms_a1 / 1e6,
-           "apply1_frac": st["apply_bytes"] / ms_a1 / 1e6 / hbm,
-           "lower1_ms": ms_l1, "sweep_kernel_16": "column-partitioned" if tuned == 0 else f"cooperative, grid_min {tuned}",
-           "apply16_ms": ms_a, "apply16_GBps": (st["apply_bytes"] + vec) / ms_a / 1e6,
-           "lower16_ms": ms_l, "upper16_ms": ms_u, "lower16_GBps": (st["lower_bytes"] + vec) / ms_l / 1e6,
-           "solve_ms": ms_solve, "iters": info["iters"], "converged": info["converged"], "ir_steps": info["ir_steps"],
-           "true_rel_res": info["true_rel_res"], "status": info.get("status"),
-           "solves_per_s": R / (ms_solve / 1e3), "peak_GBps": hbm, "peak_source": src}
-    print(json.dumps(out))
-
-
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--mode", default="solve", choices=["solve", "kernels", "scale"])
-    ap.add_argument("--scale-maxit", type=int, default=300, help="scale mode: FGMRES iteration limit")
+    ap.add_argument("--mode", default="solve", choices=["solve", "kernels"])
     ap.add_argument("--workload", default="spiral", choices=["spiral", "semicircle", "strips", "strip"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--form", default="c64", choices=["c64", "c128", "split"])
@@ -513,9 +445,6 @@ def main():
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    if args.mode == "scale":
-        run_scale(args)
-        return
     if args.mode == "kernels":
         run_kernels(args)
         return
