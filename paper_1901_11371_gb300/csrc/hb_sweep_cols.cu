@@ -379,6 +379,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep_cols(SwArgs a) {
         const SwGroup& G = s_grec[g & 31];
         const int bytes = G.bytes;
         long long spins = 0;
+        unsigned nap = 32;   // back-off while the ring is full (the compute warps keep the issue slots)
         for (;;) {
           while (oldest < g && *(volatile int*)&s_cnt[oldest % kSwSlots] == kSwWarps) ++oldest;
           __threadfence_block();
@@ -401,7 +402,8 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep_cols(SwArgs a) {
             atomicExch(&s_abort, 1);
             break;
           }
-          __nanosleep(20);
+          __nanosleep(nap);
+          if (nap < 256) nap <<= 1;
         }
         if (off >= 0) {
           const int slot = (int)(g % kSwSlots);
