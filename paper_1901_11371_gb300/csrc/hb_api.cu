@@ -149,6 +149,9 @@ int upload_factor(const PackedHost& ph, const HostFactor& hf, const Geometry& g,
       if ((rc = up(plan.batches, &dp.batches, st, df.device_bytes))) return rc;
       if ((rc = up(plan.cta_batch, &dp.cta_batch, st, df.device_bytes))) return rc;
       if ((rc = up(plan.image, &dp.image, st, df.device_bytes))) return rc;
+      HB_CU(cudaMalloc((void**)&dp.done, sizeof(int) * std::max<size_t>(plan.batches.size(), 1)));
+      HB_CU(cudaMemsetAsync(dp.done, 0, sizeof(int) * std::max<size_t>(plan.batches.size(), 1), st));
+      df.device_bytes += (int64_t)(sizeof(int) * plan.batches.size());
       HB_CU(cudaStreamSynchronize(st));
       dp.nphase = plan.nphase;
       dp.grid = sms;
@@ -240,7 +243,7 @@ void free_factor(DevFactor& df) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (DevPlan& dp : df.plan) {
-    void* pp[] = {dp.batches, dp.cta_batch, dp.image};
+    void* pp[] = {dp.batches, dp.cta_batch, dp.image, dp.done};
     for (void* p : pp)
       if (p) cudaFree(p);
   }

@@ -21,7 +21,13 @@
 //     a skeleton or candidate vector, a row of y; an exit row sums the depths'
 //     contributions in order), computing from shared memory and writing to
 //     global memory, and the warp releases the ring area;
-//   * between phases the compute warps meet at a bounded grid barrier.
+//   * there is no grid barrier between the phases: every batch lists the
+//     batches (of earlier phases, on any CTA) that wrote the entries it
+//     gathers, waits (bounded) until their completion flags carry this
+//     launch's epoch, and sets its own flag when its outputs are written, so
+//     a subtree's butterfly steps start as soon as its inputs exist.  Every
+//     CTA runs its batches in phase order and all CTAs are resident
+//     (cooperative launch), so the waits always end.
 // Every wait is bounded; a wait that gives up raises the factor's error
 // flag (reported by hb_status / the solvers) and the kernel returns after a
 // second bounded wait for the copies still in flight.
@@ -76,15 +82,6 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned b
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
                ::"r"(su32(dst)), "l"(src), "r"(bytes), "r"(su32(b)) : "memory");
 }
-__device__ __forceinline__ void cw_sync() {   // named barrier 1 among the compute warps
-  asm volatile("bar.sync 1, %0;\n" ::"n"(kA1Cw * 32) : "memory");
-}
-__device__ __forceinline__ bool cw_red_or(bool v) {
-  unsigned r;
-  asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
-               : "=r"(r) : "r"((unsigned)v), "n"(kA1Cw * 32) : "memory");
-  return r != 0;
-}
 __device__ __forceinline__ unsigned ld_acq(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
@@ -101,43 +98,12 @@ struct A1Args {
   void* y;
   void* st;
   int64_t n0;
-  GridBar* gb;        // count / generation / abort flag of this kernel's grid barrier
+  GridBar* gb;        // abort flag of this launch (err), shared by the CTAs
+  int* done;          // per batch: the epoch of the launch that completed it
+  int epoch;
   int* err_out;       // the factor's sticky error flag (hb_status)
   long long spin_limit;
 };
-
-// Grid barrier among the compute warps (the producer does not take part).
-__device__ bool a1_grid_sync(const A1Args& a, unsigned& gen, int* s_ok) {
-  // the CTA barrier orders every compute thread's writes before thread 0's
-  // device-scope fence (fences are cumulative), which publishes them
-  cw_sync();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    int ok = 1;
-    const unsigned g = gen;
-    const unsigned old = atomicAdd(&a.gb->count, 1u);
-    if (old == gridDim.x - 1) {
-      a.gb->count = 0;
-      __threadfence();
-      atomicExch(&a.gb->gen, g + 1);
-    } else {
-      long long spins = 0;
-      while (ld_acq(&a.gb->gen) == g) {
-        if (++spins > a.spin_limit || *(volatile int*)&a.gb->err) { ok = 0; break; }
-        __nanosleep(32);
-      }
-    }
-    if (!ok) {
-      atomicExch(&a.gb->err, 1);
-      atomicExch(a.err_out, 1);
-    }
-    __threadfence();
-    *s_ok = ok && !*(volatile int*)&a.gb->err;
-  }
-  gen++;
-  cw_sync();
-  return *(volatile int*)s_ok != 0;
-}
 
 // ---------------------------------------------------------------------------
 // Row-parallel execution of a batch by one warp.  Every task of the batch
@@ -343,7 +309,7 @@ __global__ void __launch_bounds__(kA1Threads, 1) k_apply1(A1Args a) {
   __shared__ int s_bdone[kA1Slots];               // q + 1 once batch q (slot q % kA1Slots) is consumed
   __shared__ __align__(8) uint64_t s_mbar[kA1Slots];
   __shared__ __align__(16) A1Batch s_brec[32];    // the producer's window of batch records
-  __shared__ int s_abort, s_issued, s_ok;
+  __shared__ int s_abort, s_issued;
   __shared__ int s_pre[kA1Cw][kA1MaxTasks + 1];   // per-warp row offsets of a batch's tasks
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int b0 = a.cta_batch[blockIdx.x], b1 = a.cta_batch[blockIdx.x + 1];
@@ -414,48 +380,54 @@ __global__ void __launch_bounds__(kA1Threads, 1) k_apply1(A1Args a) {
     __syncwarp();
   } else {
     // ---- compute warp: its batches q = warp, warp + kA1Cw, ... (in phase order)
-    unsigned gen = 0;
     bool bad = false;   // uniform within the warp
-    int q = warp;
-    A1Batch B;
-    if (q < nb) B = a.batches[b0 + q]; else B.phase = 0x7fffffff;
-    for (int p = 0; p < a.nphase; ++p) {
-      while (!bad && B.phase == p) {
-        A1Batch Bn;   // the warp's next batch record, loaded while this one runs
-        if (q + kA1Cw < nb) Bn = a.batches[b0 + q + kA1Cw]; else Bn.phase = 0x7fffffff;
-        uint64_t* mb = &s_mbar[q % kA1Slots];
-        const unsigned par = (unsigned)(q / kA1Slots) & 1u;
-        long long spins = 0;
-        bool w_ok = true;
-        while (!mb_try_wait(mb, par)) {
-          if (++spins > a.spin_limit || *(volatile int*)&s_abort) { w_ok = false; break; }
-        }
-        if (__any_sync(0xffffffffu, !w_ok)) { bad = true; break; }
-        const char* area = ring + s_off[q % kA1Slots];
-        const uint32_t* gl = (const uint32_t*)(area + B.gl_off);
-        C* sv = (C*)(ring + s_off[q % kA1Slots] + B.vec_off);
-        const C* xv = (const C*)a.x;
-        const C* yv = (const C*)a.y;
-        const C* stv = (const C*)a.st;
-        for (int e = lane; e < B.nvec; e += 32) {
-          const uint32_t s = gl[e];
-          const C* src = ((s & kA1FromY) == kA1FromY) ? yv + (s & 0x3FFFFFFFu)
-                         : (s & kA1FromX) ? xv + (s & 0x3FFFFFFFu) : stv + s;
-          sv[e] = ldcg1(src);
-        }
-        __syncwarp();
-        run_batch<T, F>(a, B, area, sv, s_pre[warp], lane);
-        if (lane == 0) {
-          __threadfence_block();
-          *(volatile int*)&s_bdone[q % kA1Slots] = q + 1;   // releases the batch's slot and ring area
-        }
-        q += kA1Cw;
-        B = Bn;
+    for (int q = warp; q < nb && !bad; q += kA1Cw) {
+      const A1Batch B = a.batches[b0 + q];
+      uint64_t* mb = &s_mbar[q % kA1Slots];
+      const unsigned par = (unsigned)(q / kA1Slots) & 1u;
+      long long spins = 0;
+      bool w_ok = true;
+      while (!mb_try_wait(mb, par)) {
+        if (++spins > a.spin_limit || *(volatile int*)&s_abort) { w_ok = false; break; }
       }
-      if (cw_red_or(bad)) { bad = true; break; }   // uniform among the compute warps (and their barrier)
-      if (p + 1 < a.nphase && !a1_grid_sync(a, gen, &s_ok)) { bad = true; break; }
+      if (__any_sync(0xffffffffu, !w_ok)) { bad = true; break; }
+      const char* area = ring + s_off[q % kA1Slots];
+      // the producers of the entries this batch gathers (lanes in parallel)
+      const int32_t* dep = (const int32_t*)(area + B.dep_off);
+      for (int k = lane; k < B.ndep; k += 32) {
+        const unsigned* fl = (const unsigned*)(a.done + dep[k]);
+        spins = 0;
+        while (ld_acq(fl) != (unsigned)a.epoch) {
+          if (++spins > a.spin_limit || *(volatile int*)&a.gb->err || *(volatile int*)&s_abort) { w_ok = false; break; }
+          __nanosleep(32);
+        }
+        if (!w_ok) break;
+      }
+      if (__any_sync(0xffffffffu, !w_ok)) { bad = true; break; }
+      const uint32_t* gl = (const uint32_t*)(area + B.gl_off);
+      C* sv = (C*)(ring + s_off[q % kA1Slots] + B.vec_off);
+      const C* xv = (const C*)a.x;
+      const C* yv = (const C*)a.y;
+      const C* stv = (const C*)a.st;
+      for (int e = lane; e < B.nvec; e += 32) {
+        const uint32_t s = gl[e];
+        const C* src = ((s & kA1FromY) == kA1FromY) ? yv + (s & 0x3FFFFFFFu)
+                       : (s & kA1FromX) ? xv + (s & 0x3FFFFFFFu) : stv + s;
+        sv[e] = ldcg1(src);
+      }
+      __syncwarp();
+      run_batch<T, F>(a, B, area, sv, s_pre[warp], lane);
+      __syncwarp();
+      if (lane == 0) {
+        // outputs first (the warp's writes, ordered by the warp barrier and this
+        // cumulative fence), then the completion flag
+        __threadfence();
+        asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(a.done + b0 + q), "r"((unsigned)a.epoch) : "memory");
+        __threadfence_block();
+        *(volatile int*)&s_bdone[q % kA1Slots] = q + 1;   // releases the batch's slot and ring area
+      }
     }
-    if (bad && threadIdx.x == 0) {
+    if (bad && lane == 0) {
       atomicExch(&s_abort, 1);
       atomicExch(a.err_out, 1);
       atomicExch(&a.gb->err, 1);
@@ -479,7 +451,7 @@ __global__ void __launch_bounds__(kA1Threads, 1) k_apply1(A1Args a) {
 
 template <class T, class F>
 int launch1(const DevFactor& df, bool adj, const void* x, void* y, void* st, cudaStream_t s) {
-  const DevPlan& pl = df.plan[adj ? 1 : 0];
+  DevPlan& pl = const_cast<DevPlan&>(df.plan[adj ? 1 : 0]);   // the epoch counter advances per launch
   auto kern = k_apply1<T, F>;
   static bool attr_done = false;
   if (!attr_done) {
@@ -497,6 +469,8 @@ int launch1(const DevFactor& df, bool adj, const void* x, void* y, void* st, cud
   a.st = st;
   a.n0 = df.n0;
   a.gb = (GridBar*)df.abar;
+  a.done = pl.done;
+  a.epoch = ++pl.epoch;
   a.err_out = &((GridBar*)df.bar)->err;
   a.spin_limit = df.spin_limit;
   if (cudaMemsetAsync(df.abar, 0, sizeof(GridBar), s) != cudaSuccess) return HB_ECUDA;

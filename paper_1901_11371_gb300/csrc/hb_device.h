@@ -18,6 +18,8 @@ struct DevPlan {
   int grid = 0;          // CTAs the plan was cut for (the device's SM count at upload)
   bool ok = false;
   int64_t nbatch = 0;
+  int* done = nullptr;   // per batch: the epoch of the launch that completed it (zeroed at upload)
+  int epoch = 0;         // the last launch's epoch
 };
 // Shared-memory staging ring of the persistent apply (bytes per CTA).
 constexpr int kA1RingBytes = 200 * 1024;

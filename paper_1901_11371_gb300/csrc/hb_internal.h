@@ -245,10 +245,11 @@ struct A1Batch {
   int32_t npar;        // the first npar ops (of ENTER / ITEM tasks) are independent: one warp each;
                        // the tasks from task0 + nptask on (DLEAF / EXIT) take one warp per task
   int32_t nptask;
-  int32_t pad;
+  int32_t ndep;        // batches (plan indices) whose outputs this batch reads: it waits for them
   int64_t gl_src;      // first gather-list entry in ApplyPlan::gl
   int64_t img;         // byte offset of the batch's image (its first tma_bytes bytes, ready to copy)
-  int64_t pad2;
+  int32_t dep_off;     // byte offset of the ndep producer indices (int32) inside the area
+  int32_t dep_src;     // first of them in ApplyPlan::deps
 };
 static_assert(sizeof(A1Task) == 16, "task record");
 static_assert(sizeof(A1Batch) == 80, "batch record");
@@ -267,6 +268,7 @@ struct ApplyPlan {
   std::vector<A1Batch> batches;
   std::vector<int32_t> cta_batch;   // [G + 1]: batches of CTA g are [cta_batch[g], cta_batch[g+1])
   std::vector<uint32_t> gl;         // gather lists of all batches
+  std::vector<int32_t> deps;        // producer batches of all batches (A1Batch::dep_src)
   // Batch images: for every batch, in plan order, the bytes the producer copies into its
   // staging area (task and op records, factor and index blocks in the factor's element
   // type, gather list), so that one bulk copy fills a batch.

@@ -322,17 +322,78 @@ void build_apply_plan(const PackedHost& ph, const HostFactor& hf, bool adj, int 
       B.nvec = nvec;
       B.gl_src = (int64_t)plan.gl.size() - (int64_t)((nvec + 3) / 4 * 4);
       off += a16(4 * (int64_t)nvec);
-      B.tma_bytes = (int32_t)off;
-      B.vec_off = (int32_t)off;
-      off += 16 * (int64_t)nvec;
-      B.area_bytes = (int32_t)a16(off);
-      if (B.area_bytes > max_area) plan.ok = false;
-      plan.max_area = std::max(plan.max_area, B.area_bytes);
+      B.dep_off = (int32_t)off;   // producer list, sized below
       plan.batches.push_back(B);
     }
   }
   plan.cta_batch[(size_t)G] = (int32_t)plan.batches.size();
   for (int i = 0; i < 16; ++i) plan.gl.push_back(0);     // tail: 16-byte bulk copies stay inside
+  // ---- producers: a batch waits only for the batches (of earlier phases, any CTA) that
+  // wrote the state entries and y rows it gathers, instead of for every CTA at a grid
+  // barrier.  Writers are tracked phase by phase (the last writer before the phase).
+  {
+    const int64_t nb = (int64_t)plan.batches.size();
+    std::vector<std::vector<int32_t>> byph((size_t)plan.nphase);
+    for (int64_t b = 0; b < nb; ++b) byph[(size_t)plan.batches[(size_t)b].phase].push_back((int32_t)b);
+    std::vector<int32_t> wst((size_t)std::max<int64_t>(ph.state_len, 1), -1), wy((size_t)ph.n, -1);
+    std::vector<std::vector<int32_t>> dl((size_t)nb);
+    for (int p = 0; p < plan.nphase; ++p) {
+      for (int32_t b : byph[(size_t)p]) {
+        const A1Batch& B = plan.batches[(size_t)b];
+        std::vector<int32_t>& d = dl[(size_t)b];
+        for (int32_t e = 0; e < B.nvec; ++e) {
+          const uint32_t s = plan.gl[(size_t)(B.gl_src + e)];
+          int32_t w = -1;
+          if ((s & kA1FromY) == kA1FromY) w = wy[(size_t)(s & 0x3FFFFFFFu)];
+          else if (!(s & kA1FromX)) w = wst[(size_t)s];
+          if (w >= 0) d.push_back(w);
+        }
+        std::sort(d.begin(), d.end());
+        d.erase(std::unique(d.begin(), d.end()), d.end());
+      }
+      for (int32_t b : byph[(size_t)p]) {
+        const A1Batch& B = plan.batches[(size_t)b];
+        auto st_range = [&](int64_t a, int64_t c) { for (int64_t i = a; i < a + c && i < (int64_t)wst.size(); ++i) wst[(size_t)i] = b; };
+        auto y_range = [&](int64_t a, int64_t c) { for (int64_t i = a; i < a + c && i < ph.n; ++i) wy[(size_t)i] = b; };
+        for (int32_t t = B.task0; t < B.task0 + B.ntasks; ++t) {
+          const A1Task& T = plan.tasks[(size_t)t];
+          if (T.kind == 3) {   // exit: the leaf's n0 rows of y
+            y_range(plan.ops[(size_t)(T.op0 + T.nops - 1)].out0, n0);
+            continue;
+          }
+          for (int32_t o = T.op0; o < T.op0 + T.nops; ++o) {
+            const FlatOp& f = plan.ops[(size_t)o];
+            const bool fadj = (f.flags & FF_ADJ) != 0;
+            if (f.kind == FK_GATHER) {
+              st_range(f.out0, f.k0);
+              if (f.flags & FF_TWO) st_range(f.out1, f.k1);
+            } else if (f.kind == FK_SCATTER) {
+              const bool two = (f.flags & FF_TWO) != 0;
+              st_range(f.out0, two ? f.split : f.c0);
+              if (two) st_range(f.out1, f.c0 - f.split);
+            } else if (f.kind == FK_MIDDLE) {
+              st_range(f.out0, fadj ? f.c0 : f.k0);
+            } else if (f.kind == FK_DLEAF) {
+              y_range(f.out0, fadj ? f.k1 : n0);
+            }
+          }
+        }
+      }
+    }
+    for (int64_t b = 0; b < nb; ++b) {
+      A1Batch& B = plan.batches[(size_t)b];
+      B.dep_src = (int32_t)plan.deps.size();
+      B.ndep = (int32_t)dl[(size_t)b].size();
+      for (int32_t w : dl[(size_t)b]) plan.deps.push_back(w);
+      int64_t off = B.dep_off + a16(4 * (int64_t)B.ndep);
+      B.tma_bytes = (int32_t)off;
+      B.vec_off = (int32_t)off;
+      off += 16 * (int64_t)B.nvec;
+      B.area_bytes = (int32_t)a16(off);
+      if (B.area_bytes > max_area) plan.ok = false;
+      plan.max_area = std::max(plan.max_area, B.area_bytes);
+    }
+  }
   if (plan.ok) plan.ok = check_apply_plan(plan, ph, fes, max_area);
   if (!plan.ok) return;
   // ---- batch images
@@ -371,6 +432,7 @@ void build_apply_plan(const PackedHost& ph, const HostFactor& hf, bool adj, int 
         std::memcpy(d + a16((int64_t)f.melems * fes), &ph.ipool[(size_t)f.ioff], 2 * (size_t)f.ielems);
     }
     std::memcpy(base + B.gl_off, &plan.gl[(size_t)B.gl_src], 4 * (size_t)B.nvec);
+    if (B.ndep > 0) std::memcpy(base + B.dep_off, &plan.deps[(size_t)B.dep_src], 4 * (size_t)B.ndep);
   }
 }
 
@@ -425,6 +487,14 @@ bool check_apply_plan(const ApplyPlan& plan, const PackedHost& ph, int fes, int 
       }
       if (op_next != B.op0 + B.nops || bytes != B.gl_off) return false;
       if (B.nptask < 0 || B.nptask > B.ntasks || B.npar < 0 || B.npar > B.nops) return false;
+      // producer list: right after the gather list, earlier phases only
+      if (B.dep_off != B.gl_off + a16(4 * (int64_t)B.nvec) || B.ndep < 0) return false;
+      if (B.dep_off + 4 * (int64_t)B.ndep > B.tma_bytes || B.vec_off != B.tma_bytes) return false;
+      if (B.dep_src < 0 || B.dep_src + (int64_t)B.ndep > (int64_t)plan.deps.size()) return false;
+      for (int32_t k = 0; k < B.ndep; ++k) {
+        const int32_t w = plan.deps[(size_t)(B.dep_src + k)];
+        if (w < 0 || w >= (int32_t)plan.batches.size() || plan.batches[(size_t)w].phase >= B.phase) return false;
+      }
       if (B.nptask < B.ntasks && plan.tasks[(size_t)(B.task0 + B.nptask)].op0 != B.op0 + B.npar) return false;
     }
   }
