@@ -674,9 +674,14 @@ int apply_internal(hb_factor_t f, Prec p, bool adj, const void* x, void* y, int6
   size_t es = (p == PREC_F32) ? 8 : 16;
   void* state = f->ws.get(WS_STATE, (size_t)f->df.state_len * R * es);
   if (!state) { set_error("apply: cannot allocate state workspace"); return HB_ENOMEM; }
+  // FP64-accurate arithmetic on complex-FP32 factors for many columns: double-float
+  const bool dd = p == PREC_F32_ACC64 && f->df.form != HB_C128 && apply_dd_ready(R);
+  void* xdd = dd ? f->ws.get(WS_DD0, (size_t)f->df.n * R * 16) : nullptr;
+  void* ydd = dd ? f->ws.get(WS_DD1, (size_t)f->df.n * R * 16) : nullptr;
+  if (dd && (!xdd || !ydd)) { set_error("apply: cannot allocate double-float workspace"); return HB_ENOMEM; }
   cudaEvent_t e;
   f->prof.begin(0, st, e);
-  int rc = launch_apply(f->df, p, adj, x, y, R, state, st);
+  int rc = dd ? launch_apply_dd(f->df, adj, x, y, R, state, xdd, ydd, st) : launch_apply(f->df, p, adj, x, y, R, state, st);
   f->prof.end(0, st, e);
   count_launch(f, (R == 1 && apply1_ready(f->df, adj)) ? 1 : (int)f->df.step_ptr.size() + 1);
   return rc;

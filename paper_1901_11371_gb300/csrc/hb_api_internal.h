@@ -13,7 +13,7 @@ struct hb_geometry_s {
 
 namespace hb {
 
-enum WsSlot { WS_STATE = 0, WS_STATE_SWEEP, WS_VEC0, WS_VEC1, WS_VEC2, WS_VEC3, WS_BASIS, WS_ZBASIS, WS_RED,
+enum WsSlot { WS_STATE = 0, WS_STATE_SWEEP, WS_VEC0, WS_VEC1, WS_VEC2, WS_VEC3, WS_BASIS, WS_ZBASIS, WS_RED, WS_DD0, WS_DD1,
               WS_SMALL, kSlots };
 
 // Grow-only device workspaces owned by a factor handle (cudaMalloc on first use

@@ -118,6 +118,12 @@ enum Prec { PREC_F64 = 0,        // double factors, double arithmetic (HB_C128)
 // `state` holds df.state_len * R complex entries of the same type.
 int launch_apply(const DevFactor& df, Prec p, bool adjoint, const void* x, void* y, int64_t R, void* state,
                  cudaStream_t st);
+// PREC_F32_ACC64 apply of 32 or more columns in double-float arithmetic (FP32 pairs,
+// about 48 significant bits): x, y double2 [row][R]; xdd, ydd, state: 16-byte-per-entry
+// scratch of n R, n R and state_len R entries.  HB_EINVAL when not applicable.
+bool apply_dd_ready(int64_t R);
+int launch_apply_dd(const DevFactor& df, bool adjoint, const void* x, void* y, int64_t R, void* state, void* xdd,
+                    void* ydd, cudaStream_t st);
 // Split-BF16 tensor-core entry (exit_jobs = false: x -> butterfly state) or
 // exit (true: state and x -> y) contractions of every leaf for R columns
 // (complex64 vectors, layout [row][R]).  HB_EUNSUPPORTED without operands.

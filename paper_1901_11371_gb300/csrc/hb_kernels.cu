@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "hb_device.h"
 
 namespace hb {
@@ -22,6 +24,41 @@ namespace hb {
 template <class T> struct C2;
 template <> struct C2<float> { using t = float2; };
 template <> struct C2<double> { using t = double2; };
+
+// Double-float numbers (a pair of FP32 values, about 48 significant bits): the
+// FP64-accurate arithmetic of the complex-FP32 factors' refinement residual at
+// FP32 instruction rates (FP64 runs at a small fraction of them on this GPU).
+// The product uses the exact FMA residual of the high parts (Dekker / Knuth
+// two-product with FMA), the sum the two-sum of the high parts with the low
+// parts added; both renormalised.
+struct Dd {
+  float h, l;
+  __host__ __device__ Dd(float v = 0.f) : h(v), l(0.f) {}
+  __host__ __device__ Dd(float hi, float lo) : h(hi), l(lo) {}
+};
+struct __align__(16) DdC {
+  Dd x, y;
+};
+template <> struct C2<Dd> { using t = DdC; };
+__device__ __forceinline__ Dd dd_norm(float s, float e) {
+  const float t = s + e;
+  return Dd(t, e - (t - s));
+}
+__device__ __forceinline__ Dd operator-(const Dd& a) { return Dd(-a.h, -a.l); }
+__device__ __forceinline__ Dd dd_add(const Dd& a, const Dd& b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  const float e = ((a.h - (s - bb)) + (b.h - bb)) + (a.l + b.l);
+  return dd_norm(s, e);
+}
+__device__ __forceinline__ Dd& operator+=(Dd& a, const Dd& b) { a = dd_add(a, b); return a; }
+// c + a * b
+__device__ __forceinline__ Dd dd_fma(const Dd& a, const Dd& b, const Dd& c) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+  return dd_add(c, dd_norm(p, e));
+}
 
 template <class T> __device__ __forceinline__ typename C2<T>::t mk(T a, T b) { return {a, b}; }
 
@@ -42,6 +79,12 @@ __device__ __forceinline__ void cfma(C& acc, const C& a, const C& b) {
   acc.x = fma(-a.y, b.y, acc.x);
   acc.y = fma(a.x, b.y, acc.y);
   acc.y = fma(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cfma(DdC& acc, const DdC& a, const DdC& b) {
+  acc.x = dd_fma(a.x, b.x, acc.x);
+  acc.x = dd_fma(-a.y, b.y, acc.x);
+  acc.y = dd_fma(a.x, b.y, acc.y);
+  acc.y = dd_fma(a.y, b.x, acc.y);
 }
 template <class C>
 __device__ __forceinline__ void cadd(C& acc, const C& a) {
@@ -274,6 +317,7 @@ constexpr int kWideMin = 32;
 
 template <class T> struct KCw { static constexpr int v = 16; };
 template <> struct KCw<double> { static constexpr int v = 8; };
+template <> struct KCw<Dd> { static constexpr int v = 8; };
 
 // B side of a V-type op (or a U-type op in adjoint): out_i = cand[q_i] + sum_j T_ij cand[p_j]
 template <class T, class F, bool UTYPE_ADJ>
@@ -605,6 +649,35 @@ static int apply_wide_tc(const DevFactor& df, const void* xv, void* yv, int64_t 
   }
   if (cudaGetLastError() != cudaSuccess) return HB_ECUDA;
   return launch_tc_jobs(df, true, xv, stv, yv, R, s);
+}
+
+// double2 <-> double-float vectors
+__global__ void k_to_dd(const double2* __restrict__ x, DdC* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = x[i];
+    const float rh = (float)v.x, ih = (float)v.y;
+    y[i] = DdC{Dd(rh, (float)(v.x - (double)rh)), Dd(ih, (float)(v.y - (double)ih))};
+  }
+}
+__global__ void k_from_dd(const DdC* __restrict__ x, double2* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const DdC v = x[i];
+    y[i] = make_double2((double)v.x.h + (double)v.x.l, (double)v.y.h + (double)v.y.l);
+  }
+}
+
+bool apply_dd_ready(int64_t R) { return R >= kWideMin; }
+
+int launch_apply_dd(const DevFactor& df, bool adjoint, const void* x, void* y, int64_t R, void* state, void* xdd,
+                    void* ydd, cudaStream_t st) {
+  if (!apply_dd_ready(R) || df.form == HB_C128) return HB_EINVAL;
+  const int64_t nn = df.n * R;
+  const unsigned g = (unsigned)std::min<int64_t>((nn + 255) / 256, 152 * 16);
+  k_to_dd<<<g, 256, 0, st>>>((const double2*)x, (DdC*)xdd, nn);
+  int rc = apply_wide<Dd, float2>(df, adjoint, xdd, ydd, R, state, st);
+  if (rc) return rc;
+  k_from_dd<<<g, 256, 0, st>>>((const DdC*)ydd, (double2*)y, nn);
+  return cudaGetLastError() == cudaSuccess ? HB_OK : HB_ECUDA;
 }
 
 int launch_apply(const DevFactor& df, Prec p, bool adjoint, const void* x, void* y, int64_t R, void* state,

@@ -136,3 +136,19 @@ def test_tfqmr_adjoint_and_errors(hb, strip_tfqmr):
     bad[7] = np.nan
     with pytest.raises(hb.HBError):
         hb.hb_tfqmr(f, _t(bad[None, :]), rstar=rs)
+
+
+def test_residual_double_float_matches_fp64_arithmetic(hb, strip_tfqmr):
+    # The refinement residual r = b - A^_F x of the complex-FP32 forms is computed with
+    # FP64-accurate arithmetic on the FP32 factors: for 32 or more columns in double-float
+    # (pairs of FP32 values, ~48 bits), below that in FP64.  The same 40 columns in one
+    # call (double-float) and in two calls of 20 (FP64) must agree to rounding of that
+    # accuracy, far below the FP32 apply's 1e-7.
+    f = strip_tfqmr["f32"]
+    x = W.complex_gaussian(1024, 80, 40).T.copy()
+    b = W.complex_gaussian(1024, 81, 40).T.copy()
+    r40 = hb.hb_residual(f, _t(b), _t(x)).cpu().numpy()
+    r20 = np.concatenate([hb.hb_residual(f, _t(b[:20]), _t(x[:20])).cpu().numpy(),
+                          hb.hb_residual(f, _t(b[20:]), _t(x[20:])).cpu().numpy()])
+    err = np.linalg.norm(r40 - r20, axis=1) / np.linalg.norm(r20, axis=1)
+    assert err.max() <= 1e-12, err.max()
