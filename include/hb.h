@@ -96,6 +96,8 @@ typedef struct {
   double seconds;         /* wall time of the call (host clock, synchronised) */
   int32_t* iters_per_rhs; /* optional out */
   double* res_per_rhs;    /* optional out */
+  int32_t graph_launches; /* hb_gmres: restart cycles run as one CUDA graph launch each */
+  int32_t pad;
 } hb_gmres_info;
 
 /* hb_geometry -- discretise an open PEC curve into n_segments pulse segments
@@ -231,6 +233,22 @@ int hb_residual(hb_factor_t f, int op, const void* b, const void* x, void* r, in
  * flag is cleared, so the next call starts clean). */
 int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int64_t nrhs, int64_t ld, int restart,
              double rtol, int maxit, hb_gmres_info* info, void* stream);
+
+/* hb_set_gmres_graph -- 1 (default): for nrhs >= 2, hb_gmres runs each restart
+ * cycle as ONE CUDA graph launch: the start vector, every Arnoldi step (the
+ * preconditioner sweeps, the operator, CGS2 with its reductions), the Givens
+ * rotations of every column's Hessenberg matrix, the convergence test and the
+ * least-squares solve all run on the device; the test closes a device flag
+ * that makes the graph's remaining steps return at once, so a cycle costs what
+ * the host-driven loop's does without a host round trip per step.  The graph
+ * is captured once and kept on the factor while the restart, nrhs, op, the
+ * factor's execution settings (hb_autotune, hb_set_sweep_kernel,
+ * hb_set_sweep_grid_min, hb_set_wait_limit, hb_profile) and its workspaces stay
+ * the same.  0: the host-driven loop (a host synchronisation per step).  Both
+ * compute the same iteration; info->graph_launches says which ran.  One
+ * right-hand side always takes the host-driven loop.  Returns HB_OK or
+ * HB_EINVAL.  Not in the paper: an execution choice. */
+int hb_set_gmres_graph(hb_factor_t f, int on);
 
 /* hb_tfqmr -- solve A x = b_phys (complex128, physical excitation, as for
  * hb_gmres) with transpose-free QMR, the Krylov solver of Sec. 4, on the

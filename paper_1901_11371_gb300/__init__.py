@@ -23,7 +23,7 @@ __all__ = ["HB_STRIP", "HB_SPIRAL", "HB_ARC", "HB_PARALLEL_STRIPS", "HB_POLYLINE
            "hb_geometry_polyline", "hb_factor", "hb_factor_host",
            "hb_factor_info", "hb_tree", "hb_apply", "hb_apply_adjoint", "hb_precond_solve", "hb_lower_solve",
            "hb_upper_solve", "hb_residual", "hb_gmres", "hb_tfqmr", "hb_rhs_plane_wave", "hb_far_field", "hb_monostatic",
-           "hb_host_apply", "hb_host_apply_plan", "hb_host_tc_apply", "hb_host_sweep", "hb_host_sweep_sched", "hb_far_field_adjoint", "hb_profile", "hb_profile_read", "hb_autotune", "hb_autotune_times", "hb_set_sweep_kernel", "lib"]
+           "hb_host_apply", "hb_host_apply_plan", "hb_host_tc_apply", "hb_host_sweep", "hb_host_sweep_sched", "hb_far_field_adjoint", "hb_profile", "hb_profile_read", "hb_autotune", "hb_autotune_times", "hb_set_sweep_kernel", "hb_set_gmres_graph", "lib"]
 
 
 def lib():
@@ -205,7 +205,7 @@ def hb_gmres(f, b_phys, op=HB_OP_N, restart=30, rtol=1e-6, maxit=1000, out=None,
                         float(rtol), int(maxit), C.byref(info), _stream(stream))
     d = dict(iters=info.iters, restarts=info.restarts, ir_steps=info.ir_steps, converged=info.converged,
              true_rel_res=info.true_rel_res, precond_rel_res=info.precond_rel_res, seconds=info.seconds,
-             iters_per_rhs=list(it), res_per_rhs=list(rr), status=rc)
+             iters_per_rhs=list(it), res_per_rhs=list(rr), graph_launches=info.graph_launches, status=rc)
     if check and rc not in (_lib.HB_OK,):
         _lib.check(rc)
     return x, d
@@ -297,6 +297,11 @@ def hb_autotune_times(f, nrhs):
     if n < 0:
         _lib.check(n)
     return {int(gm[i]): float(ms[i]) for i in range(n)}
+
+
+def hb_set_gmres_graph(f, on):
+    """1: hb_gmres runs each restart cycle as one CUDA graph launch (nrhs >= 2); 0: host-driven loop."""
+    _lib.check(lib().hb_set_gmres_graph(f._h, int(bool(on))))
 
 
 def hb_set_sweep_kernel(f, kind):

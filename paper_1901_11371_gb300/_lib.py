@@ -41,7 +41,8 @@ class FactorStats(C.Structure):
 class GmresInfo(C.Structure):
     _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("ir_steps", C.c_int32), ("converged", C.c_int32),
                 ("true_rel_res", C.c_double), ("precond_rel_res", C.c_double), ("seconds", C.c_double),
-                ("iters_per_rhs", C.POINTER(C.c_int32)), ("res_per_rhs", C.POINTER(C.c_double))]
+                ("iters_per_rhs", C.POINTER(C.c_int32)), ("res_per_rhs", C.POINTER(C.c_double)),
+                ("graph_launches", C.c_int32), ("pad", C.c_int32)]
 
 
 _VP, _I64, _INT, _DBL = C.c_void_p, C.c_int64, C.c_int, C.c_double
@@ -75,6 +76,7 @@ SIGNATURES = {
     "hb_set_sweep_grid_min": (_INT, [_VP, _INT]),
     "hb_set_sweep_kernel": (_INT, [_VP, _INT]),
     "hb_set_wait_limit": (_INT, [_VP, C.c_longlong]),
+    "hb_set_gmres_graph": (_INT, [_VP, _INT]),
     "hb_autotune": (_INT, [_VP, _I64, _VP, C.POINTER(C.c_int)]),
     "hb_autotune_times": (_INT, [_VP, _I64, C.POINTER(C.c_float), C.POINTER(C.c_int), C.c_int]),
     "hb_status": (_INT, [_VP, _VP]),

@@ -261,15 +261,25 @@ void free_factor(DevFactor& df) {
 
 void Profiler::begin(int kind, cudaStream_t st, cudaEvent_t& a) {
   a = nullptr;
-  if (!on) return;
+  if (!on || in_body) return;
   if (cudaEventCreate(&a) != cudaSuccess) { a = nullptr; return; }
-  cudaEventRecord(a, st);
+  record(a, st);
+}
+// Inside a stream capture a plain record only orders the capture; an external
+// record becomes an event-record node that stamps the event at every launch.
+void Profiler::record(cudaEvent_t e, cudaStream_t st) {
+  if (capturing) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+  else cudaEventRecord(e, st);
 }
 void Profiler::end(int kind, cudaStream_t st, cudaEvent_t a) {
   if (!on || !a) return;
   cudaEvent_t b;
   if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
-  cudaEventRecord(b, st);
+  record(b, st);
+  if (capturing) {
+    cap.push_back({kind, tag, a, b});
+    return;
+  }
   ev[kind].push_back({a, b});
   count[kind]++;
 }
@@ -278,7 +288,38 @@ void Profiler::reset() {
     for (auto& p : v) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
   ev[0].clear(); ev[1].clear();
   count[0] = count[1] = count[2] = 0;
+  acc_ms[0] = acc_ms[1] = 0.0;
 }
+int Profiler::harvest(int steps_run) {
+  for (size_t t = 0; t < cap_launches.size(); ++t)
+    if ((int)t - 1 < steps_run) count[2] += cap_launches[t];
+  for (const Tagged& t : cap) {
+    if (t.tag >= steps_run) continue;   // a skipped step: its kernels returned at once
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) != cudaSuccess) {
+      cudaGetLastError();   // not a device fault: clear it for the launch checks that follow
+      return HB_ECUDA;
+    }
+    acc_ms[t.kind] += ms;
+    count[t.kind]++;
+  }
+  return HB_OK;
+}
+void Profiler::drop_capture() {
+  for (const Tagged& t : cap) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+  cap.clear();
+  cap_launches.clear();
+}
+void CycleGraph::release(Profiler& prof) {
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  exec = nullptr;
+  graph = nullptr;
+  prof.drop_capture();
+  op = -1;
+  R = 0;
+}
+
 
 void* Workspace::get(int slot, size_t bytes) {
   if (slot < 0 || slot >= kSlots) return nullptr;
@@ -495,6 +536,9 @@ int hb_factor_info(hb_factor_t f, hb_factor_stats* s) {
 
 int hb_profile(hb_factor_t f, int enable) {
   if (!f) { set_error("hb_profile: null factor"); return HB_EINVAL; }
+  // a captured solver cycle holds (or lacks) the timing events: recapture only
+  // when profiling is switched on or off; enabling it again just resets the counts
+  if ((enable != 0) != f->prof.on) settings_changed(f);
   if (enable) f->prof.reset();
   f->prof.on = enable != 0;
   return HB_OK;
@@ -510,6 +554,7 @@ int hb_profile_read(hb_factor_t f, int kind, int64_t* count, double* total_ms) {
       cudaEventElapsedTime(&ms, p.first, p.second);
       tot += ms;
     }
+    tot += f->prof.acc_ms[kind];
   }
   if (count) *count = f->prof.count[kind];
   if (total_ms) *total_ms = tot;
@@ -518,6 +563,7 @@ int hb_profile_read(hb_factor_t f, int kind, int64_t* count, double* total_ms) {
 
 void hb_factor_destroy(hb_factor_t f) {
   if (!f) return;
+  f->cg.release(f->prof);
   f->prof.reset();
   f->ws.release();
   free_factor(f->df);
@@ -540,6 +586,7 @@ int hb_tree(hb_factor_t f, int64_t* node_begin, int64_t* node_end) {
 
 int hb_set_sweep_grid_min(hb_factor_t f, int grid_min) {
   if (!f || f->host_only || grid_min < 1) { set_error("hb_set_sweep_grid_min: bad argument"); return HB_EINVAL; }
+  settings_changed(f);
   f->df.tuned[0] = f->df.tuned[1] = -1;
   f->df.cols_won[0] = f->df.cols_won[1] = false;
   int old = f->df.grid_min;
@@ -549,6 +596,7 @@ int hb_set_sweep_grid_min(hb_factor_t f, int grid_min) {
 
 int hb_autotune(hb_factor_t f, int64_t nrhs, void* stream, int* chosen) {
   if (!f || f->host_only || nrhs < 1) { set_error("hb_autotune: bad argument"); return HB_EINVAL; }
+  settings_changed(f);
   cudaStream_t st = (cudaStream_t)stream;
   DevFactor& df = f->df;
   const Prec p = df.form == HB_C128 ? PREC_F64 : PREC_F32;
@@ -633,12 +681,21 @@ int hb_set_sweep_kernel(hb_factor_t f, int kind) {
     return HB_EUNSUPPORTED;
   }
   f->df.sweep_kernel = kind;
+  settings_changed(f);
+  return HB_OK;
+}
+
+int hb_set_gmres_graph(hb_factor_t f, int on) {
+  if (!f || f->host_only || on < 0 || on > 1) { set_error("hb_set_gmres_graph: bad argument"); return HB_EINVAL; }
+  f->gmres_graph = on;
+  settings_changed(f);
   return HB_OK;
 }
 
 int hb_set_wait_limit(hb_factor_t f, long long spins) {
   if (!f || f->host_only || spins < 1) { set_error("hb_set_wait_limit: bad argument"); return HB_EINVAL; }
   f->df.spin_limit = spins;
+  settings_changed(f);
   return HB_OK;
 }
 

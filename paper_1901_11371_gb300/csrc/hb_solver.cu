@@ -19,6 +19,7 @@
 #include <chrono>
 #include <cmath>
 #include <complex>
+#include <functional>
 #include <vector>
 
 #include "hb_api_internal.h"
@@ -410,6 +411,194 @@ struct Givens {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Restart cycle on the device (graph mode of hb_gmres).  The Arnoldi steps,
+// their CGS2 coefficients, the Givens rotations of every column's Hessenberg
+// matrix, the convergence test and the least-squares solve all stay on the
+// device, so that a whole cycle is one CUDA graph launch.  Every step is a
+// chain of conditional (IF) nodes; step j's convergence test sets step j+1's
+// conditions, so the steps after the last one needed do not run at all.  The
+// arithmetic is the host loop's (FP64 Givens, CGS2 in the basis precision
+// with FP64 reductions in the same fixed order).
+// ---------------------------------------------------------------------------
+struct Cyc {
+  int64_t R;
+  int m;
+  double2* H;       // [R][m][m+1]: column j of column c's Hessenberg matrix at H + (c m + j)(m + 1)
+  double2* cs;      // [R][m] rotations
+  double2* sn;      // [R][m]
+  double2* g;       // [R][m+1] rotated right-hand side beta e_1
+  double2* hacc;    // [m+1][R] CGS2 coefficients of the current step (sum of both passes)
+  void* cvec;       // [m+1][R] one pass's coefficients in the basis precision
+  double* hn;       // [R] ||w|| after CGS2
+  double* inv;      // [R] 1 / ||w|| (1 for a zero column)
+  const double* prm;   // [4][R] host-written per cycle: target = max(t_abs, t_rel beta); bnorm; skip
+  double* pres;     // [R] preconditioned estimate / ||b||
+  double* target;   // [R]
+  int* kuse;        // [R] 0 active, 1 not in this cycle, -(j+1) converged after step j+1
+  int* ctl;         // [0] step limit (host-written), [1] steps run
+};
+
+// the conditions of the next step's IF nodes (n = 0 after the last step)
+constexpr int kMaxSeg = 6;
+struct CondNext {
+  cudaGraphConditionalHandle h[kMaxSeg];
+  int n;
+};
+
+__device__ __forceinline__ double2 z_mul(double2 a, double2 b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ __forceinline__ double2 z_cmul(double2 a, double2 b) {   // conj(a) b
+  return {a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x};
+}
+
+// beta = ||r|| per column (the fixed-order sum of the partial dot products),
+// 1 / beta for the start vector, g = beta e_1, the column's target and state
+__global__ void k_cyc_start(const double2* __restrict__ partial, int nblk, Cyc c) {
+  const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= c.R) return;
+  double2 sum = {0.0, 0.0};
+  for (int b = 0; b < nblk; ++b) {
+    const double2 p = partial[(int64_t)b * c.R + col];
+    sum.x += p.x;
+    sum.y += p.y;
+  }
+  const double beta = sqrt(fmax(sum.x, 0.0));
+  c.inv[col] = beta > 0 ? 1.0 / beta : 1.0;
+  c.g[col * (c.m + 1)] = {beta, 0.0};
+  c.target[col] = fmax(c.prm[col], c.prm[c.R + col] * beta);
+  c.kuse[col] = c.prm[3 * c.R + col] != 0.0 ? 1 : 0;
+}
+
+// one CGS2 pass's coefficients: hacc (+)= <V_v, w>, cvec = the same in the basis precision
+template <class VT>
+__global__ void k_cgs_final(const double2* __restrict__ partial, int nblk, int nvec, Cyc c, int pass) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)nvec * c.R) return;
+  const int v = (int)(e / c.R);
+  const int64_t r = e % c.R;
+  double2 sum = {0.0, 0.0};
+  for (int b = 0; b < nblk; ++b) {
+    const double2 p = partial[((int64_t)v * nblk + b) * c.R + r];
+    sum.x += p.x;
+    sum.y += p.y;
+  }
+  double2 h = sum;
+  if (pass) h = {c.hacc[e].x + sum.x, c.hacc[e].y + sum.y};
+  c.hacc[e] = h;
+  ((VT*)c.cvec)[e] = VT{(decltype(VT::x))sum.x, (decltype(VT::x))sum.y};
+}
+
+// ||w|| and 1 / ||w|| per column
+__global__ void k_norm_final(const double2* __restrict__ partial, int nblk, Cyc c) {
+  const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= c.R) return;
+  double2 sum = {0.0, 0.0};
+  for (int b = 0; b < nblk; ++b) {
+    const double2 p = partial[(int64_t)b * c.R + col];
+    sum.x += p.x;
+    sum.y += p.y;
+  }
+  const double nrm = sqrt(fmax(sum.x, 0.0));
+  c.hn[col] = nrm;
+  c.inv[col] = nrm > 0 ? 1.0 / nrm : 1.0;
+}
+
+// Step j of every active column: insert the new Hessenberg column, apply the
+// earlier rotations, form and apply rotation j (G = [[c*, s*], [-s, c]]), and
+// test |g_{j+1}| against the column's target; one CTA, columns strided over its
+// threads.  Thread 0 records the step count and sets the next step's
+// conditions: 1 while some column is active and the step limit allows.
+__global__ void k_givens(Cyc c, int j, CondNext nx) {
+  const int m = c.m;
+  int active = 0;
+  for (int64_t col = threadIdx.x; col < c.R; col += blockDim.x) {
+    if (c.kuse[col] != 0) continue;
+    double2* h = c.H + ((size_t)col * m + j) * (m + 1);
+    for (int i = 0; i <= j; ++i) h[i] = c.hacc[(size_t)i * c.R + col];
+    h[j + 1] = {c.hn[col], 0.0};
+    double2* cs = c.cs + (size_t)col * m;
+    double2* sn = c.sn + (size_t)col * m;
+    for (int i = 0; i < j; ++i) {
+      const double2 a = h[i], b = h[i + 1];
+      const double2 t0 = z_cmul(cs[i], a), t1 = z_cmul(sn[i], b);
+      const double2 u0 = z_mul(sn[i], a), u1 = z_mul(cs[i], b);
+      h[i] = {t0.x + t1.x, t0.y + t1.y};
+      h[i + 1] = {u1.x - u0.x, u1.y - u0.y};
+    }
+    const double2 a = h[j], b = h[j + 1];
+    const double den = sqrt((a.x * a.x + a.y * a.y) + (b.x * b.x + b.y * b.y));
+    const double2 cj = den > 0 ? double2{a.x / den, a.y / den} : double2{1.0, 0.0};
+    const double2 sj = den > 0 ? double2{b.x / den, b.y / den} : double2{0.0, 0.0};
+    cs[j] = cj;
+    sn[j] = sj;
+    const double2 t0 = z_cmul(cj, a), t1 = z_cmul(sj, b);
+    h[j] = {t0.x + t1.x, t0.y + t1.y};
+    h[j + 1] = {0.0, 0.0};
+    double2* g = c.g + (size_t)col * (m + 1);
+    const double2 gj = g[j], sg = z_mul(sj, gj);
+    g[j + 1] = {-sg.x, -sg.y};
+    g[j] = z_cmul(cj, gj);
+    const double est = hypot(g[j + 1].x, g[j + 1].y);
+    const double bn = c.prm[2 * c.R + col];
+    c.pres[col] = bn > 0 ? est / bn : 0.0;
+    if (est <= c.target[col]) c.kuse[col] = -(j + 1);
+    else active = 1;
+  }
+  active = __syncthreads_or(active);
+  if (threadIdx.x == 0) {
+    c.ctl[1] = j + 1;
+    const unsigned go = (active && j + 1 < c.ctl[0]) ? 1u : 0u;
+    for (int k = 0; k < nx.n; ++k) cudaGraphSetConditional(nx.h[k], go);
+  }
+}
+
+// After the cycle: each column's least-squares solution by back substitution
+// over its own step count, written as the combination coefficients coef[i][c]
+// (basis precision) of the steps that ran; columns outside the cycle get
+// zeros.  y: [m][R] FP64 scratch.
+template <class VT>
+__global__ void k_cyc_solve(Cyc c, double2* __restrict__ y, VT* __restrict__ coef) {
+  const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= c.R) return;
+  const int m = c.m, kc = c.ctl[1];
+  const int ku = c.kuse[col];
+  const int k = ku == 1 ? 0 : (ku < 0 ? -ku : kc);
+  const double2* H = c.H + (size_t)col * m * (m + 1);
+  const double2* g = c.g + (size_t)col * (m + 1);
+  for (int i = k - 1; i >= 0; --i) {
+    double2 acc = g[i];
+    for (int l = i + 1; l < k; ++l) {
+      const double2 p = z_mul(H[(size_t)l * (m + 1) + i], y[(size_t)l * c.R + col]);
+      acc = {acc.x - p.x, acc.y - p.y};
+    }
+    const double2 d = H[(size_t)i * (m + 1) + i];
+    const double dd = d.x * d.x + d.y * d.y;
+    y[(size_t)i * c.R + col] = {(acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd};
+  }
+  using S = decltype(VT::x);
+  for (int i = 0; i < kc; ++i) {
+    const double2 v = i < k ? y[(size_t)i * c.R + col] : double2{0.0, 0.0};
+    coef[(size_t)i * c.R + col] = VT{(S)v.x, (S)v.y};
+  }
+}
+
+// CGS2 of step nvec-1 of a captured cycle: two passes (coefficients reduced on
+// the device in fixed order, accumulated in FP64), then ||w|| and w / ||w||.
+template <class VT>
+static void cgs2_graph(hb_factor_t f, const Dev& d, const Cyc& cyc, const VT* V, int nvec, VT* w, cudaStream_t s) {
+  const int64_t nR = d.n * d.R;
+  for (int pass = 0; pass < 2; ++pass) {
+    k_dots_partial<VT><<<dim3(kRedBlocks, nvec), kRedThreads, 0, s>>>(V, nR, nvec, w, d.n, d.R, d.red_partial);
+    k_cgs_final<VT><<<(unsigned)(((int64_t)nvec * d.R + 255) / 256), 256, 0, s>>>(d.red_partial, kRedBlocks, nvec, cyc,
+                                                                                pass);
+    k_sub_combo<VT><<<gsz(nR), 256, 0, s>>>(V, nR, nvec, (const VT*)cyc.cvec, w, d.n, d.R);
+  }
+  k_dots_partial<VT><<<dim3(kRedBlocks, 1), kRedThreads, 0, s>>>(w, 0, 1, w, d.n, d.R, d.red_partial);
+  k_norm_final<<<(unsigned)((d.R + 255) / 256), 256, 0, s>>>(d.red_partial, kRedBlocks, cyc);
+  k_scale_cols<VT, VT><<<gsz(nR), 256, 0, s>>>(w, cyc.inv, w, d.n, d.R);
+  count_launch(f, 9);
+}
+
 }  // namespace hb
 
 using namespace hb;
@@ -446,6 +635,49 @@ extern "C" int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int6
   double2* tmp2 = (double2*)ws.get(WS_VEC1, vbytes);
   if (!tmp || !tmp2) { set_error("hb_gmres: workspace allocation failed"); return HB_ENOMEM; }
   Dev d{f, st, n, R, red, red + (size_t)kRedBlocks * (m + 2) * R, (double*)(red + (size_t)kRedBlocks * (m + 2) * R + (size_t)(m + 2) * R)};
+
+  // graph mode: the device-side cycle state, and every workspace that the
+  // captured kernels or the steps between cycles use reserved at its largest
+  // size first, so that no allocation moves a buffer the graph holds
+  bool use_graph = f->gmres_graph != 0 && R >= 2;
+  Cyc cyc{};
+  double2* ysolve = nullptr;
+  void* coefd = nullptr;
+  if (use_graph) {
+    const size_t R_ = (size_t)R, m_ = (size_t)m;
+    const size_t parts[] = {R_ * m_ * (m_ + 1) * 16, R_ * m_ * 16, R_ * m_ * 16, R_ * (m_ + 1) * 16, (m_ + 1) * R_ * 16,
+                            (m_ + 1) * R_ * 16, R_ * 8, R_ * 8, 4 * R_ * 8, R_ * 8, R_ * 8, R_ * 4, 16, m_ * R_ * 16,
+                            m_ * R_ * 16};
+    size_t off[15], tot = 0;
+    for (int i = 0; i < 15; ++i) { off[i] = tot; tot += (parts[i] + 255) / 256 * 256; }
+    char* cb = (char*)ws.get(WS_CYC, tot);
+    const int es_sweep = mixed ? 8 : 16;
+    size_t sweep_need = (size_t)df.state_len * R * es_sweep;
+    if (df.sw[0].ok) sweep_need = std::max(sweep_need, (size_t)sweep_cols_state_entries(df, R) * 8);
+    const bool dd = mixed && apply_dd_ready(R);
+    if (!cb || !ws.get(WS_STATE, (size_t)df.state_len * R * 16) || !ws.get(WS_STATE_SWEEP, sweep_need) ||
+        (dd && (!ws.get(WS_DD0, (size_t)n * R * 16) || !ws.get(WS_DD1, (size_t)n * R * 16)))) {
+      set_error("hb_gmres: workspace allocation failed");
+      return HB_ENOMEM;
+    }
+    cyc.R = R;
+    cyc.m = m;
+    cyc.H = (double2*)(cb + off[0]);
+    cyc.cs = (double2*)(cb + off[1]);
+    cyc.sn = (double2*)(cb + off[2]);
+    cyc.g = (double2*)(cb + off[3]);
+    cyc.hacc = (double2*)(cb + off[4]);
+    cyc.cvec = cb + off[5];
+    cyc.hn = (double*)(cb + off[6]);
+    cyc.inv = (double*)(cb + off[7]);
+    cyc.prm = (const double*)(cb + off[8]);
+    cyc.pres = (double*)(cb + off[9]);
+    cyc.target = (double*)(cb + off[10]);
+    cyc.kuse = (int*)(cb + off[11]);
+    cyc.ctl = (int*)(cb + off[12]);
+    ysolve = (double2*)(cb + off[13]);
+    coefd = cb + off[14];
+  }
 
   // non-finite input check
   cudaMemsetAsync(flag, 0, sizeof(int), st);
@@ -492,92 +724,323 @@ extern "C" int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int6
   // x = 0: r = b^ (no operator application needed)
   cudaMemcpyAsync(r, bh, vbytes, cudaMemcpyDeviceToDevice, st);
   for (int64_t c = 0; c < R; ++c) res_r[c] = bnorm[c] > 0 ? 1.0 : 0.0;
+
+  // ---- graph mode: one restart cycle captured on stream s.  Each Arnoldi step
+  // is a chain of IF nodes, one per segment (a copy, a sweep, the operator,
+  // CGS2 + the Givens step), each body captured on stream sb.  Step 0's
+  // conditions default to 1 at every launch, the others' to 0; step j's
+  // Givens kernel sets step j+1's.  A conditional body holds no event nodes,
+  // so the timing events (when profiling) sit between the IF nodes, tagged
+  // with the step and read only for the steps that ran.
+  const int64_t nR = n * R;
+  const unsigned gcol = (unsigned)((R + 255) / 256);
+  const int nseg = mixed ? 5 : 6;
+  std::vector<cudaGraphConditionalHandle> hnd;
+  auto record_cycle = [&](cudaStream_t s, cudaStream_t sb) -> int {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, nullptr, nullptr, nullptr) != cudaSuccess || !g) return HB_ECUDA;
+    hnd.assign((size_t)m * nseg, cudaGraphConditionalHandle{});
+    for (int j = 0; j < m; ++j)
+      for (int k = 0; k < nseg; ++k)
+        if (cudaGraphConditionalHandleCreate(&hnd[(size_t)j * nseg + k], g, j == 0 ? 1u : 0u,
+                                             cudaGraphCondAssignDefault) != cudaSuccess)
+          return HB_ECUDA;
+    int e;
+    f->prof.tag = -1;
+    // start vector v_0 = r / ||r|| (split form: r <- L'^{-1} r first), g = beta e_1
+    if (!mixed && (e = sweep_internal(f, PREC_F64, lo, r, R, s))) return e;
+    k_dots_partial<double2><<<dim3(kRedBlocks, 1), kRedThreads, 0, s>>>(r, 0, 1, r, n, R, d.red_partial);
+    k_cyc_start<<<gcol, 256, 0, s>>>(d.red_partial, kRedBlocks, cyc);
+    if (mixed) k_scale_cols<double2, float2><<<gsz(nR), 256, 0, s>>>(r, cyc.inv, V32, n, R);
+    else k_scale_cols<double2, double2><<<gsz(nR), 256, 0, s>>>(r, cyc.inv, V, n, R);
+    count_launch(f, 3);
+    // segment k of step j: an IF node on its condition; kind 0 / 1 (apply / sweep) gets timing events
+    int seg_k = 0;
+    auto segment = [&](int j, int kind, const std::function<int(cudaStream_t)>& body) -> int {
+      const int k = seg_k++;
+      cudaEvent_t ea = nullptr, eb = nullptr;
+      if (f->prof.on && kind >= 0) {
+        if (cudaEventCreate(&ea) != cudaSuccess) return HB_ECUDA;
+        if (cudaEventCreate(&eb) != cudaSuccess) { cudaEventDestroy(ea); return HB_ECUDA; }
+        f->prof.cap.push_back({kind, j, ea, eb});
+        if (cudaEventRecordWithFlags(ea, s, cudaEventRecordExternal) != cudaSuccess) return HB_ECUDA;
+      }
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      if (cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, nullptr, &nd) != cudaSuccess) return HB_ECUDA;
+      cudaGraphNodeParams np = {};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = hnd[(size_t)j * nseg + k];
+      np.conditional.type = cudaGraphCondTypeIf;
+      np.conditional.size = 1;
+      cudaGraphNode_t node = nullptr;
+      if (cudaGraphAddNode(&node, g, deps, nullptr, nd, &np) != cudaSuccess) return HB_ECUDA;
+      if (cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+        return HB_ECUDA;
+      if (cudaStreamBeginCaptureToGraph(sb, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeRelaxed) != cudaSuccess)
+        return HB_ECUDA;
+      f->prof.in_body = true;
+      const int be = body(sb);
+      f->prof.in_body = false;
+      cudaGraph_t bg = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(sb, &bg);
+      if (be) return be;
+      if (ce != cudaSuccess) return HB_ECUDA;
+      if (eb && cudaEventRecordWithFlags(eb, s, cudaEventRecordExternal) != cudaSuccess) return HB_ECUDA;
+      return HB_OK;
+    };
+    for (int j = 0; j < m; ++j) {
+      f->prof.tag = j;
+      seg_k = 0;
+      CondNext nx{};
+      nx.n = j + 1 < m ? nseg : 0;
+      for (int k = 0; k < nx.n; ++k) nx.h[k] = hnd[(size_t)(j + 1) * nseg + k];
+      if (mixed) {   // z_j = M^{-1} v_j, w = A z_j (complex FP32)
+        float2* zj = zf + (size_t)j * nR;
+        float2* w32 = V32 + (size_t)(j + 1) * nR;
+        const float2* vj = V32 + (size_t)j * nR;
+        if ((e = segment(j, -1, [&](cudaStream_t b) {
+               return cudaMemcpyAsync(zj, vj, (size_t)nR * sizeof(float2), cudaMemcpyDeviceToDevice, b) == cudaSuccess
+                          ? HB_OK : HB_ECUDA; })))
+          return e;
+        if ((e = segment(j, 1, [&](cudaStream_t b) { return sweep_internal(f, PREC_F32, lo, zj, R, b); }))) return e;
+        if ((e = segment(j, 1, [&](cudaStream_t b) { return sweep_internal(f, PREC_F32, up, zj, R, b); }))) return e;
+        if ((e = segment(j, 0, [&](cudaStream_t b) { return apply_internal(f, PREC_F32, adj, zj, w32, R, b); })))
+          return e;
+        if ((e = segment(j, -1, [&](cudaStream_t b) {
+               cgs2_graph(f, d, cyc, (const float2*)V32, j + 1, w32, b);
+               k_givens<<<1, 256, 0, b>>>(cyc, j, nx);
+               count_launch(f, 1);
+               return cudaGetLastError() == cudaSuccess ? HB_OK : HB_ECUDA; })))
+          return e;
+      } else {       // w = L'^{-1} A U'^{-1} v_j
+        double2* vj = V + (size_t)j * nR;
+        double2* w = V + (size_t)(j + 1) * nR;
+        if ((e = segment(j, -1, [&](cudaStream_t b) {
+               return cudaMemcpyAsync(w, vj, vbytes, cudaMemcpyDeviceToDevice, b) == cudaSuccess ? HB_OK : HB_ECUDA; })))
+          return e;
+        if ((e = segment(j, 1, [&](cudaStream_t b) { return sweep_internal(f, PREC_F64, up, w, R, b); }))) return e;
+        if ((e = segment(j, 0, [&](cudaStream_t b) { return apply_internal(f, PREC_F64, adj, w, tmp2, R, b); })))
+          return e;
+        if ((e = segment(j, -1, [&](cudaStream_t b) {
+               return cudaMemcpyAsync(w, tmp2, vbytes, cudaMemcpyDeviceToDevice, b) == cudaSuccess ? HB_OK : HB_ECUDA; })))
+          return e;
+        if ((e = segment(j, 1, [&](cudaStream_t b) { return sweep_internal(f, PREC_F64, lo, w, R, b); }))) return e;
+        if ((e = segment(j, -1, [&](cudaStream_t b) {
+               cgs2_graph(f, d, cyc, (const double2*)V, j + 1, w, b);
+               k_givens<<<1, 256, 0, b>>>(cyc, j, nx);
+               count_launch(f, 1);
+               return cudaGetLastError() == cudaSuccess ? HB_OK : HB_ECUDA; })))
+          return e;
+      }
+    }
+    f->prof.tag = -1;
+    if (mixed) k_cyc_solve<float2><<<gcol, 256, 0, s>>>(cyc, ysolve, (float2*)coefd);
+    else k_cyc_solve<double2><<<gcol, 256, 0, s>>>(cyc, ysolve, (double2*)coefd);
+    count_launch(f, 1);
+    return cudaGetLastError() == cudaSuccess ? HB_OK : HB_ECUDA;
+  };
+  auto capture_cycle = [&]() -> int {
+    f->cg.release(f->prof);
+    cudaStream_t cs = nullptr, cb = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&cb, cudaStreamNonBlocking) != cudaSuccess) {
+      if (cs) cudaStreamDestroy(cs);
+      set_error("hb_gmres: cannot create the capture streams");
+      return HB_ECUDA;
+    }
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      cudaStreamDestroy(cs);
+      cudaStreamDestroy(cb);
+      set_error("hb_gmres: cannot begin the graph capture");
+      return HB_ECUDA;
+    }
+    f->prof.capturing = true;
+    f->prof.cap_launches.clear();
+    int e = record_cycle(cs, cb);
+    f->prof.capturing = false;
+    f->prof.in_body = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    cudaStreamDestroy(cb);
+    cudaGraphExec_t ge = nullptr;
+    cudaError_t ie = cudaSuccess;
+    if (!e && (ce != cudaSuccess || !g || (ie = cudaGraphInstantiate(&ge, g, 0)) != cudaSuccess)) e = HB_ECUDA;
+    if (e) {
+      if (g) cudaGraphDestroy(g);
+      f->prof.drop_capture();
+      cudaGetLastError();
+      set_error("hb_gmres: capturing the restart cycle as a CUDA graph failed (%s / %s)", cudaGetErrorString(ce),
+                cudaGetErrorString(ie));
+      return e;
+    }
+    CycleGraph& cg = f->cg;
+    cg.graph = g;
+    cg.exec = ge;
+    cg.op = op;
+    cg.R = R;
+    cg.m = m;
+    cg.mixed = mixed ? 1 : 0;
+    cg.stamp = f->stamp;
+    for (int i = 0; i < kSlots; ++i) cg.ws[i] = ws.ptr[i];
+    return HB_OK;
+  };
+  std::vector<double> prm_h(4 * R), pres_h(R);
+  std::vector<int> kuse_h(R);
+  int graph_launches = 0;
+  // one cycle: per-column targets in, graph launch, step count / states / estimates out
+  auto graph_fresh = [&]() -> bool {
+    const CycleGraph& cg = f->cg;
+    bool fresh = cg.exec && cg.op == op && cg.R == R && cg.m == m && cg.mixed == (mixed ? 1 : 0) &&
+                 cg.stamp == f->stamp;
+    for (int i = 0; fresh && i < kSlots; ++i) fresh = cg.ws[i] == ws.ptr[i];
+    return fresh;
+  };
+  auto graph_cycle = [&](int& kcyc) -> int {
+    CycleGraph& cg = f->cg;
+    int e;
+    if (!graph_fresh() && (e = capture_cycle())) return e;
+    for (int64_t c = 0; c < R; ++c) {
+      // the inner target as in the host loop: max(t_abs, t_rel beta)
+      if (mixed) {
+        prm_h[c] = rtol * bnorm[c] * tscale[c];
+        prm_h[R + c] = 2e-7;
+      } else {
+        prm_h[c] = 0.0;
+        prm_h[R + c] = rtol * tscale[c] / std::max(res_r[c] * bnorm[c], 1e-300) * bnorm[c];
+      }
+      prm_h[2 * R + c] = bnorm[c];
+      prm_h[3 * R + c] = done[c] ? 1.0 : 0.0;
+    }
+    const int ctl_in[2] = {std::min(m, maxit - iters), 0};
+    int ctl_out[2] = {0, 0};
+    cudaMemcpyAsync((void*)cyc.prm, prm_h.data(), prm_h.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(cyc.ctl, ctl_in, sizeof(ctl_in), cudaMemcpyHostToDevice, st);
+    if (cudaGraphLaunch(cg.exec, st) != cudaSuccess) { set_error("hb_gmres: graph launch failed"); return HB_ECUDA; }
+    ++graph_launches;
+    int herr = 0;
+    GridBar* gbar = (GridBar*)df.bar;
+    cudaMemcpyAsync(ctl_out, cyc.ctl, sizeof(ctl_out), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(kuse_h.data(), cyc.kuse, R * sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(pres_h.data(), cyc.pres, R * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&herr, &gbar->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("hb_gmres: CUDA error in the graph"); return HB_ECUDA; }
+    if (herr) {
+      cudaMemsetAsync(&gbar->err, 0, sizeof(int), st);
+      set_error("a bounded device-side wait expired in a sweep kernel during the solve");
+      return HB_ETIMEOUT;
+    }
+    if ((e = f->prof.harvest(ctl_out[1]))) { set_error("hb_gmres: reading the graph's timing events failed"); return e; }
+    kcyc = ctl_out[1];
+    iters += kcyc;
+    for (int64_t c = 0; c < R; ++c) {
+      if (done[c]) continue;
+      it_r[c] += kuse_h[c] < 0 ? -kuse_h[c] : kcyc;
+      pres_r[c] = pres_h[c];
+    }
+    return HB_OK;
+  };
+
+  // a capture that the runtime refuses leaves this call to the host-driven loop
+  // (info->graph_launches stays 0)
+  if (use_graph && !graph_fresh() && capture_cycle() != HB_OK) use_graph = false;
+
   while (iters < maxit) {
     nconv = 0;
     bool bad = false;
     for (int64_t c = 0; c < R; ++c) { done[c] = res_r[c] <= rtol; nconv += done[c]; bad |= !std::isfinite(res_r[c]); }
     if (nconv == R || bad) break;   // a non-finite residual ends the solve (reported as HB_ENAN)
-    // ---- start vector
-    std::vector<double> beta;
-    if (!mixed) {
-      if ((rc = sweep_internal(f, PREC_F64, lo, r, R, st))) return rc;   // r <- L'^{-1} r
-    }
-    if ((rc = norms(d, r, beta))) return rc;
-    if (mixed) normalise(d, r, beta, V32);
-    else normalise(d, r, beta, V);
-    std::vector<double> target(R);
-    for (int64_t c = 0; c < R; ++c) {
-      gv[c].reset(m, beta[c]);
-      kuse[c] = 0;
-      // aim the inner estimate at the final tolerance (scaled back when the true residual missed)
-      double want = rtol * bnorm[c] * tscale[c];
-      if (mixed) want = std::max(want, 2e-7 * beta[c]);
-      else want = rtol * tscale[c] * beta[c] / std::max(res_r[c] * bnorm[c], 1e-300) * bnorm[c];
-      target[c] = want;
-    }
-    int j = 0;
-    for (; j < m && iters < maxit; ++j) {
-      double2* vj = mixed ? nullptr : V + (size_t)j * n * R;
-      double2* w = mixed ? nullptr : V + (size_t)(j + 1) * n * R;
-      if (!mixed) {
-        // w = L'^{-1} A U'^{-1} v_j
-        cudaMemcpyAsync(w, vj, vbytes, cudaMemcpyDeviceToDevice, st);
-        if ((rc = sweep_internal(f, PREC_F64, up, w, R, st))) return rc;
-        if ((rc = apply_internal(f, PREC_F64, adj, w, tmp2, R, st))) return rc;
-        cudaMemcpyAsync(w, tmp2, vbytes, cudaMemcpyDeviceToDevice, st);
-        if ((rc = sweep_internal(f, PREC_F64, lo, w, R, st))) return rc;
-      } else {
-        // z_j = M^{-1} v_j, w = A z_j, all in complex FP32
-        float2* zj = zf + (size_t)j * n * R;
-        float2* w32 = V32 + (size_t)(j + 1) * n * R;
-        cudaMemcpyAsync(zj, V32 + (size_t)j * n * R, (size_t)n * R * sizeof(float2), cudaMemcpyDeviceToDevice, st);
-        if ((rc = sweep_internal(f, PREC_F32, lo, zj, R, st))) return rc;
-        if ((rc = sweep_internal(f, PREC_F32, up, zj, R, st))) return rc;
-        if ((rc = apply_internal(f, PREC_F32, adj, zj, w32, R, st))) return rc;
-      }
-      if (mixed) {
-        float2* w32 = V32 + (size_t)(j + 1) * n * R;
-        if ((rc = cgs2(d, V32, (int64_t)n * R, j + 1, w32, h, hn))) return rc;
-        normalise(d, w32, hn, w32);
-      } else {
-        if ((rc = cgs2(d, V, (int64_t)n * R, j + 1, w, h, hn))) return rc;
-        normalise(d, w, hn, w);
-      }
-      ++iters;
-      int active = 0;
-      for (int64_t c = 0; c < R; ++c) {
-        if (done[c] || kuse[c] < 0) continue;
-        std::vector<zc> col(j + 1);
-        for (int i = 0; i <= j; ++i) col[i] = h[(size_t)i * R + c];
-        double est = gv[c].push(j, col.data(), hn[c]);
-        pres_r[c] = bnorm[c] > 0 ? est / bnorm[c] : 0.0;
-        it_r[c]++;
-        if (est <= target[c]) kuse[c] = -(j + 1);   // converged in this cycle after j+1 steps
-        else active++;
-      }
-      if (active == 0) { ++j; break; }
-    }
-    // ---- update the iterate with each column's own step count
-    int kcyc = j;
-    std::fill(coef.begin(), coef.end(), zc(0.0));
-    for (int64_t c = 0; c < R; ++c) {
-      if (done[c]) continue;
-      int k = kuse[c] < 0 ? -kuse[c] : kcyc;
-      std::vector<zc> cf(k);
-      gv[c].solve(k, cf.data());
-      for (int i = 0; i < k; ++i) coef[(size_t)i * R + c] = cf[i];
-    }
-    std::vector<float2> coef32;
-    if (mixed) {
-      coef32.resize((size_t)kcyc * R);
-      for (size_t i = 0; i < coef32.size(); ++i) coef32[i] = float2{(float)coef[i].real(), (float)coef[i].imag()};
-      cudaMemcpyAsync(d.red_out, coef32.data(), coef32.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
+    int kcyc = 0;
+    const void* cdev = d.red_out;   // the cycle's combination coefficients (device)
+    if (use_graph) {
+      if ((rc = graph_cycle(kcyc))) return rc;
+      cdev = coefd;
     } else {
-      cudaMemcpyAsync(d.red_out, coef.data(), (size_t)kcyc * R * sizeof(double2), cudaMemcpyHostToDevice, st);
+      // ---- start vector
+      std::vector<double> beta;
+      if (!mixed) {
+        if ((rc = sweep_internal(f, PREC_F64, lo, r, R, st))) return rc;   // r <- L'^{-1} r
+      }
+      if ((rc = norms(d, r, beta))) return rc;
+      if (mixed) normalise(d, r, beta, V32);
+      else normalise(d, r, beta, V);
+      std::vector<double> target(R);
+      for (int64_t c = 0; c < R; ++c) {
+        gv[c].reset(m, beta[c]);
+        kuse[c] = 0;
+        // aim the inner estimate at the final tolerance (scaled back when the true residual missed)
+        double want = rtol * bnorm[c] * tscale[c];
+        if (mixed) want = std::max(want, 2e-7 * beta[c]);
+        else want = rtol * tscale[c] * beta[c] / std::max(res_r[c] * bnorm[c], 1e-300) * bnorm[c];
+        target[c] = want;
+      }
+      int j = 0;
+      for (; j < m && iters < maxit; ++j) {
+        double2* vj = mixed ? nullptr : V + (size_t)j * n * R;
+        double2* w = mixed ? nullptr : V + (size_t)(j + 1) * n * R;
+        if (!mixed) {
+          // w = L'^{-1} A U'^{-1} v_j
+          cudaMemcpyAsync(w, vj, vbytes, cudaMemcpyDeviceToDevice, st);
+          if ((rc = sweep_internal(f, PREC_F64, up, w, R, st))) return rc;
+          if ((rc = apply_internal(f, PREC_F64, adj, w, tmp2, R, st))) return rc;
+          cudaMemcpyAsync(w, tmp2, vbytes, cudaMemcpyDeviceToDevice, st);
+          if ((rc = sweep_internal(f, PREC_F64, lo, w, R, st))) return rc;
+        } else {
+          // z_j = M^{-1} v_j, w = A z_j, all in complex FP32
+          float2* zj = zf + (size_t)j * n * R;
+          float2* w32 = V32 + (size_t)(j + 1) * n * R;
+          cudaMemcpyAsync(zj, V32 + (size_t)j * n * R, (size_t)n * R * sizeof(float2), cudaMemcpyDeviceToDevice, st);
+          if ((rc = sweep_internal(f, PREC_F32, lo, zj, R, st))) return rc;
+          if ((rc = sweep_internal(f, PREC_F32, up, zj, R, st))) return rc;
+          if ((rc = apply_internal(f, PREC_F32, adj, zj, w32, R, st))) return rc;
+        }
+        if (mixed) {
+          float2* w32 = V32 + (size_t)(j + 1) * n * R;
+          if ((rc = cgs2(d, V32, (int64_t)n * R, j + 1, w32, h, hn))) return rc;
+          normalise(d, w32, hn, w32);
+        } else {
+          if ((rc = cgs2(d, V, (int64_t)n * R, j + 1, w, h, hn))) return rc;
+          normalise(d, w, hn, w);
+        }
+        ++iters;
+        int active = 0;
+        for (int64_t c = 0; c < R; ++c) {
+          if (done[c] || kuse[c] < 0) continue;
+          std::vector<zc> col(j + 1);
+          for (int i = 0; i <= j; ++i) col[i] = h[(size_t)i * R + c];
+          double est = gv[c].push(j, col.data(), hn[c]);
+          pres_r[c] = bnorm[c] > 0 ? est / bnorm[c] : 0.0;
+          it_r[c]++;
+          if (est <= target[c]) kuse[c] = -(j + 1);   // converged in this cycle after j+1 steps
+          else active++;
+        }
+        if (active == 0) { ++j; break; }
+      }
+      // ---- update the iterate with each column's own step count
+      kcyc = j;
+      std::fill(coef.begin(), coef.end(), zc(0.0));
+      for (int64_t c = 0; c < R; ++c) {
+        if (done[c]) continue;
+        int k = kuse[c] < 0 ? -kuse[c] : kcyc;
+        std::vector<zc> cf(k);
+        gv[c].solve(k, cf.data());
+        for (int i = 0; i < k; ++i) coef[(size_t)i * R + c] = cf[i];
+      }
+      std::vector<float2> coef32;
+      if (mixed) {
+        coef32.resize((size_t)kcyc * R);
+        for (size_t i = 0; i < coef32.size(); ++i) coef32[i] = float2{(float)coef[i].real(), (float)coef[i].imag()};
+        cudaMemcpyAsync(d.red_out, coef32.data(), coef32.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
+      } else {
+        cudaMemcpyAsync(d.red_out, coef.data(), (size_t)kcyc * R * sizeof(double2), cudaMemcpyHostToDevice, st);
+      }
     }
     if (!mixed) {
       // y += V c;  x = U'^{-1} y is formed for the residual check
-      k_add_combo<double2><<<gsz(n * R), 256, 0, st>>>(V, (int64_t)n * R, kcyc, d.red_out, xv, n, R); count_launch(f, 1);
+      k_add_combo<double2><<<gsz(n * R), 256, 0, st>>>(V, (int64_t)n * R, kcyc, (const double2*)cdev, xv, n, R); count_launch(f, 1);
       cudaMemcpyAsync(tmp2, xv, vbytes, cudaMemcpyDeviceToDevice, st);
       double2* xs = tmp2;
       if ((rc = sweep_internal(f, PREC_F64, up, xs, R, st))) return rc;
@@ -602,11 +1065,11 @@ extern "C" int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int6
       double worst_prev = 0.0;
       for (int64_t c = 0; c < R; ++c) worst_prev = std::max(worst_prev, res_r[c]);
       if (worst_prev > 1e-3) {
-        k_add_combo<float2><<<gsz(n * R), 256, 0, st>>>(zf, (int64_t)n * R, kcyc, (const float2*)d.red_out, xv, n, R); count_launch(f, 1);
+        k_add_combo<float2><<<gsz(n * R), 256, 0, st>>>(zf, (int64_t)n * R, kcyc, (const float2*)cdev, xv, n, R); count_launch(f, 1);
         if ((rc = true_residual(xv, r))) return rc;
       } else {
         cudaMemsetAsync(tmp2, 0, vbytes, st);   // dz in FP64, then rounded once to FP32
-        k_add_combo<float2><<<gsz(n * R), 256, 0, st>>>(zf, (int64_t)n * R, kcyc, (const float2*)d.red_out, tmp2, n, R); count_launch(f, 1);
+        k_add_combo<float2><<<gsz(n * R), 256, 0, st>>>(zf, (int64_t)n * R, kcyc, (const float2*)cdev, tmp2, n, R); count_launch(f, 1);
         k_axpy1<double2><<<gsz(n * R), 256, 0, st>>>(tmp2, xv, n * R); count_launch(f, 1);
         k_to_f32<<<gsz(n * R), 256, 0, st>>>(tmp2, f32s, n * R); count_launch(f, 1);
         float2* adz = (float2*)tmp2;   // A dz (FP32) reuses the scratch
@@ -649,6 +1112,7 @@ extern "C" int hb_gmres(hb_factor_t f, int op, const void* b_phys, void* x, int6
     info->precond_rel_res = worst_p;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (ipr) for (int64_t c = 0; c < R; ++c) ipr[c] = it_r[c];
+    info->graph_launches = graph_launches;
     if (rpr) for (int64_t c = 0; c < R; ++c) rpr[c] = res_r[c];
   }
   if (nonfinite) {
@@ -849,6 +1313,7 @@ extern "C" int hb_tfqmr(hb_factor_t f, int op, const void* b_phys, const void* r
     info->true_rel_res = worst;
     info->precond_rel_res = worst_b;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    info->graph_launches = 0;
     if (info->iters_per_rhs) for (int64_t c = 0; c < R; ++c) info->iters_per_rhs[c] = it_r[c];
     if (info->res_per_rhs) for (int64_t c = 0; c < R; ++c) info->res_per_rhs[c] = res_r[c];
   }
