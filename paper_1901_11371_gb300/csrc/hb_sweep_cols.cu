@@ -335,7 +335,10 @@ __device__ void run_tri(const SwDesc& D, bool rev, const float2* T, float2* win,
 }
 
 template <int NC>
-__global__ void __launch_bounds__(kSwThreads, 1) k_sweep_cols(SwArgs a) {
+// The bound of 512 threads (above the 416 launched) caps the registers at 128 a
+// thread, so that the scheduler that holds four of the 13 warps stays within its
+// 16K registers.
+__global__ void __launch_bounds__(512, 1) k_sweep_cols(SwArgs a) {
   extern __shared__ __align__(128) char smem[];
   char* ring = smem;
   float2* win = reinterpret_cast<float2*>(smem + kSwRingBytes);

@@ -582,6 +582,11 @@ const char* check_sweep_sched(const PackedHost& ph, const SwSched& S) {
   const int cb = S.coef_bytes;
   int64_t run_left = 0;   // groups of the current resident run still to come
   int32_t win_rows = 0;
+  // per window slot: the last resident phase that wrote / read it (a resident
+  // phase's batches run concurrently on the chain warps, so no slot may be
+  // written twice in a phase, nor written and read by the same phase)
+  std::vector<int64_t> wstamp((size_t)S.win_slots, -1), rstamp((size_t)S.win_slots, -1);
+  int64_t pid = 0;
   for (size_t gi = 0; gi < S.groups.size(); ++gi) {
     const SwGroup& G = S.groups[gi];
     if (G.img % 16 || G.bytes % 16 || G.bytes <= 0) return "group not 16-byte aligned";
@@ -646,12 +651,23 @@ const char* check_sweep_sched(const PackedHost& ph, const SwSched& S) {
           if (!res && (out[r] & kSwAcc)) return "global row that adds in place";
           const int32_t o = out[r] & ~kSwAcc;
           if (res ? (o < 0 || o >= S.win_slots) : (o < 0 || o >= n + ph.state_len)) return "output slot";
+          if (res) {
+            if (wstamp[o] == pid) return "window slot written twice in one phase";
+            if (rstamp[o] == pid) return "window slot read and written in one phase";
+            wstamp[o] = pid;
+          }
         }
-        for (int32_t e = 0; e < D.nent; ++e)
+        for (int32_t e = 0; e < D.nent; ++e) {
           if (res ? (in[e] < 0 || in[e] >= S.win_slots) : (in[e] < 0 || in[e] >= D.ngl)) return "input slot";
+          if (res) {
+            if (wstamp[in[e]] == pid) return "window slot read and written in one phase";
+            rstamp[in[e]] = pid;
+          }
+        }
         for (int32_t q = 0; q < D.ngl && !res; ++q)
           if (gl[q] < 0 || gl[q] >= n + ph.state_len) return "gathered slot";
       }
+      if (res && (PH.flags & SWP_END)) ++pid;
     }
   }
   if (run_left != 0) return "run not closed";
