@@ -186,7 +186,7 @@ MEASURED_TRAFFIC = {
     # profiles/k_sweep_coop_semicircle_N262144_traffic.md (autotuned 256-column launch)
     "k_sweep": {"sha": "b4653ac2957de173", "bytes": 2247096576 + 2686350592},
     # profiles/k_sweep_cols_semicircle_N262144.md (256-column launch, 128 CTAs x 2 columns)
-    "k_sweep_cols": {"sha": "f870a86e523f19df", "bytes": 2338996736 + 2601327104},
+    "k_sweep_cols": {"sha": "7d63d07b0809dd2e", "bytes": 2350072320 + 2600193280},
 }
 KERNEL_SOURCES = {
     "k_sweep": ["hb_sweep_impl.cuh", "hb_sweep.cu", "hb_sweep_f32w.cu", "hb_sweep_launch.h"],
@@ -246,6 +246,7 @@ def run_gpu(args, rank, world):
     g = hb.hb_geometry(wl.kind, wl.params, wl.n)
     t0 = time.perf_counter()
     f32 = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_SPLIT_BF16, seed=0)
+    hb.hb_set_gmres_graph(f32, args.gmres_graph)
     t_build = time.perf_counter() - t0
     st = hb.hb_factor_info(f32)
     tuned = hb.hb_autotune(f32, NRHS)
@@ -446,6 +447,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--gmres-graph", type=int, default=1, choices=[0, 1],
+                    help="1: every restart cycle one CUDA graph launch; 0: the host-driven Arnoldi loop "
+                         "(the same kernels, launched one by one: what ncu can list kernel by kernel)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
