@@ -106,6 +106,69 @@ __global__ void k_sub_combo(const VT* __restrict__ V, int64_t vstride, int nvec,
   }
 }
 
+// The first CGS2 pass's update fused with the second pass's dot products, for
+// R >= kRedThreads (one thread per column): w[row][r] -= sum_v V_v[row][r] h[v][r],
+// then partial[v][blk][r] = sum over the block's rows of conj(V_v[row][r]) w[row][r]
+// with the updated w.  V is read once for both, instead of once by k_sub_combo and
+// once by k_dots_partial; the arithmetic and the partial sums' row order are those
+// two kernels'.  NV >= nvec (the vectors' values stay in registers).
+template <class VT, int NV>
+__global__ void __launch_bounds__(kRedThreads) k_sub_dots(const VT* __restrict__ V, int64_t vstride, int nvec,
+                                                          const VT* __restrict__ h, VT* __restrict__ w, int64_t n,
+                                                          int64_t R, double2* __restrict__ partial) {
+  using S = decltype(VT::x);
+  const int64_t r = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const int64_t rows_per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t row0 = (int64_t)blockIdx.x * rows_per, row1 = min(n, row0 + rows_per);
+  VT hv[NV];
+  S ax[NV], ay[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    hv[v] = v < nvec ? h[(int64_t)v * R + r] : VT{0, 0};
+    ax[v] = 0;
+    ay[v] = 0;
+  }
+  for (int64_t row = row0; row < row1; ++row) {
+    const int64_t e = row * R + r;
+    VT vv[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) vv[v] = v < nvec ? V[(int64_t)v * vstride + e] : VT{0, 0};
+    VT acc = w[e];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      if (v < nvec) {
+        acc.x -= vv[v].x * hv[v].x - vv[v].y * hv[v].y;
+        acc.y -= vv[v].x * hv[v].y + vv[v].y * hv[v].x;
+      }
+    }
+    w[e] = acc;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      ax[v] = fma(vv[v].x, acc.x, fma(vv[v].y, acc.y, ax[v]));
+      ay[v] = fma(vv[v].x, acc.y, fma(-vv[v].y, acc.x, ay[v]));
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+    if (v < nvec) partial[((int64_t)v * gridDim.x + blockIdx.x) * R + r] = double2{(double)ax[v], (double)ay[v]};
+}
+
+// whether k_sub_dots serves nvec vectors of R columns (complex-FP32 bases: an FP64
+// basis's values would not fit the registers), and its launch
+template <class VT>
+static inline bool sub_dots_ok(int nvec, int64_t R) { return sizeof(VT) == 8 && R >= kRedThreads && nvec <= 32; }
+template <class VT>
+static void launch_sub_dots(const VT* V, int64_t vstride, int nvec, const VT* h, VT* w, int64_t n, int64_t R,
+                            double2* partial, cudaStream_t s) {
+  if constexpr (sizeof(VT) == 8) {
+    const dim3 grid(kRedBlocks, (unsigned)((R + kRedThreads - 1) / kRedThreads));
+    if (nvec <= 8) k_sub_dots<VT, 8><<<grid, kRedThreads, 0, s>>>(V, vstride, nvec, h, w, n, R, partial);
+    else if (nvec <= 16) k_sub_dots<VT, 16><<<grid, kRedThreads, 0, s>>>(V, vstride, nvec, h, w, n, R, partial);
+    else k_sub_dots<VT, 32><<<grid, kRedThreads, 0, s>>>(V, vstride, nvec, h, w, n, R, partial);
+  }
+}
+
 // dst[row][r] = src[row][r] * s[r]  (s real; src / dst double2 or float2)
 template <class SRC, class DST>
 __global__ void k_scale_cols(const SRC* __restrict__ src, const double* __restrict__ s, DST* dst, int64_t n,
@@ -301,11 +364,8 @@ struct Dev {
   double* scal;
 };
 
-// h[v][r] = <V_v, w>_r for v < nvec (host copy returned in hh[v*R + r])
-template <class VT>
-static int dots(Dev& d, const VT* V, int64_t vstride, int nvec, const VT* w, std::vector<zc>& hh) {
-  dim3 grid(kRedBlocks, nvec);
-  k_dots_partial<VT><<<grid, kRedThreads, 0, d.st>>>(V, vstride, nvec, w, d.n, d.R, d.red_partial); count_launch(d.f, 1);
+// the partial dot products in d.red_partial reduced to hh[v*R + r] (host copy)
+static int dots_finish(Dev& d, int nvec, std::vector<zc>& hh) {
   int64_t tot = (int64_t)nvec * d.R;
   k_dots_final<<<(unsigned)((tot + 255) / 256), 256, 0, d.st>>>(d.red_partial, kRedBlocks, nvec, d.R, d.red_out); count_launch(d.f, 1);
   hh.resize(tot);
@@ -325,6 +385,14 @@ static int dots(Dev& d, const VT* V, int64_t vstride, int nvec, const VT* w, std
   return HB_OK;
 }
 
+// h[v][r] = <V_v, w>_r for v < nvec (host copy returned in hh[v*R + r])
+template <class VT>
+static int dots(Dev& d, const VT* V, int64_t vstride, int nvec, const VT* w, std::vector<zc>& hh) {
+  dim3 grid(kRedBlocks, nvec);
+  k_dots_partial<VT><<<grid, kRedThreads, 0, d.st>>>(V, vstride, nvec, w, d.n, d.R, d.red_partial); count_launch(d.f, 1);
+  return dots_finish(d, nvec, hh);
+}
+
 // CGS2: orthogonalise w against V_0..V_{nvec-1}; returns h (nvec x R) and ||w|| (R).
 template <class VT>
 static int cgs2(Dev& d, const VT* V, int64_t vstride, int nvec, VT* w, std::vector<zc>& h,
@@ -332,8 +400,14 @@ static int cgs2(Dev& d, const VT* V, int64_t vstride, int nvec, VT* w, std::vect
   std::vector<zc> h1, h2;
   int rc;
   h.assign((size_t)nvec * d.R, zc(0.0));
+  // with k_sub_dots the first pass's update also forms the second pass's dot products
+  const bool fused = sub_dots_ok<VT>(nvec, d.R);
   for (int pass = 0; pass < 2; ++pass) {
-    if ((rc = dots(d, V, vstride, nvec, w, pass ? h2 : h1))) return rc;
+    if (pass == 0 || !fused) {
+      if ((rc = dots(d, V, vstride, nvec, w, pass ? h2 : h1))) return rc;
+    } else if ((rc = dots_finish(d, nvec, h2))) {
+      return rc;
+    }
     std::vector<zc>& hp = pass ? h2 : h1;
     for (size_t i = 0; i < h.size(); ++i) h[i] += hp[i];
     // the coefficients in the vectors' precision (converted once, on the host)
@@ -341,7 +415,11 @@ static int cgs2(Dev& d, const VT* V, int64_t vstride, int nvec, VT* w, std::vect
     for (size_t i = 0; i < hp.size(); ++i) hv[i] = VT{(decltype(VT::x))hp[i].real(), (decltype(VT::x))hp[i].imag()};
     if (cudaMemcpyAsync(d.red_out, hv.data(), hv.size() * sizeof(VT), cudaMemcpyHostToDevice, d.st) != cudaSuccess)
       return HB_ECUDA;
-    k_sub_combo<VT><<<gsz(d.n * d.R), 256, 0, d.st>>>(V, vstride, nvec, (const VT*)d.red_out, w, d.n, d.R);
+    if (pass == 0 && fused) {
+      launch_sub_dots<VT>(V, vstride, nvec, (const VT*)d.red_out, w, d.n, d.R, d.red_partial, d.st);
+    } else {
+      k_sub_combo<VT><<<gsz(d.n * d.R), 256, 0, d.st>>>(V, vstride, nvec, (const VT*)d.red_out, w, d.n, d.R);
+    }
     count_launch(d.f, 1);
   }
   std::vector<zc> nn;
@@ -587,16 +665,21 @@ __global__ void k_cyc_solve(Cyc c, double2* __restrict__ y, VT* __restrict__ coe
 template <class VT>
 static void cgs2_graph(hb_factor_t f, const Dev& d, const Cyc& cyc, const VT* V, int nvec, VT* w, cudaStream_t s) {
   const int64_t nR = d.n * d.R;
+  const bool fused = sub_dots_ok<VT>(nvec, d.R);   // the first update forms the second pass's dot products
+  const unsigned gfin = (unsigned)(((int64_t)nvec * d.R + 255) / 256);
   for (int pass = 0; pass < 2; ++pass) {
-    k_dots_partial<VT><<<dim3(kRedBlocks, nvec), kRedThreads, 0, s>>>(V, nR, nvec, w, d.n, d.R, d.red_partial);
-    k_cgs_final<VT><<<(unsigned)(((int64_t)nvec * d.R + 255) / 256), 256, 0, s>>>(d.red_partial, kRedBlocks, nvec, cyc,
-                                                                                pass);
-    k_sub_combo<VT><<<gsz(nR), 256, 0, s>>>(V, nR, nvec, (const VT*)cyc.cvec, w, d.n, d.R);
+    if (pass == 0 || !fused)
+      k_dots_partial<VT><<<dim3(kRedBlocks, nvec), kRedThreads, 0, s>>>(V, nR, nvec, w, d.n, d.R, d.red_partial);
+    k_cgs_final<VT><<<gfin, 256, 0, s>>>(d.red_partial, kRedBlocks, nvec, cyc, pass);
+    if (pass == 0 && fused)
+      launch_sub_dots<VT>(V, nR, nvec, (const VT*)cyc.cvec, w, d.n, d.R, d.red_partial, s);
+    else
+      k_sub_combo<VT><<<gsz(nR), 256, 0, s>>>(V, nR, nvec, (const VT*)cyc.cvec, w, d.n, d.R);
   }
   k_dots_partial<VT><<<dim3(kRedBlocks, 1), kRedThreads, 0, s>>>(w, 0, 1, w, d.n, d.R, d.red_partial);
   k_norm_final<<<(unsigned)((d.R + 255) / 256), 256, 0, s>>>(d.red_partial, kRedBlocks, cyc);
   k_scale_cols<VT, VT><<<gsz(nR), 256, 0, s>>>(w, cyc.inv, w, d.n, d.R);
-  count_launch(f, 9);
+  count_launch(f, fused ? 8 : 9);
 }
 
 }  // namespace hb

@@ -142,3 +142,23 @@ def test_graph_cycle_reports_timeout(hb, semi):
     assert lib.hb_set_wait_limit(f._h, 1 << 24) == 0
     _, info = hb.hb_gmres(f, b)
     assert info["status"] == 0 and info["true_rel_res"] <= 1e-6 and info["graph_launches"] >= 1
+
+
+def test_graph_cycle_256_columns_vs_dense_lu(hb, semi):
+    # The bench's column count: 256 right-hand sides take the fused first CGS2
+    # update with the second pass's dot products (k_sub_dots), the tensor-core
+    # leaf contractions and the tuned sweep kernel inside the captured cycle;
+    # sampled columns against the dense LU solve, and the host-driven loop.
+    p, a, g, wl = semi["p"], semi["a"], semi["g"], semi["wl"]
+    f = hb.hb_factor(g, wl.leaf, wl.eps, form=hb.HB_SPLIT_BF16)
+    hb.hb_autotune(f, 256)
+    phis = 180.0 * np.arange(256) / 256
+    cols = [0, 37, 101, 128, 190, 255]
+    x_lu = dense.solve(a, p.plane_wave(phis[cols]) * p.scale)
+    res = _both_loops(hb, f, hb.hb_rhs_plane_wave(f, phis), rtol=1e-6, restart=30, maxit=600)
+    for on in (1, 0):
+        xs, info = res[on]
+        assert info["converged"] == 256 and info["true_rel_res"] <= 1e-6
+        assert (info["graph_launches"] >= 1) == (on == 1)
+        for j, c in enumerate(cols):
+            assert _rel(xs[c], x_lu[:, j]) <= 1e-5, (on, c)
