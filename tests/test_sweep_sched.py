@@ -65,3 +65,27 @@ def test_schedule_rejects_bad_arguments(hb, strip_host):
     for which, cb, ws in ((4, 16, 0), (0, 4, 0), (0, 16, -1), (0, 16, 1 << 20)):
         with pytest.raises(hb.HBError):
             hb.hb_host_sweep_sched(f, b, which, cb, win_slots=ws)
+
+
+def test_schedule_check_names_planted_defects():
+    # tests/schedcheck.cpp, built here against the library's host code: the schedules as
+    # built pass the structural check; each planted defect (a window slot written twice
+    # or written and read within one resident phase, an input outside the window, a
+    # misaligned group, a missing ENDRUN, a global row that adds in place) is named
+    import os
+    import shutil
+    import subprocess
+    import tempfile
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    csrc = os.path.join(root, "paper_1901_11371_gb300", "csrc")
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "schedcheck")
+        cmd = [gxx, "-O2", "-std=c++17", "-fopenmp", "-I", csrc, os.path.join(root, "tests", "schedcheck.cpp"),
+               os.path.join(csrc, "hb_host.cpp"), os.path.join(csrc, "hb_swsched.cpp"), "-o", exe]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr[-2000:]
+        r = subprocess.run([exe], capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0 and r.stdout.strip().endswith("OK"), r.stdout[-3000:]
