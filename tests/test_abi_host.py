@@ -62,6 +62,11 @@ def test_error_paths_without_gpu(hb):
     assert b"no device image" in lib.hb_last_error()
     assert lib.hb_tfqmr(f._h, 0, C.c_void_p(8), None, C.c_void_p(16), 1, 64, 1e-6, 10, None, None) == hb._lib.HB_EINVAL
     assert b"no device image" in lib.hb_last_error()
+    # execution settings of the device path: refused on a host-only factor and out of range
+    assert lib.hb_set_gmres_graph(f._h, 1) == hb._lib.HB_EINVAL
+    assert lib.hb_set_gmres_graph(None, 1) == hb._lib.HB_EINVAL
+    assert lib.hb_set_sweep_kernel(f._h, 1) == hb._lib.HB_EINVAL
+    assert lib.hb_set_wait_limit(f._h, 10) == hb._lib.HB_EINVAL
 
 
 @pytest.mark.parametrize("name", ["strip_N1024", "spiral_N65536", "semicircle_N262144", "strips8_N131072"])
