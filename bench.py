@@ -186,12 +186,12 @@ MEASURED_TRAFFIC = {
     # profiles/k_sweep_coop_semicircle_N262144_traffic.md (autotuned 256-column launch)
     "k_sweep": {"sha": "b4653ac2957de173", "bytes": 2247096576 + 2686350592},
     # profiles/k_sweep_cols_semicircle_N262144.md (256-column launch, 128 CTAs x 2 columns)
-    "k_sweep_cols": {"sha": "7d63d07b0809dd2e", "bytes": 2350072320 + 2600193280},
+    "k_sweep_cols": {"sha": "7197c23169dc946a", "bytes": 2364800000 + 2608399104},
 }
 KERNEL_SOURCES = {
     "k_sweep": ["hb_sweep_impl.cuh", "hb_sweep.cu", "hb_sweep_f32w.cu", "hb_sweep_launch.h"],
     "k_apply1": ["hb_apply1.cu", "hb_plan.cpp"],
-    "k_sweep_cols": ["hb_sweep_cols.cu", "hb_swsched.cpp", "hb_sweep_launch.h"],
+    "k_sweep_cols": ["hb_sweep_cols.cu", "hb_swsched.cpp", "hb_sweep_launch.h", "hb_internal.h"],
 }
 
 

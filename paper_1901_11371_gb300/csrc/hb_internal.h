@@ -459,7 +459,7 @@ void host_apply_plan(const PackedHost& ph, const ApplyPlan& plan, int fes, bool 
 // small; a global phase part's batches go round-robin to all compute warps.
 // ---------------------------------------------------------------------------
 constexpr int kSwWarps = 12;                 // compute warps (one more warp stages the groups)
-constexpr int kSwChain = 4;                  // compute warps that execute the resident runs
+constexpr int kSwChain = 8;                  // compute warps that execute the resident runs
 constexpr int kSwWinBytes = 96 * 1024;       // resident window: rows + state of a run
 constexpr int kSwRingBytes = 104 * 1024;     // staging ring of group images
 constexpr int kSwPartBytes = 16 * 1024;      // partial sums of a triangle product

@@ -18,11 +18,12 @@
 //     vector rows and a CTA-private butterfly state in global memory: a batch
 //     first gathers its distinct inputs into its warp's slice of the window
 //     (free between runs) in one round trip;
-//   * the resident runs -- the long dependent chain -- are executed by four
-//     chain warps (one per scheduler) with their own barrier, so that the
-//     per-phase overhead is paid four times, not twelve; the other compute
-//     warps wait for the run's end; a global phase's batches go round-robin
-//     to all twelve compute warps;
+//   * the resident runs -- the long dependent chain -- are executed by eight
+//     chain warps (two per scheduler) with their own barrier: a phase's rows
+//     are spread over eight warps, and a sweep leaf's columns over 256 threads,
+//     while the per-phase overhead is paid eight times, not twelve; the other
+//     compute warps wait for the run's end; a global phase's batches go
+//     round-robin to all twelve compute warps;
 //   * a butterfly phase is a sparse product in row form; in a batch, groups of
 //     2^glog lanes share a row (entries strided over the lanes, then a shuffle
 //     reduction), so that short dot products do not serialise on one lane;
