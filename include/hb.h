@@ -347,7 +347,11 @@ int hb_status(hb_factor_t f, void* stream);
 /* hb_profile -- enable (1) / disable (0) timing of the hot-path kernels of
  * this factor.  While enabled, every apply launch sequence and every sweep
  * kernel is bracketed by CUDA events on its stream (enabling resets the
- * record).  Not in the paper: measurement support.
+ * record; enabling it again while on resets the record only).  Inside
+ * hb_gmres's graph-captured restart cycle the events sit around the
+ * conditional node of each sweep or apply and are counted for the steps
+ * that ran; switching profiling on or off discards the cached graph.  Not in
+ * the paper: measurement support.
  * hb_profile_read -- kind 0: apply (D+2 kernels per call), 1: sweep kernels,
  * 2: every kernel the library launched (count only).  Returns the number of
  * recorded calls/launches and their summed device time in ms (synchronises
