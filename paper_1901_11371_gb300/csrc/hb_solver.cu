@@ -7,12 +7,17 @@
 //            flexible GMRES right-preconditioned by U~^{-1} L~^{-1}, with the
 //            preconditioner, the operator and the Arnoldi basis in complex FP32
 //            (Hessenberg, Givens and the iterate in FP64).  The residual
-//            b - A x between steps is computed with FP64 arithmetic on the
-//            stored factors while any column is above 1e-3; below that the
-//            small correction dz is applied in FP32 and r -= A dz accumulated
-//            in FP64.
+//            b - A x between steps is computed with FP64-accurate arithmetic
+//            on the stored factors (double-float pairs of FP32 for 32 or more
+//            columns, FP64 below) while any column is above 1e-3; below that
+//            the small correction dz is applied in FP32 and r -= A dz
+//            accumulated in FP64.
 // Right-hand sides are solved together in lockstep (one Krylov space per
 // column); reductions run in a fixed order, so results are bitwise repeatable.
+// With two or more columns every restart cycle runs as one CUDA graph launch
+// (the Arnoldi steps, their CGS2, the Givens rotations and the convergence test
+// on the device; see record_cycle in hb_gmres); one column runs the
+// host-driven loop, which takes the same steps with a host round trip each.
 #include <cuda_runtime.h>
 
 #include <algorithm>
